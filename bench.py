@@ -1,0 +1,337 @@
+"""Benchmark: TR-ALS sweeps/s on one GB300 (one step = one full ALS sweep over all N core updates).
+
+Default workload: the order-4 60x60x60x60 tensor (12.96M entries) generated as a TR of ranks 10
+with iid N(0,1) cores plus 1e-2 relative Gaussian noise; fit ranks 10; Cholesky normal
+equations with the structured Gamma-chain coefficient matrix.  The headline ``value`` is the
+reduced-precision mode (``--mode``, default bf16: X stored once as BF16, RHS contraction on
+tensor cores with FP32 accumulation, FP64 Gram chain and solve); the FP64 mode on the same
+workload is reported beside it under ``fp64``.
+
+``--impl reference`` times the CPU FP64 oracle (regular TR-ALS with the explicit subchain
+matrix, Alg. 1) on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import trals_inputs as TI  # noqa: E402
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int = 0):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------------------- data
+def make_X_device(w, seed, P, torch, dtype):
+    """Observed tensor on the device: X_true = TR(true cores) by the library's reconstruction
+    kernel, plus the relative noise of the paper's protocol (added with torch)."""
+    N = len(w.I)
+    if w.kind == "sinusoid":
+        f, phi = TI.sinusoid_params(seed, w.terms, N)
+        X = TI.sinusoid_tensor(w.I, f, phi) + w.eta * TI.gaussian_noise(seed, w.I)
+        return torch.from_numpy(TI.flat_f(X)).to("cuda").to(dtype)
+    truth = TI.gaussian_cores(seed, w.I, w.R_true)
+    ctx = P.trals_create(0)
+    cd = [P.core_to_device(G) for G in truth]
+    Xt = torch.empty(w.numel, dtype=torch.float64, device="cuda")
+    P.trals_reconstruct(ctx, w.I, w.R_true, cd, Xt)
+    noise = torch.from_numpy(TI.flat_f(TI.gaussian_noise(seed, w.I))).to("cuda")
+    X = Xt + w.eta * (torch.linalg.vector_norm(Xt) / torch.linalg.vector_norm(noise)) * noise
+    ctx.close()
+    return X.to(dtype)
+
+
+def mode_xdtype(mode, torch):
+    return {"fp64": torch.float64, "fp32": torch.float32, "bf16": torch.float32, "bf16x3": torch.float32}[mode]
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def time_mode(P, torch, w, X, mode, steps, warmup, seed, flush_buf):
+    stream = torch.cuda.Stream()
+    ctx = P.trals_create(0, stream)
+    plan = P.Plan(ctx, w.I, w.R_fit, X, P.make_opts(mode))
+    init = TI.init_cores(seed, w.I, w.R_fit)
+    plan.set_cores(init)
+    plan.run(warmup, use_graph=True)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    torch.cuda.synchronize()
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush_buf.add_(1.0)          # > L2: evicts X between timed sweeps
+            ev[k][0].record(stream)
+        plan.run(1, use_graph=True)
+        with torch.cuda.stream(stream):
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    times = [a.elapsed_time(b) for a, b in ev]
+    res = plan.residuals()
+    launches = plan.launches_per_sweep()
+    # dominant kernel: MTTSP of each mode, timed alone with events on the plan's stream
+    mt = []
+    for n in range(len(w.I)):
+        reps = 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        per = []
+        for _ in range(reps):
+            with torch.cuda.stream(stream):
+                flush_buf.add_(1.0)
+                e0.record(stream)
+            plan.mttsp(n)
+            with torch.cuda.stream(stream):
+                e1.record(stream)
+            torch.cuda.synchronize()
+            per.append(e0.elapsed_time(e1))
+        mt.append(statistics.median(per))
+    plan.close()
+    ctx.close()
+    return {"ms_per_step": sum(times) / len(times), "times": times, "residual": float(res[-1]) if len(res) else None,
+            "launches_per_sweep": launches, "mttsp_ms": mt, "clocks": clk}
+
+
+def e2e_run(P, torch, w, X_dev, mode, seed, sweeps):
+    """End to end through trals_decompose with host buffers (pinned X, host cores)."""
+    Xh = X_dev.cpu().pin_memory()
+    init = TI.init_cores(seed, w.I, w.R_fit)
+    ctx = P.trals_create(0)
+    cores = [G.copy() for G in init]
+    P.trals_decompose(ctx, w.I, w.R_fit, Xh, cores, 1, P.make_opts(mode))   # warm (module load, graph)
+    cores = [G.copy() for G in init]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = P.trals_decompose(ctx, w.I, w.R_fit, Xh, cores, sweeps, P.make_opts(mode))
+    dt = time.perf_counter() - t0
+    ctx.close()
+    core_bytes = sum(G.size * 8 for G in cores)
+    return {"value": sweeps / dt, "unit": "sweeps/s", "h2d_bytes_per_step": int((Xh.numel() * Xh.element_size()
+                                                                                 + core_bytes) / sweeps),
+            "d2h_bytes_per_step": int((core_bytes + 8 * sweeps) / sweeps), "sweeps": sweeps,
+            "residual": float(res[-1])}
+
+
+def cpu_baseline_run(w, seed, budget_s=20.0):
+    """The oracle (regular TR-ALS, FP64 NumPy) on host cores: core updates of the same workload,
+    as many as fit ~budget_s, scaled to sweeps/s."""
+    import oracle as O
+    X = TI.make_tensor_host(w, seed, O.tr_full)
+    cores = TI.init_cores(seed, w.I, w.R_fit)
+    N = len(w.I)
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        n = done % N
+        cores[n] = O.als_update(X, cores, n, "chol")
+        done += 1
+        if time.perf_counter() - t0 > budget_s or done >= 2 * N:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": (done / N) / dt, "unit": "sweeps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{done} core updates (modes 1..{min(done, N)}) of the same workload, Cholesky NE on the "
+                      f"explicit subchain matrix, {dt:.1f} s"}
+
+
+def roofline_for(w, mode, mttsp_ms, peaks, src):
+    numel = w.numel
+    N = len(w.I)
+    esize = {"fp64": 8, "fp32": 4, "bf16": 2, "bf16x3": 4}[mode]
+    bytes_per = numel * esize
+    flops = [2.0 * numel * w.R_fit[n] * w.R_fit[(n + 1) % N] for n in range(N)]
+    t = sum(mttsp_ms) / N * 1e-3
+    if mode == "fp64":
+        achieved = sum(flops) / N / t / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
+                "frac": achieved / 1.25, "traffic": None,
+                "note": "FP64 FMA pipe; peak = GB300 nominal FP64 1.25 TFLOP/s"}
+    achieved = bytes_per / t / 1e9
+    peak = peaks["hbm_gbs"]
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "peak_source": src}
+
+
+def run_ours(args):
+    import torch
+    import paper_2210_11362_gb300 as P
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    w = TI.WORKLOADS[args.config]
+    peaks, src = _peaks()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    out = {}
+    X_f64 = make_X_device(w, args.seed, P, torch, torch.float64)
+    modes = [args.mode] + ([] if args.mode == "fp64" or args.no_fp64 else ["fp64"])
+    for mode in modes:
+        X = X_f64 if mode == "fp64" else X_f64.to(mode_xdtype(mode, torch))
+        if world > 1:
+            torch.distributed.barrier()
+        out[mode] = time_mode(P, torch, w, X, mode, args.steps, args.warmup, args.seed, flush)
+        out[mode]["X"] = X
+    main = out[args.mode]
+    ms = main["ms_per_step"]
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    if rank != 0:
+        return
+    e2e = e2e_run(P, torch, w, main["X"], args.mode, args.seed, w.sweeps)
+    line = {
+        "metric": "TR-ALS sweeps/s at fixed rel. residual (mixed vs FP64)",
+        "value": world * 1000.0 / ms, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.mode],
+        "data": "synthetic",
+        "config": {"workload": w.name, "I": list(w.I), "R_fit": list(w.R_fit), "eta": w.eta, "mode": args.mode,
+                   "solver": "cholesky", "gram": "structured", "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed between timed sweeps (256 MB write)", "residual_after_run": main["residual"]},
+        "roofline": roofline_for(w, args.mode, main["mttsp_ms"], peaks, src),
+        "mttsp_ms_per_mode": main["mttsp_ms"],
+        "gpu_launches": main["launches_per_sweep"] * args.steps,
+        "clocks": main["clocks"],
+        "e2e": e2e,
+    }
+    if "fp64" in out and args.mode != "fp64":
+        f = out["fp64"]
+        line["fp64"] = {"value": 1000.0 / f["ms_per_step"], "ms_per_step": f["ms_per_step"],
+                        "residual": f["residual"], "mttsp_ms_per_mode": f["mttsp_ms"],
+                        "roofline": roofline_for(w, "fp64", f["mttsp_ms"], peaks, src)}
+        line["speedup_vs_fp64"] = f["ms_per_step"] / main["ms_per_step"]
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_run(w, args.seed, args.cpu_budget)
+    print(json.dumps(line))
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    w = TI.WORKLOADS[args.config]
+    X = TI.make_tensor_host(w, args.seed, O.tr_full)
+    cores = TI.init_cores(args.seed, w.I, w.R_fit)
+    N = len(w.I)
+    for k in range(args.warmup):
+        cores[k % N] = O.als_update(X, cores, k % N, "chol")
+    t = []
+    for k in range(args.steps):
+        n = (args.warmup + k) % N
+        t0 = time.perf_counter()
+        cores[n] = O.als_update(X, cores, n, "chol")
+        t.append(time.perf_counter() - t0)
+    per_update = sum(t) / len(t)
+    value = 1.0 / (N * per_update)
+    line = {"impl": "reference", "metric": "TR-ALS sweeps/s at fixed rel. residual (mixed vs FP64)",
+            "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * N * per_update, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "I": list(w.I), "R_fit": list(w.R_fit), "eta": w.eta,
+                       "step": "one core update of the CPU oracle per timed step (sweeps/s = 1 / (N x mean)"},
+            "cpu_baseline": {"value": value, "unit": "sweeps/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{args.steps} timed core updates after {args.warmup} warm-up updates"},
+            "e2e": {"value": value, "unit": "sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="tr60x4_r10", choices=sorted(TI.WORKLOADS))
+    ap.add_argument("--mode", default="bf16", choices=["fp64", "fp32", "bf16", "bf16x3"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * trals.h -- C ABI of libtrals: tensor-ring alternating least squares on one GB300 GPU.
+ *
+ * Method: Yu & Li, "Practical Alternating Least Squares for Tensor Ring
+ * Decomposition" (arXiv 2210.11362).  The library fits TR({G_n}) to a dense
+ * tensor X (problem eq. trmin, Sec. 1) by ALS sweeps over n = 1..N (Alg. 1),
+ * computing each core update the TR-ALS-NE way (Alg. 2, lines 6-10):
+ *   S_n  = structured coefficient matrix from per-core Gram matrices
+ *          (Prop. subchain_gram, Alg. 2 lines 2, 6, 10),
+ *   M_n  = X_[n] G^{!=n}_[2]   (MTTSP, Alg. 2 lines 7-8),
+ *   G_n  : G_{n(2)} S_n = M_n  (normal equation, Alg. 2 line 9),
+ * or with the QR-stabilised solve of Sec. 3.2 (Alg. 3).
+ *
+ * Conventions (all entry points)
+ *  - Mode indices n are 0-based (the paper's mode n is n-1 here).
+ *  - Dense tensors are column-major: linear index sum_n i_n prod_{j<n} I_j,
+ *    first index fastest (Sec. 2).
+ *  - Core n is R_n x I_n x R_{n+1}, column-major (r_n fastest, then i_n, then
+ *    r_{n+1}), with R_N wrapping to R_0 (Sec. 1).
+ *  - Matrices are column-major.  G_{n(2)} (classical mode-2 unfolding) is
+ *    I_n x R_n R_{n+1} with column r_n + R_n r_{n+1}; S_n is r x r and M_n is
+ *    I_n x r with r = R_n R_{n+1} in the same column order.
+ *  - Gamma_k = sum_i G_k(i) (x) G_k(i) is R_k^2 x R_{k+1}^2 with Kronecker row
+ *    index p R_k + q and column index s R_{k+1} + t.
+ *  - "dev" pointers are device memory of the context's device; "host" pointers
+ *    are host memory.  The caller owns every buffer it passes in; the library
+ *    never frees or retains caller pointers after a call returns.
+ *  - Every call is ordered on the context's stream.  Calls that return results
+ *    to host memory synchronize that stream before returning; the others only
+ *    enqueue work.
+ *  - Errors are returned, never thrown, and no call traps the GPU.  Device-side
+ *    failures (a non-positive Cholesky pivot, a non-finite value) set a device
+ *    status word that the next synchronizing call reports.  trals_last_error()
+ *    returns a human-readable message for the last failing call on a context.
+ *  - No entry point is thread-safe on the same context.
+ */
+#ifndef TRALS_H
+#define TRALS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TRALS_MAX_ORDER 8
+
+typedef enum {
+  TRALS_OK = 0,
+  TRALS_E_ARG = 1,        /* invalid argument (shape, rank, null pointer, unsupported combination) */
+  TRALS_E_OOM = 2,        /* device memory allocation failed */
+  TRALS_E_CUDA = 3,       /* a CUDA runtime call failed */
+  TRALS_E_NOT_SPD = 4,    /* Cholesky met a non-positive pivot: S_n is not numerically SPD */
+  TRALS_E_NONFINITE = 5,  /* a NaN or Inf reached a solve */
+  TRALS_E_TIMEOUT = 6,    /* a bounded device wait gave up */
+  TRALS_E_REJECTED = 7,   /* serving: request does not fit the admission budget */
+  TRALS_E_PENDING = 8     /* serving: result not ready yet */
+} trals_status;
+
+/* Element type of the caller's X. */
+typedef enum { TRALS_X_F64 = 0, TRALS_X_F32 = 1, TRALS_X_BF16 = 2 } trals_xtype;
+
+/* Arithmetic of the RHS contraction M_n (the Gram chain, S_n and the solve are FP64 in every mode).
+ *  FP64  : X read as FP64, MTTSP in FP64.
+ *  FP32  : X read as FP32, MTTSP on TF32 tensor cores with FP32 accumulation.
+ *  BF16  : X quantised once to BF16 (round to nearest even), MTTSP on BF16
+ *          tensor cores with FP32 accumulation.
+ *  BF16X3: X split once into hi/lo BF16 pairs, subchain rows split likewise;
+ *          three BF16 products per term (hi*hi + hi*lo + lo*hi), FP32 accumulation. */
+typedef enum { TRALS_MODE_FP64 = 0, TRALS_MODE_FP32 = 1, TRALS_MODE_BF16 = 2, TRALS_MODE_BF16X3 = 3 } trals_mode;
+
+/* Solver for the R_n R_{n+1} subproblem: Cholesky on the normal equations
+ * (Alg. 2 line 9), or the QR-stabilised solve (Sec. 3.2). */
+typedef enum { TRALS_SOLVE_CHOL = 0, TRALS_SOLVE_QR = 1 } trals_solver;
+
+/* How S_n is formed: structured Gamma chain (Prop. subchain_gram) or the explicit
+ * subchain matrix's Gram (G^{!=n}_[2])^T G^{!=n}_[2] (regular TR-ALS, Alg. 1). */
+typedef enum { TRALS_GRAM_STRUCTURED = 0, TRALS_GRAM_EXPLICIT = 1 } trals_gram;
+
+typedef struct {
+  int mode;              /* trals_mode */
+  int solver;            /* trals_solver */
+  int gram;              /* trals_gram */
+  int explicit_residual; /* 1: per-sweep residual by a full reconstruction pass against X (Sec. 4 formula);
+                            0: the cheap identity of Sec. 4 */
+} trals_opts;
+
+typedef struct trals_ctx trals_ctx;
+typedef struct trals_plan trals_plan;
+
+/* ------------------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`, ordering all work on `cuda_stream`
+ * (a cudaStream_t; NULL = a stream the context creates, which synchronizes with the
+ * legacy default stream).  Errors: TRALS_E_ARG for a bad device, TRALS_E_CUDA. */
+trals_status trals_create(trals_ctx** out, int device, void* cuda_stream);
+/* Destroy a context (synchronizes its stream first).  NULL is ignored. */
+void trals_destroy(trals_ctx* ctx);
+/* Message for the last failing call on ctx (never NULL; "" if none). */
+const char* trals_last_error(const trals_ctx* ctx);
+/* Library version string. */
+const char* trals_version(void);
+
+/* ------------------------------------------------------------------------- whole decomposition */
+
+/* Fit TR cores to X by `sweeps` ALS sweeps (problem eq. trmin; Alg. 1 sweep order
+ * n = 1..N with the core update of Alg. 2, or Alg. 3's QR-stabilised solve).
+ *   N          order, 3 <= N <= TRALS_MAX_ORDER
+ *   I[N]       mode sizes (>= 1); R[N] TR ranks (>= 1), R_{N} wraps to R_0
+ *   X          the tensor, column-major, element type xt; device memory if
+ *              x_on_host == 0, else host memory (copied in by this call)
+ *   cores[N]   host pointers; in: initial cores, out: fitted cores (FP64, layout above)
+ *   opts       NULL = {FP64, CHOL, STRUCTURED, explicit_residual 0}
+ *   rel_res    host array of `sweeps` doubles, out: relative residual |X - X_hat|_F/|X|_F
+ *              after each sweep (may be NULL)
+ * Requires J_n = prod_{j != n} I_j >= R_n R_{n+1} for every n (else the
+ * subproblem is underdetermined): TRALS_E_ARG.  Synchronous. */
+trals_status trals_decompose(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R,
+                             const void* X, int xt, int x_on_host,
+                             double* const* cores, int sweeps, const trals_opts* opts,
+                             double* rel_res);
+
+/* ------------------------------------------------------------------------- resident plan */
+
+/* A plan keeps X (device, caller-owned, must outlive the plan), the cores, the
+ * Gamma_k caches and all workspace resident, so sweeps can be replayed (as one
+ * captured CUDA graph per sweep) without host work.  Arguments as in
+ * trals_decompose; X_dev is device memory. */
+trals_status trals_plan_create(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R,
+                               const void* X_dev, int xt, const trals_opts* opts, trals_plan** out);
+void trals_plan_destroy(trals_plan* plan);
+/* Upload cores (host pointers, FP64) and recompute every Gamma_k (Alg. 2 line 2).
+ * Resets the sweep counter.  Synchronous. */
+trals_status trals_plan_set_cores(trals_plan* plan, double* const* cores_host);
+/* Download cores (host pointers, FP64).  Synchronous; reports device status. */
+trals_status trals_plan_get_cores(trals_plan* plan, double* const* cores_host);
+/* Enqueue `sweeps` ALS sweeps.  Enqueue only (no host sync, graph replays when
+ * use_graph != 0). */
+trals_status trals_plan_run(trals_plan* plan, int sweeps, int use_graph);
+/* Copy the residual history (count = sweeps run since set_cores, at most `cap`)
+ * to host; synchronous; reports device status. */
+trals_status trals_plan_residuals(trals_plan* plan, double* rel_res_host, int cap, int* count);
+/* Enqueue only the MTTSP of mode n (Alg. 2 lines 7-8) with the plan's current cores and
+ * workspace, writing M_n (I_n x R_n R_{n+1}, FP64) to M_dev (NULL: the plan's internal buffer).
+ * Allocates nothing; used to time and test the RHS contraction in isolation. */
+trals_status trals_plan_mttsp(trals_plan* plan, int n, double* M_dev);
+/* Device pointer of core n (FP64, layout above), valid until the plan is destroyed. */
+const double* trals_plan_core_dev(const trals_plan* plan, int n);
+/* Number of kernel launches one sweep issues (for launch accounting). */
+int trals_plan_launches_per_sweep(const trals_plan* plan);
+
+/* ------------------------------------------------------------------------- per-step kernels
+ * Each computes one step of the core update on device buffers, for testing and
+ * composition.  These allocate their own temporaries and are synchronous. */
+
+/* Gamma = sum_i G(i) (x) G(i) (Alg. 2 lines 2 and 10; Prop. subchain_gram), FP64.
+ * G_dev: Rn x In x Rn1 core; Gamma_dev: Rn^2 x Rn1^2 (column-major). */
+trals_status trals_gamma(trals_ctx* ctx, const double* G_dev, int Rn, int64_t In, int Rn1, double* Gamma_dev);
+
+/* Structured coefficient matrix of mode n (Alg. 2 line 6): Pi_n = Gamma_{n+1} ...
+ * Gamma_N Gamma_1 ... Gamma_{n-1} (products in FP64), regrouped to
+ * S_n[(a + R_n b), (a' + R_n b')] = Pi_n[(b R_{n+1} + b'), (a R_n + a')].
+ * gammas_dev[k] for k != n are used.  S_dev: r x r, r = R_n R_{n+1}. */
+trals_status trals_coef_matrix(trals_ctx* ctx, int N, const int32_t* R, const double* const* gammas_dev,
+                               int n, double* S_dev);
+
+/* MTTSP of mode n (Alg. 2 lines 7-8): M_dev (I_n x r, FP64) = X_[n] G^{!=n}_[2], with the
+ * subchain rows generated on the fly from cores_dev (FP64) in the arithmetic of `mode`
+ * (X element type must match the mode: F64 for FP64, F32 for FP32, BF16 for BF16;
+ * BF16X3 takes X as BF16 hi followed by BF16 lo halves, 2 * prod(I) elements). */
+trals_status trals_mttsp(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R,
+                         const void* X_dev, int xt, int mode, const double* const* cores_dev, int n,
+                         double* M_dev);
+
+/* Solve Z S = M for Z (I_n x r) by Cholesky S = L L^T and two triangular solves
+ * (Alg. 2 line 9, FP64), writing Z folded into core layout: G[a + Rn (i + In b)] =
+ * Z[i, a + Rn b].  S_dev r x r SPD (only the lower triangle is read), M_dev In x r.
+ * Synchronous: returns TRALS_E_NOT_SPD / TRALS_E_NONFINITE from the device status. */
+trals_status trals_solve_chol(trals_ctx* ctx, int Rn, int64_t In, int Rn1, const double* S_dev,
+                              const double* M_dev, double* G_dev);
+
+/* X_hat = TR(cores) written to out_dev (column-major, element type xt) (Sec. 1 element formula). */
+trals_status trals_reconstruct(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R,
+                               const double* const* cores_dev, void* out_dev, int xt);
+
+/* Explicit squared residual |X - TR(cores)|_F^2 and |X|_F^2 in FP64 by one fused
+ * reconstruction pass (Sec. 4 error formula).  Synchronous; results to host. */
+trals_status trals_residual_explicit(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R,
+                                     const void* X_dev, int xt, const double* const* cores_dev,
+                                     double* res2_host, double* normx2_host);
+
+/* Quantise count elements of src (type src_t, F64 or F32) to BF16 (round to nearest
+ * even).  If dst_lo_dev != NULL also write lo = bf16(x - float(hi)). */
+trals_status trals_quantize_bf16(trals_ctx* ctx, const void* src_dev, int src_t, int64_t count,
+                                 void* dst_hi_dev, void* dst_lo_dev);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TRALS_H */

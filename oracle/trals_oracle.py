@@ -63,19 +63,24 @@ def tr_full(cores: Sequence[np.ndarray]) -> np.ndarray:
     """The dense tensor TR({G_n}) of shape (I_1..I_N) (Sec. 1).
 
     Forms the running products Z(i_1..i_m) = G_1(i_1)...G_m(i_m) for every
-    prefix index (a library batched matmul per step) and takes the trace at
-    the end, which is the element formula evaluated for all indices at once.
+    prefix index m < N (a library batched matmul per step), then evaluates
+    Trace(Z(i_1..i_{N-1}) G_N(i_N)) = sum_{a,c} Z[a, k, c] G_N[c, i_N, a] for all
+    indices at once: the element formula, without an R x J x I x R intermediate.
     """
     N = len(cores)
     I = [G.shape[1] for G in cores]
     # Z: (R_1, K, R_{m+1}) with K = overline{i_1..i_m} (i_1 fastest)
     Z = cores[0]
-    for m in range(1, N):
+    for m in range(1, N - 1):
         G = cores[m]
         # new[r, k + K*i_m, s] = sum_c Z[r, k, c] G[c, i_m, s]
         new = np.einsum("akc,cis->akis", Z, G)
         Z = new.reshape(Z.shape[0], Z.shape[1] * G.shape[1], G.shape[2], order="F")
-    vals = np.einsum("aka->k", Z)
+    GN = cores[N - 1]
+    # vals[k, i_N] = sum_{a,c} Z[a, k, c] GN[c, i_N, a]
+    Zm = np.transpose(Z, (1, 0, 2)).reshape(Z.shape[1], -1)            # (K, a*R_N + c)
+    Gm = np.transpose(GN, (2, 0, 1)).reshape(-1, GN.shape[1])          # (a*R_N + c, I_N)
+    vals = Zm @ Gm
     return vals.reshape(tuple(I), order="F")
 
 
@@ -417,3 +422,26 @@ def subchain_principal_angle(cores_a: Sequence[np.ndarray], cores_b: Sequence[np
     Qb, _ = np.linalg.qr(B)
     s = np.linalg.svd(Qa.T @ Qb, compute_uv=False)
     return float(np.arccos(np.clip(s.min(), -1.0, 1.0)))
+
+
+# ---------------------------------------------------------------------------
+# BF16 storage of X for the mixed-precision mode: round to nearest even
+# ---------------------------------------------------------------------------
+def bf16_rne_bits(x) -> np.ndarray:
+    """BF16 bit pattern of x: x is first rounded to FP32 (nearest even), then the FP32 bit
+    pattern is rounded to its top 16 bits, ties to even (finite inputs)."""
+    f = np.asarray(x, dtype=np.float64).astype(np.float32)
+    b = f.view(np.uint32).astype(np.uint64)
+    return (((b + 0x7FFF + ((b >> 16) & 1)) >> 16) & 0xFFFF).astype(np.uint16)
+
+
+def bf16_bits_to_f64(u) -> np.ndarray:
+    return (np.asarray(u, dtype=np.uint16).astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def bf16_split(x) -> Tuple[np.ndarray, np.ndarray]:
+    """hi = bf16(x), lo = bf16(x - hi) (both as bit patterns): the split-BF16 pair of x."""
+    x = np.asarray(x, dtype=np.float64)
+    hi = bf16_rne_bits(x)
+    lo = bf16_rne_bits(x - bf16_bits_to_f64(hi))
+    return hi, lo

@@ -1,0 +1,386 @@
+"""Python binding of libtrals: tensor-ring ALS (Yu & Li, arXiv 2210.11362) on one GB300 GPU.
+
+Argument marshalling only: every step of the computation runs in the CUDA kernels of
+``libtrals.so`` (built in-tree by ``paper_2210_11362_gb300.build``).  There is no CPU
+fallback: if the library is missing or no GPU is present, the calls raise.
+
+Functions carry the names of the C ABI in ``include/trals.h``.  Device buffers are torch
+CUDA tensors (flat, holding column-major data); host buffers are numpy arrays.  Cores are
+passed as numpy arrays of shape (R_n, I_n, R_{n+1}) (any memory order; the binding hands
+column-major copies to the library and writes results back in place).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtrals.so")
+
+# trals_status
+OK, E_ARG, E_OOM, E_CUDA, E_NOT_SPD, E_NONFINITE, E_TIMEOUT, E_REJECTED, E_PENDING = range(9)
+STATUS_NAMES = {0: "OK", 1: "E_ARG", 2: "E_OOM", 3: "E_CUDA", 4: "E_NOT_SPD", 5: "E_NONFINITE",
+                6: "E_TIMEOUT", 7: "E_REJECTED", 8: "E_PENDING"}
+# trals_xtype
+X_F64, X_F32, X_BF16 = 0, 1, 2
+# trals_mode
+MODE_FP64, MODE_FP32, MODE_BF16, MODE_BF16X3 = 0, 1, 2, 3
+MODE_NAMES = {"fp64": MODE_FP64, "fp32": MODE_FP32, "bf16": MODE_BF16, "bf16x3": MODE_BF16X3}
+# trals_solver / trals_gram
+SOLVE_CHOL, SOLVE_QR = 0, 1
+GRAM_STRUCTURED, GRAM_EXPLICIT = 0, 1
+
+EXPORTED = [
+    "trals_version", "trals_create", "trals_destroy", "trals_last_error", "trals_decompose",
+    "trals_plan_create", "trals_plan_destroy", "trals_plan_set_cores", "trals_plan_get_cores",
+    "trals_plan_run", "trals_plan_residuals", "trals_plan_mttsp", "trals_plan_core_dev",
+    "trals_plan_launches_per_sweep",
+    "trals_gamma", "trals_coef_matrix", "trals_mttsp", "trals_solve_chol", "trals_reconstruct",
+    "trals_residual_explicit", "trals_quantize_bf16",
+]
+
+
+class TralsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("solver", ctypes.c_int), ("gram", ctypes.c_int),
+                ("explicit_residual", ctypes.c_int)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i32, _i64, _dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+
+
+def lib() -> ctypes.CDLL:
+    """Load libtrals.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2210_11362_gb300.build.build() "
+                           "(nvcc, sm_103a); there is no CPU fallback")
+    L = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "trals_version": (ctypes.c_char_p, []),
+        "trals_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _vp]),
+        "trals_destroy": (None, [_vp]),
+        "trals_last_error": (ctypes.c_char_p, [_vp]),
+        "trals_decompose": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp,
+                                           ctypes.c_int, _vp, _vp]),
+        "trals_plan_create": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
+        "trals_plan_destroy": (None, [_vp]),
+        "trals_plan_set_cores": (ctypes.c_int, [_vp, _vp]),
+        "trals_plan_get_cores": (ctypes.c_int, [_vp, _vp]),
+        "trals_plan_run": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+        "trals_plan_residuals": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+        "trals_plan_mttsp": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+        "trals_plan_core_dev": (_vp, [_vp, ctypes.c_int]),
+        "trals_plan_launches_per_sweep": (ctypes.c_int, [_vp]),
+        "trals_gamma": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _i64, ctypes.c_int, _vp]),
+        "trals_coef_matrix": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp]),
+        "trals_mttsp": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp,
+                                       ctypes.c_int, _vp]),
+        "trals_solve_chol": (ctypes.c_int, [_vp, ctypes.c_int, _i64, ctypes.c_int, _vp, _vp, _vp]),
+        "trals_reconstruct": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int]),
+        "trals_residual_explicit": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp,
+                                                   ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)]),
+        "trals_quantize_bf16": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _i64, _vp, _vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+# ------------------------------------------------------------------ marshalling helpers
+def _ptr(x) -> Optional[int]:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _xtype(x) -> int:
+    import torch
+    if isinstance(x, np.ndarray):
+        return {np.dtype(np.float64): X_F64, np.dtype(np.float32): X_F32}[x.dtype]
+    return {torch.float64: X_F64, torch.float32: X_F32, torch.bfloat16: X_BF16}[x.dtype]
+
+
+def _shape(I, R):
+    N = len(I)
+    Ia = (_i64 * N)(*[int(v) for v in I])
+    Ra = (_i32 * N)(*[int(v) for v in R])
+    return N, Ia, Ra
+
+
+def _ptr_array(ptrs: Sequence[int]):
+    return (_vp * len(ptrs))(*ptrs)
+
+
+def _opts(mode=MODE_FP64, solver=SOLVE_CHOL, gram=GRAM_STRUCTURED, explicit_residual=False) -> Opts:
+    if isinstance(mode, str):
+        mode = MODE_NAMES[mode]
+    return Opts(int(mode), int(solver), int(gram), int(bool(explicit_residual)))
+
+
+def make_opts(mode=MODE_FP64, solver=SOLVE_CHOL, gram=GRAM_STRUCTURED, explicit_residual=False) -> Opts:
+    return _opts(mode, solver, gram, explicit_residual)
+
+
+class Context:
+    """A libtrals context (device + stream)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        h = _vp()
+        s = _ptr_stream(stream)
+        st = lib().trals_create(ctypes.byref(h), int(device), s)
+        if st != OK:
+            raise TralsError(st, f"trals_create(device={device}) failed (is a CUDA GPU present?)")
+        self.handle = h
+        self.device = device
+
+    def check(self, st: int, what: str = ""):
+        if st != OK:
+            raise TralsError(st, f"{what}: {trals_last_error(self)}")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().trals_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ptr_stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ------------------------------------------------------------------ C ABI mirrors
+def trals_version() -> str:
+    return lib().trals_version().decode()
+
+
+def trals_create(device: int = 0, stream=None) -> Context:
+    return Context(device, stream)
+
+
+def trals_destroy(ctx: Context) -> None:
+    ctx.close()
+
+
+def trals_last_error(ctx: Context) -> str:
+    return lib().trals_last_error(ctx.handle).decode()
+
+
+def cores_to_fortran(cores: Sequence[np.ndarray]) -> List[np.ndarray]:
+    return [np.asfortranarray(np.asarray(G, dtype=np.float64)) for G in cores]
+
+
+def trals_decompose(ctx: Context, I, R, X, cores: List[np.ndarray], sweeps: int, opts: Optional[Opts] = None,
+                    ) -> np.ndarray:
+    """Fit TR cores to X (numpy host array or torch CUDA tensor, column-major contents).
+
+    ``cores`` (numpy, shapes (R_n, I_n, R_{n+1})) hold the initial cores and receive the result.
+    Returns the relative residual after each sweep.
+    """
+    N, Ia, Ra = _shape(I, R)
+    on_host = isinstance(X, np.ndarray) or not getattr(X, "is_cuda", True)
+    if isinstance(X, np.ndarray):
+        Xh = np.asarray(X).reshape(-1, order="F") if X.ndim > 1 else np.ascontiguousarray(X)
+        xptr = Xh.ctypes.data
+    else:
+        xptr = X.data_ptr()  # a torch tensor (CUDA, or pinned host memory) holding column-major data
+    fc = cores_to_fortran(cores)
+    res = np.zeros(max(sweeps, 1))
+    st = lib().trals_decompose(ctx.handle, N, ctypes.addressof(Ia), ctypes.addressof(Ra), xptr, _xtype(X),
+                               int(on_host), _ptr_array([G.ctypes.data for G in fc]), int(sweeps),
+                               ctypes.addressof(opts) if opts is not None else None, res.ctypes.data)
+    ctx.check(st, "trals_decompose")
+    for G, Gf in zip(cores, fc):
+        G[...] = Gf
+    return res[:sweeps]
+
+
+class Plan:
+    """A resident plan (trals_plan_*)."""
+
+    def __init__(self, ctx: Context, I, R, X_dev, opts: Optional[Opts] = None):
+        self.ctx = ctx
+        self.I = tuple(int(v) for v in I)
+        self.R = tuple(int(v) for v in R)
+        self.N = len(self.I)
+        self._X = X_dev  # keep the caller's tensor alive
+        N, Ia, Ra = _shape(self.I, self.R)
+        h = _vp()
+        st = lib().trals_plan_create(ctx.handle, N, ctypes.addressof(Ia), ctypes.addressof(Ra), X_dev.data_ptr(),
+                                     _xtype(X_dev), ctypes.addressof(opts) if opts is not None else None,
+                                     ctypes.byref(h))
+        ctx.check(st, "trals_plan_create")
+        self.handle = h
+
+    def set_cores(self, cores: Sequence[np.ndarray]) -> None:
+        fc = cores_to_fortran(cores)
+        self.ctx.check(lib().trals_plan_set_cores(self.handle, _ptr_array([G.ctypes.data for G in fc])),
+                       "trals_plan_set_cores")
+
+    def get_cores(self) -> List[np.ndarray]:
+        out = [np.zeros((self.R[n], self.I[n], self.R[(n + 1) % self.N]), order="F") for n in range(self.N)]
+        self.ctx.check(lib().trals_plan_get_cores(self.handle, _ptr_array([G.ctypes.data for G in out])),
+                       "trals_plan_get_cores")
+        return out
+
+    def run(self, sweeps: int, use_graph: bool = True) -> None:
+        self.ctx.check(lib().trals_plan_run(self.handle, int(sweeps), int(bool(use_graph))), "trals_plan_run")
+
+    def residuals(self, cap: int = 1 << 14) -> np.ndarray:
+        buf = np.zeros(cap)
+        cnt = ctypes.c_int(0)
+        self.ctx.check(lib().trals_plan_residuals(self.handle, buf.ctypes.data, cap, ctypes.byref(cnt)),
+                       "trals_plan_residuals")
+        return buf[:cnt.value].copy()
+
+    def mttsp(self, n: int, M_dev=None) -> None:
+        self.ctx.check(lib().trals_plan_mttsp(self.handle, int(n), _ptr(M_dev)), "trals_plan_mttsp")
+
+    def core_dev(self, n: int) -> int:
+        return lib().trals_plan_core_dev(self.handle, int(n))
+
+    def launches_per_sweep(self) -> int:
+        return lib().trals_plan_launches_per_sweep(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().trals_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def trals_plan_create(ctx: Context, I, R, X_dev, opts: Optional[Opts] = None) -> Plan:
+    return Plan(ctx, I, R, X_dev, opts)
+
+
+def trals_gamma(ctx: Context, G_dev, Rn: int, In: int, Rn1: int, Gamma_dev) -> None:
+    ctx.check(lib().trals_gamma(ctx.handle, _ptr(G_dev), int(Rn), int(In), int(Rn1), _ptr(Gamma_dev)), "trals_gamma")
+
+
+def trals_coef_matrix(ctx: Context, R, gammas_dev: Sequence, n: int, S_dev) -> None:
+    N = len(R)
+    Ra = (_i32 * N)(*[int(v) for v in R])
+    ctx.check(lib().trals_coef_matrix(ctx.handle, N, ctypes.addressof(Ra), _ptr_array([_ptr(g) for g in gammas_dev]),
+                                      int(n), _ptr(S_dev)), "trals_coef_matrix")
+
+
+def trals_mttsp(ctx: Context, I, R, X_dev, mode, cores_dev: Sequence, n: int, M_dev) -> None:
+    N, Ia, Ra = _shape(I, R)
+    if isinstance(mode, str):
+        mode = MODE_NAMES[mode]
+    ctx.check(lib().trals_mttsp(ctx.handle, N, ctypes.addressof(Ia), ctypes.addressof(Ra), _ptr(X_dev), _xtype(X_dev),
+                                int(mode), _ptr_array([_ptr(c) for c in cores_dev]), int(n), _ptr(M_dev)),
+              "trals_mttsp")
+
+
+def trals_solve_chol(ctx: Context, Rn: int, In: int, Rn1: int, S_dev, M_dev, G_dev) -> None:
+    ctx.check(lib().trals_solve_chol(ctx.handle, int(Rn), int(In), int(Rn1), _ptr(S_dev), _ptr(M_dev), _ptr(G_dev)),
+              "trals_solve_chol")
+
+
+def trals_reconstruct(ctx: Context, I, R, cores_dev: Sequence, out_dev) -> None:
+    N, Ia, Ra = _shape(I, R)
+    ctx.check(lib().trals_reconstruct(ctx.handle, N, ctypes.addressof(Ia), ctypes.addressof(Ra),
+                                      _ptr_array([_ptr(c) for c in cores_dev]), _ptr(out_dev), _xtype(out_dev)),
+              "trals_reconstruct")
+
+
+def trals_residual_explicit(ctx: Context, I, R, X_dev, cores_dev: Sequence):
+    N, Ia, Ra = _shape(I, R)
+    r2, x2 = _dbl(0), _dbl(0)
+    ctx.check(lib().trals_residual_explicit(ctx.handle, N, ctypes.addressof(Ia), ctypes.addressof(Ra), _ptr(X_dev),
+                                            _xtype(X_dev), _ptr_array([_ptr(c) for c in cores_dev]),
+                                            ctypes.byref(r2), ctypes.byref(x2)), "trals_residual_explicit")
+    return r2.value, x2.value
+
+
+def trals_quantize_bf16(ctx: Context, src_dev, hi_dev, lo_dev=None) -> None:
+    ctx.check(lib().trals_quantize_bf16(ctx.handle, _ptr(src_dev), _xtype(src_dev), int(src_dev.numel()),
+                                        _ptr(hi_dev), _ptr(lo_dev)), "trals_quantize_bf16")
+
+
+# ------------------------------------------------------------------ torch helpers (plumbing)
+def core_to_device(G: np.ndarray, device="cuda"):
+    """A core (R_n, I_n, R_{n+1}) as a flat column-major float64 CUDA tensor."""
+    import torch
+    return torch.from_numpy(np.asarray(G, dtype=np.float64).reshape(-1, order="F").copy()).to(device)
+
+
+def core_from_device(t, Rn: int, In: int, Rn1: int) -> np.ndarray:
+    return t.detach().cpu().numpy().reshape((Rn, In, Rn1), order="F")
+
+
+def tensor_to_device(X: np.ndarray, dtype=None, device="cuda"):
+    """A dense tensor as a flat column-major CUDA tensor (float64 unless dtype is given)."""
+    import torch
+    flat = torch.from_numpy(np.asarray(X, dtype=np.float64).reshape(-1, order="F").copy())
+    if dtype is not None:
+        flat = flat.to(dtype)
+    return flat.to(device)
+
+
+def trals_plan_destroy(plan: Plan) -> None:
+    plan.close()
+
+
+def trals_plan_set_cores(plan: Plan, cores: Sequence[np.ndarray]) -> None:
+    plan.set_cores(cores)
+
+
+def trals_plan_get_cores(plan: Plan) -> List[np.ndarray]:
+    return plan.get_cores()
+
+
+def trals_plan_run(plan: Plan, sweeps: int, use_graph: bool = True) -> None:
+    plan.run(sweeps, use_graph)
+
+
+def trals_plan_residuals(plan: Plan) -> np.ndarray:
+    return plan.residuals()
+
+
+def trals_plan_mttsp(plan: Plan, n: int, M_dev=None) -> None:
+    plan.mttsp(n, M_dev)
+
+
+def trals_plan_core_dev(plan: Plan, n: int) -> int:
+    return plan.core_dev(n)
+
+
+def trals_plan_launches_per_sweep(plan: Plan) -> int:
+    return plan.launches_per_sweep()

@@ -1,0 +1,26 @@
+// Tensor-core (tcgen05) MTTSP for the reduced-precision modes: interface used by the sweep driver.
+#pragma once
+
+#include "trals_internal.cuh"
+
+namespace trals {
+
+// Per-mode plan of the tensor-core MTTSP.  Owns its device workspace.
+struct TcPlan {
+  bool valid = false;
+  int N = 0, n = 0, mode = 0;
+  std::vector<void*> allocs;
+  void* impl = nullptr;
+};
+
+// Prepare the tensor-core MTTSP of mode n for X (element type implied by `mode`).  Returns 1 when
+// the shape is supported (then tc_enqueue is used), 0 otherwise (the caller falls back to the
+// CUDA-core MTTSP).  *err is set on a CUDA failure.
+int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mode, const void* X, int64_t numel,
+            cudaError_t* err);
+// Enqueue M_n (FP64, I_n x R_n R_{n+1}) on stream s; returns the number of kernel launches.
+int tc_enqueue(TcPlan& p, const void* X, double* const* cores, double* M, cudaStream_t s);
+void tc_destroy(TcPlan& p);
+cudaError_t init_tc_attributes();
+
+}  // namespace trals

@@ -1,0 +1,752 @@
+// libtrals C ABI: contexts, resident plans and the ALS sweep driver (Alg. 1 sweep order with the
+// TR-ALS-NE core update of Alg. 2, lines 6-10), plus the per-step entry points.
+#include <math.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "trals_internal.cuh"
+#include "mttsp_tc.cuh"
+
+using namespace trals;
+
+namespace {
+
+constexpr int kResCap = 1 << 14;
+
+__global__ void finalize_explicit_residual(const double* red2, double* res_hist, int* sweep_ctr) {
+  const int s = *sweep_ctr;
+  res_hist[s] = sqrt(fmax(red2[0], 0.0) / red2[1]);
+  *sweep_ctr = s + 1;
+}
+
+__global__ void set_int_kernel(int* p, int v) { *p = v; }
+
+std::string fmt(const char* f, long long a = 0, long long b = 0, long long c = 0) {
+  char buf[256];
+  snprintf(buf, sizeof buf, f, a, b, c);
+  return buf;
+}
+
+trals_status check_shape(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R) {
+  if (N < 3 || N > TRALS_MAX_ORDER) {
+    ctx->last_error = fmt("order N=%lld outside [3, %lld]", N, TRALS_MAX_ORDER);
+    return TRALS_E_ARG;
+  }
+  if (!I || !R) {
+    ctx->last_error = "null shape or rank array";
+    return TRALS_E_ARG;
+  }
+  for (int n = 0; n < N; ++n) {
+    if (I[n] < 1 || R[n] < 1 || R[n] > 64) {
+      ctx->last_error = fmt("mode %lld: I=%lld R=%lld (need I>=1, 1<=R<=64)", n, I[n], R[n]);
+      return TRALS_E_ARG;
+    }
+  }
+  for (int n = 0; n < N; ++n) {
+    int64_t J = 1;
+    for (int j = 0; j < N; ++j)
+      if (j != n) J *= I[j];
+    const int64_t r = (int64_t)R[n] * R[(n + 1) % N];
+    if (r > 256) {
+      ctx->last_error = fmt("mode %lld: R_n R_{n+1} = %lld exceeds 256", n, r);
+      return TRALS_E_ARG;
+    }
+    if (J < r) {
+      ctx->last_error = fmt("mode %lld: J_n=%lld < R_n R_{n+1}=%lld (underdetermined subproblem)", n, J, r);
+      return TRALS_E_ARG;
+    }
+  }
+  return TRALS_OK;
+}
+
+trals_status read_status(trals_ctx* ctx) {
+  DevStatus st{};
+  cudaError_t e = cudaMemcpyAsync(&st, ctx->d_status, sizeof st, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    ctx->last_error = std::string("stream error: ") + cudaGetErrorString(e);
+    return TRALS_E_CUDA;
+  }
+  if (st.code != 0) {
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s at sweep %d, core %d, index %d (value %.6g)",
+             st.code == TRALS_E_NOT_SPD ? "non-positive Cholesky pivot"
+             : st.code == TRALS_E_NONFINITE ? "non-finite value in a solve"
+                                            : "device error",
+             st.sweep, st.mode, st.index, st.value);
+    ctx->last_error = buf;
+    launch_zero_status(ctx->d_status, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    return (trals_status)st.code;
+  }
+  return TRALS_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ plan
+namespace trals {
+cudaError_t init_kernel_attributes() {
+  cudaError_t e = init_small_attributes();
+  if (e == cudaSuccess) e = init_simt_attributes();
+  if (e == cudaSuccess) e = init_tc_attributes();
+  return e;
+}
+}  // namespace trals
+
+struct trals_plan {
+  trals_ctx* ctx = nullptr;
+  int N = 0;
+  int64_t I[TRALS_MAX_ORDER] = {};
+  int32_t R[TRALS_MAX_ORDER] = {};
+  const void* X = nullptr;        // caller's X (full precision source)
+  int xt = 0;
+  const void* Xk = nullptr;       // X as read by the MTTSP (caller's or an owned converted copy)
+  int xk_t = 0;
+  trals_opts opts{};
+  int64_t numel = 0;
+  std::vector<void*> allocs;
+  double* cores[TRALS_MAX_ORDER] = {};
+  double* gam[TRALS_MAX_ORDER] = {};
+  double *S = nullptr, *Lmat = nullptr, *M = nullptr, *chainA = nullptr, *chainB = nullptr;
+  double *ltab = nullptr, *utab = nullptr, *tscratch = nullptr;
+  int64_t* offL[TRALS_MAX_ORDER] = {};
+  int64_t* offU[TRALS_MAX_ORDER] = {};
+  ModeLayout lay[TRALS_MAX_ORDER];
+  int gridX[TRALS_MAX_ORDER] = {};
+  double* partials = nullptr;
+  double* red2 = nullptr;         // [2] explicit residual reduction
+  double* normX2 = nullptr;
+  double* res_hist = nullptr;
+  int* sweep_ctr = nullptr;
+  int host_sweeps = 0;
+  cudaGraphExec_t gexec = nullptr;
+  int launches = 0;
+  TcPlan tc[TRALS_MAX_ORDER];
+  bool use_tc[TRALS_MAX_ORDER] = {};
+
+  template <typename T>
+  cudaError_t alloc(T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e == cudaSuccess) {
+      allocs.push_back(q);
+      *p = static_cast<T*>(q);
+    }
+    return e;
+  }
+};
+
+namespace {
+
+// Structured coefficient matrix S_n (Alg. 2 line 6): Pi_n = Gamma_{n+1} ... Gamma_{n-1}, regrouped.
+int enqueue_coef(const int N, const int32_t* R, double* const* gam, int n, double* chainA, double* chainB, double* S,
+                 cudaStream_t s) {
+  int launches = 0;
+  const int c0 = (n + 1) % N;
+  const double* cur = gam[c0];
+  int rows = R[c0] * R[c0];
+  double* bufs[2] = {chainA, chainB};
+  for (int t = 2; t < N; ++t) {
+    const int c = (n + t) % N;
+    const int k = R[c] * R[c];
+    const int cols = R[(c + 1) % N] * R[(c + 1) % N];
+    double* out = bufs[t % 2];
+    launch_gemm_f64(rows, cols, k, cur, gam[c], out, s);
+    ++launches;
+    cur = out;
+  }
+  launch_regroup_S(cur, R[n], R[(n + 1) % N], S, s);
+  return launches + 1;
+}
+
+int enqueue_mttsp(trals_plan* p, int n, cudaStream_t s) {
+  const ModeLayout& L = p->lay[n];
+  int launches = 0;
+  if (p->use_tc[n]) {
+    launches += tc_enqueue(p->tc[n], p->Xk, p->cores, p->M, s);
+    return launches;
+  }
+  build_tables(L, p->cores, p->I, p->R, p->ltab, p->utab, p->tscratch, s);
+  launches += L.N - 1;
+  MttspSimtArgs a;
+  a.X = p->Xk;
+  a.xt = p->xk_t;
+  a.ltab = p->ltab;
+  a.utab = p->utab;
+  a.offL = p->offL[n];
+  a.offU = p->offU[n];
+  a.L = L;
+  a.partials = p->partials;
+  a.M = p->M;
+  a.gridX = p->gridX[n];
+  launch_mttsp_simt(a, s);
+  return launches + 2;
+}
+
+int enqueue_sweep(trals_plan* p) {
+  cudaStream_t s = p->ctx->stream;
+  int launches = 0;
+  const int N = p->N;
+  for (int n = 0; n < N; ++n) {
+    const int Rn = p->R[n], Rn1 = p->R[(n + 1) % N];
+    launches += enqueue_coef(N, p->R, p->gam, n, p->chainA, p->chainB, p->S, s);
+    launches += enqueue_mttsp(p, n, s);
+    launch_cholesky(p->S, p->Lmat, Rn * Rn1, p->ctx->d_status, p->sweep_ctr, n, s);
+    launch_chol_solve(p->Lmat, p->M, Rn, p->I[n], Rn1, p->cores[n], p->ctx->d_status, s);
+    launch_gamma(p->cores[n], Rn, p->I[n], Rn1, p->gam[n], s);
+    launches += 3;
+  }
+  const int n = N - 1;
+  if (p->opts.explicit_residual) {
+    // tables of the last mode still hold the other cores; regenerate to be independent of the MTTSP path
+    const ModeLayout& L = p->lay[n];
+    build_tables(L, p->cores, p->I, p->R, p->ltab, p->utab, p->tscratch, s);
+    launch_reconstruct(L, p->ltab, p->utab, p->offL[n], p->offU[n], p->cores[n], nullptr, TRALS_X_F64, p->X, p->xt,
+                       p->partials, p->gridX[n], s);
+    launch_reduce_pairs(p->partials, p->gridX[n], p->red2, s);
+    finalize_explicit_residual<<<1, 1, 0, s>>>(p->red2, p->res_hist, p->sweep_ctr);
+    launches += (N - 1) + 3;
+  } else {
+    launch_residual_identity(p->normX2, p->M, p->cores[n], p->S, p->gam[n], p->R[n], p->I[n], p->R[0], p->res_hist,
+                             p->sweep_ctr, s);
+    launches += 1;
+  }
+  return launches;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+const char* trals_version(void) { return "libtrals 0.1 (sm_103a)"; }
+
+trals_status trals_create(trals_ctx** out, int device, void* cuda_stream) {
+  if (!out) return TRALS_E_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) return TRALS_E_ARG;
+  trals_ctx* ctx = new trals_ctx();
+  ctx->device = device;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) {
+    if (cuda_stream) {
+      ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+      e = cudaStreamCreate(&ctx->stream);
+      ctx->owns_stream = true;
+    }
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(DevStatus));
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status, 0, sizeof(DevStatus), ctx->stream);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_zero_ctr, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_zero_ctr, 0, sizeof(int), ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess) e = init_kernel_attributes();
+  if (e != cudaSuccess) {
+    trals_destroy(ctx);
+    return TRALS_E_CUDA;
+  }
+  *out = ctx;
+  return TRALS_OK;
+}
+
+void trals_destroy(trals_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->d_zero_ctr) cudaFree(ctx->d_zero_ctr);
+  if (ctx->owns_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char* trals_last_error(const trals_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+void trals_plan_destroy(trals_plan* p) {
+  if (!p) return;
+  if (p->ctx && p->ctx->stream) cudaStreamSynchronize(p->ctx->stream);
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  for (int n = 0; n < p->N; ++n) tc_destroy(p->tc[n]);
+  for (void* q : p->allocs) cudaFree(q);
+  delete p;
+}
+
+trals_status trals_plan_create(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R, const void* X_dev, int xt,
+                               const trals_opts* opts, trals_plan** out) {
+  if (!ctx || !out) return TRALS_E_ARG;
+  *out = nullptr;
+  trals_status st = check_shape(ctx, N, I, R);
+  if (st != TRALS_OK) return st;
+  if (!X_dev) {
+    ctx->last_error = "null X";
+    return TRALS_E_ARG;
+  }
+  trals_opts o = opts ? *opts : trals_opts{TRALS_MODE_FP64, TRALS_SOLVE_CHOL, TRALS_GRAM_STRUCTURED, 0};
+  if (o.mode < TRALS_MODE_FP64 || o.mode > TRALS_MODE_BF16X3 || xt < TRALS_X_F64 || xt > TRALS_X_BF16) {
+    ctx->last_error = "unknown mode or X type";
+    return TRALS_E_ARG;
+  }
+  if (o.solver != TRALS_SOLVE_CHOL || o.gram != TRALS_GRAM_STRUCTURED) {
+    if (!(o.solver == TRALS_SOLVE_QR || o.gram == TRALS_GRAM_EXPLICIT)) {
+      ctx->last_error = "unknown solver or gram option";
+      return TRALS_E_ARG;
+    }
+  }
+  if (o.mode == TRALS_MODE_FP64 && xt != TRALS_X_F64) {
+    ctx->last_error = "FP64 mode needs an FP64 X";
+    return TRALS_E_ARG;
+  }
+  if (o.mode == TRALS_MODE_FP32 && xt == TRALS_X_BF16) {
+    ctx->last_error = "FP32 mode needs an FP32 or FP64 X";
+    return TRALS_E_ARG;
+  }
+  if (o.mode == TRALS_MODE_BF16X3 && xt == TRALS_X_BF16) {
+    ctx->last_error = "BF16X3 mode needs an FP32 or FP64 X (to split into hi/lo)";
+    return TRALS_E_ARG;
+  }
+  cudaSetDevice(ctx->device);
+  trals_plan* p = new trals_plan();
+  p->ctx = ctx;
+  p->N = N;
+  for (int n = 0; n < N; ++n) {
+    p->I[n] = I[n];
+    p->R[n] = R[n];
+  }
+  p->X = X_dev;
+  p->xt = xt;
+  p->opts = o;
+  p->numel = 1;
+  for (int n = 0; n < N; ++n) p->numel *= I[n];
+  cudaStream_t s = ctx->stream;
+  cudaError_t e = cudaSuccess;
+#define PLAN_TRY(call)                                                      \
+  do {                                                                      \
+    e = (call);                                                             \
+    if (e != cudaSuccess) {                                                 \
+      ctx->last_error = std::string(#call) + ": " + cudaGetErrorString(e);  \
+      trals_plan_destroy(p);                                                \
+      return e == cudaErrorMemoryAllocation ? TRALS_E_OOM : TRALS_E_CUDA;   \
+    }                                                                       \
+  } while (0)
+
+  int maxR2 = 0, maxr = 0;
+  int64_t maxMr = 0, maxTab = 0;
+  size_t maxPart = 0;
+  for (int n = 0; n < N; ++n) {
+    const int Rn = R[n], Rn1 = R[(n + 1) % N];
+    PLAN_TRY(p->alloc(&p->cores[n], (size_t)Rn * I[n] * Rn1));
+    PLAN_TRY(p->alloc(&p->gam[n], (size_t)Rn * Rn * Rn1 * Rn1));
+    maxR2 = std::max(maxR2, Rn * Rn);
+    maxr = std::max(maxr, Rn * Rn1);
+    maxMr = std::max<int64_t>(maxMr, I[n] * Rn * Rn1);
+    p->lay[n] = make_mode_layout(N, I, R, n);
+    maxTab = std::max<int64_t>(maxTab, table_level_max_elems(p->lay[n], I, R));
+    p->gridX[n] = mttsp_simt_default_grid(p->lay[n]);
+    maxPart = std::max(maxPart, mttsp_simt_partials_elems(p->lay[n], p->gridX[n]));
+    maxPart = std::max(maxPart, (size_t)2 * p->gridX[n]);
+    std::vector<int64_t> offL, offU;
+    mode_offsets(N, I, p->lay[n], offL, offU);
+    PLAN_TRY(p->alloc(&p->offL[n], offL.size()));
+    PLAN_TRY(p->alloc(&p->offU[n], offU.size()));
+    PLAN_TRY(cudaMemcpy(p->offL[n], offL.data(), offL.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    PLAN_TRY(cudaMemcpy(p->offU[n], offU.data(), offU.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+  }
+  PLAN_TRY(p->alloc(&p->S, (size_t)maxr * maxr));
+  PLAN_TRY(p->alloc(&p->Lmat, (size_t)maxr * maxr));
+  PLAN_TRY(p->alloc(&p->chainA, (size_t)maxR2 * maxR2));
+  PLAN_TRY(p->alloc(&p->chainB, (size_t)maxR2 * maxR2));
+  PLAN_TRY(p->alloc(&p->M, (size_t)maxMr));
+  PLAN_TRY(p->alloc(&p->ltab, (size_t)maxTab));
+  PLAN_TRY(p->alloc(&p->utab, (size_t)maxTab));
+  PLAN_TRY(p->alloc(&p->tscratch, (size_t)maxTab));
+  PLAN_TRY(p->alloc(&p->partials, std::max<size_t>(maxPart, 2 * 1024)));
+  PLAN_TRY(p->alloc(&p->red2, 2));
+  PLAN_TRY(p->alloc(&p->normX2, 1));
+  PLAN_TRY(p->alloc(&p->res_hist, kResCap));
+  PLAN_TRY(p->alloc(&p->sweep_ctr, 1));
+  PLAN_TRY(cudaMemsetAsync(p->sweep_ctr, 0, sizeof(int), s));
+
+  // X as the MTTSP reads it (quantised once, K7), and |X|^2 from the full-precision source.
+  p->Xk = X_dev;
+  p->xk_t = xt;
+  if (o.mode == TRALS_MODE_BF16 && xt != TRALS_X_BF16) {
+    __nv_bfloat16* q = nullptr;
+    PLAN_TRY(p->alloc(&q, (size_t)p->numel));
+    launch_quantize(X_dev, xt, p->numel, q, nullptr, s);
+    p->Xk = q;
+    p->xk_t = TRALS_X_BF16;
+  } else if (o.mode == TRALS_MODE_BF16X3) {
+    __nv_bfloat16* q = nullptr;
+    PLAN_TRY(p->alloc(&q, (size_t)p->numel * 2));
+    launch_quantize(X_dev, xt, p->numel, q, q + p->numel, s);
+    p->Xk = q;
+    p->xk_t = TRALS_X_BF16;   // hi half; the SIMT path reads only hi (lo is used by the tensor-core path)
+  } else if (o.mode == TRALS_MODE_FP32 && xt == TRALS_X_F64) {
+    float* q = nullptr;
+    PLAN_TRY(p->alloc(&q, (size_t)p->numel));
+    launch_convert_f32(X_dev, p->numel, q, s);
+    p->Xk = q;
+    p->xk_t = TRALS_X_F32;
+  }
+  {
+    const int g = 152 * 4;
+    launch_sumsq(X_dev, xt, p->numel, p->partials, g, p->normX2, s);
+  }
+  // tensor-core MTTSP plans for the reduced-precision modes
+  for (int n = 0; n < N; ++n) {
+    p->use_tc[n] = false;
+    if (o.mode != TRALS_MODE_FP64) {
+      const int ok = tc_plan(p->tc[n], N, I, R, n, o.mode, p->Xk, p->numel, &e);
+      if (e != cudaSuccess) PLAN_TRY(e);
+      p->use_tc[n] = ok != 0;
+    }
+  }
+  PLAN_TRY(cudaStreamSynchronize(s));
+#undef PLAN_TRY
+  *out = p;
+  return TRALS_OK;
+}
+
+trals_status trals_plan_set_cores(trals_plan* p, double* const* cores_host) {
+  if (!p || !cores_host) return TRALS_E_ARG;
+  trals_ctx* ctx = p->ctx;
+  cudaStream_t s = ctx->stream;
+  for (int n = 0; n < p->N; ++n) {
+    if (!cores_host[n]) {
+      ctx->last_error = "null core pointer";
+      return TRALS_E_ARG;
+    }
+    const size_t cnt = (size_t)p->R[n] * p->I[n] * p->R[(n + 1) % p->N];
+    TRALS_CUDA_TRY(ctx, cudaMemcpyAsync(p->cores[n], cores_host[n], cnt * sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_gamma(p->cores[n], p->R[n], p->I[n], p->R[(n + 1) % p->N], p->gam[n], s);
+  }
+  set_int_kernel<<<1, 1, 0, s>>>(p->sweep_ctr, 0);
+  TRALS_CUDA_TRY(ctx, cudaGetLastError());
+  // host copies are pageable: make them complete before returning
+  TRALS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  p->host_sweeps = 0;
+  return TRALS_OK;
+}
+
+trals_status trals_plan_get_cores(trals_plan* p, double* const* cores_host) {
+  if (!p || !cores_host) return TRALS_E_ARG;
+  trals_ctx* ctx = p->ctx;
+  for (int n = 0; n < p->N; ++n) {
+    const size_t cnt = (size_t)p->R[n] * p->I[n] * p->R[(n + 1) % p->N];
+    TRALS_CUDA_TRY(ctx, cudaMemcpyAsync(cores_host[n], p->cores[n], cnt * sizeof(double), cudaMemcpyDeviceToHost,
+                                        ctx->stream));
+  }
+  return read_status(ctx);
+}
+
+trals_status trals_plan_run(trals_plan* p, int sweeps, int use_graph) {
+  if (!p || sweeps < 0) return TRALS_E_ARG;
+  trals_ctx* ctx = p->ctx;
+  if (p->host_sweeps + sweeps > kResCap) {
+    ctx->last_error = "residual history full: call trals_plan_set_cores to restart";
+    return TRALS_E_ARG;
+  }
+  cudaStream_t s = ctx->stream;
+  for (int k = 0; k < sweeps; ++k) {
+    if (use_graph) {
+      if (!p->gexec) {
+        cudaGraph_t g = nullptr;
+        TRALS_CUDA_TRY(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        p->launches = enqueue_sweep(p);
+        cudaError_t e = cudaStreamEndCapture(s, &g);
+        if (e != cudaSuccess) {
+          ctx->last_error = std::string("graph capture: ") + cudaGetErrorString(e);
+          return TRALS_E_CUDA;
+        }
+        e = cudaGraphInstantiate(&p->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+          ctx->last_error = std::string("graph instantiate: ") + cudaGetErrorString(e);
+          p->gexec = nullptr;
+          return TRALS_E_CUDA;
+        }
+      }
+      TRALS_CUDA_TRY(ctx, cudaGraphLaunch(p->gexec, s));
+    } else {
+      p->launches = enqueue_sweep(p);
+      TRALS_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    ++p->host_sweeps;
+  }
+  return TRALS_OK;
+}
+
+trals_status trals_plan_residuals(trals_plan* p, double* rel_res_host, int cap, int* count) {
+  if (!p) return TRALS_E_ARG;
+  trals_ctx* ctx = p->ctx;
+  const int n = std::min(cap, p->host_sweeps);
+  if (rel_res_host && n > 0)
+    TRALS_CUDA_TRY(ctx, cudaMemcpyAsync(rel_res_host, p->res_hist, n * sizeof(double), cudaMemcpyDeviceToHost,
+                                        ctx->stream));
+  if (count) *count = n;
+  return read_status(ctx);
+}
+
+trals_status trals_plan_mttsp(trals_plan* p, int n, double* M_dev) {
+  if (!p || n < 0 || n >= p->N) return TRALS_E_ARG;
+  double* keep = p->M;
+  if (M_dev) p->M = M_dev;
+  enqueue_mttsp(p, n, p->ctx->stream);
+  p->M = keep;
+  TRALS_CUDA_TRY(p->ctx, cudaGetLastError());
+  return TRALS_OK;
+}
+
+const double* trals_plan_core_dev(const trals_plan* p, int n) {
+  if (!p || n < 0 || n >= p->N) return nullptr;
+  return p->cores[n];
+}
+
+int trals_plan_launches_per_sweep(const trals_plan* p) {
+  if (!p) return 0;
+  if (p->launches == 0) {
+    // count by a dry enqueue is not possible without launching; report the analytic count
+    return 0;
+  }
+  return p->launches;
+}
+
+trals_status trals_decompose(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R, const void* X, int xt,
+                             int x_on_host, double* const* cores, int sweeps, const trals_opts* opts,
+                             double* rel_res) {
+  if (!ctx || !X || !cores || sweeps < 0) return TRALS_E_ARG;
+  trals_status st = check_shape(ctx, N, I, R);
+  if (st != TRALS_OK) return st;
+  void* Xd = nullptr;
+  const void* Xuse = X;
+  if (x_on_host) {
+    int64_t numel = 1;
+    for (int n = 0; n < N; ++n) numel *= I[n];
+    const size_t es = xt == TRALS_X_F64 ? 8 : xt == TRALS_X_F32 ? 4 : 2;
+    TRALS_CUDA_TRY(ctx, cudaMalloc(&Xd, (size_t)numel * es));
+    cudaError_t e = cudaMemcpyAsync(Xd, X, (size_t)numel * es, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) {
+      cudaFree(Xd);
+      ctx->last_error = cudaGetErrorString(e);
+      return TRALS_E_CUDA;
+    }
+    Xuse = Xd;
+  }
+  trals_plan* p = nullptr;
+  st = trals_plan_create(ctx, N, I, R, Xuse, xt, opts, &p);
+  if (st == TRALS_OK) st = trals_plan_set_cores(p, cores);
+  if (st == TRALS_OK) st = trals_plan_run(p, sweeps, 1);
+  if (st == TRALS_OK) st = trals_plan_residuals(p, rel_res, sweeps, nullptr);
+  if (st == TRALS_OK) st = trals_plan_get_cores(p, cores);
+  trals_plan_destroy(p);
+  if (Xd) cudaFree(Xd);
+  return st;
+}
+
+// ------------------------------------------------------------------ per-step entry points
+trals_status trals_gamma(trals_ctx* ctx, const double* G_dev, int Rn, int64_t In, int Rn1, double* Gamma_dev) {
+  if (!ctx || !G_dev || !Gamma_dev || Rn < 1 || Rn1 < 1 || In < 1) return TRALS_E_ARG;
+  launch_gamma(G_dev, Rn, In, Rn1, Gamma_dev, ctx->stream);
+  TRALS_CUDA_TRY(ctx, cudaGetLastError());
+  TRALS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return TRALS_OK;
+}
+
+trals_status trals_coef_matrix(trals_ctx* ctx, int N, const int32_t* R, const double* const* gammas_dev, int n,
+                               double* S_dev) {
+  if (!ctx || !R || !gammas_dev || !S_dev || N < 3 || N > TRALS_MAX_ORDER || n < 0 || n >= N) return TRALS_E_ARG;
+  int maxR2 = 0;
+  for (int k = 0; k < N; ++k) maxR2 = std::max(maxR2, R[k] * R[k]);
+  double *a = nullptr, *b = nullptr;
+  TRALS_CUDA_TRY(ctx, cudaMalloc(&a, (size_t)maxR2 * maxR2 * sizeof(double)));
+  cudaError_t e = cudaMalloc(&b, (size_t)maxR2 * maxR2 * sizeof(double));
+  if (e == cudaSuccess) {
+    enqueue_coef(N, R, const_cast<double* const*>(gammas_dev), n, a, b, S_dev, ctx->stream);
+    e = cudaStreamSynchronize(ctx->stream);
+  }
+  cudaFree(a);
+  if (b) cudaFree(b);
+  TRALS_CUDA_TRY(ctx, e);
+  return TRALS_OK;
+}
+
+trals_status trals_mttsp(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R, const void* X_dev, int xt,
+                         int mode, const double* const* cores_dev, int n, double* M_dev) {
+  if (!ctx || !X_dev || !cores_dev || !M_dev || n < 0 || n >= N) return TRALS_E_ARG;
+  trals_status st = check_shape(ctx, N, I, R);
+  if (st != TRALS_OK) return st;
+  const bool ok_type = (mode == TRALS_MODE_FP64 && xt == TRALS_X_F64) || (mode == TRALS_MODE_FP32 && xt == TRALS_X_F32) ||
+                       ((mode == TRALS_MODE_BF16 || mode == TRALS_MODE_BF16X3) && xt == TRALS_X_BF16);
+  if (!ok_type) {
+    ctx->last_error = "X element type does not match the mode";
+    return TRALS_E_ARG;
+  }
+  cudaStream_t s = ctx->stream;
+  int64_t numel = 1;
+  for (int k = 0; k < N; ++k) numel *= I[k];
+  TcPlan tc;
+  cudaError_t e = cudaSuccess;
+  const int use_tc = (mode != TRALS_MODE_FP64) ? tc_plan(tc, N, I, R, n, mode, X_dev, numel, &e) : 0;
+  TRALS_CUDA_TRY(ctx, e);
+  if (use_tc) {
+    tc_enqueue(tc, X_dev, const_cast<double* const*>(cores_dev), M_dev, s);
+    e = cudaStreamSynchronize(s);
+    tc_destroy(tc);
+    TRALS_CUDA_TRY(ctx, e);
+    TRALS_CUDA_TRY(ctx, cudaGetLastError());
+    return TRALS_OK;
+  }
+  const ModeLayout L = make_mode_layout(N, I, R, n);
+  const int64_t tab = table_level_max_elems(L, I, R);
+  const int gridX = mttsp_simt_default_grid(L);
+  std::vector<int64_t> offL, offU;
+  mode_offsets(N, I, L, offL, offU);
+  double *lt = nullptr, *ut = nullptr, *sc = nullptr, *part = nullptr;
+  int64_t *dL = nullptr, *dU = nullptr;
+  e = cudaMalloc(&lt, tab * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&ut, tab * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&sc, tab * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&part, mttsp_simt_partials_elems(L, gridX) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&dL, offL.size() * sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&dU, offU.size() * sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMemcpy(dL, offL.data(), offL.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dU, offU.data(), offU.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    build_tables(L, cores_dev, I, R, lt, ut, sc, s);
+    MttspSimtArgs a;
+    a.X = X_dev;
+    a.xt = xt;
+    a.ltab = lt;
+    a.utab = ut;
+    a.offL = dL;
+    a.offU = dU;
+    a.L = L;
+    a.partials = part;
+    a.M = M_dev;
+    a.gridX = gridX;
+    launch_mttsp_simt(a, s);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  cudaFree(lt);
+  cudaFree(ut);
+  cudaFree(sc);
+  cudaFree(part);
+  cudaFree(dL);
+  cudaFree(dU);
+  TRALS_CUDA_TRY(ctx, e);
+  return TRALS_OK;
+}
+
+trals_status trals_solve_chol(trals_ctx* ctx, int Rn, int64_t In, int Rn1, const double* S_dev, const double* M_dev,
+                              double* G_dev) {
+  if (!ctx || !S_dev || !M_dev || !G_dev || Rn < 1 || Rn1 < 1 || In < 1 || Rn * Rn1 > 256) return TRALS_E_ARG;
+  const int r = Rn * Rn1;
+  double* Lm = nullptr;
+  TRALS_CUDA_TRY(ctx, cudaMalloc(&Lm, (size_t)r * r * sizeof(double)));
+  launch_cholesky(S_dev, Lm, r, ctx->d_status, nullptr, -1, ctx->stream);
+  launch_chol_solve(Lm, M_dev, Rn, In, Rn1, G_dev, ctx->d_status, ctx->stream);
+  cudaError_t e = cudaGetLastError();
+  trals_status st = (e == cudaSuccess) ? read_status(ctx) : TRALS_E_CUDA;
+  cudaFree(Lm);
+  if (e != cudaSuccess) ctx->last_error = cudaGetErrorString(e);
+  return st;
+}
+
+trals_status trals_reconstruct(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R,
+                               const double* const* cores_dev, void* out_dev, int xt) {
+  if (!ctx || !cores_dev || !out_dev) return TRALS_E_ARG;
+  trals_status st = check_shape(ctx, N, I, R);
+  if (st != TRALS_OK) return st;
+  const int n = N - 1;
+  const ModeLayout L = make_mode_layout(N, I, R, n);
+  const int64_t tab = table_level_max_elems(L, I, R);
+  std::vector<int64_t> offL, offU;
+  mode_offsets(N, I, L, offL, offU);
+  const int gridX = mttsp_simt_default_grid(L);
+  double *lt = nullptr, *ut = nullptr, *sc = nullptr;
+  int64_t *dL = nullptr, *dU = nullptr;
+  cudaError_t e = cudaMalloc(&lt, tab * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&ut, tab * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&sc, tab * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&dL, offL.size() * sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&dU, offU.size() * sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMemcpy(dL, offL.data(), offL.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dU, offU.data(), offU.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    build_tables(L, cores_dev, I, R, lt, ut, sc, ctx->stream);
+    launch_reconstruct(L, lt, ut, dL, dU, cores_dev[n], out_dev, xt, nullptr, TRALS_X_F64, nullptr, gridX,
+                       ctx->stream);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  }
+  cudaFree(lt);
+  cudaFree(ut);
+  cudaFree(sc);
+  cudaFree(dL);
+  cudaFree(dU);
+  TRALS_CUDA_TRY(ctx, e);
+  return TRALS_OK;
+}
+
+trals_status trals_residual_explicit(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R, const void* X_dev,
+                                     int xt, const double* const* cores_dev, double* res2_host, double* normx2_host) {
+  if (!ctx || !cores_dev || !X_dev) return TRALS_E_ARG;
+  trals_status st = check_shape(ctx, N, I, R);
+  if (st != TRALS_OK) return st;
+  const int n = N - 1;
+  const ModeLayout L = make_mode_layout(N, I, R, n);
+  const int64_t tab = table_level_max_elems(L, I, R);
+  std::vector<int64_t> offL, offU;
+  mode_offsets(N, I, L, offL, offU);
+  const int gridX = mttsp_simt_default_grid(L);
+  double *lt = nullptr, *ut = nullptr, *sc = nullptr, *part = nullptr, *red = nullptr;
+  int64_t *dL = nullptr, *dU = nullptr;
+  cudaError_t e = cudaMalloc(&lt, tab * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&ut, tab * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&sc, tab * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&part, 2 * gridX * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&red, 2 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&dL, offL.size() * sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&dU, offU.size() * sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMemcpy(dL, offL.data(), offL.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dU, offU.data(), offU.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+  double h[2] = {0, 0};
+  if (e == cudaSuccess) {
+    build_tables(L, cores_dev, I, R, lt, ut, sc, ctx->stream);
+    launch_reconstruct(L, lt, ut, dL, dU, cores_dev[n], nullptr, TRALS_X_F64, X_dev, xt, part, gridX, ctx->stream);
+    launch_reduce_pairs(part, gridX, red, ctx->stream);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, red, sizeof h, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  }
+  cudaFree(lt);
+  cudaFree(ut);
+  cudaFree(sc);
+  cudaFree(part);
+  cudaFree(red);
+  cudaFree(dL);
+  cudaFree(dU);
+  TRALS_CUDA_TRY(ctx, e);
+  if (res2_host) *res2_host = h[0];
+  if (normx2_host) *normx2_host = h[1];
+  return TRALS_OK;
+}
+
+trals_status trals_quantize_bf16(trals_ctx* ctx, const void* src_dev, int src_t, int64_t count, void* dst_hi_dev,
+                                 void* dst_lo_dev) {
+  if (!ctx || !src_dev || !dst_hi_dev || count < 0 || (src_t != TRALS_X_F64 && src_t != TRALS_X_F32))
+    return TRALS_E_ARG;
+  launch_quantize(src_dev, src_t, count, static_cast<__nv_bfloat16*>(dst_hi_dev),
+                  static_cast<__nv_bfloat16*>(dst_lo_dev), ctx->stream);
+  TRALS_CUDA_TRY(ctx, cudaGetLastError());
+  TRALS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return TRALS_OK;
+}
+
+}  // extern "C"

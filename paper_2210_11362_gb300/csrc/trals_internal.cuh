@@ -1,0 +1,133 @@
+// Internal declarations shared by the libtrals translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/trals.h"
+
+namespace trals {
+
+constexpr int kMaxOrder = TRALS_MAX_ORDER;
+
+// Device status word: first failure wins (atomicCAS on code).
+struct DevStatus {
+  int code;    // trals_status
+  int sweep;   // sweep index (plan runs) or -1
+  int mode;    // core index n or -1
+  int index;   // pivot / element index
+  double value;
+};
+
+// ---------------------------------------------------------------- per-mode MTTSP layout
+// The other modes of mode n in subchain order c_1..c_{N-1} = n+1..N,1..n-1 (eq. subchain_new)
+// are split into Left = c_1..c_m and Right = c_{m+1}..c_{N-1}.  G^{!=n}(k) = L(l) U(u) with
+// k = l + |L| u.  Ltab[l] is R_{n+1} x R_s, Utab[u] is R_s x R_n (s = c_{m+1}), column-major.
+// offL[l] + offU[u] is the memory offset of X(i) with i_n = 0; i_n adds i_n * strideN.
+struct ModeLayout {
+  int N;
+  int n;
+  int chain[kMaxOrder];
+  int m;                 // number of Left modes
+  int64_t nL, nU;        // table entries
+  int Rn, Rn1, Rs;       // R_n, R_{n+1}, R at the split
+  int64_t In, strideN;   // I_n, prod_{j<n} I_j
+  int64_t J;             // prod_{j != n} I_j
+};
+
+// Build the layout for mode n choosing the split that minimises nL + nU.
+ModeLayout make_mode_layout(int N, const int64_t* I, const int32_t* R, int n);
+// Host-side offsets for the layout (sizes nL and nU).
+void mode_offsets(int N, const int64_t* I, const ModeLayout& L, std::vector<int64_t>& offL,
+                  std::vector<int64_t>& offU);
+
+// ---------------------------------------------------------------- kernel launchers (stream-ordered)
+// Gamma_k (K1).
+void launch_gamma(const double* G, int Rn, int64_t In, int Rn1, double* Gamma, cudaStream_t s);
+// C (m x n) = A (m x k) * B (k x n), column-major FP64.
+void launch_gemm_f64(int m, int n, int k, const double* A, const double* B, double* C, cudaStream_t s);
+// S_n regroup of Pi (R_{n+1}^2 x R_n^2) -> S (r x r).
+void launch_regroup_S(const double* Pi, int Rn, int Rn1, double* S, cudaStream_t s);
+// Chain table: out[l + nPrev * i][x + Ra * y] = sum_c prev[l][x + Ra c] * G[c + Rc (i + I y)]
+// (prev == nullptr: out = core slices, Ra = Rc).
+void launch_chain_level(const double* prev, int64_t nPrev, int Ra, int Rc, const double* G, int64_t Ii,
+                        int Rb, double* out, cudaStream_t s);
+// Tables for one mode layout into ltab/utab.
+void build_tables(const ModeLayout& L, const double* const* cores, const int64_t* I, const int32_t* R,
+                  double* ltab, double* utab, double* scratch, cudaStream_t s);
+// Largest level of either table (elements); ltab, utab and scratch each need this many doubles.
+int64_t table_level_max_elems(const ModeLayout& L, const int64_t* I, const int32_t* R);
+
+// MTTSP on CUDA cores (any X type): partial sums per block then a fixed-order reduction.
+struct MttspSimtArgs {
+  const void* X;
+  int xt;               // trals_xtype (F64, F32, BF16)
+  const double* ltab;
+  const double* utab;
+  const int64_t* offL;
+  const int64_t* offU;
+  ModeLayout L;
+  double* partials;     // [gridX][I_n * r]
+  double* M;            // I_n x r
+  int gridX;
+};
+size_t mttsp_simt_partials_elems(const ModeLayout& L, int gridX);
+int mttsp_simt_default_grid(const ModeLayout& L);
+void launch_mttsp_simt(const MttspSimtArgs& a, cudaStream_t s);
+
+// Reconstruction / explicit residual (same layout as the MTTSP): for each column k,
+// xhat(i_n, k) = sum_r Z[i_n, r] G^{!=n}(k)[b, a] with Z the unfolding of core n.
+void launch_reconstruct(const ModeLayout& L, const double* ltab, const double* utab, const int64_t* offL,
+                        const int64_t* offU, const double* coreN, void* out, int out_t, const void* X, int xt,
+                        double* partials, int gridX, cudaStream_t s);
+// Sum of `count` partials into out[0] (and out[1] if two interleaved series), fixed order.
+void launch_reduce_pairs(const double* partials, int count, double* out, cudaStream_t s);
+
+// Cholesky (K4): factor S (r x r, lower triangle) into L (r x r) in place on a copy; status on failure.
+void launch_cholesky(const double* S, double* Lmat, int r, DevStatus* st, const int* sweep_ctr, int mode,
+                     cudaStream_t s);
+// Triangular solves with In right-hand sides; writes core layout.
+void launch_chol_solve(const double* Lmat, const double* M, int Rn, int64_t In, int Rn1, double* G,
+                       DevStatus* st, cudaStream_t s);
+
+// Residual identity (K6): res2 = normX2 - 2<M, Z> + <S, Z^T Z>; Gamma holds the regrouped Z^T Z.
+void launch_residual_identity(const double* normX2, const double* M, const double* coreN, const double* S,
+                              const double* gammaN, int Rn, int64_t In, int Rn1, double* res_hist,
+                              int* sweep_ctr, cudaStream_t s);
+// sum of squares of X in FP64 -> partials then reduce
+void launch_sumsq(const void* X, int xt, int64_t count, double* partials, int gridX, double* out, cudaStream_t s);
+// BF16 quantisation (K7).
+void launch_quantize(const void* src, int src_t, int64_t count, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                     cudaStream_t s);
+// FP64 -> FP32 copy (FP32 mode fed with an FP64 X).
+void launch_convert_f32(const void* src_f64, int64_t count, float* dst, cudaStream_t s);
+void launch_zero_status(DevStatus* st, cudaStream_t s);
+// One-time kernel attribute setup (dynamic shared memory opt-in); called at context creation.
+cudaError_t init_small_attributes();
+cudaError_t init_simt_attributes();
+cudaError_t init_kernel_attributes();
+
+}  // namespace trals
+
+// ---------------------------------------------------------------- context
+struct trals_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool owns_stream = false;
+  std::string last_error;
+  trals::DevStatus* d_status = nullptr;   // per-context device status word
+  int* d_zero_ctr = nullptr;              // a device int holding 0 (sweep counter for one-off calls)
+};
+
+#define TRALS_CUDA_TRY(ctx, call)                                                        \
+  do {                                                                                   \
+    cudaError_t e__ = (call);                                                            \
+    if (e__ != cudaSuccess) {                                                            \
+      if (ctx) (ctx)->last_error = std::string(#call) + ": " + cudaGetErrorString(e__); \
+      return e__ == cudaErrorMemoryAllocation ? TRALS_E_OOM : TRALS_E_CUDA;              \
+    }                                                                                    \
+  } while (0)

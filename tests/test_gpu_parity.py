@@ -1,0 +1,235 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, step by step and end to end.
+
+Tolerances: the FP64 path must match the oracle's cores after one sweep within 1e-9
+relative; single steps in FP64 within 1e-12 relative (FP64 rounding of sums of a few
+thousand terms); integer/byte work (BF16 quantisation) bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import trals_inputs as TI
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU hosts
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2210_11362_gb300 as P  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return P.trals_create(0)
+
+
+def rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+
+
+SHAPES = [
+    ((7, 5, 9, 4), (2, 3, 4, 2)),           # ragged sizes, mixed ranks
+    ((20, 20, 20), (3, 3, 3)),              # the 20^3 rank-3 workload shape
+    ((3, 11, 6), (2, 2, 3)),                # I_1 < R_1 R_2
+    ((13, 3, 5, 2, 4), (2, 3, 2, 2, 3)),    # order 5, tiny modes
+    ((33, 17, 40), (5, 4, 6)),              # several tiles per block, ragged tail
+]
+
+
+def _problem(I, R, seed=3, eta=1e-2):
+    truth = TI.gaussian_cores(seed, I, R)
+    X = TI.add_relative_noise(O.tr_full(truth), TI.gaussian_noise(seed, I), eta)
+    return X, TI.init_cores(seed, I, R)
+
+
+def test_gamma_matches_definition(ctx):
+    for (Rn, In, Rn1) in [(3, 20, 3), (2, 7, 5), (10, 60, 10), (16, 3, 16), (1, 4, 1)]:
+        G = np.random.default_rng(Rn * 100 + In).standard_normal((Rn, In, Rn1))
+        Gd = P.core_to_device(G)
+        out = torch.zeros(Rn * Rn * Rn1 * Rn1, dtype=torch.float64, device="cuda")
+        P.trals_gamma(ctx, Gd, Rn, In, Rn1, out)
+        ref = O.gamma(G)
+        got = out.cpu().numpy().reshape(Rn * Rn, Rn1 * Rn1, order="F")
+        assert rel(got, ref) < 1e-13
+
+
+@pytest.mark.parametrize("I,R", SHAPES)
+def test_coef_matrix_equals_explicit_gram(ctx, I, R):
+    cores = TI.gaussian_cores(5, I, R)
+    gams = []
+    for G in cores:
+        g = O.gamma(G)
+        gams.append(torch.from_numpy(g.reshape(-1, order="F").copy()).cuda())
+    N = len(I)
+    for n in range(N):
+        r = R[n] * R[(n + 1) % N]
+        S = torch.zeros(r * r, dtype=torch.float64, device="cuda")
+        P.trals_coef_matrix(ctx, R, gams, n, S)
+        A = O.subchain_unfolded(cores, n)
+        ref = A.T @ A
+        assert rel(S.cpu().numpy().reshape(r, r, order="F"), ref) < 1e-12
+
+
+@pytest.mark.parametrize("I,R", SHAPES)
+def test_mttsp_fp64_matches_oracle(ctx, I, R):
+    X, _ = _problem(I, R)
+    cores = TI.gaussian_cores(9, I, R)
+    Xd = P.tensor_to_device(X)
+    cd = [P.core_to_device(G) for G in cores]
+    N = len(I)
+    for n in range(N):
+        r = R[n] * R[(n + 1) % N]
+        M = torch.zeros(I[n] * r, dtype=torch.float64, device="cuda")
+        P.trals_mttsp(ctx, I, R, Xd, "fp64", cd, n, M)
+        ref = O.unfold_mode(X, n) @ O.subchain_unfolded(cores, n)
+        assert rel(M.cpu().numpy().reshape(I[n], r, order="F"), ref) < 1e-12
+
+
+def test_solve_chol_matches_oracle(ctx):
+    I, R = (9, 8, 7), (3, 4, 2)
+    X, init = _problem(I, R)
+    for n in range(3):
+        S, M = O.normal_equation_terms(X, init, n)
+        Rn, Rn1 = R[n], R[(n + 1) % 3]
+        G = torch.zeros(Rn * I[n] * Rn1, dtype=torch.float64, device="cuda")
+        P.trals_solve_chol(ctx, Rn, I[n], Rn1, torch.from_numpy(S.reshape(-1, order="F").copy()).cuda(),
+                           torch.from_numpy(M.reshape(-1, order="F").copy()).cuda(), G)
+        ref = O.core_fold2(O.ls_solve_normal(S, M), Rn, Rn1)
+        assert rel(P.core_from_device(G, Rn, I[n], Rn1), ref) < 1e-10
+
+
+def test_solve_chol_reports_not_spd(ctx):
+    r = 6
+    S = -np.eye(r)
+    M = np.ones((4, r))
+    G = torch.zeros(2 * 4 * 3, dtype=torch.float64, device="cuda")
+    with pytest.raises(P.TralsError) as e:
+        P.trals_solve_chol(ctx, 2, 4, 3, torch.from_numpy(S.reshape(-1, order="F").copy()).cuda(),
+                           torch.from_numpy(M.reshape(-1, order="F").copy()).cuda(), G)
+    assert e.value.status == P.E_NOT_SPD
+    # the context stays usable afterwards
+    test_gamma_matches_definition(ctx)
+
+
+@pytest.mark.parametrize("I,R", SHAPES)
+def test_decompose_fp64_one_sweep_matches_oracle(ctx, I, R):
+    X, init = _problem(I, R)
+    cores = [G.copy() for G in init]
+    res = P.trals_decompose(ctx, I, R, X, cores, 1)
+    ref, ref_res = O.tr_als(X, init, 1, "qr")
+    for a, b in zip(cores, ref):
+        assert rel(a, b) < 1e-9
+    assert abs(res[0] - ref_res[0]) <= 1e-9 * ref_res[0]
+
+
+def test_tr20_rank3_ten_sweeps(ctx):
+    """The 20x20x20 rank-3 workload: 1e-3 noise, seeded N(0,1) init, 10 sweeps, Cholesky."""
+    w = TI.WORKLOADS["tr20x3_r3"]
+    X = TI.make_tensor_host(w, 0, O.tr_full)
+    init = TI.init_cores(0, w.I, w.R_fit)
+    cores = [G.copy() for G in init]
+    res = P.trals_decompose(ctx, w.I, w.R_fit, X, cores, w.sweeps)
+    c1 = [G.copy() for G in init]
+    P.trals_decompose(ctx, w.I, w.R_fit, X, c1, 1)
+    ref1, _ = O.tr_als(X, init, 1, "chol", residual=False)
+    for a, b in zip(c1, ref1):
+        assert rel(a, b) < 1e-9
+    ref, ref_res = O.tr_als(X, init, w.sweeps, "chol")
+    np.testing.assert_allclose(res, ref_res, rtol=1e-7)
+    for r0, r1 in zip(res, res[1:]):
+        assert r1 <= r0 * (1 + 1e-9)
+
+
+def test_plan_graph_replay_is_bitwise_equal_to_eager(ctx):
+    I, R = (17, 12, 9, 10), (3, 4, 2, 3)
+    X, init = _problem(I, R)
+    Xd = P.tensor_to_device(X)
+    outs = []
+    for use_graph in (False, True, True):
+        plan = P.Plan(ctx, I, R, Xd)
+        plan.set_cores(init)
+        plan.run(3, use_graph=use_graph)
+        outs.append((plan.get_cores(), plan.residuals()))
+        plan.close()
+    for cores, res in outs[1:]:
+        for a, b in zip(cores, outs[0][0]):
+            np.testing.assert_array_equal(a, b)
+        np.testing.assert_array_equal(res, outs[0][1])
+
+
+def test_reconstruct_and_explicit_residual(ctx):
+    for I, R in SHAPES:
+        cores = TI.gaussian_cores(4, I, R)
+        cd = [P.core_to_device(G) for G in cores]
+        out = torch.zeros(int(np.prod(I)), dtype=torch.float64, device="cuda")
+        P.trals_reconstruct(ctx, I, R, cd, out)
+        ref = O.tr_full(cores)
+        assert rel(TI.unflat_f(out.cpu().numpy(), I), ref) < 1e-12
+        X = ref + 0.1 * TI.gaussian_noise(4, I)
+        r2, x2 = P.trals_residual_explicit(ctx, I, R, P.tensor_to_device(X), cd)
+        assert abs(r2 - np.sum((X - ref) ** 2)) <= 1e-10 * np.sum(X ** 2)
+        assert abs(x2 - np.sum(X ** 2)) <= 1e-12 * np.sum(X ** 2)
+
+
+def test_explicit_residual_option_matches_identity(ctx):
+    I, R = (11, 10, 9), (2, 3, 2)
+    X, init = _problem(I, R, eta=0.05)
+    a = [G.copy() for G in init]
+    b = [G.copy() for G in init]
+    ra = P.trals_decompose(ctx, I, R, X, a, 4)
+    rb = P.trals_decompose(ctx, I, R, X, b, 4, P.make_opts("fp64", explicit_residual=True))
+    np.testing.assert_allclose(ra, rb, rtol=1e-8)
+    _, ref_res = O.tr_als(X, init, 4, "qr")
+    np.testing.assert_allclose(rb, ref_res, rtol=1e-9)
+
+
+def test_quantize_bitexact(ctx):
+    x = np.random.default_rng(8).standard_normal(100003) * 10.0 ** np.random.default_rng(9).integers(-6, 6, 100003)
+    xd = torch.from_numpy(x).cuda()
+    hi = torch.zeros(x.size, dtype=torch.bfloat16, device="cuda")
+    lo = torch.zeros(x.size, dtype=torch.bfloat16, device="cuda")
+    P.trals_quantize_bf16(ctx, xd, hi, lo)
+    rh, rl = O.bf16_split(x)
+    np.testing.assert_array_equal(hi.view(torch.int16).cpu().numpy().view(np.uint16), rh)
+    np.testing.assert_array_equal(lo.view(torch.int16).cpu().numpy().view(np.uint16), rl)
+
+
+def test_argument_errors(ctx):
+    X = torch.zeros(2 * 2 * 2, dtype=torch.float64, device="cuda")
+    with pytest.raises(P.TralsError) as e:   # J_n = 4 < R_n R_{n+1} = 9
+        P.Plan(ctx, (2, 2, 2), (3, 3, 3), X)
+    assert e.value.status == P.E_ARG
+    with pytest.raises(P.TralsError):        # order 2
+        P.Plan(ctx, (4, 4), (2, 2), torch.zeros(16, dtype=torch.float64, device="cuda"))
+    with pytest.raises(P.TralsError):        # FP64 mode with an FP32 X
+        P.Plan(ctx, (4, 4, 4), (2, 2, 2), torch.zeros(64, dtype=torch.float32, device="cuda"))
+
+
+@pytest.mark.parametrize("mode", ["fp32", "bf16", "bf16x3"])
+def test_reduced_precision_residual_gap(ctx, mode):
+    """Reduced-precision modes reach the FP64 oracle's residual within 1e-4 (absolute)."""
+    w = TI.WORKLOADS["tr20x3_r3"]
+    X = TI.make_tensor_host(w, 1, O.tr_full)
+    init = TI.init_cores(1, w.I, w.R_fit)
+    cores = [G.copy() for G in init]
+    Xd = P.tensor_to_device(X, torch.float32)
+    P.trals_decompose(ctx, w.I, w.R_fit, Xd, cores, w.sweeps, P.make_opts(mode))
+    _, ref_res = O.tr_als(X, init, w.sweeps, "chol")
+    gap = abs(O.rel_residual(X, cores) - ref_res[-1])
+    assert gap <= 1e-4, gap
+
+
+def test_tr60x4_rank10_full_size_one_sweep(ctx):
+    """60^4 (12.96M entries), ranks 10: GPU FP64 cores after one sweep vs the oracle (blockwise NE)."""
+    w = TI.WORKLOADS["tr60x4_r10"]
+    X = TI.make_tensor_host(w, 0, O.tr_full)
+    init = TI.init_cores(0, w.I, w.R_fit)
+    cores = [G.copy() for G in init]
+    P.trals_decompose(ctx, w.I, w.R_fit, X, cores, 1)
+    ref = [G.copy() for G in init]
+    for n in range(4):
+        S, M = O.normal_equation_terms(X, ref, n)
+        ref[n] = O.core_fold2(O.ls_solve_normal(S, M), ref[n].shape[0], ref[n].shape[2])
+    for a, b in zip(cores, ref):
+        assert rel(a, b) < 1e-9

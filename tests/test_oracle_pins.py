@@ -385,3 +385,20 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     flipped = float(np.sum(Xn * Xn) + 2.0 * np.sum(M * Z) + np.sum(S * (Z.T @ Z)))
     assert abs(flipped - explicit) > 1e-3 * explicit
     assert abs(O.residual_identity(float(np.sum(Xn * Xn)), M, Z, S) - explicit) < 1e-9 * np.sum(Xn * Xn)
+
+
+# --------------------------------------------------------------------------- BF16 storage
+def test_bf16_rne_matches_torch_and_ties():
+    import torch
+    rng = np.random.default_rng(50)
+    x = np.concatenate([rng.standard_normal(10000) * 10.0 ** rng.integers(-8, 8, 10000),
+                        [0.0, -0.0, 1.0, -2.5, 3.0e38, 1e-40]])
+    bits = O.bf16_rne_bits(x)
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    np.testing.assert_array_equal(bits, ref)
+    # exact ties: 1 + 2^-8 lies halfway between 1 and 1 + 2^-7 -> even (1.0); 1 + 3*2^-8 -> 1 + 2^-6
+    assert O.bf16_bits_to_f64(O.bf16_rne_bits(1.0 + 2.0 ** -8))[()] == 1.0
+    assert O.bf16_bits_to_f64(O.bf16_rne_bits(1.0 + 3 * 2.0 ** -8))[()] == 1.0 + 2.0 ** -6
+    hi, lo = O.bf16_split(x[:10000])
+    rel = np.abs(O.bf16_bits_to_f64(hi) + O.bf16_bits_to_f64(lo) - x[:10000]) / np.abs(x[:10000])
+    assert rel.max() < 2.0 ** -16
