@@ -318,7 +318,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="tr60x4_r10", choices=sorted(TI.WORKLOADS))
+    ap.add_argument("--config", default="tr40x5_r8-12", choices=sorted(TI.WORKLOADS))
     ap.add_argument("--mode", default="bf16", choices=["fp64", "fp32", "bf16", "bf16x3"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-fp64", action="store_true")

@@ -180,6 +180,13 @@ trals_status trals_mttsp(trals_ctx* ctx, int N, const int64_t* I, const int32_t*
 trals_status trals_solve_chol(trals_ctx* ctx, int Rn, int64_t In, int Rn1, const double* S_dev,
                               const double* M_dev, double* G_dev);
 
+/* Which kernel computes the MTTSP of mode n in `mode` (host-only query, needs no GPU):
+ * 0 = CUDA cores (the FP64 path, and shapes the tensor-core kernel does not take);
+ * 1 = tensor cores, X K-major with the stage-2 factor on the left;
+ * 2 = tensor cores, X K-major with the stage-2 factor on the right;
+ * 3 = tensor cores, X MN-major.  Negative on invalid arguments. */
+int trals_mttsp_path(int N, const int64_t* I, const int32_t* R, int n, int mode);
+
 /* X_hat = TR(cores) written to out_dev (column-major, element type xt) (Sec. 1 element formula). */
 trals_status trals_reconstruct(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R,
                                const double* const* cores_dev, void* out_dev, int xt);

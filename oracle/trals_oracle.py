@@ -74,7 +74,7 @@ def tr_full(cores: Sequence[np.ndarray]) -> np.ndarray:
     for m in range(1, N - 1):
         G = cores[m]
         # new[r, k + K*i_m, s] = sum_c Z[r, k, c] G[c, i_m, s]
-        new = np.einsum("akc,cis->akis", Z, G)
+        new = np.einsum("akc,cis->akis", Z, G, optimize=True)
         Z = new.reshape(Z.shape[0], Z.shape[1] * G.shape[1], G.shape[2], order="F")
     GN = cores[N - 1]
     # vals[k, i_N] = sum_{a,c} Z[a, k, c] GN[c, i_N, a]

@@ -38,7 +38,7 @@ EXPORTED = [
     "trals_plan_create", "trals_plan_destroy", "trals_plan_set_cores", "trals_plan_get_cores",
     "trals_plan_run", "trals_plan_residuals", "trals_plan_mttsp", "trals_plan_core_dev",
     "trals_plan_launches_per_sweep",
-    "trals_gamma", "trals_coef_matrix", "trals_mttsp", "trals_solve_chol", "trals_reconstruct",
+    "trals_gamma", "trals_coef_matrix", "trals_mttsp", "trals_mttsp_path", "trals_solve_chol", "trals_reconstruct",
     "trals_residual_explicit", "trals_quantize_bf16",
 ]
 
@@ -88,6 +88,7 @@ def lib() -> ctypes.CDLL:
         "trals_coef_matrix": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp]),
         "trals_mttsp": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp,
                                        ctypes.c_int, _vp]),
+        "trals_mttsp_path": (ctypes.c_int, [ctypes.c_int, _vp, _vp, ctypes.c_int, ctypes.c_int]),
         "trals_solve_chol": (ctypes.c_int, [_vp, ctypes.c_int, _i64, ctypes.c_int, _vp, _vp, _vp]),
         "trals_reconstruct": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int]),
         "trals_residual_explicit": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp,
@@ -306,6 +307,17 @@ def trals_mttsp(ctx: Context, I, R, X_dev, mode, cores_dev: Sequence, n: int, M_
     ctx.check(lib().trals_mttsp(ctx.handle, N, ctypes.addressof(Ia), ctypes.addressof(Ra), _ptr(X_dev), _xtype(X_dev),
                                 int(mode), _ptr_array([_ptr(c) for c in cores_dev]), int(n), _ptr(M_dev)),
               "trals_mttsp")
+
+
+MTTSP_PATHS = {0: "cuda-cores", 1: "tc-kmajor-left", 2: "tc-kmajor-right", 3: "tc-mnmajor"}
+
+
+def trals_mttsp_path(I, R, n: int, mode) -> int:
+    """Kernel the MTTSP of mode n uses in `mode` (0 = CUDA cores, 1-3 = tensor-core variants)."""
+    N, Ia, Ra = _shape(I, R)
+    if isinstance(mode, str):
+        mode = MODE_NAMES[mode]
+    return lib().trals_mttsp_path(N, ctypes.addressof(Ia), ctypes.addressof(Ra), int(n), int(mode))
 
 
 def trals_solve_chol(ctx: Context, Rn: int, In: int, Rn1: int, S_dev, M_dev, G_dev) -> None:

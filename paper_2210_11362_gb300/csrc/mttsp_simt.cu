@@ -109,7 +109,8 @@ __device__ __forceinline__ void gen_tile(const ModeLayout& L, const double* __re
 }
 
 template <typename XT>
-__global__ void __launch_bounds__(THREADS) mttsp_simt_kernel(const void* __restrict__ X, const double* __restrict__ ltab,
+__global__ void __launch_bounds__(THREADS) mttsp_simt_kernel(const void* __restrict__ X, const void* __restrict__ Xlo,
+                                                             const double* __restrict__ ltab,
                                                              const double* __restrict__ utab,
                                                              const int64_t* __restrict__ offL,
                                                              const int64_t* __restrict__ offU, ModeLayout L,
@@ -135,7 +136,12 @@ __global__ void __launch_bounds__(THREADS) mttsp_simt_kernel(const void* __restr
       const int64_t i = e % In;
       const int kk = (int)(e / In);
       const int64_t bo = base[kk];
-      Xs[i * KT + kk] = (bo >= 0) ? ld<XT>(X, bo + i * L.strideN) : 0.0;
+      double v = 0.0;
+      if (bo >= 0) {
+        v = ld<XT>(X, bo + i * L.strideN);
+        if (Xlo != nullptr) v += ld<XT>(Xlo, bo + i * L.strideN);   // split-BF16 pair: hi + lo
+      }
+      Xs[i * KT + kk] = v;
     }
     __syncthreads();
 #pragma unroll
@@ -255,11 +261,12 @@ void launch_mttsp_simt(const MttspSimtArgs& a, cudaStream_t s) {
   dim3 grid(a.gridX, (unsigned)((outN + OUTC - 1) / OUTC));
   const size_t smem = simt_smem(L);
   if (a.xt == TRALS_X_F64)
-    mttsp_simt_kernel<double><<<grid, THREADS, smem, s>>>(a.X, a.ltab, a.utab, a.offL, a.offU, L, a.partials);
+    mttsp_simt_kernel<double><<<grid, THREADS, smem, s>>>(a.X, nullptr, a.ltab, a.utab, a.offL, a.offU, L, a.partials);
   else if (a.xt == TRALS_X_F32)
-    mttsp_simt_kernel<float><<<grid, THREADS, smem, s>>>(a.X, a.ltab, a.utab, a.offL, a.offU, L, a.partials);
+    mttsp_simt_kernel<float><<<grid, THREADS, smem, s>>>(a.X, nullptr, a.ltab, a.utab, a.offL, a.offU, L, a.partials);
   else
-    mttsp_simt_kernel<__nv_bfloat16><<<grid, THREADS, smem, s>>>(a.X, a.ltab, a.utab, a.offL, a.offU, L, a.partials);
+    mttsp_simt_kernel<__nv_bfloat16><<<grid, THREADS, smem, s>>>(a.X, a.Xlo, a.ltab, a.utab, a.offL, a.offU, L,
+                                                                   a.partials);
   const int rg = (int)std::min<int64_t>((outN + 255) / 256, 152 * 8);
   reduce_partials_kernel<<<rg, 256, 0, s>>>(a.partials, a.gridX, outN, a.M);
 }

@@ -1,23 +1,827 @@
-// Tensor-core (tcgen05) MTTSP.  Not yet available: every shape reports unsupported and the sweep
-// driver uses the CUDA-core MTTSP.
+// Tensor-core MTTSP (Alg. 2 lines 7-8) for the BF16 mode on sm_103a: tcgen05.mma with TMEM
+// accumulators, operands staged by TMA (cp.async.bulk.tensor) into 128B-swizzled shared memory.
+//
+// The contraction M_n[i_n, a + R_n b] = sum_k X_[n][i_n, k] G^{!=n}(k)[b, a] runs in two stages so
+// that X is streamed from HBM exactly once and G^{!=n} is never formed:
+//   stage 1 (tensor cores):  T[row, w] = sum_{s in S} X(row, s) Tab[w, s]
+//       S is a block of modes that is contiguous both in memory and in the subchain order
+//       (eq. subchain_new); Tab(s) is the product of the cores of S (a table rebuilt per update),
+//       a "row" fixes i_n and every mode outside S.
+//   stage 2 (CUDA cores):    M[i_n(row), :] += F(row) applied to T[row, :]
+//       where F(row) is the product of the remaining cores (one small matrix per row, from a
+//       second table), on one side of T only (the other side is the identity).
+// Three tile geometries (chosen per mode on the host):
+//   KM-L : S = modes 0..n-1 (K-major X), F = G_{n+1}...G_N on the left   (n < N-1)
+//   KM-R : S = modes 0..s,    (K-major X), F = G_{s+1}...G_{N-1} on the right (n = N-1)
+//   MM   : S = modes n+1..m  (MN-major X), F = G_{m+1}...G_N G_1...G_{n-1} on the right
+// Rows of a tile map to distinct (i_n, factor) pairs; stage 2 reduces rows with equal i_n in a
+// fixed order into a per-CTA FP32 accumulator; CTA partials are summed in FP64 by a second kernel.
+#include <cuda.h>
+
+#include <algorithm>
+#include <cstdio>
+
 #include "mttsp_tc.cuh"
 
 namespace trals {
 
-int tc_plan(TcPlan& p, int, const int64_t*, const int32_t*, int, int, const void*, int64_t, cudaError_t* err) {
-  p.valid = false;
-  if (err) *err = cudaSuccess;
-  return 0;
+namespace {
+
+constexpr int kRows = 128;                    // MMA M (TMEM lanes)
+constexpr int kKT = 64;                       // K elements per stage (one 128-byte swizzle row of BF16)
+constexpr int kNS = 3;                        // pipeline stages
+constexpr int kThreads = 192;                 // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kABytes = kRows * 128;          // X tile: 128 rows x 128 B
+constexpr int kAtomBytes = 64 * 128;          // MN-major atom: 64 K rows x 128 B (64 MN elements)
+constexpr int kMaxW = 128;                    // stage-1 table width (MMA N) limit
+constexpr int kVxStride = 17;
+constexpr long long kSpinLimit = 4000000000LL;  // ~2 s at 2 GHz
+
+enum { KM_L = 0, KM_R = 1, MM = 2 };
+
+struct TcArgs {
+  int variant;
+  int ksteps, n_kc, kc_len;
+  int64_t n_units;
+  int In;
+  int nrep;          // KM: factor values per tile
+  int64_t n_fac;     // KM: factor entries along the tiled mode (K_post or K_mid)
+  int64_t P, K_pre, K_hi, pchunks;   // MM
+  int NX, NY, Sy, Rn, r, W_pad, ts_stride;
+  uint32_t tx_bytes;
+  uint32_t idesc;
+  const float* F;    // [fac][NX][16]
+  float* partials;   // [grid][In * r]
+  DevStatus* status;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-int tc_enqueue(TcPlan&, const void*, double* const*, double*, cudaStream_t) { return 0; }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false when the limit passes or another role raised the abort flag.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kSpinLimit) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, 128-byte swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;          // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;          // SWIZZLE_128B
+  return d;
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+__device__ __forceinline__ void raise_timeout(DevStatus* st, int where) {
+  if (st != nullptr && atomicCAS(&st->code, 0, (int)TRALS_E_TIMEOUT) == 0) {
+    st->sweep = -1;
+    st->mode = -2;
+    st->index = where;
+    st->value = 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    mttsp_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmT, const TcArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int bBytes = ((a.W_pad * 128) + 1023) & ~1023;
+  const int stageBytes = kABytes + bBytes;
+  float* T_s = reinterpret_cast<float*>(base + kNS * stageBytes);
+  float* Vx_s = T_s + kRows * a.ts_stride;
+  float* M_s = Vx_s + kRows * kVxStride;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(M_s + ((a.In * a.r + 1) & ~1));
+  uint64_t* full = bars;
+  uint64_t* empty = bars + kNS;
+  uint64_t* accf = bars + 2 * kNS;
+  uint64_t* acce = bars + 2 * kNS + 2;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * kNS + 4);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+  volatile int* epi_stop = reinterpret_cast<volatile int*>(tmem_holder + 2);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int E = a.In * a.r;
+
+  for (int e = threadIdx.x; e < E; e += blockDim.x) M_s[e] = 0.0f;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kNS; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 128);
+    }
+    *abort_flag = 0;
+    *epi_stop = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_holder))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      for (int64_t u = blockIdx.x; u < a.n_units && !*abort_flag; u += gridDim.x) {
+        const int64_t tile = u / a.n_kc;
+        const int kc = (int)(u % a.n_kc);
+        const int ks0 = kc * a.kc_len, ks1 = min(a.ksteps, ks0 + a.kc_len);
+        for (int ks = ks0; ks < ks1; ++ks) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
+            *abort_flag = 1;
+            raise_timeout(a.status, 1);
+            break;
+          }
+          uint8_t* A = base + stage * stageBytes;
+          uint8_t* B = A + kABytes;
+          mbar_expect_tx(&full[stage], a.tx_bytes);
+          const int k0 = ks * kKT;
+          if (a.variant == KM_L) {
+            tma_load_3d(A, &tmX, &full[stage], k0, 0, (int)(tile * a.nrep));
+          } else if (a.variant == KM_R) {
+            tma_load_3d(A, &tmX, &full[stage], k0, (int)(tile * a.nrep), 0);
+          } else {
+            for (int at = 0; at < 2; ++at) {
+              const int64_t aid = 2 * tile + at;
+              const int pc = (int)(aid % a.pchunks);
+              const int o = (int)(aid / a.pchunks);
+              tma_load_3d(A + at * kAtomBytes, &tmX, &full[stage], pc * 64, k0, o);
+            }
+          }
+          tma_load_2d(B, &tmT, &full[stage], k0, 0);
+          if (++stage == kNS) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int lu = 0;
+      for (int64_t u = blockIdx.x; u < a.n_units && !*abort_flag; u += gridDim.x, ++lu) {
+        const int kc = (int)(u % a.n_kc);
+        const int ks0 = kc * a.kc_len, ks1 = min(a.ksteps, ks0 + a.kc_len);
+        const int buf = lu & 1;
+        if (!mbar_wait(&acce[buf], (uint32_t)(((lu >> 1) & 1) ^ 1), abort_flag)) {
+          *abort_flag = 1;
+          raise_timeout(a.status, 2);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(buf * 256);
+        bool ok = true;
+        for (int ks = ks0; ks < ks1; ++ks) {
+          if (!mbar_wait(&full[stage], phase, abort_flag)) {
+            *abort_flag = 1;
+            raise_timeout(a.status, 3);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t A = smem_u32(base + stage * stageBytes);
+          const uint32_t B = A + kABytes;
+#pragma unroll
+          for (int j = 0; j < kKT / 16; ++j) {
+            const uint64_t ad = (a.variant == MM) ? sdesc(A + 2048u * j, kAtomBytes, 1024) : sdesc(A + 32u * j, 16, 1024);
+            const uint64_t bd = sdesc(B + 32u * j, 16, 1024);
+            umma_bf16(d, ad, bd, a.idesc, (ks > ks0 || j > 0) ? 1u : 0u);
+          }
+          umma_commit(&empty[stage]);
+          if (++stage == kNS) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        umma_commit(&accf[buf]);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue (stage 2)
+    const int q = warp & 3;            // TMEM lane quarter of this warp
+    const int row = 32 * q + lane;
+    const int et = threadIdx.x - 64;   // 0..127 among the epilogue threads
+    int lu = 0;
+    for (int64_t u = blockIdx.x; u < a.n_units; u += gridDim.x, ++lu) {
+      const int buf = lu & 1;
+      const bool got = mbar_wait(&accf[buf], (uint32_t)((lu >> 1) & 1), abort_flag);
+      if (!got) {
+        *abort_flag = 1;
+        *epi_stop = 1;
+        raise_timeout(a.status, 4);
+      }
+      // Uniform decision: epi_stop is written only before this barrier and read right after it;
+      // no epilogue thread can write it again before passing the next barrier of this iteration.
+      epi_bar();
+      if (*epi_stop) break;
+      tc_fence_after();
+      const int64_t tile = u / a.n_kc;
+      // row meta: validity and factor index
+      bool valid;
+      int64_t fi = 0;
+      if (a.variant == KM_L) {
+        const int rep = row / a.In, i = row % a.In;
+        const int64_t f = tile * a.nrep + rep;
+        valid = rep < a.nrep && f < a.n_fac;
+        fi = f;
+        (void)i;
+      } else if (a.variant == KM_R) {
+        const int rep = row % a.nrep, i = row / a.nrep;
+        const int64_t f = tile * a.nrep + rep;
+        valid = i < a.In && f < a.n_fac;
+        fi = f;
+      } else {
+        const int at = row / 64;
+        const int64_t aid = 2 * tile + at;
+        const int64_t pc = aid % a.pchunks, o = aid / a.pchunks;
+        const int64_t p = pc * 64 + (row % 64);
+        valid = o < a.K_hi && p < a.P;
+        fi = o + a.K_hi * (p % a.K_pre);
+      }
+      // copy this row's stage-1 result from TMEM to shared memory
+      const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * 256);
+      for (int c0 = 0; c0 < a.W_pad; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld32(taddr + (uint32_t)c0, v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (c0 + j < a.W_pad) T_s[row * a.ts_stride + c0 + j] = __uint_as_float(v[j]);
+      }
+      tc_fence_before();
+      mbar_arrive(&acce[buf]);
+      // stage 2: one factor row (x) at a time, then a fixed-order reduction over rows with equal i_n
+      for (int x = 0; x < a.NX; ++x) {
+        float f[16];
+        if (valid) {
+          const float4* fp = reinterpret_cast<const float4*>(a.F + ((size_t)fi * a.NX + x) * 16);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float4 t = __ldg(fp + j);
+            f[4 * j] = t.x;
+            f[4 * j + 1] = t.y;
+            f[4 * j + 2] = t.z;
+            f[4 * j + 3] = t.w;
+          }
+        }
+        for (int y = 0; y < a.NY; ++y) {
+          float acc = 0.0f;
+          if (valid) {
+            const float* tr = T_s + row * a.ts_stride + y * a.Sy;
+#pragma unroll
+            for (int d = 0; d < 16; ++d)
+              if (d < a.Sy) acc = fmaf(f[d], tr[d], acc);
+          }
+          Vx_s[row * kVxStride + y] = acc;
+        }
+        epi_bar();
+        if (a.variant == KM_L || a.variant == KM_R) {
+          const int cnt = a.In * a.NY;
+          for (int o = et; o < cnt; o += 128) {
+            const int i = o / a.NY, y = o % a.NY;
+            float s = 0.0f;
+            for (int rep = 0; rep < a.nrep; ++rep) {
+              const int rr = (a.variant == KM_L) ? (i + a.In * rep) : (rep + a.nrep * i);
+              s += Vx_s[rr * kVxStride + y];
+            }
+            const int e = (a.variant == KM_L) ? (y + a.Rn * x) : (x + a.Rn * y);
+            M_s[i * a.r + e] += s;
+          }
+        } else {
+          for (int at = 0; at < 2; ++at) {
+            const int64_t aid = 2 * tile + at;
+            const int64_t pc = aid % a.pchunks, o = aid / a.pchunks;
+            if (o < a.K_hi) {
+              const int64_t p_lo = pc * 64, p_hi = min(a.P, p_lo + 64);   // [p_lo, p_hi)
+              const int64_t i_lo = p_lo / a.K_pre, i_hi = (p_hi - 1) / a.K_pre;
+              const int cnt = (int)(i_hi - i_lo + 1) * a.NY;
+              for (int oo = et; oo < cnt; oo += 128) {
+                const int64_t i = i_lo + oo / a.NY;
+                const int y = oo % a.NY;
+                const int64_t r0 = max(p_lo, i * a.K_pre) - p_lo, r1 = min(p_hi, (i + 1) * a.K_pre) - p_lo;
+                float s = 0.0f;
+                for (int64_t rr = r0; rr < r1; ++rr) s += Vx_s[(at * 64 + (int)rr) * kVxStride + y];
+                M_s[i * a.r + (x + a.Rn * y)] += s;
+              }
+            }
+            if (at == 0) epi_bar();
+          }
+        }
+        epi_bar();
+      }
+    }
+    // write this CTA's partial (column-major I_n x r)
+    epi_bar();
+    if (!*abort_flag) {
+      float* out = a.partials + (size_t)blockIdx.x * E;
+      for (int e = et; e < E; e += 128) {
+        const int i = e % a.In, c = e / a.In;
+        out[e] = M_s[i * a.r + c];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+}
+
+// M[e] = sum_g partials[g * E + e] (FP64, fixed order)
+__global__ void tc_reduce_kernel(const float* __restrict__ partials, int G, int64_t E, double* __restrict__ M) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int g = 0; g < G; ++g) s += (double)partials[(int64_t)g * E + e];
+    M[e] = s;
+  }
+}
+
+// Stage-1 table: Tab[w * Kpad + k] = bf16(P_k[x + Ra y]) with w = x + Ra y (colmajor) or y + Rb x (rowmajor).
+__global__ void pack_tab_kernel(const double* __restrict__ src, int64_t K, int64_t Kpad, int Ra, int Rb, int rowmajor,
+                                int W_pad, __nv_bfloat16* __restrict__ dst) {
+  const int64_t total = (int64_t)W_pad * Kpad;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = e % Kpad;
+    const int w = (int)(e / Kpad);
+    float v = 0.0f;
+    if (k < K && w < Ra * Rb) {
+      const int x = rowmajor ? (w / Rb) : (w % Ra);
+      const int y = rowmajor ? (w % Rb) : (w / Ra);
+      v = (float)src[k * (int64_t)Ra * Rb + x + (int64_t)Ra * y];
+    }
+    dst[e] = __float2bfloat16_rn(v);
+  }
+}
+
+// Stage-2 factors: F[(f * NX + x) * 16 + z] = P_f[leftT ? (x + Ra z) : (z + Ra x)] for z < Sy, else 0.
+__global__ void pack_fac_kernel(const double* __restrict__ src, int64_t nf, int Ra, int Rb, int leftT, int NX, int Sy,
+                                float* __restrict__ dst) {
+  const int64_t total = nf * NX * 16;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int z = (int)(e % 16);
+    const int x = (int)((e / 16) % NX);
+    const int64_t f = e / (16 * NX);
+    float v = 0.0f;
+    if (z < Sy) v = (float)src[f * (int64_t)Ra * Rb + (leftT ? (x + (int64_t)Ra * z) : (z + (int64_t)Ra * x))];
+    dst[e] = v;
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+bool encode_bf16(CUtensorMap* m, const void* ptr, int rank, const uint64_t* dims, const uint64_t* strides_bytes,
+                 const uint32_t* box) {
+  EncodeTiledFn fn = get_encode();
+  if (!fn) return false;
+  cuuint64_t gd[5], gs[4];
+  cuuint32_t bd[5], es[5];
+  for (int i = 0; i < rank; ++i) {
+    gd[i] = dims[i];
+    bd[i] = box[i];
+    es[i] = 1;
+  }
+  for (int i = 0; i + 1 < rank; ++i) gs[i] = strides_bytes[i];
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(ptr), gd, gs, bd, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// Host-side plan of one mode.
+struct TcImpl {
+  TcArgs args{};
+  CUtensorMap tmX{}, tmT{};
+  int grid = 0;
+  size_t smem = 0;
+  // stage-1 table build: chain modes S (cyclic order), FP64 scratch, packed BF16 table
+  std::vector<int> s_modes, f_modes;
+  int tabRa = 0, tabRb = 0, tab_rowmajor = 0;
+  int64_t K_S = 0, Kpad = 0;
+  int facRa = 0, facRb = 0, fac_leftT = 0;
+  int64_t n_fac_total = 0;
+  double* chainA = nullptr;
+  double* chainB = nullptr;
+  __nv_bfloat16* tab = nullptr;
+  float* F = nullptr;
+  float* partials = nullptr;
+  int64_t E = 0;
+  const int64_t* I = nullptr;
+  int64_t Icopy[kMaxOrder];
+  int32_t Rcopy[kMaxOrder];
+  int N = 0;
+};
+
+int64_t prod_range(const int64_t* I, int lo, int hi) {  // prod I[lo..hi-1]
+  int64_t p = 1;
+  for (int j = lo; j < hi; ++j) p *= I[j];
+  return p;
+}
+
+// Level sizes of a chain build over consecutive cyclic modes `modes`; returns the largest level.
+int64_t chain_max_elems(const std::vector<int>& modes, const int64_t* I, const int32_t* R, int N) {
+  int64_t n = 1, mx = 0;
+  const int Ra = R[modes[0]];
+  for (int m : modes) {
+    n *= I[m];
+    mx = std::max<int64_t>(mx, n * Ra * R[(m + 1) % N]);
+  }
+  return mx;
+}
+
+// Build the chain table over `modes` into dst (ping-ponging with scr); returns the entry count.
+const double* build_chain(const std::vector<int>& modes, double* const* cores, const int64_t* I, const int32_t* R,
+                          int N, double* bufA, double* bufB, cudaStream_t s, int* launches) {
+  const double* prev = nullptr;
+  int64_t nPrev = 1;
+  const int Ra = R[modes[0]];
+  double* bufs[2] = {bufA, bufB};
+  int t = 0;
+  for (int m : modes) {
+    double* out = bufs[t++ % 2];
+    launch_chain_level(prev, nPrev, Ra, R[m], cores[m], I[m], R[(m + 1) % N], out, s);
+    ++*launches;
+    prev = out;
+    nPrev *= I[m];
+  }
+  return prev;
+}
+
+}  // namespace
+
+TcChoice tc_choose(int N, const int64_t* I, const int32_t* R, int n) {
+  TcChoice best;
+  int maxR = 0;
+  for (int j = 0; j < N; ++j) maxR = std::max(maxR, (int)R[j]);
+  const int Rn = R[n], Rn1 = R[(n + 1) % N];
+  const int r = Rn * Rn1;
+  const int64_t In = I[n];
+  if (maxR > 16 || r > 256 || In * r > 8192) return best;
+  auto consider = [&](TcChoice c, int W) {
+    if (c.K_S < 256 || W > kMaxW) return;
+    const int64_t tabBytes = c.K_S * (int64_t)((W + 15) / 16 * 16) * 2;
+    if (tabBytes > (int64_t)64 << 20) return;
+    c.cost = (c.variant == MM) ? tabBytes + tabBytes / 4 + 1 : tabBytes;   // prefer K-major X unless MN-major is clearly cheaper
+    if (best.variant < 0 || c.cost < best.cost) best = c;
+  };
+  // KM-L: S = modes 0..n-1 (needs post modes)
+  if (n >= 1 && n <= N - 2) {
+    TcChoice c;
+    c.variant = KM_L;
+    c.s_lo = 0;
+    c.s_hi = n - 1;
+    c.K_S = prod_range(I, 0, n);
+    if ((c.K_S * 2) % 16 == 0 && In <= kRows) consider(c, R[0] * Rn);
+  }
+  // KM-R: n = N-1, S = modes 0..s with s <= N-3
+  if (n == N - 1) {
+    for (int s = 0; s <= N - 3; ++s) {
+      TcChoice c;
+      c.variant = KM_R;
+      c.s_lo = 0;
+      c.s_hi = s;
+      c.K_S = prod_range(I, 0, s + 1);
+      if ((c.K_S * 2) % 16 == 0 && In <= kRows) consider(c, R[0] * R[s + 1]);
+    }
+  }
+  // MM: S = modes n+1..m, not the whole chain
+  {
+    const int64_t P = prod_range(I, 0, n + 1);
+    if ((P * 2) % 16 == 0) {
+      for (int m = n + 1; m <= N - 1; ++m) {
+        if (n == 0 && m == N - 1) continue;
+        TcChoice c;
+        c.variant = MM;
+        c.s_lo = n + 1;
+        c.s_hi = m;
+        c.K_S = prod_range(I, n + 1, m + 1);
+        consider(c, Rn1 * R[(m + 1) % N]);
+      }
+    }
+  }
+  return best;
+}
+
+int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mode, const void* X, int64_t numel,
+            cudaError_t* err) {
+  if (err) *err = cudaSuccess;
+  p.valid = false;
+  if (mode != TRALS_MODE_BF16) return 0;
+  if ((reinterpret_cast<uintptr_t>(X) & 15) != 0) return 0;
+  if (!get_encode()) return 0;
+  const int Rn = R[n], Rn1 = R[(n + 1) % N];
+  const int r = Rn * Rn1;
+  const int64_t In = I[n];
+
+  const TcChoice best = tc_choose(N, I, R, n);
+  if (best.variant < 0) return 0;
+
+  TcImpl* impl = new TcImpl();
+  impl->N = N;
+  for (int j = 0; j < N; ++j) {
+    impl->Icopy[j] = I[j];
+    impl->Rcopy[j] = R[j];
+  }
+  TcArgs& A = impl->args;
+  A.variant = best.variant;
+  A.In = (int)In;
+  A.Rn = Rn;
+  A.r = r;
+  impl->K_S = best.K_S;
+  impl->Kpad = (best.K_S + 7) / 8 * 8;
+  A.ksteps = (int)((best.K_S + kKT - 1) / kKT);
+  for (int m = best.s_lo; m <= best.s_hi; ++m) impl->s_modes.push_back(m);
+  impl->tabRa = R[best.s_lo];
+  impl->tabRb = R[(best.s_hi + 1) % N];
+  const int W = impl->tabRa * impl->tabRb;
+  A.W_pad = (W + 15) / 16 * 16;
+  A.ts_stride = A.W_pad + 1;
+  uint64_t dims[3], strides[2];
+  uint32_t box[3];
+  int64_t n_tiles = 0;
+  if (A.variant == KM_L) {
+    // T = c x a (colmajor), F = L = G_{n+1}..G_{N-1} (R_{n+1} x R_0) on the left
+    impl->tab_rowmajor = 0;
+    for (int m = n + 1; m <= N - 1; ++m) impl->f_modes.push_back(m);
+    impl->facRa = Rn1;
+    impl->facRb = R[0];
+    impl->fac_leftT = 1;
+    A.NX = Rn1;
+    A.NY = Rn;
+    A.Sy = R[0];
+    const int64_t K_post = prod_range(I, n + 1, N);
+    A.nrep = std::max<int>(1, (int)(kRows / In));
+    A.n_fac = K_post;
+    n_tiles = (K_post + A.nrep - 1) / A.nrep;
+    dims[0] = best.K_S; dims[1] = In; dims[2] = K_post;
+    strides[0] = best.K_S * 2; strides[1] = best.K_S * In * 2;
+    box[0] = kKT; box[1] = (uint32_t)In; box[2] = (uint32_t)A.nrep;
+    A.tx_bytes = (uint32_t)(kKT * 2 * In * A.nrep);
+  } else if (A.variant == KM_R) {
+    // T = b x d (rowmajor), F = Rm = G_{s+1}..G_{N-2} (R_{s+1} x R_n) on the right
+    impl->tab_rowmajor = 1;
+    for (int m = best.s_hi + 1; m <= N - 2; ++m) impl->f_modes.push_back(m);
+    impl->facRa = R[best.s_hi + 1];
+    impl->facRb = Rn;
+    impl->fac_leftT = 0;
+    A.NX = Rn;
+    A.NY = Rn1;
+    A.Sy = impl->tabRb;
+    const int64_t K_mid = prod_range(I, best.s_hi + 1, N - 1);
+    A.nrep = std::max<int>(1, (int)(kRows / In));
+    A.n_fac = K_mid;
+    n_tiles = (K_mid + A.nrep - 1) / A.nrep;
+    dims[0] = best.K_S; dims[1] = K_mid; dims[2] = In;
+    strides[0] = best.K_S * 2; strides[1] = best.K_S * K_mid * 2;
+    box[0] = kKT; box[1] = (uint32_t)A.nrep; box[2] = (uint32_t)In;
+    A.tx_bytes = (uint32_t)(kKT * 2 * In * A.nrep);
+  } else {
+    // T = b x d (rowmajor), F = Rm = G_{m+1}..G_{N-1} G_0..G_{n-1} (R_{m+1} x R_n) on the right
+    impl->tab_rowmajor = 1;
+    for (int m = best.s_hi + 1; m <= N - 1; ++m) impl->f_modes.push_back(m);
+    for (int m = 0; m <= n - 1; ++m) impl->f_modes.push_back(m);
+    impl->facRa = R[(best.s_hi + 1) % N];
+    impl->facRb = Rn;
+    impl->fac_leftT = 0;
+    A.NX = Rn;
+    A.NY = Rn1;
+    A.Sy = impl->tabRb;
+    A.P = prod_range(I, 0, n + 1);
+    A.K_pre = prod_range(I, 0, n);
+    A.K_hi = prod_range(I, best.s_hi + 1, N);
+    A.pchunks = (A.P + 63) / 64;
+    n_tiles = (A.pchunks * A.K_hi + 1) / 2;
+    dims[0] = A.P; dims[1] = best.K_S; dims[2] = A.K_hi;
+    strides[0] = A.P * 2; strides[1] = A.P * best.K_S * 2;
+    box[0] = 64; box[1] = kKT; box[2] = 1;
+    A.tx_bytes = (uint32_t)(2 * kAtomBytes);
+  }
+  A.tx_bytes += (uint32_t)(A.W_pad * 128);
+  // MMA instruction descriptor: D=F32, A=B=BF16, A major per variant, B K-major, N=W_pad, M=128
+  A.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((A.variant == MM ? 1u : 0u) << 15) |
+            ((uint32_t)(A.W_pad >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+
+  // units: split K so that the grid gets a few units per SM
+  int nsm = 152;
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int64_t want = 4LL * nsm;
+  int n_kc = (int)std::min<int64_t>(std::max<int64_t>(1, (want + n_tiles - 1) / n_tiles), std::max(1, A.ksteps / 4));
+  A.kc_len = (A.ksteps + n_kc - 1) / n_kc;
+  A.n_kc = (A.ksteps + A.kc_len - 1) / A.kc_len;
+  A.n_units = n_tiles * A.n_kc;
+  impl->grid = (int)std::min<int64_t>(A.n_units, nsm);
+  impl->E = In * r;
+
+  // ---- allocations
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](void** q, size_t bytes) {
+    if (e != cudaSuccess) return;
+    e = cudaMalloc(q, std::max<size_t>(bytes, 16));
+    if (e == cudaSuccess) p.allocs.push_back(*q);
+  };
+  const int64_t chainMax = std::max(chain_max_elems(impl->s_modes, I, R, N), chain_max_elems(impl->f_modes, I, R, N));
+  int64_t nfac = 1;
+  for (int m : impl->f_modes) nfac *= I[m];
+  impl->n_fac_total = nfac;
+  alloc(reinterpret_cast<void**>(&impl->chainA), chainMax * sizeof(double));
+  alloc(reinterpret_cast<void**>(&impl->chainB), chainMax * sizeof(double));
+  alloc(reinterpret_cast<void**>(&impl->tab), (size_t)A.W_pad * impl->Kpad * sizeof(__nv_bfloat16));
+  alloc(reinterpret_cast<void**>(&impl->F), (size_t)nfac * A.NX * 16 * sizeof(float));
+  alloc(reinterpret_cast<void**>(&impl->partials), (size_t)impl->grid * impl->E * sizeof(float));
+  if (e != cudaSuccess) {
+    if (err) *err = e;
+    delete impl;
+    for (void* q : p.allocs) cudaFree(q);
+    p.allocs.clear();
+    return 0;
+  }
+  A.F = impl->F;
+  A.partials = impl->partials;
+  // ---- tensor maps
+  bool ok = encode_bf16(&impl->tmX, X, 3, dims, strides, box);
+  {
+    uint64_t td[2] = {(uint64_t)impl->Kpad, (uint64_t)A.W_pad};
+    uint64_t ts[1] = {(uint64_t)impl->Kpad * 2};
+    uint32_t tb[2] = {kKT, (uint32_t)A.W_pad};
+    ok = ok && encode_bf16(&impl->tmT, impl->tab, 2, td, ts, tb);
+  }
+  if (!ok) {
+    delete impl;
+    for (void* q : p.allocs) cudaFree(q);
+    p.allocs.clear();
+    return 0;
+  }
+  const int bBytes = ((A.W_pad * 128) + 1023) & ~1023;
+  impl->smem = 1024 + (size_t)kNS * (kABytes + bBytes) + (size_t)kRows * A.ts_stride * 4 + (size_t)kRows * kVxStride * 4 +
+               (size_t)((impl->E + 1) & ~1) * 4 + (2 * kNS + 4) * 8 + 32;
+  if (impl->smem > 227 * 1024) {
+    delete impl;
+    for (void* q : p.allocs) cudaFree(q);
+    p.allocs.clear();
+    return 0;
+  }
+  p.impl = impl;
+  p.valid = true;
+  p.N = N;
+  p.n = n;
+  p.mode = mode;
+  (void)numel;
+  return 1;
+}
+
+int tc_enqueue(TcPlan& p, const void* X, double* const* cores, double* M, cudaStream_t s) {
+  TcImpl* impl = static_cast<TcImpl*>(p.impl);
+  (void)X;
+  int launches = 0;
+  const int64_t* I = impl->Icopy;
+  const int32_t* R = impl->Rcopy;
+  const int N = impl->N;
+  TcArgs A = impl->args;
+  // stage-1 table (Alg. 2 line 8's subchain factors over S) and stage-2 factors
+  const double* tsrc = build_chain(impl->s_modes, cores, I, R, N, impl->chainA, impl->chainB, s, &launches);
+  {
+    const int64_t total = (int64_t)A.W_pad * impl->Kpad;
+    const int g = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    pack_tab_kernel<<<g, 256, 0, s>>>(tsrc, impl->K_S, impl->Kpad, impl->tabRa, impl->tabRb, impl->tab_rowmajor,
+                                      A.W_pad, impl->tab);
+    ++launches;
+  }
+  const double* fsrc = build_chain(impl->f_modes, cores, I, R, N, impl->chainA, impl->chainB, s, &launches);
+  {
+    const int64_t total = impl->n_fac_total * A.NX * 16;
+    const int g = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    pack_fac_kernel<<<g, 256, 0, s>>>(fsrc, impl->n_fac_total, impl->facRa, impl->facRb, impl->fac_leftT, A.NX, A.Sy,
+                                      impl->F);
+    ++launches;
+  }
+  mttsp_tc_kernel<<<impl->grid, kThreads, impl->smem, s>>>(impl->tmX, impl->tmT, A);
+  ++launches;
+  {
+    const int g = (int)std::min<int64_t>((impl->E + 255) / 256, 152 * 4);
+    tc_reduce_kernel<<<g, 256, 0, s>>>(impl->partials, impl->grid, impl->E, M);
+    ++launches;
+  }
+  return launches;
+}
+
+void tc_set_status(TcPlan& p, DevStatus* st) {
+  if (p.impl) static_cast<TcImpl*>(p.impl)->args.status = st;
+}
 
 void tc_destroy(TcPlan& p) {
   for (void* q : p.allocs) cudaFree(q);
   p.allocs.clear();
+  delete static_cast<TcImpl*>(p.impl);
+  p.impl = nullptr;
   p.valid = false;
 }
 
-cudaError_t init_tc_attributes() { return cudaSuccess; }
+cudaError_t init_tc_attributes() {
+  return cudaFuncSetAttribute(mttsp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
 
 }  // namespace trals

@@ -13,6 +13,17 @@ struct TcPlan {
   void* impl = nullptr;
 };
 
+// Geometry the tensor-core MTTSP would use for mode n (host only; variant -1 = not supported):
+// 0 = K-major X with the factor on the left, 1 = K-major X with the factor on the right,
+// 2 = MN-major X.  S = modes [s_lo, s_hi] is contracted on the tensor cores.
+struct TcChoice {
+  int variant = -1;
+  int s_lo = 0, s_hi = 0;
+  int64_t K_S = 0;
+  int64_t cost = 0;
+};
+TcChoice tc_choose(int N, const int64_t* I, const int32_t* R, int n);
+
 // Prepare the tensor-core MTTSP of mode n for X (element type implied by `mode`).  Returns 1 when
 // the shape is supported (then tc_enqueue is used), 0 otherwise (the caller falls back to the
 // CUDA-core MTTSP).  *err is set on a CUDA failure.
@@ -21,6 +32,8 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
 // Enqueue M_n (FP64, I_n x R_n R_{n+1}) on stream s; returns the number of kernel launches.
 int tc_enqueue(TcPlan& p, const void* X, double* const* cores, double* M, cudaStream_t s);
 void tc_destroy(TcPlan& p);
+// Device status word the kernel reports a bounded-wait timeout into.
+void tc_set_status(TcPlan& p, DevStatus* st);
 cudaError_t init_tc_attributes();
 
 }  // namespace trals

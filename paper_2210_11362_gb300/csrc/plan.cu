@@ -106,6 +106,7 @@ struct trals_plan {
   const void* X = nullptr;        // caller's X (full precision source)
   int xt = 0;
   const void* Xk = nullptr;       // X as read by the MTTSP (caller's or an owned converted copy)
+  const void* Xk_lo = nullptr;    // BF16X3: lo half of the split pair
   int xk_t = 0;
   trals_opts opts{};
   int64_t numel = 0;
@@ -175,6 +176,7 @@ int enqueue_mttsp(trals_plan* p, int n, cudaStream_t s) {
   launches += L.N - 1;
   MttspSimtArgs a;
   a.X = p->Xk;
+  a.Xlo = p->Xk_lo;
   a.xt = p->xk_t;
   a.ltab = p->ltab;
   a.utab = p->utab;
@@ -385,7 +387,8 @@ trals_status trals_plan_create(trals_ctx* ctx, int N, const int64_t* I, const in
     PLAN_TRY(p->alloc(&q, (size_t)p->numel * 2));
     launch_quantize(X_dev, xt, p->numel, q, q + p->numel, s);
     p->Xk = q;
-    p->xk_t = TRALS_X_BF16;   // hi half; the SIMT path reads only hi (lo is used by the tensor-core path)
+    p->Xk_lo = q + p->numel;
+    p->xk_t = TRALS_X_BF16;
   } else if (o.mode == TRALS_MODE_FP32 && xt == TRALS_X_F64) {
     float* q = nullptr;
     PLAN_TRY(p->alloc(&q, (size_t)p->numel));
@@ -404,6 +407,7 @@ trals_status trals_plan_create(trals_ctx* ctx, int N, const int64_t* I, const in
       const int ok = tc_plan(p->tc[n], N, I, R, n, o.mode, p->Xk, p->numel, &e);
       if (e != cudaSuccess) PLAN_TRY(e);
       p->use_tc[n] = ok != 0;
+      if (ok) tc_set_status(p->tc[n], ctx->d_status);
     }
   }
   PLAN_TRY(cudaStreamSynchronize(s));
@@ -594,6 +598,7 @@ trals_status trals_mttsp(trals_ctx* ctx, int N, const int64_t* I, const int32_t*
   const int use_tc = (mode != TRALS_MODE_FP64) ? tc_plan(tc, N, I, R, n, mode, X_dev, numel, &e) : 0;
   TRALS_CUDA_TRY(ctx, e);
   if (use_tc) {
+    tc_set_status(tc, ctx->d_status);
     tc_enqueue(tc, X_dev, const_cast<double* const*>(cores_dev), M_dev, s);
     e = cudaStreamSynchronize(s);
     tc_destroy(tc);
@@ -620,6 +625,7 @@ trals_status trals_mttsp(trals_ctx* ctx, int N, const int64_t* I, const int32_t*
     build_tables(L, cores_dev, I, R, lt, ut, sc, s);
     MttspSimtArgs a;
     a.X = X_dev;
+    a.Xlo = (mode == TRALS_MODE_BF16X3) ? static_cast<const __nv_bfloat16*>(X_dev) + numel : nullptr;
     a.xt = xt;
     a.ltab = lt;
     a.utab = ut;
@@ -641,6 +647,13 @@ trals_status trals_mttsp(trals_ctx* ctx, int N, const int64_t* I, const int32_t*
   cudaFree(dU);
   TRALS_CUDA_TRY(ctx, e);
   return TRALS_OK;
+}
+
+int trals_mttsp_path(int N, const int64_t* I, const int32_t* R, int n, int mode) {
+  if (N < 3 || N > TRALS_MAX_ORDER || !I || !R || n < 0 || n >= N) return -1;
+  if (mode != TRALS_MODE_BF16) return 0;
+  const TcChoice c = tc_choose(N, I, R, n);
+  return c.variant < 0 ? 0 : c.variant + 1;
 }
 
 trals_status trals_solve_chol(trals_ctx* ctx, int Rn, int64_t In, int Rn1, const double* S_dev, const double* M_dev,

@@ -65,6 +65,7 @@ int64_t table_level_max_elems(const ModeLayout& L, const int64_t* I, const int32
 // MTTSP on CUDA cores (any X type): partial sums per block then a fixed-order reduction.
 struct MttspSimtArgs {
   const void* X;
+  const void* Xlo = nullptr;   // BF16 X only: the lo half of a split-BF16 pair (NULL: none)
   int xt;               // trals_xtype (F64, F32, BF16)
   const double* ltab;
   const double* utab;

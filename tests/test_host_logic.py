@@ -1,0 +1,31 @@
+"""Host-side logic that needs no GPU: the MTTSP kernel choice per mode and argument checks."""
+import pytest
+
+import paper_2210_11362_gb300 as P
+
+
+def test_mttsp_path_choice_40x5():
+    I, R = (40,) * 5, (8, 10, 12, 10, 8)
+    paths = [P.trals_mttsp_path(I, R, n, "bf16") for n in range(5)]
+    # every mode of the 40^5 workload runs on tensor cores; modes 0-1 need the MN-major tile
+    assert paths == [3, 3, 1, 1, 2]
+
+
+def test_mttsp_path_choice_fp64_is_cuda_cores():
+    I, R = (40,) * 5, (8, 10, 12, 10, 8)
+    assert all(P.trals_mttsp_path(I, R, n, "fp64") == 0 for n in range(5))
+
+
+def test_mttsp_path_falls_back_when_unaligned_or_too_large():
+    # 60^4: mode 0's 120-byte BF16 rows cannot be described to TMA -> CUDA cores
+    assert P.trals_mttsp_path((60,) * 4, (10,) * 4, 0, "bf16") == 0
+    assert all(P.trals_mttsp_path((60,) * 4, (10,) * 4, n, "bf16") > 0 for n in (1, 2, 3))
+    # rank-16 cores: stage-1 table wider than the 128-column accumulator -> CUDA cores
+    assert all(P.trals_mttsp_path((256, 256, 3, 256), (16,) * 4, n, "bf16") == 0 for n in range(4))
+    # tiny tensors: contraction too short for a tensor-core tile
+    assert all(P.trals_mttsp_path((20, 20, 20), (3, 3, 3), n, "bf16") == 0 for n in range(3))
+
+
+def test_mttsp_path_rejects_bad_arguments():
+    assert P.trals_mttsp_path((4, 4), (2, 2), 0, "bf16") < 0
+    assert P.trals_mttsp_path((4, 4, 4), (2, 2, 2), 3, "bf16") < 0
