@@ -29,12 +29,12 @@ namespace {
 
 constexpr int kRows = 128;                    // MMA M (TMEM lanes)
 constexpr int kKT = 64;                       // K elements per stage (one 128-byte swizzle row of BF16)
-constexpr int kNS = 3;                        // pipeline stages
+constexpr int kNSMax = 6;                     // pipeline stages (upper bound; the host picks what fits)
 constexpr int kThreads = 192;                 // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr int kABytes = kRows * 128;          // X tile: 128 rows x 128 B
 constexpr int kAtomBytes = 64 * 128;          // MN-major atom: 64 K rows x 128 B (64 MN elements)
 constexpr int kMaxW = 128;                    // stage-1 table width (MMA N) limit
-constexpr int kVxStride = 17;
+constexpr int kSmemBudget = 227 * 1024;
 constexpr long long kSpinLimit = 4000000000LL;  // ~2 s at 2 GHz
 
 enum { KM_L = 0, KM_R = 1, MM = 2 };
@@ -47,10 +47,11 @@ struct TcArgs {
   int nrep;          // KM: factor values per tile
   int64_t n_fac;     // KM: factor entries along the tiled mode (K_post or K_mid)
   int64_t P, K_pre, K_hi, pchunks;   // MM
-  int NX, NY, Sy, Rn, r, W_pad, ts_stride;
+  int64_t opairs;                    // MM: ceil(K_hi / 2) o-pairs per p-chunk
+  int NX, NY, Sy, Rn, r, W_pad, fs_stride, ms_stride, ns;
   uint32_t tx_bytes;
   uint32_t idesc;
-  const float* F;    // [fac][NX][16]
+  const float* F;    // [fac][NX][SYP]
   float* partials;   // [grid][In * r]
   DevStatus* status;
 };
@@ -140,6 +141,29 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
       : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Unit u of this CTA (u counts this CTA's own units).  K-major tiles: a static round robin over all
+// units.  MN-major tiles: CTA c keeps one p-chunk (pc = c % pchunks) for its whole life so that each
+// lane's i_n never changes; the CTAs sharing a p-chunk split its (o-pair, K-chunk) units.
+struct UnitSched {
+  int64_t first, step, count;   // unit ids first + j*step, j < count (K-major); j-th unit of the chunk (MN-major)
+};
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
@@ -152,30 +176,65 @@ __device__ __forceinline__ void raise_timeout(DevStatus* st, int where) {
   }
 }
 
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// The j-th unit of this CTA: K-major tiles take units blockIdx.x + j * gridDim.x of all (tile, K-chunk)
+// units; MN-major tiles pin the CTA to p-chunk pc = blockIdx.x % pchunks and take every G-th of that
+// chunk's (o-pair, K-chunk) units, so each lane keeps the same rows (hence the same i_n) throughout.
+__device__ __forceinline__ bool get_unit(const TcArgs& a, int64_t j, int64_t& tile, int64_t& op, int64_t& pc,
+                                         int& kc) {
+  if (a.variant != MM) {
+    const int64_t u = blockIdx.x + j * (int64_t)gridDim.x;
+    if (u >= a.n_units) return false;
+    tile = u / a.n_kc;
+    kc = (int)(u % a.n_kc);
+    op = 0;
+    pc = 0;
+    return true;
+  }
+  pc = blockIdx.x % a.pchunks;
+  const int64_t g = blockIdx.x / a.pchunks;
+  const int64_t G = (gridDim.x - pc + a.pchunks - 1) / a.pchunks;   // CTAs sharing this p-chunk
+  const int64_t w = g + j * G;
+  if (w >= a.opairs * a.n_kc) return false;
+  op = w / a.n_kc;
+  kc = (int)(w % a.n_kc);
+  tile = 0;
+  return true;
+}
+
+// SYP: the stage-2 dot length (inner subchain rank padded to a multiple of 4); the stage-1 result of a
+// row is T[y * SYP + z] (y < NY, z < SYP) and is held in registers.
+template <int SYP>
 __global__ void __launch_bounds__(kThreads, 1)
     mttsp_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmT, const TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int bBytes = ((a.W_pad * 128) + 1023) & ~1023;
   const int stageBytes = kABytes + bBytes;
-  float* T_s = reinterpret_cast<float*>(base + kNS * stageBytes);
-  float* Vx_s = T_s + kRows * a.ts_stride;
-  float* M_s = Vx_s + kRows * kVxStride;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(M_s + ((a.In * a.r + 1) & ~1));
+  const int NS = a.ns;
+  float* F_s = reinterpret_cast<float*>(base + NS * stageBytes);     // per row: its stage-2 factor block
+  float* M_s = F_s + kRows * a.fs_stride;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(M_s + ((a.In * a.ms_stride + 1) & ~1));
   uint64_t* full = bars;
-  uint64_t* empty = bars + kNS;
-  uint64_t* accf = bars + 2 * kNS;
-  uint64_t* acce = bars + 2 * kNS + 2;
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * kNS + 4);
+  uint64_t* empty = bars + kNSMax;
+  uint64_t* accf = bars + 2 * kNSMax;
+  uint64_t* acce = bars + 2 * kNSMax + 2;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * kNSMax + 4);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
   volatile int* epi_stop = reinterpret_cast<volatile int*>(tmem_holder + 2);
+  volatile int* epi_stop_any = abort_flag;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int E = a.In * a.r;
 
-  for (int e = threadIdx.x; e < E; e += blockDim.x) M_s[e] = 0.0f;
+  for (int e = threadIdx.x; e < a.In * a.ms_stride; e += blockDim.x) M_s[e] = 0.0f;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kNS; ++s) {
+    for (int s = 0; s < NS; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -184,7 +243,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&acce[b], 128);
     }
     *abort_flag = 0;
-    *epi_stop = 0;
+    epi_stop[0] = 0;
+    epi_stop[1] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -202,9 +262,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      for (int64_t u = blockIdx.x; u < a.n_units && !*abort_flag; u += gridDim.x) {
-        const int64_t tile = u / a.n_kc;
-        const int kc = (int)(u % a.n_kc);
+      int64_t tile, op, pc;
+      int kc;
+      for (int64_t j = 0; get_unit(a, j, tile, op, pc, kc) && !*abort_flag; ++j) {
         const int ks0 = kc * a.kc_len, ks1 = min(a.ksteps, ks0 + a.kc_len);
         for (int ks = ks0; ks < ks1; ++ks) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
@@ -221,15 +281,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           } else if (a.variant == KM_R) {
             tma_load_3d(A, &tmX, &full[stage], k0, (int)(tile * a.nrep), 0);
           } else {
-            for (int at = 0; at < 2; ++at) {
-              const int64_t aid = 2 * tile + at;
-              const int pc = (int)(aid % a.pchunks);
-              const int o = (int)(aid / a.pchunks);
-              tma_load_3d(A + at * kAtomBytes, &tmX, &full[stage], pc * 64, k0, o);
-            }
+            for (int at = 0; at < 2; ++at)
+              tma_load_3d(A + at * kAtomBytes, &tmX, &full[stage], (int)(pc * 64), k0, (int)(2 * op + at));
           }
           tma_load_2d(B, &tmT, &full[stage], k0, 0);
-          if (++stage == kNS) {
+          if (++stage == NS) {
             stage = 0;
             phase ^= 1u;
           }
@@ -242,18 +298,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      int lu = 0;
-      for (int64_t u = blockIdx.x; u < a.n_units && !*abort_flag; u += gridDim.x, ++lu) {
-        const int kc = (int)(u % a.n_kc);
+      int64_t tile, op, pc;
+      int kc;
+      for (int64_t j = 0; get_unit(a, j, tile, op, pc, kc) && !*abort_flag; ++j) {
         const int ks0 = kc * a.kc_len, ks1 = min(a.ksteps, ks0 + a.kc_len);
-        const int buf = lu & 1;
-        if (!mbar_wait(&acce[buf], (uint32_t)(((lu >> 1) & 1) ^ 1), abort_flag)) {
+        const int buf = (int)(j & 1);
+        if (!mbar_wait(&acce[buf], (uint32_t)(((j >> 1) & 1) ^ 1), abort_flag)) {
           *abort_flag = 1;
           raise_timeout(a.status, 2);
           break;
         }
         tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)(buf * 256);
+        const uint32_t d = tmem + (uint32_t)(buf * 128);
         bool ok = true;
         for (int ks = ks0; ks < ks1; ++ks) {
           if (!mbar_wait(&full[stage], phase, abort_flag)) {
@@ -266,13 +322,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t A = smem_u32(base + stage * stageBytes);
           const uint32_t B = A + kABytes;
 #pragma unroll
-          for (int j = 0; j < kKT / 16; ++j) {
-            const uint64_t ad = (a.variant == MM) ? sdesc(A + 2048u * j, kAtomBytes, 1024) : sdesc(A + 32u * j, 16, 1024);
-            const uint64_t bd = sdesc(B + 32u * j, 16, 1024);
-            umma_bf16(d, ad, bd, a.idesc, (ks > ks0 || j > 0) ? 1u : 0u);
+          for (int jj = 0; jj < kKT / 16; ++jj) {
+            const uint64_t ad =
+                (a.variant == MM) ? sdesc(A + 2048u * jj, kAtomBytes, 1024) : sdesc(A + 32u * jj, 16, 1024);
+            const uint64_t bd = sdesc(B + 32u * jj, 16, 1024);
+            umma_bf16(d, ad, bd, a.idesc, (ks > ks0 || jj > 0) ? 1u : 0u);
           }
           umma_commit(&empty[stage]);
-          if (++stage == kNS) {
+          if (++stage == NS) {
             stage = 0;
             phase ^= 1u;
           }
@@ -287,122 +344,166 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = warp & 3;            // TMEM lane quarter of this warp
     const int row = 32 * q + lane;
     const int et = threadIdx.x - 64;   // 0..127 among the epilogue threads
-    int lu = 0;
-    for (int64_t u = blockIdx.x; u < a.n_units; u += gridDim.x, ++lu) {
-      const int buf = lu & 1;
-      const bool got = mbar_wait(&accf[buf], (uint32_t)((lu >> 1) & 1), abort_flag);
+    const int fblk = a.NX * SYP;       // floats per factor block
+    float* myF = F_s + row * a.fs_stride;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
+    const uint32_t vacc = lane_base + 256u;   // this lane's running V[x][y] at column 256 + 16 x + y
+    // Fixed row geometry: the i_n of this lane never changes (see get_unit).
+    bool lane_ok;
+    int my_i, rep = 0;
+    int64_t k_pre = 0;
+    int at = 0;
+    if (a.variant == KM_L) {
+      rep = row / a.In;
+      my_i = row % a.In;
+      lane_ok = rep < a.nrep;
+    } else if (a.variant == KM_R) {
+      rep = row % a.nrep;
+      my_i = row / a.nrep;
+      lane_ok = my_i < a.In;
+    } else {
+      at = row / 64;
+      const int64_t pc0 = blockIdx.x % a.pchunks;
+      const int64_t p = pc0 * 64 + (row % 64);
+      lane_ok = p < a.P;
+      my_i = lane_ok ? (int)(p / a.K_pre) : 0;
+      k_pre = p % a.K_pre;
+    }
+    {
+      uint32_t z[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) z[j] = 0u;
+      for (int x = 0; x < a.NX; ++x) tmem_st16(vacc + 16u * x, z);
+      tmem_wait_st();
+    }
+    int64_t tile, op, pc;
+    int kc;
+    for (int64_t j = 0; get_unit(a, j, tile, op, pc, kc); ++j) {
+      const int buf = (int)(j & 1);
+      bool valid;
+      int64_t fi;
+      if (a.variant == MM) {
+        const int64_t o = 2 * op + at;
+        valid = lane_ok && o < a.K_hi;
+        fi = o + a.K_hi * k_pre;
+      } else {
+        fi = tile * a.nrep + rep;
+        valid = lane_ok && fi < a.n_fac;
+      }
+      // prefetch this row's factor block into shared memory while the MMAs run
+      if (valid) {
+        const float* src = a.F + (size_t)fi * fblk;
+        for (int c = 0; c < fblk; c += 4) cp_async16(myF + c, src + c);
+      }
+      cp_async_commit();
+      const bool got = mbar_wait(&accf[buf], (uint32_t)((j >> 1) & 1), abort_flag);
       if (!got) {
         *abort_flag = 1;
-        *epi_stop = 1;
+        epi_stop[j & 1] = 1;
         raise_timeout(a.status, 4);
       }
-      // Uniform decision: epi_stop is written only before this barrier and read right after it;
-      // no epilogue thread can write it again before passing the next barrier of this iteration.
+      // Uniform decision: slot (j & 1) is written only before this unit's barrier and read right after
+      // it; the next write to the same slot comes two units later, after every thread has passed the
+      // following unit's barrier, i.e. after every thread has read this slot.
       epi_bar();
-      if (*epi_stop) break;
-      tc_fence_after();
-      const int64_t tile = u / a.n_kc;
-      // row meta: validity and factor index
-      bool valid;
-      int64_t fi = 0;
-      if (a.variant == KM_L) {
-        const int rep = row / a.In, i = row % a.In;
-        const int64_t f = tile * a.nrep + rep;
-        valid = rep < a.nrep && f < a.n_fac;
-        fi = f;
-        (void)i;
-      } else if (a.variant == KM_R) {
-        const int rep = row % a.nrep, i = row / a.nrep;
-        const int64_t f = tile * a.nrep + rep;
-        valid = i < a.In && f < a.n_fac;
-        fi = f;
-      } else {
-        const int at = row / 64;
-        const int64_t aid = 2 * tile + at;
-        const int64_t pc = aid % a.pchunks, o = aid / a.pchunks;
-        const int64_t p = pc * 64 + (row % 64);
-        valid = o < a.K_hi && p < a.P;
-        fi = o + a.K_hi * (p % a.K_pre);
+      if (epi_stop[j & 1]) {
+        cp_async_wait_all();
+        break;
       }
-      // copy this row's stage-1 result from TMEM to shared memory
-      const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * 256);
-      for (int c0 = 0; c0 < a.W_pad; c0 += 32) {
-        uint32_t v[32];
-        tmem_ld32(taddr + (uint32_t)c0, v);
-        tmem_wait_ld();
+      tc_fence_after();
+      // this row's stage-1 result: TMEM -> registers
+      float T[128];
+      const uint32_t taddr = lane_base + (uint32_t)(buf * 128);
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (c0 + j < a.W_pad) T_s[row * a.ts_stride + c0 + j] = __uint_as_float(v[j]);
+      for (int c0 = 0; c0 < 128; c0 += 32) {
+        if (c0 < a.W_pad) {
+          uint32_t v[32];
+          tmem_ld32(taddr + (uint32_t)c0, v);
+          tmem_wait_ld();
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) T[c0 + jj] = __uint_as_float(v[jj]);
+        }
       }
       tc_fence_before();
       mbar_arrive(&acce[buf]);
-      // stage 2: one factor row (x) at a time, then a fixed-order reduction over rows with equal i_n
+      cp_async_wait_all();
+      // stage 2: V[x][y] += f_x . T[y]  (independent accumulators over y), kept per lane in TMEM
+      constexpr int YMAX = (128 / SYP) < 16 ? (128 / SYP) : 16;
       for (int x = 0; x < a.NX; ++x) {
-        float f[16];
+        float f[SYP];
+#pragma unroll
+        for (int jj = 0; jj < SYP / 4; ++jj) {
+          float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (valid) t = *reinterpret_cast<const float4*>(myF + x * SYP + 4 * jj);
+          f[4 * jj] = t.x;
+          f[4 * jj + 1] = t.y;
+          f[4 * jj + 2] = t.z;
+          f[4 * jj + 3] = t.w;
+        }
+        uint32_t v[16];
+        tmem_ld16(vacc + 16u * x, v);
+        float acc[YMAX];
+#pragma unroll
+        for (int y = 0; y < YMAX; ++y) acc[y] = 0.0f;
         if (valid) {
-          const float4* fp = reinterpret_cast<const float4*>(a.F + ((size_t)fi * a.NX + x) * 16);
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const float4 t = __ldg(fp + j);
-            f[4 * j] = t.x;
-            f[4 * j + 1] = t.y;
-            f[4 * j + 2] = t.z;
-            f[4 * j + 3] = t.w;
+          for (int z = 0; z < SYP; ++z) {
+#pragma unroll
+            for (int y = 0; y < YMAX; ++y) acc[y] = fmaf(f[z], T[y * SYP + z], acc[y]);
           }
         }
-        for (int y = 0; y < a.NY; ++y) {
-          float acc = 0.0f;
-          if (valid) {
-            const float* tr = T_s + row * a.ts_stride + y * a.Sy;
+        tmem_wait_ld();
 #pragma unroll
-            for (int d = 0; d < 16; ++d)
-              if (d < a.Sy) acc = fmaf(f[d], tr[d], acc);
-          }
-          Vx_s[row * kVxStride + y] = acc;
-        }
-        epi_bar();
-        if (a.variant == KM_L || a.variant == KM_R) {
-          const int cnt = a.In * a.NY;
-          for (int o = et; o < cnt; o += 128) {
-            const int i = o / a.NY, y = o % a.NY;
-            float s = 0.0f;
-            for (int rep = 0; rep < a.nrep; ++rep) {
-              const int rr = (a.variant == KM_L) ? (i + a.In * rep) : (rep + a.nrep * i);
-              s += Vx_s[rr * kVxStride + y];
-            }
-            const int e = (a.variant == KM_L) ? (y + a.Rn * x) : (x + a.Rn * y);
-            M_s[i * a.r + e] += s;
-          }
-        } else {
-          for (int at = 0; at < 2; ++at) {
-            const int64_t aid = 2 * tile + at;
-            const int64_t pc = aid % a.pchunks, o = aid / a.pchunks;
-            if (o < a.K_hi) {
-              const int64_t p_lo = pc * 64, p_hi = min(a.P, p_lo + 64);   // [p_lo, p_hi)
-              const int64_t i_lo = p_lo / a.K_pre, i_hi = (p_hi - 1) / a.K_pre;
-              const int cnt = (int)(i_hi - i_lo + 1) * a.NY;
-              for (int oo = et; oo < cnt; oo += 128) {
-                const int64_t i = i_lo + oo / a.NY;
-                const int y = oo % a.NY;
-                const int64_t r0 = max(p_lo, i * a.K_pre) - p_lo, r1 = min(p_hi, (i + 1) * a.K_pre) - p_lo;
-                float s = 0.0f;
-                for (int64_t rr = r0; rr < r1; ++rr) s += Vx_s[(at * 64 + (int)rr) * kVxStride + y];
-                M_s[i * a.r + (x + a.Rn * y)] += s;
+        for (int y = 0; y < YMAX; ++y) v[y] = __float_as_uint(__uint_as_float(v[y]) + acc[y]);
+        tmem_st16(vacc + 16u * x, v);
+      }
+      tmem_wait_st();
+    }
+    // Combine the lanes' running sums into the CTA accumulator: one warp at a time (no write races),
+    // lanes sharing i_n inside a warp pre-summed by a segmented shuffle (runs are contiguous).
+    const bool seg = (a.variant == KM_R) || (a.variant == MM && a.K_pre > 1);
+    const int key = lane_ok ? my_i : -1 - lane;
+    const int prev_key = __shfl_up_sync(0xffffffffu, key, 1);
+    const bool head = !seg || lane == 0 || prev_key != key;
+    int nbr_key[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) nbr_key[k] = __shfl_down_sync(0xffffffffu, key, 1 << k);
+    for (int ph = 0; ph < 4; ++ph) {
+      if (ph == warp - 2 && !*epi_stop_any) {
+        for (int x = 0; x < a.NX; ++x) {
+          uint32_t v[16];
+          tmem_ld16(vacc + 16u * x, v);
+          tmem_wait_ld();
+          float val[16];
+#pragma unroll
+          for (int y = 0; y < 16; ++y) val[y] = __uint_as_float(v[y]);
+          if (seg) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+              const bool take = (lane + (1 << k) < 32) && (nbr_key[k] == key);
+#pragma unroll
+              for (int y = 0; y < 16; ++y) {
+                const float o = __shfl_down_sync(0xffffffffu, val[y], 1 << k);
+                if (take) val[y] += o;
               }
             }
-            if (at == 0) epi_bar();
+          }
+          if (lane_ok && head) {
+            float* dst = M_s + my_i * a.ms_stride;
+#pragma unroll
+            for (int y = 0; y < 16; ++y)
+              if (y < a.NY) dst[a.variant == KM_L ? (y + a.Rn * x) : (x + a.Rn * y)] += val[y];
           }
         }
-        epi_bar();
       }
+      epi_bar();
     }
     // write this CTA's partial (column-major I_n x r)
-    epi_bar();
     if (!*abort_flag) {
       float* out = a.partials + (size_t)blockIdx.x * E;
       for (int e = et; e < E; e += 128) {
         const int i = e % a.In, c = e / a.In;
-        out[e] = M_s[i * a.r + c];
+        out[e] = M_s[i * a.ms_stride + c];
       }
     }
   }
@@ -412,43 +513,75 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
 }
 
-// M[e] = sum_g partials[g * E + e] (FP64, fixed order)
+// M[e] = sum_g partials[g * E + e] in FP64: a block takes 32 consecutive e; warp w sums g = w, w+8, ...
+// (coalesced 128-byte rows), then the 8 warp sums are added in a fixed order.
 __global__ void tc_reduce_kernel(const float* __restrict__ partials, int G, int64_t E, double* __restrict__ M) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int g = 0; g < G; ++g) s += (double)partials[(int64_t)g * E + e];
-    M[e] = s;
+  __shared__ double red[8][32];
+  const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+  const int64_t e = blockIdx.x * 32LL + lane;
+  double s = 0.0;
+  if (e < E)
+    for (int g = w; g < G; g += 8) s += (double)partials[(int64_t)g * E + e];
+  red[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && e < E) {
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += red[k][lane];
+    M[e] = t;
   }
 }
 
-// Stage-1 table: Tab[w * Kpad + k] = bf16(P_k[x + Ra y]) with w = x + Ra y (colmajor) or y + Rb x (rowmajor).
-__global__ void pack_tab_kernel(const double* __restrict__ src, int64_t K, int64_t Kpad, int Ra, int Rb, int rowmajor,
-                                int W_pad, __nv_bfloat16* __restrict__ dst) {
+// Stage-1 table: Tab[w * Kpad + k] = bf16(P_k[...]) with w = z + SYP y (z: inner/dot index, y: outer):
+// kindL (factor on the left): P = c x a (Ra = Sy rows), value P[z + Ra y]; otherwise P = b x d
+// (Ra = NY rows), value P[y + Ra z].  Zero for z >= Sy, y >= NY or k >= K.
+__global__ void pack_tab_kernel(const float* __restrict__ src, int64_t K, int64_t Kpad, int Ra, int Rb, int kindL,
+                                int Sy, int SYP, int NY, int W_pad, __nv_bfloat16* __restrict__ dst) {
   const int64_t total = (int64_t)W_pad * Kpad;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = e % Kpad;
     const int w = (int)(e / Kpad);
+    const int z = w % SYP, y = w / SYP;
     float v = 0.0f;
-    if (k < K && w < Ra * Rb) {
-      const int x = rowmajor ? (w / Rb) : (w % Ra);
-      const int y = rowmajor ? (w % Rb) : (w / Ra);
-      v = (float)src[k * (int64_t)Ra * Rb + x + (int64_t)Ra * y];
-    }
+    if (k < K && z < Sy && y < NY) v = src[k * (int64_t)Ra * Rb + (kindL ? (z + (int64_t)Ra * y) : (y + (int64_t)Ra * z))];
     dst[e] = __float2bfloat16_rn(v);
   }
 }
 
-// Stage-2 factors: F[(f * NX + x) * 16 + z] = P_f[leftT ? (x + Ra z) : (z + Ra x)] for z < Sy, else 0.
-__global__ void pack_fac_kernel(const double* __restrict__ src, int64_t nf, int Ra, int Rb, int leftT, int NX, int Sy,
-                                float* __restrict__ dst) {
-  const int64_t total = nf * NX * 16;
+// Stage-2 factors: F[(f * NX + x) * SYP + z] = kindL ? P_f[x + Ra z] (L[b=x][c=z]) : P_f[z + Ra x] (Rm[d=z][a=x]).
+__global__ void pack_fac_kernel(const float* __restrict__ src, int64_t nf, int Ra, int Rb, int kindL, int NX, int Sy,
+                                int SYP, float* __restrict__ dst) {
+  const int64_t total = nf * NX * SYP;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int z = (int)(e % 16);
-    const int x = (int)((e / 16) % NX);
-    const int64_t f = e / (16 * NX);
+    const int z = (int)(e % SYP);
+    const int x = (int)((e / SYP) % NX);
+    const int64_t f = e / ((int64_t)SYP * NX);
     float v = 0.0f;
-    if (z < Sy) v = (float)src[f * (int64_t)Ra * Rb + (leftT ? (x + (int64_t)Ra * z) : (z + (int64_t)Ra * x))];
+    if (z < Sy) v = src[f * (int64_t)Ra * Rb + (kindL ? (x + (int64_t)Ra * z) : (z + (int64_t)Ra * x))];
     dst[e] = v;
+  }
+}
+
+// FP32 subchain table level (reduced precision is enough here: the table is rounded to BF16 for the
+// tensor cores, and the factors feed an FP32 stage):
+// out[l + nPrev i][x + Ra y] = sum_c prev[l][x + Ra c] G[c + Rc (i + Ii y)]   (prev == nullptr: core slices)
+__global__ void chain_level_f32_kernel(const float* __restrict__ prev, int64_t nPrev, int Ra, int Rc,
+                                       const double* __restrict__ G, int64_t Ii, int Rb, float* __restrict__ out) {
+  const int64_t per = (int64_t)Ra * Rb;
+  const int64_t total = nPrev * Ii * per;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ent = e / per;
+    const int xy = (int)(e % per);
+    const int x = xy % Ra, y = xy / Ra;
+    const int64_t l = ent % nPrev, i = ent / nPrev;
+    float acc;
+    if (prev == nullptr) {
+      acc = (float)G[x + (int64_t)Rc * (i + Ii * y)];
+    } else {
+      const float* P = prev + l * (int64_t)Ra * Rc;
+      acc = 0.0f;
+      for (int c = 0; c < Rc; ++c) acc = fmaf(P[x + (int64_t)Ra * c], (float)G[c + (int64_t)Rc * (i + Ii * y)], acc);
+    }
+    out[e] = acc;
   }
 }
 
@@ -496,12 +629,13 @@ struct TcImpl {
   size_t smem = 0;
   // stage-1 table build: chain modes S (cyclic order), FP64 scratch, packed BF16 table
   std::vector<int> s_modes, f_modes;
-  int tabRa = 0, tabRb = 0, tab_rowmajor = 0;
+  int tabRa = 0, tabRb = 0, kindL = 0;
   int64_t K_S = 0, Kpad = 0;
-  int facRa = 0, facRb = 0, fac_leftT = 0;
+  int facRa = 0, facRb = 0;
   int64_t n_fac_total = 0;
-  double* chainA = nullptr;
-  double* chainB = nullptr;
+  float* chainA = nullptr;
+  float* chainB = nullptr;
+  int SYP = 4;
   __nv_bfloat16* tab = nullptr;
   float* F = nullptr;
   float* partials = nullptr;
@@ -529,17 +663,19 @@ int64_t chain_max_elems(const std::vector<int>& modes, const int64_t* I, const i
   return mx;
 }
 
-// Build the chain table over `modes` into dst (ping-ponging with scr); returns the entry count.
-const double* build_chain(const std::vector<int>& modes, double* const* cores, const int64_t* I, const int32_t* R,
-                          int N, double* bufA, double* bufB, cudaStream_t s, int* launches) {
-  const double* prev = nullptr;
+// Build the FP32 chain table over consecutive cyclic `modes` (ping-ponging bufA/bufB); returns the result.
+const float* build_chain(const std::vector<int>& modes, double* const* cores, const int64_t* I, const int32_t* R,
+                         int N, float* bufA, float* bufB, cudaStream_t s, int* launches) {
+  const float* prev = nullptr;
   int64_t nPrev = 1;
   const int Ra = R[modes[0]];
-  double* bufs[2] = {bufA, bufB};
+  float* bufs[2] = {bufA, bufB};
   int t = 0;
   for (int m : modes) {
-    double* out = bufs[t++ % 2];
-    launch_chain_level(prev, nPrev, Ra, R[m], cores[m], I[m], R[(m + 1) % N], out, s);
+    float* out = bufs[t++ % 2];
+    const int64_t total = nPrev * I[m] * Ra * R[(m + 1) % N];
+    const int g = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    chain_level_f32_kernel<<<g, 256, 0, s>>>(prev, nPrev, Ra, R[m], cores[m], I[m], R[(m + 1) % N], out);
     ++*launches;
     prev = out;
     nPrev *= I[m];
@@ -571,7 +707,8 @@ TcChoice tc_choose(int N, const int64_t* I, const int32_t* R, int n) {
     c.s_lo = 0;
     c.s_hi = n - 1;
     c.K_S = prod_range(I, 0, n);
-    if ((c.K_S * 2) % 16 == 0 && In <= kRows) consider(c, R[0] * Rn);
+    // rows i + I_n rep: lanes of a warp must hold distinct i_n, so I_n >= 32
+    if ((c.K_S * 2) % 16 == 0 && In <= kRows && In >= 32) consider(c, (R[0] + 3) / 4 * 4 * Rn);
   }
   // KM-R: n = N-1, S = modes 0..s with s <= N-3
   if (n == N - 1) {
@@ -581,13 +718,13 @@ TcChoice tc_choose(int N, const int64_t* I, const int32_t* R, int n) {
       c.s_lo = 0;
       c.s_hi = s;
       c.K_S = prod_range(I, 0, s + 1);
-      if ((c.K_S * 2) % 16 == 0 && In <= kRows) consider(c, R[0] * R[s + 1]);
+      if ((c.K_S * 2) % 16 == 0 && In <= kRows) consider(c, (R[s + 1] + 3) / 4 * 4 * R[0]);
     }
   }
   // MM: S = modes n+1..m, not the whole chain
   {
     const int64_t P = prod_range(I, 0, n + 1);
-    if ((P * 2) % 16 == 0) {
+    if ((P * 2) % 16 == 0 && (P + 63) / 64 <= 128) {   // one p-chunk per CTA
       for (int m = n + 1; m <= N - 1; ++m) {
         if (n == 0 && m == N - 1) continue;
         TcChoice c;
@@ -595,7 +732,7 @@ TcChoice tc_choose(int N, const int64_t* I, const int32_t* R, int n) {
         c.s_lo = n + 1;
         c.s_hi = m;
         c.K_S = prod_range(I, n + 1, m + 1);
-        consider(c, Rn1 * R[(m + 1) % N]);
+        consider(c, (R[(m + 1) % N] + 3) / 4 * 4 * Rn1);
       }
     }
   }
@@ -633,19 +770,15 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   for (int m = best.s_lo; m <= best.s_hi; ++m) impl->s_modes.push_back(m);
   impl->tabRa = R[best.s_lo];
   impl->tabRb = R[(best.s_hi + 1) % N];
-  const int W = impl->tabRa * impl->tabRb;
-  A.W_pad = (W + 15) / 16 * 16;
-  A.ts_stride = A.W_pad + 1;
   uint64_t dims[3], strides[2];
   uint32_t box[3];
   int64_t n_tiles = 0;
   if (A.variant == KM_L) {
-    // T = c x a (colmajor), F = L = G_{n+1}..G_{N-1} (R_{n+1} x R_0) on the left
-    impl->tab_rowmajor = 0;
+    // T = c x a (c = dot index, Sy = R_0); F = L = G_{n+1}..G_{N-1} (R_{n+1} x R_0) on the left
+    impl->kindL = 1;
     for (int m = n + 1; m <= N - 1; ++m) impl->f_modes.push_back(m);
     impl->facRa = Rn1;
     impl->facRb = R[0];
-    impl->fac_leftT = 1;
     A.NX = Rn1;
     A.NY = Rn;
     A.Sy = R[0];
@@ -658,12 +791,11 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
     box[0] = kKT; box[1] = (uint32_t)In; box[2] = (uint32_t)A.nrep;
     A.tx_bytes = (uint32_t)(kKT * 2 * In * A.nrep);
   } else if (A.variant == KM_R) {
-    // T = b x d (rowmajor), F = Rm = G_{s+1}..G_{N-2} (R_{s+1} x R_n) on the right
-    impl->tab_rowmajor = 1;
+    // T = b x d (d = dot index, Sy = R_{s+1}); F = Rm = G_{s+1}..G_{N-2} (R_{s+1} x R_n) on the right
+    impl->kindL = 0;
     for (int m = best.s_hi + 1; m <= N - 2; ++m) impl->f_modes.push_back(m);
     impl->facRa = R[best.s_hi + 1];
     impl->facRb = Rn;
-    impl->fac_leftT = 0;
     A.NX = Rn;
     A.NY = Rn1;
     A.Sy = impl->tabRb;
@@ -676,13 +808,12 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
     box[0] = kKT; box[1] = (uint32_t)A.nrep; box[2] = (uint32_t)In;
     A.tx_bytes = (uint32_t)(kKT * 2 * In * A.nrep);
   } else {
-    // T = b x d (rowmajor), F = Rm = G_{m+1}..G_{N-1} G_0..G_{n-1} (R_{m+1} x R_n) on the right
-    impl->tab_rowmajor = 1;
+    // T = b x d (d = dot index, Sy = R_{m+1}); F = Rm = G_{m+1}..G_{N-1} G_0..G_{n-1} (R_{m+1} x R_n) on the right
+    impl->kindL = 0;
     for (int m = best.s_hi + 1; m <= N - 1; ++m) impl->f_modes.push_back(m);
     for (int m = 0; m <= n - 1; ++m) impl->f_modes.push_back(m);
     impl->facRa = R[(best.s_hi + 1) % N];
     impl->facRb = Rn;
-    impl->fac_leftT = 0;
     A.NX = Rn;
     A.NY = Rn1;
     A.Sy = impl->tabRb;
@@ -690,12 +821,19 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
     A.K_pre = prod_range(I, 0, n);
     A.K_hi = prod_range(I, best.s_hi + 1, N);
     A.pchunks = (A.P + 63) / 64;
-    n_tiles = (A.pchunks * A.K_hi + 1) / 2;
+    A.opairs = (A.K_hi + 1) / 2;
+    n_tiles = A.pchunks * A.opairs;
     dims[0] = A.P; dims[1] = best.K_S; dims[2] = A.K_hi;
     strides[0] = A.P * 2; strides[1] = A.P * best.K_S * 2;
     box[0] = 64; box[1] = kKT; box[2] = 1;
     A.tx_bytes = (uint32_t)(2 * kAtomBytes);
   }
+  impl->SYP = (A.Sy + 3) / 4 * 4;
+  const int W = impl->SYP * A.NY;
+  A.W_pad = (W + 15) / 16 * 16;
+  A.fs_stride = (A.NX * impl->SYP + 7) / 8 * 8 + 4;
+  A.ms_stride = A.r | 1;   // odd row stride: lanes with different i_n hit different banks
+
   A.tx_bytes += (uint32_t)(A.W_pad * 128);
   // MMA instruction descriptor: D=F32, A=B=BF16, A major per variant, B K-major, N=W_pad, M=128
   A.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((A.variant == MM ? 1u : 0u) << 15) |
@@ -713,7 +851,15 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   A.kc_len = (A.ksteps + n_kc - 1) / n_kc;
   A.n_kc = (A.ksteps + A.kc_len - 1) / A.kc_len;
   A.n_units = n_tiles * A.n_kc;
-  impl->grid = (int)std::min<int64_t>(A.n_units, nsm);
+  if (A.variant == MM) {
+    if (A.pchunks > nsm) {   // each CTA keeps a single p-chunk
+      delete impl;
+      return 0;
+    }
+    impl->grid = nsm;
+  } else {
+    impl->grid = (int)std::min<int64_t>(A.n_units, nsm);
+  }
   impl->E = In * r;
 
   // ---- allocations
@@ -727,10 +873,10 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   int64_t nfac = 1;
   for (int m : impl->f_modes) nfac *= I[m];
   impl->n_fac_total = nfac;
-  alloc(reinterpret_cast<void**>(&impl->chainA), chainMax * sizeof(double));
-  alloc(reinterpret_cast<void**>(&impl->chainB), chainMax * sizeof(double));
+  alloc(reinterpret_cast<void**>(&impl->chainA), chainMax * sizeof(float));
+  alloc(reinterpret_cast<void**>(&impl->chainB), chainMax * sizeof(float));
   alloc(reinterpret_cast<void**>(&impl->tab), (size_t)A.W_pad * impl->Kpad * sizeof(__nv_bfloat16));
-  alloc(reinterpret_cast<void**>(&impl->F), (size_t)nfac * A.NX * 16 * sizeof(float));
+  alloc(reinterpret_cast<void**>(&impl->F), (size_t)nfac * A.NX * impl->SYP * sizeof(float));
   alloc(reinterpret_cast<void**>(&impl->partials), (size_t)impl->grid * impl->E * sizeof(float));
   if (e != cudaSuccess) {
     if (err) *err = e;
@@ -756,14 +902,18 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
     return 0;
   }
   const int bBytes = ((A.W_pad * 128) + 1023) & ~1023;
-  impl->smem = 1024 + (size_t)kNS * (kABytes + bBytes) + (size_t)kRows * A.ts_stride * 4 + (size_t)kRows * kVxStride * 4 +
-               (size_t)((impl->E + 1) & ~1) * 4 + (2 * kNS + 4) * 8 + 32;
-  if (impl->smem > 227 * 1024) {
+  const size_t fixed = 1024 + (size_t)kRows * A.fs_stride * 4 +
+                       (size_t)((In * A.ms_stride + 1) & ~1) * 4 + (2 * kNSMax + 4) * 8 + 64;
+  const size_t stage = (size_t)kABytes + bBytes;
+  const int ns = (int)std::min<size_t>(kNSMax, fixed < (size_t)kSmemBudget ? (kSmemBudget - fixed) / stage : 0);
+  if (ns < 2) {
     delete impl;
     for (void* q : p.allocs) cudaFree(q);
     p.allocs.clear();
     return 0;
   }
+  A.ns = ns;
+  impl->smem = fixed + (size_t)ns * stage;
   p.impl = impl;
   p.valid = true;
   p.N = N;
@@ -782,29 +932,31 @@ int tc_enqueue(TcPlan& p, const void* X, double* const* cores, double* M, cudaSt
   const int N = impl->N;
   TcArgs A = impl->args;
   // stage-1 table (Alg. 2 line 8's subchain factors over S) and stage-2 factors
-  const double* tsrc = build_chain(impl->s_modes, cores, I, R, N, impl->chainA, impl->chainB, s, &launches);
+  const float* tsrc = build_chain(impl->s_modes, cores, I, R, N, impl->chainA, impl->chainB, s, &launches);
   {
     const int64_t total = (int64_t)A.W_pad * impl->Kpad;
     const int g = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
-    pack_tab_kernel<<<g, 256, 0, s>>>(tsrc, impl->K_S, impl->Kpad, impl->tabRa, impl->tabRb, impl->tab_rowmajor,
-                                      A.W_pad, impl->tab);
+    pack_tab_kernel<<<g, 256, 0, s>>>(tsrc, impl->K_S, impl->Kpad, impl->tabRa, impl->tabRb, impl->kindL, A.Sy,
+                                      impl->SYP, A.NY, A.W_pad, impl->tab);
     ++launches;
   }
-  const double* fsrc = build_chain(impl->f_modes, cores, I, R, N, impl->chainA, impl->chainB, s, &launches);
+  const float* fsrc = build_chain(impl->f_modes, cores, I, R, N, impl->chainA, impl->chainB, s, &launches);
   {
-    const int64_t total = impl->n_fac_total * A.NX * 16;
+    const int64_t total = impl->n_fac_total * A.NX * impl->SYP;
     const int g = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
-    pack_fac_kernel<<<g, 256, 0, s>>>(fsrc, impl->n_fac_total, impl->facRa, impl->facRb, impl->fac_leftT, A.NX, A.Sy,
-                                      impl->F);
+    pack_fac_kernel<<<g, 256, 0, s>>>(fsrc, impl->n_fac_total, impl->facRa, impl->facRb, impl->kindL, A.NX, A.Sy,
+                                      impl->SYP, impl->F);
     ++launches;
   }
-  mttsp_tc_kernel<<<impl->grid, kThreads, impl->smem, s>>>(impl->tmX, impl->tmT, A);
+  switch (impl->SYP) {
+    case 4: mttsp_tc_kernel<4><<<impl->grid, kThreads, impl->smem, s>>>(impl->tmX, impl->tmT, A); break;
+    case 8: mttsp_tc_kernel<8><<<impl->grid, kThreads, impl->smem, s>>>(impl->tmX, impl->tmT, A); break;
+    case 12: mttsp_tc_kernel<12><<<impl->grid, kThreads, impl->smem, s>>>(impl->tmX, impl->tmT, A); break;
+    default: mttsp_tc_kernel<16><<<impl->grid, kThreads, impl->smem, s>>>(impl->tmX, impl->tmT, A); break;
+  }
   ++launches;
-  {
-    const int g = (int)std::min<int64_t>((impl->E + 255) / 256, 152 * 4);
-    tc_reduce_kernel<<<g, 256, 0, s>>>(impl->partials, impl->grid, impl->E, M);
-    ++launches;
-  }
+  tc_reduce_kernel<<<(unsigned)((impl->E + 31) / 32), 256, 0, s>>>(impl->partials, impl->grid, impl->E, M);
+  ++launches;
   return launches;
 }
 
@@ -821,7 +973,11 @@ void tc_destroy(TcPlan& p) {
 }
 
 cudaError_t init_tc_attributes() {
-  return cudaFuncSetAttribute(mttsp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(mttsp_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(mttsp_tc_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(mttsp_tc_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(mttsp_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
+  return e;
 }
 
 }  // namespace trals
