@@ -227,7 +227,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * kNSMax + 4);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
   volatile int* epi_stop = reinterpret_cast<volatile int*>(tmem_holder + 2);
-  volatile int* epi_stop_any = abort_flag;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int E = a.In * a.r;
@@ -262,6 +261,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
+      int issued[kNSMax] = {0, 0, 0, 0, 0, 0};
       int64_t tile, op, pc;
       int kc;
       for (int64_t j = 0; get_unit(a, j, tile, op, pc, kc) && !*abort_flag; ++j) {
@@ -285,11 +285,19 @@ __global__ void __launch_bounds__(kThreads, 1)
               tma_load_3d(A + at * kAtomBytes, &tmX, &full[stage], (int)(pc * 64), k0, (int)(2 * op + at));
           }
           tma_load_2d(B, &tmT, &full[stage], k0, 0);
+          ++issued[stage];
           if (++stage == NS) {
             stage = 0;
             phase ^= 1u;
           }
         }
+      }
+      if (*abort_flag) {
+        // Do not leave copies in flight into this CTA's shared memory: wait (bounded) for the last
+        // load issued into every stage.
+        volatile int never = 0;
+        for (int st = 0; st < NS; ++st)
+          if (issued[st] > 0) mbar_wait(&full[st], (uint32_t)((issued[st] - 1) & 1), &never);
       }
     }
     __syncwarp();
@@ -459,45 +467,51 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       tmem_wait_st();
     }
-    // Combine the lanes' running sums into the CTA accumulator: one warp at a time (no write races),
-    // lanes sharing i_n inside a warp pre-summed by a segmented shuffle (runs are contiguous).
-    const bool seg = (a.variant == KM_R) || (a.variant == MM && a.K_pre > 1);
-    const int key = lane_ok ? my_i : -1 - lane;
-    const int prev_key = __shfl_up_sync(0xffffffffu, key, 1);
-    const bool head = !seg || lane == 0 || prev_key != key;
-    int nbr_key[5];
+    // Combine the lanes' running sums into the CTA accumulator.  The pipeline buffers are idle now
+    // (every MMA and copy has been consumed), so lanes stage V[x][y] there and threads then own
+    // outputs (i_n, x, y), adding the rows of their i_n in a fixed order.
+    epi_bar();
+    float* S = reinterpret_cast<float*>(base);
+    const int nv = a.NX * a.NY, ss = nv | 1;
+    {
+      float* myS = S + row * ss;
+      for (int x = 0; x < a.NX; ++x) {
+        uint32_t v[16];
+        tmem_ld16(vacc + 16u * x, v);
+        tmem_wait_ld();
 #pragma unroll
-    for (int k = 0; k < 5; ++k) nbr_key[k] = __shfl_down_sync(0xffffffffu, key, 1 << k);
-    for (int ph = 0; ph < 4; ++ph) {
-      if (ph == warp - 2 && !*epi_stop_any) {
-        for (int x = 0; x < a.NX; ++x) {
-          uint32_t v[16];
-          tmem_ld16(vacc + 16u * x, v);
-          tmem_wait_ld();
-          float val[16];
-#pragma unroll
-          for (int y = 0; y < 16; ++y) val[y] = __uint_as_float(v[y]);
-          if (seg) {
-#pragma unroll
-            for (int k = 0; k < 5; ++k) {
-              const bool take = (lane + (1 << k) < 32) && (nbr_key[k] == key);
-#pragma unroll
-              for (int y = 0; y < 16; ++y) {
-                const float o = __shfl_down_sync(0xffffffffu, val[y], 1 << k);
-                if (take) val[y] += o;
-              }
-            }
-          }
-          if (lane_ok && head) {
-            float* dst = M_s + my_i * a.ms_stride;
-#pragma unroll
-            for (int y = 0; y < 16; ++y)
-              if (y < a.NY) dst[a.variant == KM_L ? (y + a.Rn * x) : (x + a.Rn * y)] += val[y];
-          }
-        }
+        for (int y = 0; y < 16; ++y)
+          if (y < a.NY) myS[x * a.NY + y] = lane_ok ? __uint_as_float(v[y]) : 0.0f;
       }
-      epi_bar();
     }
+    epi_bar();
+    if (!*abort_flag) {
+      int64_t i_lo = 0, i_hi = a.In - 1, p0 = 0, p1 = 0;
+      if (a.variant == MM) {
+        p0 = (blockIdx.x % a.pchunks) * 64;
+        p1 = min(a.P, p0 + 64);
+        i_lo = p0 / a.K_pre;
+        i_hi = (p1 - 1) / a.K_pre;
+      }
+      const int cnt = (int)(i_hi - i_lo + 1) * nv;
+      for (int o = et; o < cnt; o += 128) {
+        const int g = o / nv, xy = o % nv;
+        const int x = xy / a.NY, y = xy % a.NY;
+        const int64_t i = i_lo + g;
+        float sum = 0.0f;
+        if (a.variant == KM_L) {
+          for (int rp = 0; rp < a.nrep; ++rp) sum += S[(i + a.In * rp) * ss + xy];
+        } else if (a.variant == KM_R) {
+          for (int rp = 0; rp < a.nrep; ++rp) sum += S[(rp + a.nrep * i) * ss + xy];
+        } else {
+          const int r0 = (int)(max(p0, i * a.K_pre) - p0), r1 = (int)(min(p1, (i + 1) * a.K_pre) - p0);
+          for (int at2 = 0; at2 < 2; ++at2)
+            for (int rr = r0; rr < r1; ++rr) sum += S[(at2 * 64 + rr) * ss + xy];
+        }
+        M_s[i * a.ms_stride + (a.variant == KM_L ? (y + a.Rn * x) : (x + a.Rn * y))] = sum;
+      }
+    }
+    epi_bar();
     // write this CTA's partial (column-major I_n x r)
     if (!*abort_flag) {
       float* out = a.partials + (size_t)blockIdx.x * E;
@@ -531,9 +545,12 @@ __global__ void tc_reduce_kernel(const float* __restrict__ partials, int G, int6
   }
 }
 
-// Stage-1 table: Tab[w * Kpad + k] = bf16(P_k[...]) with w = z + SYP y (z: inner/dot index, y: outer):
-// kindL (factor on the left): P = c x a (Ra = Sy rows), value P[z + Ra y]; otherwise P = b x d
-// (Ra = NY rows), value P[y + Ra z].  Zero for z >= Sy, y >= NY or k >= K.
+// The FP32 subchain tables below are stored entry-fastest ("structure of arrays"): element (x, y) of
+// entry l sits at P[(x + Ra y) * count + l], so consecutive threads touch consecutive addresses.
+
+// Stage-1 table: Tab[w * Kpad + k] = bf16(P_k(...)) with w = z + SYP y (z: inner/dot index, y: outer):
+// kindL (factor on the left): P = c x a (Ra = Sy rows), element (z, y); otherwise P = b x d (Ra = NY rows),
+// element (y, z).  Zero for z >= Sy, y >= NY or k >= K.
 __global__ void pack_tab_kernel(const float* __restrict__ src, int64_t K, int64_t Kpad, int Ra, int Rb, int kindL,
                                 int Sy, int SYP, int NY, int W_pad, __nv_bfloat16* __restrict__ dst) {
   const int64_t total = (int64_t)W_pad * Kpad;
@@ -542,12 +559,12 @@ __global__ void pack_tab_kernel(const float* __restrict__ src, int64_t K, int64_
     const int w = (int)(e / Kpad);
     const int z = w % SYP, y = w / SYP;
     float v = 0.0f;
-    if (k < K && z < Sy && y < NY) v = src[k * (int64_t)Ra * Rb + (kindL ? (z + (int64_t)Ra * y) : (y + (int64_t)Ra * z))];
+    if (k < K && z < Sy && y < NY) v = src[(int64_t)(kindL ? (z + Ra * y) : (y + Ra * z)) * K + k];
     dst[e] = __float2bfloat16_rn(v);
   }
 }
 
-// Stage-2 factors: F[(f * NX + x) * SYP + z] = kindL ? P_f[x + Ra z] (L[b=x][c=z]) : P_f[z + Ra x] (Rm[d=z][a=x]).
+// Stage-2 factors: F[(f * NX + x) * SYP + z] = kindL ? P_f(x, z) (L[b=x][c=z]) : P_f(z, x) (Rm[d=z][a=x]).
 __global__ void pack_fac_kernel(const float* __restrict__ src, int64_t nf, int Ra, int Rb, int kindL, int NX, int Sy,
                                 int SYP, float* __restrict__ dst) {
   const int64_t total = nf * NX * SYP;
@@ -556,32 +573,47 @@ __global__ void pack_fac_kernel(const float* __restrict__ src, int64_t nf, int R
     const int x = (int)((e / SYP) % NX);
     const int64_t f = e / ((int64_t)SYP * NX);
     float v = 0.0f;
-    if (z < Sy) v = src[f * (int64_t)Ra * Rb + (kindL ? (x + (int64_t)Ra * z) : (z + (int64_t)Ra * x))];
+    if (z < Sy) v = src[(int64_t)(kindL ? (x + Ra * z) : (z + Ra * x)) * nf + f];
     dst[e] = v;
   }
 }
 
 // FP32 subchain table level (reduced precision is enough here: the table is rounded to BF16 for the
 // tensor cores, and the factors feed an FP32 stage):
-// out[l + nPrev i][x + Ra y] = sum_c prev[l][x + Ra c] G[c + Rc (i + Ii y)]   (prev == nullptr: core slices)
+// out(l + nPrev i)[x + Ra y] = sum_c prev(l)[x + Ra c] G[c + Rc (i + Ii y)]   (prev == nullptr: core slices)
 __global__ void chain_level_f32_kernel(const float* __restrict__ prev, int64_t nPrev, int Ra, int Rc,
-                                       const double* __restrict__ G, int64_t Ii, int Rb, float* __restrict__ out) {
-  const int64_t per = (int64_t)Ra * Rb;
-  const int64_t total = nPrev * Ii * per;
+                                       const float* __restrict__ G, int64_t Ii, int Rb, float* __restrict__ out) {
+  const int64_t nOut = nPrev * Ii;
+  const int64_t total = nOut * Ra * Rb;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t ent = e / per;
-    const int xy = (int)(e % per);
+    const int64_t ent = e % nOut;
+    const int xy = (int)(e / nOut);
     const int x = xy % Ra, y = xy / Ra;
     const int64_t l = ent % nPrev, i = ent / nPrev;
     float acc;
     if (prev == nullptr) {
-      acc = (float)G[x + (int64_t)Rc * (i + Ii * y)];
+      acc = G[x + (int64_t)Rc * (i + Ii * y)];
     } else {
-      const float* P = prev + l * (int64_t)Ra * Rc;
       acc = 0.0f;
-      for (int c = 0; c < Rc; ++c) acc = fmaf(P[x + (int64_t)Ra * c], (float)G[c + (int64_t)Rc * (i + Ii * y)], acc);
+      for (int c = 0; c < Rc; ++c)
+        acc = fmaf(prev[(int64_t)(x + Ra * c) * nPrev + l], G[c + (int64_t)Rc * (i + Ii * y)], acc);
     }
     out[e] = acc;
+  }
+}
+
+// FP64 cores -> one FP32 copy (conversions run once per update, not once per table element).
+struct CorePtrs {
+  const double* p[kMaxOrder];
+  int64_t off[kMaxOrder + 1];
+  int N;
+};
+__global__ void cores_to_f32_kernel(const CorePtrs c, float* __restrict__ dst) {
+  const int64_t total = c.off[c.N];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int j = 0;
+    while (e >= c.off[j + 1]) ++j;
+    dst[e] = (float)c.p[j][e - c.off[j]];
   }
 }
 
@@ -635,6 +667,8 @@ struct TcImpl {
   int64_t n_fac_total = 0;
   float* chainA = nullptr;
   float* chainB = nullptr;
+  float* cores32 = nullptr;                 // FP32 copy of every core, concatenated
+  int64_t core_off[kMaxOrder + 1] = {};
   int SYP = 4;
   __nv_bfloat16* tab = nullptr;
   float* F = nullptr;
@@ -664,7 +698,7 @@ int64_t chain_max_elems(const std::vector<int>& modes, const int64_t* I, const i
 }
 
 // Build the FP32 chain table over consecutive cyclic `modes` (ping-ponging bufA/bufB); returns the result.
-const float* build_chain(const std::vector<int>& modes, double* const* cores, const int64_t* I, const int32_t* R,
+const float* build_chain(const std::vector<int>& modes, const float* const* cores, const int64_t* I, const int32_t* R,
                          int N, float* bufA, float* bufB, cudaStream_t s, int* launches) {
   const float* prev = nullptr;
   int64_t nPrev = 1;
@@ -873,6 +907,8 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   int64_t nfac = 1;
   for (int m : impl->f_modes) nfac *= I[m];
   impl->n_fac_total = nfac;
+  for (int j = 0; j < N; ++j) impl->core_off[j + 1] = impl->core_off[j] + (int64_t)R[j] * I[j] * R[(j + 1) % N];
+  alloc(reinterpret_cast<void**>(&impl->cores32), (size_t)impl->core_off[N] * sizeof(float));
   alloc(reinterpret_cast<void**>(&impl->chainA), chainMax * sizeof(float));
   alloc(reinterpret_cast<void**>(&impl->chainB), chainMax * sizeof(float));
   alloc(reinterpret_cast<void**>(&impl->tab), (size_t)A.W_pad * impl->Kpad * sizeof(__nv_bfloat16));
@@ -914,6 +950,17 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   }
   A.ns = ns;
   impl->smem = fixed + (size_t)ns * stage;
+  {
+    // the end-of-kernel lane staging reuses the pipeline buffers and the factor blocks
+    const size_t stage_area = (size_t)ns * stage + (size_t)kRows * A.fs_stride * 4;
+    const size_t need = (size_t)kRows * ((A.NX * A.NY) | 1) * 4;
+    if (need > stage_area) {
+      delete impl;
+      for (void* q : p.allocs) cudaFree(q);
+      p.allocs.clear();
+      return 0;
+    }
+  }
   p.impl = impl;
   p.valid = true;
   p.N = N;
@@ -932,7 +979,20 @@ int tc_enqueue(TcPlan& p, const void* X, double* const* cores, double* M, cudaSt
   const int N = impl->N;
   TcArgs A = impl->args;
   // stage-1 table (Alg. 2 line 8's subchain factors over S) and stage-2 factors
-  const float* tsrc = build_chain(impl->s_modes, cores, I, R, N, impl->chainA, impl->chainB, s, &launches);
+  const float* c32[kMaxOrder];
+  {
+    CorePtrs cp;
+    cp.N = N;
+    for (int j = 0; j <= N; ++j) cp.off[j] = impl->core_off[j];
+    for (int j = 0; j < N; ++j) {
+      cp.p[j] = cores[j];
+      c32[j] = impl->cores32 + impl->core_off[j];
+    }
+    cores_to_f32_kernel<<<(unsigned)std::min<int64_t>((impl->core_off[N] + 255) / 256, 152), 256, 0, s>>>(cp,
+                                                                                                     impl->cores32);
+    ++launches;
+  }
+  const float* tsrc = build_chain(impl->s_modes, c32, I, R, N, impl->chainA, impl->chainB, s, &launches);
   {
     const int64_t total = (int64_t)A.W_pad * impl->Kpad;
     const int g = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
@@ -940,7 +1000,7 @@ int tc_enqueue(TcPlan& p, const void* X, double* const* cores, double* M, cudaSt
                                       impl->SYP, A.NY, A.W_pad, impl->tab);
     ++launches;
   }
-  const float* fsrc = build_chain(impl->f_modes, cores, I, R, N, impl->chainA, impl->chainB, s, &launches);
+  const float* fsrc = build_chain(impl->f_modes, c32, I, R, N, impl->chainA, impl->chainB, s, &launches);
   {
     const int64_t total = impl->n_fac_total * A.NX * impl->SYP;
     const int g = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
