@@ -116,8 +116,11 @@ __global__ void chain_level_kernel(const double* __restrict__ prev, int64_t nPre
 }
 
 // ------------------------------------------------------------------ K4: Cholesky (single CTA)
-// Right-looking column Cholesky of the lower triangle of S (r x r), Golub & Van Loan Sec. 5.3.2
-// method cited for Alg. 2 line 9.  Works in shared memory when r <= kCholSmemMax, else in Lmat.
+// Right-looking column Cholesky of the lower triangle of S (r x r), the Golub & Van Loan Sec. 5.3.2
+// method cited for Alg. 2 line 9, in FP64.  The matrix lives in shared memory (r <= kCholSmemMax),
+// else in Lmat.  Column j's trailing update is split by columns k over warps and rows i >= k over
+// lanes (no index division).  The reciprocal diagonal 1/L_jj is stored after the matrix (Lmat[r*r + j])
+// so the triangular solves never divide.
 constexpr int kCholSmemMax = 128;
 constexpr int kCholThreads = 1024;
 
@@ -125,10 +128,12 @@ __global__ void __launch_bounds__(kCholThreads) cholesky_kernel(const double* __
                                                                  int r, DevStatus* st, const int* sweep_ctr, int mode) {
   extern __shared__ double sm[];
   __shared__ int fail;
+  __shared__ double invd_s;
   const bool in_smem = r <= kCholSmemMax;
   double* A = in_smem ? sm : Lmat;
   const int lda = r;
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid / 32, lane = tid % 32, nw = nt / 32;
   for (int e = tid; e < r * r; e += nt) {
     const int i = e % r, j = e / r;
     A[e] = (i >= j) ? S[e] : 0.0;
@@ -142,18 +147,21 @@ __global__ void __launch_bounds__(kCholThreads) cholesky_kernel(const double* __
         fail = 1;
         set_status(st, isfinite(d) ? TRALS_E_NOT_SPD : TRALS_E_NONFINITE, sweep_ctr ? *sweep_ctr : -1, mode, j, d);
       } else {
-        A[j + lda * j] = sqrt(d);
+        const double l = sqrt(d);
+        A[j + lda * j] = l;
+        invd_s = 1.0 / l;
+        Lmat[r * r + j] = 1.0 / l;
       }
     }
     __syncthreads();
     if (fail) return;
-    const double djj = A[j + lda * j];
-    for (int i = j + 1 + tid; i < r; i += nt) A[i + lda * j] = A[i + lda * j] / djj;
+    const double inv = invd_s;
+    for (int i = j + 1 + tid; i < r; i += nt) A[i + lda * j] *= inv;
     __syncthreads();
-    const int m = r - j - 1;
-    for (int e = tid; e < m * m; e += nt) {
-      const int i = j + 1 + e % m, k = j + 1 + e / m;
-      if (i >= k) A[i + lda * k] = fma(-A[i + lda * j], A[k + lda * j], A[i + lda * k]);
+    // A[i][k] -= A[i][j] A[k][j] for j < k <= i: column k -> warp, rows i -> lanes
+    for (int k = j + 1 + warp; k < r; k += nw) {
+      const double akj = A[k + lda * j];
+      for (int i = k + lane; i < r; i += 32) A[i + lda * k] = fma(-A[i + lda * j], akj, A[i + lda * k]);
     }
     __syncthreads();
   }
@@ -161,31 +169,167 @@ __global__ void __launch_bounds__(kCholThreads) cholesky_kernel(const double* __
     for (int e = tid; e < r * r; e += nt) Lmat[e] = A[e];
 }
 
-// Two triangular solves per right-hand side (one warp per row i of M):  L y = M[i,:]^T,
-// L^T z = y, then G[a + Rn (i + In b)] = z[a + Rn b] (classical mode-2 folding).
+// ------------------------------------------------------------------ K4, blocked over many SMs
+// FP64 throughput per SM is small on this GPU, so larger systems use a right-looking blocked Cholesky
+// in kPanel-wide panels, two kernels per panel (Golub & Van Loan Sec. 4.2, the same factorization):
+//   update: A[i][j] -= sum_{k < p0} L[i][k] L[j][k]   for the panel's columns j and rows i >= j
+//   factor: every CTA factors the panel's diagonal block redundantly in shared memory, then solves
+//           its share of the rows below: L[i][p0:p1] = A[i][p0:p1] L_pp^{-T}.
+// L is the lower triangle of Lmat (column-major, leading dimension r); 1/L_jj goes to Lmat[r*r + j].
+constexpr int kPanel = 32;
+
+__global__ void chol_panel_update_kernel(double* __restrict__ A, int r, int p0) {
+  // one thread per (i, j) with j in [p0, p0 + kPanel), i in [j, r)
+  const int p1 = min(r, p0 + kPanel);
+  const int nj = p1 - p0;
+  const int total = (r - p0) * nj;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int i = p0 + e % (r - p0), j = p0 + e / (r - p0);
+    if (i < j) continue;
+    double acc = 0.0;
+    for (int k = 0; k < p0; ++k) acc = fma(A[i + (int64_t)r * k], A[j + (int64_t)r * k], acc);
+    A[i + (int64_t)r * j] -= acc;
+  }
+}
+
+__global__ void chol_panel_factor_kernel(double* __restrict__ A, int r, int p0, DevStatus* st, const int* sweep_ctr,
+                                         int mode) {
+  __shared__ double D[kPanel][kPanel + 1];
+  __shared__ double invd[kPanel];
+  __shared__ int fail;
+  const int p1 = min(r, p0 + kPanel);
+  const int nb = p1 - p0;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < nb * nb; e += blockDim.x) {
+    const int i = e % nb, j = e / nb;
+    D[i][j] = (i >= j) ? A[(p0 + i) + (int64_t)r * (p0 + j)] : 0.0;
+  }
+  if (tid == 0) fail = 0;
+  __syncthreads();
+  // factor the diagonal block (one warp, column by column)
+  if (tid < 32) {
+    for (int j = 0; j < nb; ++j) {
+      if (tid == 0) {
+        const double d = D[j][j];
+        if (!(d > 0.0) || !isfinite(d)) {
+          fail = 1;
+          if (blockIdx.x == 0)
+            set_status(st, isfinite(d) ? TRALS_E_NOT_SPD : TRALS_E_NONFINITE, sweep_ctr ? *sweep_ctr : -1, mode,
+                       p0 + j, d);
+          D[j][j] = 1.0;
+          invd[j] = 1.0;
+        } else {
+          const double l = sqrt(d);
+          D[j][j] = l;
+          invd[j] = 1.0 / l;
+        }
+      }
+      __syncwarp();
+      const double inv = invd[j];
+      if (tid > j && tid < nb) D[tid][j] *= inv;
+      __syncwarp();
+      // trailing update inside the block: lane i updates its row i >= k > j
+      if (tid > j && tid < nb) {
+        const double lij = D[tid][j];
+        for (int k = j + 1; k <= tid; ++k) D[tid][k] = fma(-lij, D[k][j], D[tid][k]);
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (fail) return;
+  if (blockIdx.x == 0) {
+    for (int e = tid; e < nb * nb; e += blockDim.x) {
+      const int i = e % nb, j = e / nb;
+      if (i >= j) A[(p0 + i) + (int64_t)r * (p0 + j)] = D[i][j];
+    }
+    for (int j = tid; j < nb; j += blockDim.x) A[(int64_t)r * r + p0 + j] = invd[j];
+  }
+  // rows below the block: x L_pp^T = a  (forward substitution per row, one warp per row)
+  const int warp = tid / 32, lane = tid % 32, nw = blockDim.x / 32;
+  for (int i = p1 + blockIdx.x * nw + warp; i < r; i += gridDim.x * nw) {
+    double x = (lane < nb) ? A[i + (int64_t)r * (p0 + lane)] : 0.0;
+    for (int j = 0; j < nb; ++j) {
+      const double xj = __shfl_sync(0xffffffffu, x, j) * invd[j];
+      if (lane == j) x = xj;
+      if (lane > j && lane < nb) x = fma(-D[lane][j], xj, x);
+    }
+    if (lane < nb) A[i + (int64_t)r * (p0 + lane)] = x;
+  }
+}
+
+// Two triangular solves per right-hand side (one warp per row i of M; L staged in shared memory when it
+// fits): L y = M[i,:]^T, then L^T z = y, then G[a + Rn (i + In b)] = z[a + Rn b] (classical mode-2
+// folding).  Both sweeps are blocked in kPanel-wide panels: a panel first takes the contribution of the
+// finished entries (one row of L per lane, independent partial sums), then a kPanel-step substitution
+// with shuffles.  Divisions are replaced by the stored reciprocal diagonal.
+template <bool kLInSmem>
 __global__ void chol_solve_kernel(const double* __restrict__ Lmat, const double* __restrict__ M, int Rn, int64_t In,
                                   int Rn1, double* __restrict__ G, DevStatus* st) {
-  extern __shared__ double y[];
+  extern __shared__ double sh[];
   const int r = Rn * Rn1;
-  const int lane = threadIdx.x;
+  double* y = sh;                                      // r
+  double* inv = y + r;                                 // r
+  double* Ls = inv + r;                                // r x r, column-major (when staged)
+  const double* L = kLInSmem ? Ls : Lmat;
   const int64_t i = blockIdx.x;
-  for (int j = lane; j < r; j += 32) y[j] = M[i + In * (int64_t)j];
-  __syncwarp();
-  for (int j = 0; j < r; ++j) {
-    const double yj = y[j] / Lmat[j + (int64_t)r * j];
-    __syncwarp();
-    if (lane == 0) y[j] = yj;
-    for (int k = j + 1 + lane; k < r; k += 32) y[k] = fma(-Lmat[k + (int64_t)r * j], yj, y[k]);
+  if (kLInSmem)
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) Ls[e] = Lmat[e];
+  for (int j = threadIdx.x; j < r; j += blockDim.x) {
+    y[j] = M[i + In * (int64_t)j];
+    inv[j] = Lmat[r * r + j];
+  }
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  // forward: for each panel, y_p -= L[p, 0:p0] y[0:p0], then solve L_pp y_p = rhs
+  for (int p0 = 0; p0 < r; p0 += kPanel) {
+    const int nb = min(kPanel, r - p0);
+    double x = 0.0;
+    if (lane < nb) {
+      const int row = p0 + lane;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int k = 0;
+      for (; k + 3 < p0; k += 4) {
+        a0 = fma(L[row + r * k], y[k], a0);
+        a1 = fma(L[row + r * (k + 1)], y[k + 1], a1);
+        a2 = fma(L[row + r * (k + 2)], y[k + 2], a2);
+        a3 = fma(L[row + r * (k + 3)], y[k + 3], a3);
+      }
+      for (; k < p0; ++k) a0 = fma(L[row + r * k], y[k], a0);
+      x = y[row] - ((a0 + a1) + (a2 + a3));
+    }
+    for (int j = 0; j < nb; ++j) {
+      const double xj = __shfl_sync(0xffffffffu, x, j) * inv[p0 + j];
+      if (lane == j) x = xj;
+      if (lane > j && lane < nb) x = fma(-L[(p0 + lane) + r * (p0 + j)], xj, x);
+    }
+    if (lane < nb) y[p0 + lane] = x;
     __syncwarp();
   }
-  for (int j = r - 1; j >= 0; --j) {
-    double part = 0.0;
-    for (int k = j + 1 + lane; k < r; k += 32) part = fma(Lmat[k + (int64_t)r * j], y[k], part);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    const double zj = (y[j] - part) / Lmat[j + (int64_t)r * j];
-    __syncwarp();
-    if (lane == 0) y[j] = zj;
+  // backward: for each panel from the last, y_p -= L[p1:r, p]^T z[p1:r], then solve L_pp^T z_p = rhs
+  for (int p0 = ((r - 1) / kPanel) * kPanel; p0 >= 0; p0 -= kPanel) {
+    const int nb = min(kPanel, r - p0), p1 = p0 + nb;
+    double x = 0.0;
+    if (lane < nb) {
+      const int col = p0 + lane;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int k = p1;
+      for (; k + 3 < r; k += 4) {
+        a0 = fma(L[k + r * col], y[k], a0);
+        a1 = fma(L[(k + 1) + r * col], y[k + 1], a1);
+        a2 = fma(L[(k + 2) + r * col], y[k + 2], a2);
+        a3 = fma(L[(k + 3) + r * col], y[k + 3], a3);
+      }
+      for (; k < r; ++k) a0 = fma(L[k + r * col], y[k], a0);
+      x = y[col] - ((a0 + a1) + (a2 + a3));
+    }
+    for (int j = nb - 1; j >= 0; --j) {
+      const double xj = __shfl_sync(0xffffffffu, x, j) * inv[p0 + j];
+      if (lane == j) x = xj;
+      if (lane < j) x = fma(-L[(p0 + j) + r * (p0 + lane)], xj, x);
+    }
+    if (lane < nb) y[p0 + lane] = x;
     __syncwarp();
   }
   for (int c = lane; c < r; c += 32) {
@@ -376,16 +520,45 @@ int64_t table_level_max_elems(const ModeLayout& L, const int64_t* I, const int32
   return mx;
 }
 
-void launch_cholesky(const double* S, double* Lmat, int r, DevStatus* st, const int* sweep_ctr, int mode,
-                     cudaStream_t s) {
-  const size_t smem = (r <= kCholSmemMax) ? (size_t)r * r * sizeof(double) : 0;
-  cholesky_kernel<<<1, kCholThreads, smem, s>>>(S, Lmat, r, st, sweep_ctr, mode);
+__global__ void copy_lower_kernel(const double* __restrict__ S, double* __restrict__ A, int r) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * r; e += gridDim.x * blockDim.x) {
+    const int i = e % r, j = e / r;
+    A[e] = (i >= j) ? S[e] : 0.0;
+  }
+}
+
+int launch_cholesky(const double* S, double* Lmat, int r, DevStatus* st, const int* sweep_ctr, int mode,
+                    cudaStream_t s) {
+  if (r <= kCholSmemMax) {
+    // one CTA, matrix in shared memory: all 32 warps share the SM's FP64 pipes with one sync pair per column
+    const size_t smem = (size_t)r * r * sizeof(double);
+    cholesky_kernel<<<1, kCholThreads, smem, s>>>(S, Lmat, r, st, sweep_ctr, mode);
+    return 1;
+  }
+  int launches = 1;
+  copy_lower_kernel<<<grid_for((int64_t)r * r, 256), 256, 0, s>>>(S, Lmat, r);
+  for (int p0 = 0; p0 < r; p0 += kPanel) {
+    if (p0 > 0) {
+      const int total = (r - p0) * std::min(kPanel, r - p0);
+      chol_panel_update_kernel<<<(total + 63) / 64, 64, 0, s>>>(Lmat, r, p0);
+      ++launches;
+    }
+    const int rows_below = std::max(0, r - std::min(r, p0 + kPanel));
+    const int blocks = std::max(1, std::min(64, (rows_below + 3) / 4));
+    chol_panel_factor_kernel<<<blocks, 128, 0, s>>>(Lmat, r, p0, st, sweep_ctr, mode);
+    ++launches;
+  }
+  return launches;
 }
 
 void launch_chol_solve(const double* Lmat, const double* M, int Rn, int64_t In, int Rn1, double* G, DevStatus* st,
                        cudaStream_t s) {
   const int r = Rn * Rn1;
-  chol_solve_kernel<<<(unsigned)In, 32, (size_t)r * sizeof(double), s>>>(Lmat, M, Rn, In, Rn1, G, st);
+  const size_t smem = ((size_t)r * r + 2 * (size_t)r) * sizeof(double);
+  if (smem <= 227 * 1024)
+    chol_solve_kernel<true><<<(unsigned)In, 256, smem, s>>>(Lmat, M, Rn, In, Rn1, G, st);
+  else
+    chol_solve_kernel<false><<<(unsigned)In, 256, 2 * (size_t)r * sizeof(double), s>>>(Lmat, M, Rn, In, Rn1, G, st);
 }
 
 void launch_residual_identity(const double* normX2, const double* M, const double* coreN, const double* S,
@@ -423,8 +596,12 @@ void launch_convert_f32(const void* src_f64, int64_t count, float* dst, cudaStre
 }
 
 cudaError_t init_small_attributes() {
-  return cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              kCholSmemMax * kCholSmemMax * (int)sizeof(double));
+  cudaError_t e = cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kCholSmemMax * kCholSmemMax * (int)sizeof(double));
+  // solve: L (r x r) plus two vectors, r <= 160 (the QR path's solves use larger r from global memory)
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(chol_solve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  return e;
 }
 
 }  // namespace trals

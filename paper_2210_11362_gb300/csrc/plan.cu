@@ -198,10 +198,10 @@ int enqueue_sweep(trals_plan* p) {
     const int Rn = p->R[n], Rn1 = p->R[(n + 1) % N];
     launches += enqueue_coef(N, p->R, p->gam, n, p->chainA, p->chainB, p->S, s);
     launches += enqueue_mttsp(p, n, s);
-    launch_cholesky(p->S, p->Lmat, Rn * Rn1, p->ctx->d_status, p->sweep_ctr, n, s);
+    launches += launch_cholesky(p->S, p->Lmat, Rn * Rn1, p->ctx->d_status, p->sweep_ctr, n, s);
     launch_chol_solve(p->Lmat, p->M, Rn, p->I[n], Rn1, p->cores[n], p->ctx->d_status, s);
     launch_gamma(p->cores[n], Rn, p->I[n], Rn1, p->gam[n], s);
-    launches += 3;
+    launches += 2;
   }
   const int n = N - 1;
   if (p->opts.explicit_residual) {
@@ -359,7 +359,7 @@ trals_status trals_plan_create(trals_ctx* ctx, int N, const int64_t* I, const in
     PLAN_TRY(cudaMemcpy(p->offU[n], offU.data(), offU.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
   }
   PLAN_TRY(p->alloc(&p->S, (size_t)maxr * maxr));
-  PLAN_TRY(p->alloc(&p->Lmat, (size_t)maxr * maxr));
+  PLAN_TRY(p->alloc(&p->Lmat, (size_t)maxr * maxr + maxr));   // L and its reciprocal diagonal
   PLAN_TRY(p->alloc(&p->chainA, (size_t)maxR2 * maxR2));
   PLAN_TRY(p->alloc(&p->chainB, (size_t)maxR2 * maxR2));
   PLAN_TRY(p->alloc(&p->M, (size_t)maxMr));
@@ -661,7 +661,7 @@ trals_status trals_solve_chol(trals_ctx* ctx, int Rn, int64_t In, int Rn1, const
   if (!ctx || !S_dev || !M_dev || !G_dev || Rn < 1 || Rn1 < 1 || In < 1 || Rn * Rn1 > 256) return TRALS_E_ARG;
   const int r = Rn * Rn1;
   double* Lm = nullptr;
-  TRALS_CUDA_TRY(ctx, cudaMalloc(&Lm, (size_t)r * r * sizeof(double)));
+  TRALS_CUDA_TRY(ctx, cudaMalloc(&Lm, ((size_t)r * r + r) * sizeof(double)));
   launch_cholesky(S_dev, Lm, r, ctx->d_status, nullptr, -1, ctx->stream);
   launch_chol_solve(Lm, M_dev, Rn, In, Rn1, G_dev, ctx->d_status, ctx->stream);
   cudaError_t e = cudaGetLastError();

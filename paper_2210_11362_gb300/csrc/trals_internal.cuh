@@ -88,9 +88,11 @@ void launch_reconstruct(const ModeLayout& L, const double* ltab, const double* u
 // Sum of `count` partials into out[0] (and out[1] if two interleaved series), fixed order.
 void launch_reduce_pairs(const double* partials, int count, double* out, cudaStream_t s);
 
-// Cholesky (K4): factor S (r x r, lower triangle) into L (r x r) in place on a copy; status on failure.
-void launch_cholesky(const double* S, double* Lmat, int r, DevStatus* st, const int* sweep_ctr, int mode,
-                     cudaStream_t s);
+// Cholesky (K4): factor S (r x r, lower triangle) into L (r x r, then r reciprocal diagonal entries, so
+// Lmat holds r*r + r doubles); status on failure.
+// Returns the number of kernel launches.
+int launch_cholesky(const double* S, double* Lmat, int r, DevStatus* st, const int* sweep_ctr, int mode,
+                    cudaStream_t s);
 // Triangular solves with In right-hand sides; writes core layout.
 void launch_chol_solve(const double* Lmat, const double* M, int Rn, int64_t In, int Rn1, double* G,
                        DevStatus* st, cudaStream_t s);
