@@ -180,6 +180,19 @@ trals_status trals_mttsp(trals_ctx* ctx, int N, const int64_t* I, const int32_t*
 trals_status trals_solve_chol(trals_ctx* ctx, int Rn, int64_t In, int Rn1, const double* S_dev,
                               const double* M_dev, double* G_dev);
 
+/* trals_mttsp in FP64 mode (X FP64) without any device allocation, for callers that cannot allocate:
+ * code running where cudaMalloc/cudaFree are unavailable or forbidden (a host callback, an allocator
+ * hook that must not re-enter the CUDA allocator, a fixed-budget real-time loop, a runtime that owns
+ * all device memory).  The paper has no counterpart; it is an interface convenience.  Its subchain
+ * tables, offsets and per-block partial sums live in one static 32 MiB device array that every GPU
+ * loading the library holds until process exit; shapes whose tables plus one block's partial sums do
+ * not fit return TRALS_E_ARG with a message.  The array's address is looked up on the first call made
+ * on each device (make that call before any stream capture).  All calls share the array, so calls
+ * that overlap on the GPU race: serialise them on one stream.  Synchronous.  Arguments and result
+ * layout as trals_mttsp. */
+trals_status trals_mttsp_noalloc(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R, const void* X_dev,
+                                 const double* const* cores_dev, int n, double* M_dev);
+
 /* Which kernel computes the MTTSP of mode n in `mode` (host-only query, needs no GPU):
  * 0 = CUDA cores (the FP64 path, and shapes the tensor-core kernel does not take);
  * 1 = tensor cores, X K-major with the stage-2 factor on the left;

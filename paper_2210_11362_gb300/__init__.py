@@ -38,7 +38,7 @@ EXPORTED = [
     "trals_plan_create", "trals_plan_destroy", "trals_plan_set_cores", "trals_plan_get_cores",
     "trals_plan_run", "trals_plan_residuals", "trals_plan_mttsp", "trals_plan_core_dev",
     "trals_plan_launches_per_sweep",
-    "trals_gamma", "trals_coef_matrix", "trals_mttsp", "trals_mttsp_path", "trals_solve_chol", "trals_reconstruct",
+    "trals_gamma", "trals_coef_matrix", "trals_mttsp", "trals_mttsp_noalloc", "trals_mttsp_path", "trals_solve_chol", "trals_reconstruct",
     "trals_residual_explicit", "trals_quantize_bf16",
 ]
 
@@ -89,6 +89,7 @@ def lib() -> ctypes.CDLL:
         "trals_mttsp": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp,
                                        ctypes.c_int, _vp]),
         "trals_mttsp_path": (ctypes.c_int, [ctypes.c_int, _vp, _vp, ctypes.c_int, ctypes.c_int]),
+        "trals_mttsp_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
         "trals_solve_chol": (ctypes.c_int, [_vp, ctypes.c_int, _i64, ctypes.c_int, _vp, _vp, _vp]),
         "trals_reconstruct": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int]),
         "trals_residual_explicit": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp,
@@ -307,6 +308,14 @@ def trals_mttsp(ctx: Context, I, R, X_dev, mode, cores_dev: Sequence, n: int, M_
     ctx.check(lib().trals_mttsp(ctx.handle, N, ctypes.addressof(Ia), ctypes.addressof(Ra), _ptr(X_dev), _xtype(X_dev),
                                 int(mode), _ptr_array([_ptr(c) for c in cores_dev]), int(n), _ptr(M_dev)),
               "trals_mttsp")
+
+
+def trals_mttsp_noalloc(ctx: Context, I, R, X_dev, cores_dev: Sequence, n: int, M_dev) -> None:
+    """FP64 MTTSP of mode n with no device allocation (static scratch; see include/trals.h)."""
+    N, Ia, Ra = _shape(I, R)
+    ctx.check(lib().trals_mttsp_noalloc(ctx.handle, N, ctypes.addressof(Ia), ctypes.addressof(Ra), _ptr(X_dev),
+                                        _ptr_array([_ptr(c) for c in cores_dev]), int(n), _ptr(M_dev)),
+              "trals_mttsp_noalloc")
 
 
 MTTSP_PATHS = {0: "cuda-cores", 1: "tc-kmajor-left", 2: "tc-kmajor-right", 3: "tc-mnmajor"}
