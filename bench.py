@@ -1,11 +1,15 @@
 """Benchmark: TR-ALS sweeps/s on one GB300 (one step = one full ALS sweep over all N core updates).
 
-Default workload: the order-4 60x60x60x60 tensor (12.96M entries) generated as a TR of ranks 10
-with iid N(0,1) cores plus 1e-2 relative Gaussian noise; fit ranks 10; Cholesky normal
-equations with the structured Gamma-chain coefficient matrix.  The headline ``value`` is the
-reduced-precision mode (``--mode``, default bf16: X stored once as BF16, RHS contraction on
-tensor cores with FP32 accumulation, FP64 Gram chain and solve); the FP64 mode on the same
-workload is reported beside it under ``fp64``.
+Default workload: the order-5 40^5 tensor (102.4M entries) generated as a TR of ranks
+(8,10,12,10,8) with iid N(0,1) cores plus 1e-3 relative Gaussian noise; fit ranks (8,10,12,10,8);
+Cholesky normal equations with the structured Gamma-chain coefficient matrix.  The headline
+``value`` is the reduced-precision mode (``--mode``, default bf16: X stored once as BF16, RHS
+contraction on tensor cores with FP32 accumulation, FP64 Gram chain and solve); the FP64 mode on
+the same workload is reported beside it under ``fp64``.  ``--config`` selects another workload.
+
+The roofline object covers the dominant kernel, the RHS contraction (MTTSP, Alg. 2 lines 7-8):
+its main kernel is timed alone with CUDA events on the plan's stream after an L2 flush, once per
+mode; ``achieved`` = the bytes of X it must read (the algorithmic traffic) / that time.
 
 ``--impl reference`` times the CPU FP64 oracle (regular TR-ALS with the explicit subchain
 matrix, Alg. 1) on the same workload instead.
@@ -24,6 +28,7 @@ import time
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+METRIC = "TR-ALS sweeps/s at fixed rel. residual, mixed vs FP64; p50/p99 serving latency"
 sys.path.insert(0, ROOT)
 
 import trals_inputs as TI  # noqa: E402
@@ -52,7 +57,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -121,7 +126,7 @@ def mode_xdtype(mode, torch):
 
 
 # ----------------------------------------------------------------------------- GPU arm
-def time_mode(P, torch, w, X, mode, steps, warmup, seed, flush_buf):
+def time_mode(P, torch, w, X, mode, steps, warmup, seed, flush_buf, X_full):
     stream = torch.cuda.Stream()
     ctx = P.trals_create(0, stream)
     plan = P.Plan(ctx, w.I, w.R_fit, X, P.make_opts(mode))
@@ -145,26 +150,27 @@ def time_mode(P, torch, w, X, mode, steps, warmup, seed, flush_buf):
     times = [a.elapsed_time(b) for a, b in ev]
     res = plan.residuals()
     launches = plan.launches_per_sweep()
-    # dominant kernel: MTTSP of each mode, timed alone with events on the plan's stream
-    mt = []
+    # relative residual of the cores after the run, measured against the full-precision X
+    r2, x2 = P.trals_residual_explicit(ctx, w.I, w.R_fit, X_full, [plan.core_dev(n) for n in range(len(w.I))])
+    res_explicit = float(np.sqrt(max(r2, 0.0) / x2))
+    # dominant kernel: the MTTSP of each mode, its main kernel timed alone (events on the plan's
+    # stream, recorded by the library around that launch) after an L2 flush
+    kern, whole = [], []
     for n in range(len(w.I)):
-        reps = 5
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        per = []
-        for _ in range(reps):
+        per_k, per_t = [], []
+        for _ in range(7):
             with torch.cuda.stream(stream):
                 flush_buf.add_(1.0)
-                e0.record(stream)
-            plan.mttsp(n)
-            with torch.cuda.stream(stream):
-                e1.record(stream)
-            torch.cuda.synchronize()
-            per.append(e0.elapsed_time(e1))
-        mt.append(statistics.median(per))
+            k_ms, t_ms = plan.time_mttsp(n)
+            per_k.append(k_ms)
+            per_t.append(t_ms)
+        kern.append(statistics.median(per_k))
+        whole.append(statistics.median(per_t))
     plan.close()
     ctx.close()
-    return {"ms_per_step": sum(times) / len(times), "times": times, "residual": float(res[-1]) if len(res) else None,
-            "launches_per_sweep": launches, "mttsp_ms": mt, "clocks": clk}
+    return {"ms_per_step": sum(times) / len(times), "times": times, "residual": res_explicit,
+            "residual_in_sweep": float(res[-1]) if len(res) else None, "sweeps_run": warmup + steps,
+            "launches_per_sweep": launches, "mttsp_kernel_ms": kern, "mttsp_ms": whole, "clocks": clk}
 
 
 def e2e_run(P, torch, w, X_dev, mode, seed, sweeps):
@@ -185,6 +191,62 @@ def e2e_run(P, torch, w, X_dev, mode, seed, sweeps):
                                                                                  + core_bytes) / sweeps),
             "d2h_bytes_per_step": int((core_bytes + 8 * sweeps) / sweeps), "sweeps": sweeps,
             "residual": float(res[-1])}
+
+
+def serve_run(P, torch, seed, count, budget_bytes, slots, mode="bf16"):
+    """The serving workload: `count` TR-ALS requests with Poisson arrivals at 200/s, order uniform in
+    3-5, mode sizes uniform in 16-64, ranks uniform in 2-8, FP32 X = TR(N(0,1) cores) + 1e-2 relative
+    noise generated on the device from each request's seed, 15 sweeps each, run by the serving loop
+    (continuous batching).  X is generated before the clock starts (reported separately); latency is
+    arrival -> result back on the host, on the server's clock."""
+    reqs = TI.request_stream(seed, count)
+    ctx = P.trals_create(0)
+    data = []
+    t0 = time.perf_counter()
+    for q in reqs:
+        numel = int(np.prod(q.I))
+        cd = [P.core_to_device(G) for G in TI.gaussian_cores(q.seed, q.I, q.R)]
+        X = torch.empty(numel, dtype=torch.float32, device="cuda")
+        P.trals_reconstruct(ctx, q.I, q.R, cd, X)
+        g = torch.Generator(device="cuda")
+        g.manual_seed(q.seed)
+        noise = torch.randn(numel, generator=g, device="cuda", dtype=torch.float32)
+        X.add_(noise * (q.eta * torch.linalg.vector_norm(X) / torch.linalg.vector_norm(noise)))
+        del noise
+        data.append((X, TI.init_cores(q.seed, q.I, q.R)))
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    ctx.close()
+    opts = P.make_opts(mode)
+    srv = P.Server(0, hbm_budget_bytes=budget_bytes, max_slots=slots)
+    try:
+        tickets = []
+        start = time.perf_counter()
+        for q, (X, init) in zip(reqs, data):
+            delay = start + q.arrival_s - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(q.I, q.R, X, init, q.sweeps, opts))
+        out = [srv.wait(t, timeout=900.0) for t in tickets]
+        wall = time.perf_counter() - start
+        stats = srv.stats()
+    finally:
+        srv.close()
+    bad = [o for o in out if o is None or o[0]["status"] != P.OK]
+    lat = np.array([o[0]["done_s"] - o[0]["submit_s"] for o in out if o is not None])
+    first = min(o[0]["submit_s"] for o in out)
+    last = max(o[0]["done_s"] for o in out)
+    fin = np.array([o[2][-1] for o in out if o is not None])
+    sweeps = sum(q.sweeps for q in reqs)
+    return {"requests": count, "failed": len(bad), "p50_latency_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_latency_ms": float(np.percentile(lat, 99) * 1e3), "max_latency_ms": float(lat.max() * 1e3),
+            "throughput_req_s": count / (last - first), "sweeps_per_s": sweeps / (last - first),
+            "span_s": last - first, "wall_s": wall, "arrival_window_s": reqs[-1].arrival_s,
+            "data_generation_s": gen_s, "mode": mode, "slots": slots, "hbm_budget_gb": budget_bytes / 2**30,
+            "peak_active": stats["peak_active"], "peak_used_gb": stats["peak_used_bytes"] / 2**30,
+            "final_residual_median": float(np.median(fin)),
+            "workload": "512 requests, Poisson 200/s, order U{3..5}, sizes U{16..64}, ranks U{2..8}, "
+                        "FP32 X = TR + 1e-2 noise, 15 sweeps"}
 
 
 def cpu_baseline_run(w, seed, budget_s=20.0):
@@ -208,22 +270,48 @@ def cpu_baseline_run(w, seed, budget_s=20.0):
                       f"explicit subchain matrix, {dt:.1f} s"}
 
 
-def roofline_for(w, mode, mttsp_ms, peaks, src):
+def _recorded_traffic(config, mode):
+    """DRAM bytes per launch of the MTTSP main kernel, per mode, from the committed ncu summary of
+    this workload -- or None when the kernel source changed since that capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"mttsp_tc_{config}.md")
+    src = os.path.join(ROOT, "paper_2210_11362_gb300", "csrc", "mttsp_tc.cu")
+    if mode != "bf16" or not os.path.exists(path):
+        return None
+    rec = {}
+    with open(path) as f:
+        for ln in f:
+            if ln.startswith("kernel_source_sha256:"):
+                rec["sha"] = ln.split(":", 1)[1].strip()
+            elif ln.startswith("dram_bytes_per_launch:"):
+                rec["bytes"] = [float(v) for v in ln.split(":", 1)[1].split(",")]
+    with open(src) as f:
+        text = f.read()
+    # the kernel and its device helpers precede the host-side planner in the source
+    sha = hashlib.sha256(text[:text.index("TcChoice tc_choose(")].encode()).hexdigest()
+    if rec.get("sha") != sha or "bytes" not in rec:
+        return None
+    return rec["bytes"]
+
+
+def roofline_for(w, mode, kernel_ms, peaks, src):
     numel = w.numel
     N = len(w.I)
     esize = {"fp64": 8, "fp32": 4, "bf16": 2, "bf16x3": 4}[mode]
     bytes_per = numel * esize
     flops = [2.0 * numel * w.R_fit[n] * w.R_fit[(n + 1) % N] for n in range(N)]
-    t = sum(mttsp_ms) / N * 1e-3
+    t = sum(kernel_ms) * 1e-3          # all N launches
     if mode == "fp64":
-        achieved = sum(flops) / N / t / 1e12
+        achieved = sum(flops) / t / 1e12
         return {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
                 "frac": achieved / 1.25, "traffic": None,
-                "note": "FP64 FMA pipe; peak = GB300 nominal FP64 1.25 TFLOP/s"}
-    achieved = bytes_per / t / 1e9
+                "note": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz = 1.26 TFLOP/s (nominal 1.25)"}
+    achieved = N * bytes_per / t / 1e9
     peak = peaks["hbm_gbs"]
+    tr = _recorded_traffic(w.name, mode)
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "peak_source": src}
+            "traffic": (sum(tr) / len(tr)) if tr else None, "peak_source": f"{src} hbm_gbs (burst copy)",
+            "algorithmic_bytes_per_launch": bytes_per, "launch_ms_per_mode": kernel_ms}
 
 
 def run_ours(args):
@@ -244,7 +332,9 @@ def run_ours(args):
         X = X_f64 if mode == "fp64" else X_f64.to(mode_xdtype(mode, torch))
         if world > 1:
             torch.distributed.barrier()
-        out[mode] = time_mode(P, torch, w, X, mode, args.steps, args.warmup, args.seed, flush)
+        # the FP64 mode beside the headline runs ~60x slower per sweep: a tenth of the steps
+        steps = args.steps if mode == args.mode else max(10, args.steps // 10)
+        out[mode] = time_mode(P, torch, w, X, mode, steps, args.warmup, args.seed, flush, X_f64)
         out[mode]["X"] = X
     main = out[args.mode]
     ms = main["ms_per_step"]
@@ -256,7 +346,7 @@ def run_ours(args):
         return
     e2e = e2e_run(P, torch, w, main["X"], args.mode, args.seed, w.sweeps)
     line = {
-        "metric": "TR-ALS sweeps/s at fixed rel. residual (mixed vs FP64)",
+        "metric": METRIC,
         "value": world * 1000.0 / ms, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.mode],
@@ -264,7 +354,7 @@ def run_ours(args):
         "config": {"workload": w.name, "I": list(w.I), "R_fit": list(w.R_fit), "eta": w.eta, "mode": args.mode,
                    "solver": "cholesky", "gram": "structured", "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed between timed sweeps (256 MB write)", "residual_after_run": main["residual"]},
-        "roofline": roofline_for(w, args.mode, main["mttsp_ms"], peaks, src),
+        "roofline": roofline_for(w, args.mode, main["mttsp_kernel_ms"], peaks, src),
         "mttsp_ms_per_mode": main["mttsp_ms"],
         "gpu_launches": main["launches_per_sweep"] * args.steps,
         "clocks": main["clocks"],
@@ -272,10 +362,17 @@ def run_ours(args):
     }
     if "fp64" in out and args.mode != "fp64":
         f = out["fp64"]
-        line["fp64"] = {"value": 1000.0 / f["ms_per_step"], "ms_per_step": f["ms_per_step"],
+        line["fp64"] = {"value": 1000.0 / f["ms_per_step"], "ms_per_step": f["ms_per_step"], "steps": len(f["times"]),
                         "residual": f["residual"], "mttsp_ms_per_mode": f["mttsp_ms"],
-                        "roofline": roofline_for(w, "fp64", f["mttsp_ms"], peaks, src)}
+                        "roofline": roofline_for(w, "fp64", f["mttsp_kernel_ms"], peaks, src)}
         line["speedup_vs_fp64"] = f["ms_per_step"] / main["ms_per_step"]
+    if not args.no_serve:
+        for k in list(out):
+            out[k].pop("X", None)
+        X = X_f64 = flush = None
+        torch.cuda.empty_cache()
+        line["serving"] = serve_run(P, torch, args.seed, args.serve_requests, int(args.serve_budget_gb * 2**30),
+                                    args.serve_slots)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_run(w, args.seed, args.cpu_budget)
     print(json.dumps(line))
@@ -300,7 +397,7 @@ def run_reference(args):
         t.append(time.perf_counter() - t0)
     per_update = sum(t) / len(t)
     value = 1.0 / (N * per_update)
-    line = {"impl": "reference", "metric": "TR-ALS sweeps/s at fixed rel. residual (mixed vs FP64)",
+    line = {"impl": "reference", "metric": METRIC,
             "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * N * per_update, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -315,7 +412,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="tr40x5_r8-12", choices=sorted(TI.WORKLOADS))
@@ -324,6 +421,10 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=512)
+    ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -61,13 +61,16 @@ typedef enum {
 /* Element type of the caller's X. */
 typedef enum { TRALS_X_F64 = 0, TRALS_X_F32 = 1, TRALS_X_BF16 = 2 } trals_xtype;
 
-/* Arithmetic of the RHS contraction M_n (the Gram chain, S_n and the solve are FP64 in every mode).
- *  FP64  : X read as FP64, MTTSP in FP64.
- *  FP32  : X read as FP32, MTTSP on TF32 tensor cores with FP32 accumulation.
- *  BF16  : X quantised once to BF16 (round to nearest even), MTTSP on BF16
- *          tensor cores with FP32 accumulation.
- *  BF16X3: X split once into hi/lo BF16 pairs, subchain rows split likewise;
- *          three BF16 products per term (hi*hi + hi*lo + lo*hi), FP32 accumulation. */
+/* Storage of X and arithmetic of the RHS contraction M_n (the Gram chain, S_n and the solve are
+ * FP64 in every mode).
+ *  FP64  : X read as FP64, MTTSP in FP64 on the CUDA cores.
+ *  FP32  : X read as FP32 (converted once from FP64 if needed); MTTSP on the CUDA cores with FP64
+ *          arithmetic on the FP32 values.
+ *  BF16  : X quantised once to BF16 (round to nearest even); MTTSP on BF16 tensor cores
+ *          (tcgen05) with FP32 accumulation where trals_mttsp_path reports a tensor-core
+ *          geometry, else on the CUDA cores in FP64 arithmetic.
+ *  BF16X3: X split once into hi/lo BF16 pairs (hi = bf16(x), lo = bf16(x - hi)); MTTSP on the
+ *          CUDA cores reading hi + lo with FP64 arithmetic. */
 typedef enum { TRALS_MODE_FP64 = 0, TRALS_MODE_FP32 = 1, TRALS_MODE_BF16 = 2, TRALS_MODE_BF16X3 = 3 } trals_mode;
 
 /* Solver for the R_n R_{n+1} subproblem: Cholesky on the normal equations
@@ -82,8 +85,12 @@ typedef struct {
   int mode;              /* trals_mode */
   int solver;            /* trals_solver */
   int gram;              /* trals_gram */
-  int explicit_residual; /* 1: per-sweep residual by a full reconstruction pass against X (Sec. 4 formula);
-                            0: the cheap identity of Sec. 4 */
+  int explicit_residual; /* 1: per-sweep residual by a full reconstruction pass against X (Sec. 4 formula;
+                               FP64 reconstruction in the FP64 mode, FP32 in the others);
+                            0: the cheap identity of Sec. 4 in the FP64 mode.  The reduced-precision
+                               modes then record NaN per sweep: with BF16 rounding in M_N the
+                               identity's cancellation leaves no accurate digits at small residuals
+                               (trals_decompose still fills the last entry by one explicit pass). */
 } trals_opts;
 
 typedef struct trals_ctx trals_ctx;
@@ -113,7 +120,8 @@ const char* trals_version(void);
  *   cores[N]   host pointers; in: initial cores, out: fitted cores (FP64, layout above)
  *   opts       NULL = {FP64, CHOL, STRUCTURED, explicit_residual 0}
  *   rel_res    host array of `sweeps` doubles, out: relative residual |X - X_hat|_F/|X|_F
- *              after each sweep (may be NULL)
+ *              after each sweep (may be NULL); see trals_opts.explicit_residual for the
+ *              reduced-precision modes, whose last entry is always the explicit residual
  * Requires J_n = prod_{j != n} I_j >= R_n R_{n+1} for every n (else the
  * subproblem is underdetermined): TRALS_E_ARG.  Synchronous. */
 trals_status trals_decompose(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R,
@@ -126,9 +134,18 @@ trals_status trals_decompose(trals_ctx* ctx, int N, const int64_t* I, const int3
 /* A plan keeps X (device, caller-owned, must outlive the plan), the cores, the
  * Gamma_k caches and all workspace resident, so sweeps can be replayed (as one
  * captured CUDA graph per sweep) without host work.  Arguments as in
- * trals_decompose; X_dev is device memory. */
+ * trals_decompose; X_dev is device memory.  The workspace is allocated stream-ordered
+ * (cudaMallocAsync on the context's stream) and freed the same way by trals_plan_destroy,
+ * so plans can come and go while other streams keep the device busy. */
 trals_status trals_plan_create(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R,
                                const void* X_dev, int xt, const trals_opts* opts, trals_plan** out);
+/* Bytes of device workspace trals_plan_create would allocate for these arguments (X itself not
+ * included), computed on the host without allocating or launching anything: the admission
+ * figure of the serving loop.  X_dev is only inspected for alignment. */
+trals_status trals_plan_footprint(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R,
+                                  const void* X_dev, int xt, const trals_opts* opts, size_t* bytes);
+/* Bytes of device workspace a plan holds (equals trals_plan_footprint for its arguments). */
+size_t trals_plan_bytes(const trals_plan* plan);
 void trals_plan_destroy(trals_plan* plan);
 /* Upload cores (host pointers, FP64) and recompute every Gamma_k (Alg. 2 line 2).
  * Resets the sweep counter.  Synchronous. */
@@ -145,8 +162,23 @@ trals_status trals_plan_residuals(trals_plan* plan, double* rel_res_host, int ca
  * workspace, writing M_n (I_n x R_n R_{n+1}, FP64) to M_dev (NULL: the plan's internal buffer).
  * Allocates nothing; used to time and test the RHS contraction in isolation. */
 trals_status trals_plan_mttsp(trals_plan* plan, int n, double* M_dev);
+/* Measurement hook (the paper has no counterpart): enqueue the MTTSP of mode n once, exactly as a
+ * sweep does, with CUDA events around the whole step (table builds, contraction, reduction) and
+ * around its main contraction kernel alone; waits for it and returns both durations in
+ * milliseconds.  The caller may flush L2 on the context's stream beforehand.  Not for use while
+ * the stream is being captured. */
+/* Relative residual |X - TR(cores)|_F / |X|_F of the plan's current cores against the caller's X
+ * (the explicit error of Sec. 4), by one pass over X that regenerates X_hat: in FP64 in the FP64
+ * mode, in FP32 (differences and sums in FP64) in the reduced-precision modes, where the
+ * regeneration error (~1e-7 relative) is far below the residuals being compared.  Synchronous. */
+trals_status trals_plan_explicit_residual(trals_plan* plan, double* rel_res_host);
+trals_status trals_plan_time_mttsp(trals_plan* plan, int n, float* kernel_ms, float* total_ms);
 /* Device pointer of core n (FP64, layout above), valid until the plan is destroyed. */
 const double* trals_plan_core_dev(const trals_plan* plan, int n);
+/* Which kernel the plan uses for the MTTSP of mode n (codes of trals_mttsp_path).  This can differ
+ * from trals_mttsp_path when the TMA descriptor encoder rejects a tensor-core geometry or X is not
+ * 16-byte aligned: the plan then falls back to the CUDA cores. */
+int trals_plan_mttsp_path(const trals_plan* plan, int n);
 /* Number of kernel launches one sweep issues (for launch accounting). */
 int trals_plan_launches_per_sweep(const trals_plan* plan);
 
@@ -214,6 +246,74 @@ trals_status trals_residual_explicit(trals_ctx* ctx, int N, const int64_t* I, co
  * even).  If dst_lo_dev != NULL also write lo = bf16(x - float(hi)). */
 trals_status trals_quantize_bf16(trals_ctx* ctx, const void* src_dev, int src_t, int64_t count,
                                  void* dst_hi_dev, void* dst_lo_dev);
+
+/* ------------------------------------------------------------------------- serving
+ * A request loop that runs many TR decompositions at once on one GPU (continuous batching; the
+ * paper has no counterpart -- it runs one decomposition at a time).  Requests of any order, sizes
+ * and ranks are submitted from any host thread and queue in arrival order.  A worker thread admits
+ * the head of the queue as soon as a slot is free and the request's device footprint (the plan
+ * workspace of trals_plan_footprint, plus a device copy of X when X is on the host) fits in what
+ * is left of the HBM budget.  Each admitted request runs as a resident plan on its slot's own
+ * stream, all its sweeps enqueued as replays of the plan's captured per-sweep CUDA graph, so the
+ * work of every active request overlaps on the device.  A request computes exactly what
+ * trals_decompose computes for it alone: kernels are deterministic and slots share no device
+ * state, so results do not depend on what else is in flight. */
+typedef struct trals_server trals_server;
+
+typedef struct {
+  int N;                            /* order, 3 <= N <= TRALS_MAX_ORDER */
+  const int64_t* I;                 /* [N] mode sizes (copied at submit) */
+  const int32_t* R;                 /* [N] TR ranks (copied at submit) */
+  const void* X;                    /* column-major tensor of element type xt: device memory of the
+                                       server's device, or host memory when x_on_host != 0 (pinned
+                                       memory copies fastest).  Caller-owned; must stay valid and
+                                       unchanged until the result is ready. */
+  int xt;                           /* trals_xtype */
+  int x_on_host;
+  const double* const* init_cores;  /* [N] host pointers, initial cores (copied at submit) */
+  int sweeps;                       /* ALS sweeps to run */
+  trals_opts opts;                  /* as for trals_decompose */
+} trals_request;
+
+typedef struct {
+  trals_status status;     /* outcome of the decomposition (TRALS_OK, or its error) */
+  int sweeps;
+  double submit_s;         /* host clock, seconds since the server was created */
+  double admit_s;          /* when the request got a slot and its memory */
+  double done_s;           /* when its results were back on the host */
+  size_t footprint_bytes;  /* device memory it held while active */
+} trals_result;
+
+typedef struct {
+  int queued;              /* submitted, not yet admitted */
+  int active;              /* holding a slot */
+  uint64_t completed;
+  size_t used_bytes;       /* footprint of the active requests */
+  size_t peak_used_bytes;
+  int peak_active;
+} trals_server_info;
+
+/* Start a server on `device` with at most max_slots requests in flight whose footprints sum to at
+ * most hbm_budget_bytes.  Starts one worker thread. */
+trals_status trals_server_create(trals_server** out, int device, size_t hbm_budget_bytes, int max_slots);
+/* Stop the server: requests still queued are dropped, active ones finish; results not yet taken
+ * are freed.  Joins the worker thread. */
+void trals_server_destroy(trals_server* server);
+/* Queue a request (non-blocking).  TRALS_E_ARG for invalid shapes or arguments (see
+ * trals_decompose), TRALS_E_REJECTED when its footprint alone exceeds the budget. */
+trals_status trals_server_submit(trals_server* server, const trals_request* request, uint64_t* ticket);
+/* TRALS_E_PENDING while the request runs; TRALS_OK once it is done, after filling *result and
+ * copying the fitted cores (host pointers [N], core layout, may be NULL) and the per-sweep
+ * residuals (host array of `sweeps`, may be NULL; same semantics as trals_decompose).  The ticket
+ * is then released (a further poll returns TRALS_E_ARG). */
+trals_status trals_server_poll(trals_server* server, uint64_t ticket, trals_result* result,
+                               double* const* cores_out, double* rel_res_out);
+/* As trals_server_poll, but blocks up to timeout_s seconds (negative: no limit). */
+trals_status trals_server_wait(trals_server* server, uint64_t ticket, double timeout_s, trals_result* result,
+                               double* const* cores_out, double* rel_res_out);
+trals_status trals_server_stats(trals_server* server, trals_server_info* out);
+/* Message for the last rejected submit or failed request taken by poll/wait. */
+const char* trals_server_last_error(const trals_server* server);
 
 #ifdef __cplusplus
 }

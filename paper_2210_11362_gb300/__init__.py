@@ -36,10 +36,13 @@ GRAM_STRUCTURED, GRAM_EXPLICIT = 0, 1
 EXPORTED = [
     "trals_version", "trals_create", "trals_destroy", "trals_last_error", "trals_decompose",
     "trals_plan_create", "trals_plan_destroy", "trals_plan_set_cores", "trals_plan_get_cores",
-    "trals_plan_run", "trals_plan_residuals", "trals_plan_mttsp", "trals_plan_core_dev",
-    "trals_plan_launches_per_sweep",
+    "trals_plan_run", "trals_plan_residuals", "trals_plan_mttsp", "trals_plan_time_mttsp", "trals_plan_core_dev",
+    "trals_plan_explicit_residual", "trals_plan_footprint", "trals_plan_bytes",
+    "trals_plan_launches_per_sweep", "trals_plan_mttsp_path",
     "trals_gamma", "trals_coef_matrix", "trals_mttsp", "trals_mttsp_noalloc", "trals_mttsp_path", "trals_solve_chol", "trals_reconstruct",
     "trals_residual_explicit", "trals_quantize_bf16",
+    "trals_server_create", "trals_server_destroy", "trals_server_submit", "trals_server_poll",
+    "trals_server_wait", "trals_server_stats", "trals_server_last_error",
 ]
 
 
@@ -52,6 +55,23 @@ class TralsError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("solver", ctypes.c_int), ("gram", ctypes.c_int),
                 ("explicit_residual", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("I", ctypes.c_void_p), ("R", ctypes.c_void_p), ("X", ctypes.c_void_p),
+                ("xt", ctypes.c_int), ("x_on_host", ctypes.c_int), ("init_cores", ctypes.c_void_p),
+                ("sweeps", ctypes.c_int), ("opts", Opts)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("sweeps", ctypes.c_int), ("submit_s", ctypes.c_double),
+                ("admit_s", ctypes.c_double), ("done_s", ctypes.c_double), ("footprint_bytes", ctypes.c_size_t)]
+
+
+class ServerInfo(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int), ("active", ctypes.c_int), ("completed", ctypes.c_uint64),
+                ("used_bytes", ctypes.c_size_t), ("peak_used_bytes", ctypes.c_size_t),
+                ("peak_active", ctypes.c_int)]
 
 
 _lib = None
@@ -82,8 +102,15 @@ def lib() -> ctypes.CDLL:
         "trals_plan_run": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
         "trals_plan_residuals": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "trals_plan_mttsp": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+        "trals_plan_explicit_residual": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
+        "trals_plan_footprint": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp,
+                                                ctypes.POINTER(ctypes.c_size_t)]),
+        "trals_plan_bytes": (ctypes.c_size_t, [_vp]),
+        "trals_plan_time_mttsp": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                                                 ctypes.POINTER(ctypes.c_float)]),
         "trals_plan_core_dev": (_vp, [_vp, ctypes.c_int]),
         "trals_plan_launches_per_sweep": (ctypes.c_int, [_vp]),
+        "trals_plan_mttsp_path": (ctypes.c_int, [_vp, ctypes.c_int]),
         "trals_gamma": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _i64, ctypes.c_int, _vp]),
         "trals_coef_matrix": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp]),
         "trals_mttsp": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp,
@@ -95,6 +122,14 @@ def lib() -> ctypes.CDLL:
         "trals_residual_explicit": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp,
                                                    ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)]),
         "trals_quantize_bf16": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _i64, _vp, _vp]),
+        "trals_server_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_size_t, ctypes.c_int]),
+        "trals_server_destroy": (None, [_vp]),
+        "trals_server_submit": (ctypes.c_int, [_vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+        "trals_server_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(Result), _vp, _vp]),
+        "trals_server_wait": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(Result), _vp,
+                                             _vp]),
+        "trals_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(ServerInfo)]),
+        "trals_server_last_error": (ctypes.c_char_p, [_vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -268,8 +303,28 @@ class Plan:
     def mttsp(self, n: int, M_dev=None) -> None:
         self.ctx.check(lib().trals_plan_mttsp(self.handle, int(n), _ptr(M_dev)), "trals_plan_mttsp")
 
+    def explicit_residual(self) -> float:
+        """|X - TR(cores)|_F / |X|_F of the current cores by one explicit pass over X."""
+        v = ctypes.c_double()
+        self.ctx.check(lib().trals_plan_explicit_residual(self.handle, ctypes.byref(v)),
+                       "trals_plan_explicit_residual")
+        return float(v.value)
+
+    def nbytes(self) -> int:
+        return int(lib().trals_plan_bytes(self.handle))
+
+    def time_mttsp(self, n: int):
+        """(main contraction kernel ms, whole MTTSP step ms) of one enqueue of mode n."""
+        k, t = ctypes.c_float(), ctypes.c_float()
+        self.ctx.check(lib().trals_plan_time_mttsp(self.handle, int(n), ctypes.byref(k), ctypes.byref(t)),
+                       "trals_plan_time_mttsp")
+        return float(k.value), float(t.value)
+
     def core_dev(self, n: int) -> int:
         return lib().trals_plan_core_dev(self.handle, int(n))
+
+    def mttsp_path(self, n: int) -> int:
+        return lib().trals_plan_mttsp_path(self.handle, int(n))
 
     def launches_per_sweep(self) -> int:
         return lib().trals_plan_launches_per_sweep(self.handle)
@@ -399,9 +454,142 @@ def trals_plan_mttsp(plan: Plan, n: int, M_dev=None) -> None:
     plan.mttsp(n, M_dev)
 
 
+def trals_plan_explicit_residual(plan: Plan) -> float:
+    return plan.explicit_residual()
+
+
+def trals_plan_bytes(plan: Plan) -> int:
+    return plan.nbytes()
+
+
+def trals_plan_footprint(ctx: Context, I, R, X_dev, opts: Optional[Opts] = None) -> int:
+    """Device workspace bytes a plan for these arguments would allocate (host-side count)."""
+    N, Ia, Ra = _shape(I, R)
+    b = ctypes.c_size_t()
+    ctx.check(lib().trals_plan_footprint(ctx.handle, N, ctypes.addressof(Ia), ctypes.addressof(Ra), _ptr(X_dev),
+                                         _xtype(X_dev), ctypes.addressof(opts) if opts is not None else None,
+                                         ctypes.byref(b)), "trals_plan_footprint")
+    return int(b.value)
+
+
+def trals_plan_time_mttsp(plan: Plan, n: int):
+    return plan.time_mttsp(n)
+
+
 def trals_plan_core_dev(plan: Plan, n: int) -> int:
     return plan.core_dev(n)
 
 
+def trals_plan_mttsp_path(plan: Plan, n: int) -> int:
+    return plan.mttsp_path(n)
+
+
 def trals_plan_launches_per_sweep(plan: Plan) -> int:
     return plan.launches_per_sweep()
+
+
+# ------------------------------------------------------------------ serving
+class Server:
+    """The serving loop (trals_server_*): continuous batching of decompositions on one GPU."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 64 << 30, max_slots: int = 8):
+        h = _vp()
+        st = lib().trals_server_create(ctypes.byref(h), int(device), int(hbm_budget_bytes), int(max_slots))
+        if st != OK:
+            raise TralsError(st, "trals_server_create failed")
+        self.handle = h
+        self._pending = {}   # ticket -> (X, shapes): X must stay alive until the request is done
+
+    def _err(self, st, what):
+        raise TralsError(st, f"{what}: {lib().trals_server_last_error(self.handle).decode()}")
+
+    def submit(self, I, R, X, init_cores: Sequence[np.ndarray], sweeps: int, opts: Optional[Opts] = None) -> int:
+        N, Ia, Ra = _shape(I, R)
+        on_host = isinstance(X, np.ndarray) or not getattr(X, "is_cuda", True)
+        if isinstance(X, np.ndarray) and X.ndim > 1:
+            X = np.asarray(X).reshape(-1, order="F").copy()   # column-major contents, kept alive below
+        fc = cores_to_fortran(init_cores)
+        ptrs = _ptr_array([G.ctypes.data for G in fc])
+        q = Request(N, ctypes.addressof(Ia), ctypes.addressof(Ra), _ptr(X), _xtype(X), int(on_host),
+                    ctypes.addressof(ptrs), int(sweeps), opts if opts is not None else _opts())
+        t = ctypes.c_uint64()
+        st = lib().trals_server_submit(self.handle, ctypes.byref(q), ctypes.byref(t))
+        if st != OK:
+            self._err(st, "trals_server_submit")
+        self._pending[t.value] = (X, tuple(int(v) for v in I), tuple(int(v) for v in R), int(sweeps))
+        return t.value
+
+    def _take(self, ticket, fn, *extra):
+        if ticket not in self._pending:
+            raise TralsError(E_ARG, f"unknown or already taken ticket {ticket}")
+        X, I, R, sweeps = self._pending[ticket]
+        N = len(I)
+        out = [np.zeros(R[n] * I[n] * R[(n + 1) % N]) for n in range(N)]
+        res = np.zeros(max(sweeps, 1))
+        r = Result()
+        st = fn(self.handle, ctypes.c_uint64(ticket), *extra, ctypes.byref(r), _ptr_array([o.ctypes.data for o in out]),
+                res.ctypes.data)
+        if st == E_PENDING:
+            return None
+        if st != OK:
+            self._err(st, "trals_server_poll")
+        del self._pending[ticket]
+        cores = [o.reshape((R[n], I[n], R[(n + 1) % N]), order="F") for n, o in enumerate(out)]
+        info = {"status": r.status, "sweeps": r.sweeps, "submit_s": r.submit_s, "admit_s": r.admit_s,
+                "done_s": r.done_s, "footprint_bytes": r.footprint_bytes}
+        if r.status != OK:
+            info["error"] = lib().trals_server_last_error(self.handle).decode()
+        return info, cores, res[:sweeps]
+
+    def poll(self, ticket: int):
+        """None while pending, else (info dict, fitted cores, per-sweep residuals)."""
+        return self._take(ticket, lib().trals_server_poll)
+
+    def wait(self, ticket: int, timeout: float = -1.0):
+        return self._take(ticket, lib().trals_server_wait, ctypes.c_double(timeout))
+
+    def stats(self) -> dict:
+        s = ServerInfo()
+        st = lib().trals_server_stats(self.handle, ctypes.byref(s))
+        if st != OK:
+            self._err(st, "trals_server_stats")
+        return {f: getattr(s, f) for f, _ in ServerInfo._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().trals_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def trals_server_create(device: int = 0, hbm_budget_bytes: int = 64 << 30, max_slots: int = 8) -> Server:
+    return Server(device, hbm_budget_bytes, max_slots)
+
+
+def trals_server_destroy(server: Server) -> None:
+    server.close()
+
+
+def trals_server_submit(server: Server, I, R, X, init_cores, sweeps: int, opts: Optional[Opts] = None) -> int:
+    return server.submit(I, R, X, init_cores, sweeps, opts)
+
+
+def trals_server_poll(server: Server, ticket: int):
+    return server.poll(ticket)
+
+
+def trals_server_wait(server: Server, ticket: int, timeout: float = -1.0):
+    return server.wait(ticket, timeout)
+
+
+def trals_server_stats(server: Server) -> dict:
+    return server.stats()
+
+
+def trals_server_last_error(server: Server) -> str:
+    return lib().trals_server_last_error(server.handle).decode()

@@ -83,28 +83,38 @@ __device__ __forceinline__ double ld<__nv_bfloat16>(const void* p, int64_t i) {
   return (double)__bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]);
 }
 
-// Subchain rows of one tile: Gs[kk * r + (a + Rn b)] = sum_c Ltab[l][b + Rn1 c] Utab[u][c + Rs a]
+// Subchain rows of one tile: Gs[kk * r + (a + Rn b)] = sum_c Ltab[l][b + Rn1 c] Utab[u][c + Rs a].
+// base[] needs room for 3 KT entries: the X offsets of the tile's columns, then l and u per column.
 __device__ __forceinline__ void gen_tile(const ModeLayout& L, const double* __restrict__ ltab,
                                          const double* __restrict__ utab, const int64_t* __restrict__ offL,
                                          const int64_t* __restrict__ offU, int64_t kbase, int64_t kend, double* Gs,
                                          int64_t* base) {
   const int r = L.Rn * L.Rn1;
-  for (int e = threadIdx.x; e < KT * r; e += blockDim.x) {
-    const int kk = e / r, rr = e % r;
+  int64_t* lrow = base + KT;
+  int64_t* urow = lrow + KT;
+  __syncthreads();   // the previous tile's readers of base are done
+  for (int kk = threadIdx.x; kk < KT; kk += blockDim.x) {
     const int64_t k = kbase + kk;
-    double acc = 0.0;
     if (k < kend) {
       const int64_t l = k % L.nL, u = k / L.nL;
+      lrow[kk] = l;
+      urow[kk] = u;
+      base[kk] = offL[l] + offU[u];
+    } else {
+      base[kk] = -1;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < KT * r; e += blockDim.x) {
+    const int kk = e / r, rr = e % r;
+    double acc = 0.0;
+    if (base[kk] >= 0) {
       const int a = rr % L.Rn, b = rr / L.Rn;
-      const double* Lp = ltab + l * (int64_t)L.Rn1 * L.Rs;
-      const double* Up = utab + u * (int64_t)L.Rs * L.Rn;
+      const double* Lp = ltab + lrow[kk] * (int64_t)L.Rn1 * L.Rs;
+      const double* Up = utab + urow[kk] * (int64_t)L.Rs * L.Rn;
       for (int c = 0; c < L.Rs; ++c) acc = fma(Lp[b + L.Rn1 * c], Up[c + L.Rs * a], acc);
     }
     Gs[e] = acc;
-  }
-  for (int kk = threadIdx.x; kk < KT; kk += blockDim.x) {
-    const int64_t k = kbase + kk;
-    base[kk] = (k < kend) ? offL[k % L.nL] + offU[k / L.nL] : -1;
   }
 }
 
@@ -239,7 +249,327 @@ __global__ void __launch_bounds__(THREADS) reconstruct_kernel(const double* __re
   }
 }
 
+// ---- MTTSP on CUDA cores in FP32 arithmetic (reduced-precision modes, shapes the tensor-core
+// kernel does not take).
+//
+// Columns of X_[n] are visited in memory order t = p + K_pre q (p over the modes before n, q over the
+// modes after n), which is a permutation of the subchain order k = q + Q p; the sum over k does not
+// depend on the order.  A tile holds FKT consecutive t: its X block is read coalesced, its subchain
+// rows are generated from FP32 copies of the two partial-chain tables, and each thread accumulates
+// a 4 x 4 block of M_n (rows i_n, columns a + R_n b) in FP32.  Per-CTA partials go out in FP64.
+constexpr int FKT = 64;
+constexpr int kF32CtasPerSm = 6;
+
+template <typename XT>
+__global__ void __launch_bounds__(THREADS, 4) mttsp_simt_f32_kernel(const void* __restrict__ X,
+                                                                 const void* __restrict__ Xlo,
+                                                                 const float* __restrict__ ltab,
+                                                                 const float* __restrict__ utab,
+                                                                 const int64_t* __restrict__ offL,
+                                                                 const int64_t* __restrict__ offU, ModeLayout L,
+                                                                 int64_t Kpre, int64_t Q, double* __restrict__ partials) {
+  extern __shared__ float fs[];
+  const int r = L.Rn * L.Rn1;
+  const int In = (int)L.In;
+  const int rp = (r + 3) & ~3, inp = (In + 3) & ~3;
+  float* Gs = fs;                          // [FKT][rp]
+  float* Xs = Gs + FKT * rp;               // [FKT][inp]
+  int64_t* base = reinterpret_cast<int64_t*>(Xs + FKT * inp);
+  int64_t* lrow = base + FKT;              // table rows of column kk: Left l(k) and Right u(k)
+  int64_t* urow = lrow + FKT;
+  const int nrq = rp / 4, niq = inp / 4;
+  const int mt = blockIdx.y * THREADS + threadIdx.x;
+  const bool active = mt < nrq * niq;
+  const int rq = mt % nrq, iq = mt / nrq;
+  const int64_t chunk = (L.J + gridDim.x - 1) / gridDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * chunk;
+  const int64_t t1 = min(L.J, t0 + chunk);
+  float acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+  for (int64_t tb = t0; tb < t1; tb += FKT) {
+    // index arithmetic once per column (64-bit divisions are costly)
+    for (int kk = threadIdx.x; kk < FKT; kk += blockDim.x) {
+      const int64_t t = tb + kk;
+      if (t < t1) {
+        const int64_t k = t / Kpre + Q * (t % Kpre);
+        const int64_t l = k % L.nL, u = k / L.nL;
+        lrow[kk] = l;
+        urow[kk] = u;
+        base[kk] = offL[l] + offU[u];
+      } else {
+        base[kk] = -1;
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < FKT * rp; e += blockDim.x) {
+      const int kk = e / rp, rr = e % rp;
+      float g = 0.f;
+      if (base[kk] >= 0 && rr < r) {
+        const int a = rr % L.Rn, b = rr / L.Rn;
+        const float* Lp = ltab + lrow[kk] * (int64_t)L.Rn1 * L.Rs;
+        const float* Up = utab + urow[kk] * (int64_t)L.Rs * L.Rn;
+        for (int c = 0; c < L.Rs; ++c) g = fmaf(Lp[b + L.Rn1 * c], Up[c + L.Rs * a], g);
+      }
+      Gs[e] = g;
+    }
+    for (int e = threadIdx.x; e < FKT * inp; e += blockDim.x) {
+      int i, kk;
+      if (Kpre == 1) {   // mode 0: memory is contiguous along i
+        i = e % inp;
+        kk = e / inp;
+      } else {           // memory is contiguous along t
+        kk = e % FKT;
+        i = e / FKT;
+      }
+      const int64_t bo = base[kk];
+      float v = 0.f;
+      if (i < In && bo >= 0) {
+        const int64_t off = bo + (int64_t)i * L.strideN;
+        v = (float)ld<XT>(X, off);
+        if (Xlo != nullptr) v += (float)ld<XT>(Xlo, off);   // split-BF16 pair: hi + lo
+      }
+      Xs[kk * inp + i] = v;
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll 4
+      for (int kk = 0; kk < FKT; ++kk) {
+        const float4 xv = *reinterpret_cast<const float4*>(Xs + kk * inp + 4 * iq);
+        const float4 gv = *reinterpret_cast<const float4*>(Gs + kk * rp + 4 * rq);
+        const float xa[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          acc[u][0] = fmaf(xa[u], gv.x, acc[u][0]);
+          acc[u][1] = fmaf(xa[u], gv.y, acc[u][1]);
+          acc[u][2] = fmaf(xa[u], gv.z, acc[u][2]);
+          acc[u][3] = fmaf(xa[u], gv.w, acc[u][3]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (!active) return;
+  const int64_t outN = (int64_t)In * r;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = 4 * iq + u;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int rr = 4 * rq + v;
+      if (i < In && rr < r) partials[(int64_t)blockIdx.x * outN + i + (int64_t)In * rr] = (double)acc[u][v];
+    }
+  }
+}
+
+// ---- explicit residual with X_hat regenerated in FP32 (reduced-precision modes)
+//
+// |X - X_hat|^2 and |X|^2 against the caller's full-precision X, with X_hat = G_{n(2)} (G^{!=n}_[2])^T
+// (Sec. 1 element formula, unfolded) evaluated in FP32 from FP32 copies of the subchain tables and
+// of core n; the differences are formed and squared in FP64.  The FP32 regeneration error (about
+// 1e-7 relative to |X_hat|) is far below what the residual is compared against (1e-4), while the
+// FP64 arithmetic of the reconstruction above would cost ~100x more on GB300's FP64 pipe.
+constexpr int RKT = 128;          // columns of X_[n] per tile
+constexpr int RIC = 32;           // rows of X_[n] per chunk: 8 warps x 4 rows
+
+__global__ void tables_to_f32_kernel(const double* __restrict__ a, int64_t na, float* __restrict__ fa,
+                                     const double* __restrict__ b, int64_t nb, float* __restrict__ fb) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < na + nb; e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < na)
+      fa[e] = (float)a[e];
+    else
+      fb[e - na] = (float)b[e - na];
+  }
+}
+
+template <typename XT>
+__global__ void __launch_bounds__(THREADS) residual_f32_kernel(const float* __restrict__ ltab,
+                                                               const float* __restrict__ utab,
+                                                               const int64_t* __restrict__ offL,
+                                                               const int64_t* __restrict__ offU, ModeLayout L,
+                                                               const double* __restrict__ coreN,
+                                                               const void* __restrict__ X, double* __restrict__ partials) {
+  extern __shared__ float fsm[];
+  __shared__ double red[2][THREADS / 32];
+  const int r = L.Rn * L.Rn1;
+  const int64_t In = L.In;
+  float* Gt = fsm;                         // [r][RKT]: subchain rows, transposed
+  float* Cs = Gt + (size_t)r * RKT;        // [RIC][r]: rows of G_{n(2)}
+  int64_t* base = reinterpret_cast<int64_t*>(Cs + (size_t)RIC * r + 4);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t chunk = (L.J + gridDim.x - 1) / gridDim.x;
+  const int64_t k0 = (int64_t)blockIdx.x * chunk;
+  const int64_t k1 = min(L.J, k0 + chunk);
+  double d2 = 0.0, x2 = 0.0;
+  int64_t* lrow = base + RKT;
+  int64_t* urow = lrow + RKT;
+  for (int64_t kb = k0; kb < k1; kb += RKT) {
+    for (int kk = threadIdx.x; kk < RKT; kk += blockDim.x) {
+      const int64_t k = kb + kk;
+      if (k < k1) {
+        const int64_t l = k % L.nL, u = k / L.nL;
+        lrow[kk] = l;
+        urow[kk] = u;
+        base[kk] = offL[l] + offU[u];
+      } else {
+        base[kk] = -1;
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < RKT * r; e += blockDim.x) {
+      const int kk = e % RKT, rr = e / RKT;
+      float acc = 0.f;
+      if (base[kk] >= 0) {
+        const int a = rr % L.Rn, b = rr / L.Rn;
+        const float* Lp = ltab + lrow[kk] * (int64_t)L.Rn1 * L.Rs;
+        const float* Up = utab + urow[kk] * (int64_t)L.Rs * L.Rn;
+        for (int c = 0; c < L.Rs; ++c) acc = fmaf(Lp[b + L.Rn1 * c], Up[c + L.Rs * a], acc);
+      }
+      Gt[rr * RKT + kk] = acc;
+    }
+    for (int64_t i0 = 0; i0 < In; i0 += RIC) {
+      __syncthreads();   // Gt/base written; previous chunk's Cs reads done
+      for (int e = threadIdx.x; e < RIC * r; e += blockDim.x) {
+        const int ii = e / r, c = e % r;
+        const int64_t i = i0 + ii;
+        const int a = c % L.Rn, b = c / L.Rn;
+        Cs[ii * r + c] = (i < In) ? (float)coreN[a + (int64_t)L.Rn * (i + In * b)] : 0.f;
+      }
+      __syncthreads();
+      // micro-tile: rows i0 + 4 warp .. +3, columns 4 lane .. +3
+      float acc[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+      const float* C0 = Cs + (warp * 4) * r;
+      for (int c = 0; c < r; ++c) {
+        const float4 g = *reinterpret_cast<const float4*>(Gt + c * RKT + 4 * lane);
+        const float cv[4] = {C0[c], C0[r + c], C0[2 * r + c], C0[3 * r + c]};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          acc[u][0] = fmaf(cv[u], g.x, acc[u][0]);
+          acc[u][1] = fmaf(cv[u], g.y, acc[u][1]);
+          acc[u][2] = fmaf(cv[u], g.z, acc[u][2]);
+          acc[u][3] = fmaf(cv[u], g.w, acc[u][3]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t i = i0 + warp * 4 + u;
+        if (i >= In) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int64_t bo = base[4 * lane + v];
+          if (bo < 0) continue;
+          const double xv = ld<XT>(X, bo + i * L.strideN);
+          const double d = xv - (double)acc[u][v];
+          d2 = fma(d, d, d2);
+          x2 = fma(xv, xv, x2);
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+    x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+  }
+  if (lane == 0) {
+    red[0][warp] = d2;
+    red[1][warp] = x2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < THREADS / 32; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    partials[2 * blockIdx.x] = a;
+    partials[2 * blockIdx.x + 1] = b;
+  }
+}
+
 }  // namespace
+
+size_t mttsp_simt_f32_smem(const ModeLayout& L) {
+  const int r = L.Rn * L.Rn1;
+  const int64_t rp = (r + 3) & ~3, inp = (L.In + 3) & ~3;
+  return (size_t)(FKT * (rp + inp)) * sizeof(float) + 3 * FKT * sizeof(int64_t);
+}
+
+bool mttsp_simt_f32_fits(const ModeLayout& L) { return L.In <= 4096 && mttsp_simt_f32_smem(L) <= 200 * 1024; }
+
+int mttsp_simt_f32_grid(const ModeLayout& L) {
+  const int r = L.Rn * L.Rn1;
+  const int64_t mts = (int64_t)((r + 3) / 4) * ((L.In + 3) / 4);
+  const int64_t gy = (mts + THREADS - 1) / THREADS;
+  // several CTAs per SM: each tile is a short chain of dependent steps, so SMs need many in flight
+  const int64_t tiles = (L.J + FKT - 1) / FKT;
+  const int64_t by_partials = ((int64_t)8 << 20) / std::max<int64_t>(1, L.In * r);   // partials <= 64 MB
+  return (int)std::max<int64_t>(
+      1, std::min<int64_t>({tiles / 4, std::max<int64_t>(1, 152 * kF32CtasPerSm / gy), by_partials}));
+}
+
+void launch_mttsp_simt_f32(const MttspSimtArgs& a, const float* fl, const float* fu, cudaStream_t s) {
+  const ModeLayout& L = a.L;
+  const int r = L.Rn * L.Rn1;
+  const int64_t outN = L.In * r;
+  const int64_t mts = (int64_t)((r + 3) / 4) * ((L.In + 3) / 4);
+  dim3 grid(a.gridX, (unsigned)((mts + THREADS - 1) / THREADS));
+  const int64_t Kpre = L.strideN;
+  const int64_t Q = L.J / Kpre;
+  const size_t smem = mttsp_simt_f32_smem(L);
+  if (a.ev0) cudaEventRecord(a.ev0, s);
+  if (a.xt == TRALS_X_F32)
+    mttsp_simt_f32_kernel<float><<<grid, THREADS, smem, s>>>(a.X, nullptr, fl, fu, a.offL, a.offU, L, Kpre, Q,
+                                                             a.partials);
+  else if (a.xt == TRALS_X_BF16)
+    mttsp_simt_f32_kernel<__nv_bfloat16><<<grid, THREADS, smem, s>>>(a.X, a.Xlo, fl, fu, a.offL, a.offU, L, Kpre, Q,
+                                                                     a.partials);
+  else
+    mttsp_simt_f32_kernel<double><<<grid, THREADS, smem, s>>>(a.X, nullptr, fl, fu, a.offL, a.offU, L, Kpre, Q,
+                                                              a.partials);
+  if (a.ev1) cudaEventRecord(a.ev1, s);
+  const int rg = (int)std::min<int64_t>((outN + 255) / 256, 152 * 8);
+  reduce_partials_kernel<<<rg, 256, 0, s>>>(a.partials, a.gridX, outN, a.M);
+}
+
+void launch_tables_to_f32(const double* a, int64_t na, float* fa, const double* b, int64_t nb, float* fb,
+                          cudaStream_t s) {
+  const int g = (int)std::max<int64_t>(1, std::min<int64_t>((na + nb + 255) / 256, 152 * 4));
+  tables_to_f32_kernel<<<g, 256, 0, s>>>(a, na, fa, b, nb, fb);
+}
+
+size_t residual_f32_smem(const ModeLayout& L) {
+  const int r = L.Rn * L.Rn1;
+  return ((size_t)r * RKT + (size_t)RIC * r + 4) * sizeof(float) + 3 * RKT * sizeof(int64_t);
+}
+
+int residual_f32_grid(const ModeLayout& L) {
+  const int64_t tiles = (L.J + RKT - 1) / RKT;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, 152 * 2));
+}
+
+void launch_residual_f32(const ModeLayout& L, const double* ltab, const double* utab, float* ftab, int64_t ltab_elems,
+                         int64_t utab_elems, const int64_t* offL, const int64_t* offU, const double* coreN,
+                         const void* X, int xt, double* partials, int gridX, cudaStream_t s) {
+  float* fl = ftab;
+  float* fu = ftab + ltab_elems;
+  const int g = (int)std::min<int64_t>((ltab_elems + utab_elems + 255) / 256, 152 * 4);
+  tables_to_f32_kernel<<<g, 256, 0, s>>>(ltab, ltab_elems, fl, utab, utab_elems, fu);
+  const size_t smem = residual_f32_smem(L);
+  if (xt == TRALS_X_F32)
+    residual_f32_kernel<float><<<gridX, THREADS, smem, s>>>(fl, fu, offL, offU, L, coreN, X, partials);
+  else if (xt == TRALS_X_BF16)
+    residual_f32_kernel<__nv_bfloat16><<<gridX, THREADS, smem, s>>>(fl, fu, offL, offU, L, coreN, X, partials);
+  else
+    residual_f32_kernel<double><<<gridX, THREADS, smem, s>>>(fl, fu, offL, offU, L, coreN, X, partials);
+}
 
 size_t mttsp_simt_partials_elems(const ModeLayout& L, int gridX) {
   return (size_t)gridX * (size_t)(L.In * L.Rn * L.Rn1);
@@ -252,7 +582,7 @@ int mttsp_simt_default_grid(const ModeLayout& L) {
 
 static size_t simt_smem(const ModeLayout& L) {
   const int r = L.Rn * L.Rn1;
-  return (size_t)KT * r * sizeof(double) + (size_t)L.In * KT * sizeof(double) + KT * sizeof(int64_t);
+  return (size_t)KT * r * sizeof(double) + (size_t)L.In * KT * sizeof(double) + 3 * KT * sizeof(int64_t);
 }
 
 void launch_mttsp_simt(const MttspSimtArgs& a, cudaStream_t s) {
@@ -260,6 +590,7 @@ void launch_mttsp_simt(const MttspSimtArgs& a, cudaStream_t s) {
   const int64_t outN = L.In * L.Rn * L.Rn1;
   dim3 grid(a.gridX, (unsigned)((outN + OUTC - 1) / OUTC));
   const size_t smem = simt_smem(L);
+  if (a.ev0) cudaEventRecord(a.ev0, s);
   if (a.xt == TRALS_X_F64)
     mttsp_simt_kernel<double><<<grid, THREADS, smem, s>>>(a.X, nullptr, a.ltab, a.utab, a.offL, a.offU, L, a.partials);
   else if (a.xt == TRALS_X_F32)
@@ -267,12 +598,27 @@ void launch_mttsp_simt(const MttspSimtArgs& a, cudaStream_t s) {
   else
     mttsp_simt_kernel<__nv_bfloat16><<<grid, THREADS, smem, s>>>(a.X, a.Xlo, a.ltab, a.utab, a.offL, a.offU, L,
                                                                    a.partials);
+  if (a.ev1) cudaEventRecord(a.ev1, s);
   const int rg = (int)std::min<int64_t>((outN + 255) / 256, 152 * 8);
   reduce_partials_kernel<<<rg, 256, 0, s>>>(a.partials, a.gridX, outN, a.M);
 }
 
 cudaError_t init_simt_attributes() {
   cudaError_t e = cudaFuncSetAttribute(mttsp_simt_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mttsp_simt_f32_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mttsp_simt_f32_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mttsp_simt_f32_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(residual_f32_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(residual_f32_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(residual_f32_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(mttsp_simt_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e == cudaSuccess)
@@ -284,7 +630,7 @@ void launch_reconstruct(const ModeLayout& L, const double* ltab, const double* u
                         const int64_t* offU, const double* coreN, void* out, int out_t, const void* X, int xt,
                         double* partials, int gridX, cudaStream_t s) {
   const int r = L.Rn * L.Rn1;
-  const size_t smem = (size_t)KT * r * sizeof(double) + KT * sizeof(int64_t);
+  const size_t smem = (size_t)KT * r * sizeof(double) + 3 * KT * sizeof(int64_t);
 #define TRALS_RECON(XT_, OT_) \
   reconstruct_kernel<XT_, OT_><<<gridX, THREADS, smem, s>>>(ltab, utab, offL, offU, L, coreN, (OT_*)out, X, partials)
   if (out == nullptr || out_t == TRALS_X_F64) {

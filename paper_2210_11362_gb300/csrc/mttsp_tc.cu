@@ -774,7 +774,7 @@ TcChoice tc_choose(int N, const int64_t* I, const int32_t* R, int n) {
 }
 
 int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mode, const void* X, int64_t numel,
-            cudaError_t* err) {
+            cudaError_t* err, cudaStream_t s, size_t* count_bytes) {
   if (err) *err = cudaSuccess;
   p.valid = false;
   if (mode != TRALS_MODE_BF16) return 0;
@@ -896,47 +896,7 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   }
   impl->E = In * r;
 
-  // ---- allocations
-  cudaError_t e = cudaSuccess;
-  auto alloc = [&](void** q, size_t bytes) {
-    if (e != cudaSuccess) return;
-    e = cudaMalloc(q, std::max<size_t>(bytes, 16));
-    if (e == cudaSuccess) p.allocs.push_back(*q);
-  };
-  const int64_t chainMax = std::max(chain_max_elems(impl->s_modes, I, R, N), chain_max_elems(impl->f_modes, I, R, N));
-  int64_t nfac = 1;
-  for (int m : impl->f_modes) nfac *= I[m];
-  impl->n_fac_total = nfac;
-  for (int j = 0; j < N; ++j) impl->core_off[j + 1] = impl->core_off[j] + (int64_t)R[j] * I[j] * R[(j + 1) % N];
-  alloc(reinterpret_cast<void**>(&impl->cores32), (size_t)impl->core_off[N] * sizeof(float));
-  alloc(reinterpret_cast<void**>(&impl->chainA), chainMax * sizeof(float));
-  alloc(reinterpret_cast<void**>(&impl->chainB), chainMax * sizeof(float));
-  alloc(reinterpret_cast<void**>(&impl->tab), (size_t)A.W_pad * impl->Kpad * sizeof(__nv_bfloat16));
-  alloc(reinterpret_cast<void**>(&impl->F), (size_t)nfac * A.NX * impl->SYP * sizeof(float));
-  alloc(reinterpret_cast<void**>(&impl->partials), (size_t)impl->grid * impl->E * sizeof(float));
-  if (e != cudaSuccess) {
-    if (err) *err = e;
-    delete impl;
-    for (void* q : p.allocs) cudaFree(q);
-    p.allocs.clear();
-    return 0;
-  }
-  A.F = impl->F;
-  A.partials = impl->partials;
-  // ---- tensor maps
-  bool ok = encode_bf16(&impl->tmX, X, 3, dims, strides, box);
-  {
-    uint64_t td[2] = {(uint64_t)impl->Kpad, (uint64_t)A.W_pad};
-    uint64_t ts[1] = {(uint64_t)impl->Kpad * 2};
-    uint32_t tb[2] = {kKT, (uint32_t)A.W_pad};
-    ok = ok && encode_bf16(&impl->tmT, impl->tab, 2, td, ts, tb);
-  }
-  if (!ok) {
-    delete impl;
-    for (void* q : p.allocs) cudaFree(q);
-    p.allocs.clear();
-    return 0;
-  }
+  // ---- shared-memory plan (checked before anything is allocated)
   const int bBytes = ((A.W_pad * 128) + 1023) & ~1023;
   const size_t fixed = 1024 + (size_t)kRows * A.fs_stride * 4 +
                        (size_t)((In * A.ms_stride + 1) & ~1) * 4 + (2 * kNSMax + 4) * 8 + 64;
@@ -944,8 +904,6 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   const int ns = (int)std::min<size_t>(kNSMax, fixed < (size_t)kSmemBudget ? (kSmemBudget - fixed) / stage : 0);
   if (ns < 2) {
     delete impl;
-    for (void* q : p.allocs) cudaFree(q);
-    p.allocs.clear();
     return 0;
   }
   A.ns = ns;
@@ -956,10 +914,69 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
     const size_t need = (size_t)kRows * ((A.NX * A.NY) | 1) * 4;
     if (need > stage_area) {
       delete impl;
-      for (void* q : p.allocs) cudaFree(q);
-      p.allocs.clear();
       return 0;
     }
+  }
+
+  // ---- tensor maps: validated before anything is allocated, so that the counting pass and the real
+  // plan agree on whether this mode runs on the tensor cores (the table's map is encoded again once
+  // the table exists; the encoder only checks the address's alignment)
+  const uint64_t tdims[2] = {(uint64_t)impl->Kpad, (uint64_t)A.W_pad};
+  const uint64_t tstrides[1] = {(uint64_t)impl->Kpad * 2};
+  const uint32_t tbox[2] = {kKT, (uint32_t)A.W_pad};
+  if (!encode_bf16(&impl->tmX, X, 3, dims, strides, box) ||
+      !encode_bf16(&impl->tmT, reinterpret_cast<const void*>(uintptr_t(1) << 40), 2, tdims, tstrides, tbox)) {
+    delete impl;
+    return 0;
+  }
+
+  // ---- allocations (stream-ordered on s; in the counting pass only summed)
+  const int64_t chainMax = std::max(chain_max_elems(impl->s_modes, I, R, N), chain_max_elems(impl->f_modes, I, R, N));
+  int64_t nfac = 1;
+  for (int m : impl->f_modes) nfac *= I[m];
+  impl->n_fac_total = nfac;
+  for (int j = 0; j < N; ++j) impl->core_off[j + 1] = impl->core_off[j] + (int64_t)R[j] * I[j] * R[(j + 1) % N];
+  const size_t sizes[6] = {(size_t)impl->core_off[N] * sizeof(float), chainMax * sizeof(float),
+                           chainMax * sizeof(float), (size_t)A.W_pad * impl->Kpad * sizeof(__nv_bfloat16),
+                           (size_t)nfac * A.NX * impl->SYP * sizeof(float),
+                           (size_t)impl->grid * impl->E * sizeof(float)};
+  if (count_bytes) {
+    for (size_t b : sizes) *count_bytes += (std::max<size_t>(b, 16) + 255) & ~(size_t)255;
+    delete impl;
+    return 1;
+  }
+  p.stream = s;
+  cudaError_t e = cudaSuccess;
+  void* q[6] = {};
+  p.bytes = 0;
+  for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
+    const size_t b = (std::max<size_t>(sizes[k], 16) + 255) & ~(size_t)255;
+    e = cudaMallocAsync(&q[k], b, s);
+    if (e == cudaSuccess) {
+      p.allocs.push_back(q[k]);
+      p.bytes += b;
+    }
+  }
+  if (e != cudaSuccess) {
+    if (err) *err = e;
+    delete impl;
+    for (void* a : p.allocs) cudaFreeAsync(a, s);
+    p.allocs.clear();
+    return 0;
+  }
+  impl->cores32 = static_cast<float*>(q[0]);
+  impl->chainA = static_cast<float*>(q[1]);
+  impl->chainB = static_cast<float*>(q[2]);
+  impl->tab = static_cast<__nv_bfloat16*>(q[3]);
+  impl->F = static_cast<float*>(q[4]);
+  impl->partials = static_cast<float*>(q[5]);
+  A.F = impl->F;
+  A.partials = impl->partials;
+  if (!encode_bf16(&impl->tmT, impl->tab, 2, tdims, tstrides, tbox)) {
+    delete impl;
+    for (void* a : p.allocs) cudaFreeAsync(a, s);
+    p.allocs.clear();
+    return 0;
   }
   p.impl = impl;
   p.valid = true;
@@ -970,7 +987,8 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   return 1;
 }
 
-int tc_enqueue(TcPlan& p, const void* X, double* const* cores, double* M, cudaStream_t s) {
+int tc_enqueue(TcPlan& p, const void* X, double* const* cores, double* M, cudaStream_t s, cudaEvent_t ev0,
+               cudaEvent_t ev1) {
   TcImpl* impl = static_cast<TcImpl*>(p.impl);
   (void)X;
   int launches = 0;
@@ -1008,6 +1026,7 @@ int tc_enqueue(TcPlan& p, const void* X, double* const* cores, double* M, cudaSt
                                       impl->SYP, impl->F);
     ++launches;
   }
+  if (ev0) cudaEventRecord(ev0, s);
   switch (impl->SYP) {
     case 4: mttsp_tc_kernel<4><<<impl->grid, kThreads, impl->smem, s>>>(impl->tmX, impl->tmT, A); break;
     case 8: mttsp_tc_kernel<8><<<impl->grid, kThreads, impl->smem, s>>>(impl->tmX, impl->tmT, A); break;
@@ -1015,17 +1034,20 @@ int tc_enqueue(TcPlan& p, const void* X, double* const* cores, double* M, cudaSt
     default: mttsp_tc_kernel<16><<<impl->grid, kThreads, impl->smem, s>>>(impl->tmX, impl->tmT, A); break;
   }
   ++launches;
+  if (ev1) cudaEventRecord(ev1, s);
   tc_reduce_kernel<<<(unsigned)((impl->E + 31) / 32), 256, 0, s>>>(impl->partials, impl->grid, impl->E, M);
   ++launches;
   return launches;
 }
+
+int tc_variant(const TcPlan& p) { return p.impl ? static_cast<const TcImpl*>(p.impl)->args.variant : -1; }
 
 void tc_set_status(TcPlan& p, DevStatus* st) {
   if (p.impl) static_cast<TcImpl*>(p.impl)->args.status = st;
 }
 
 void tc_destroy(TcPlan& p) {
-  for (void* q : p.allocs) cudaFree(q);
+  for (void* q : p.allocs) cudaFreeAsync(q, p.stream);
   p.allocs.clear();
   delete static_cast<TcImpl*>(p.impl);
   p.impl = nullptr;

@@ -9,7 +9,9 @@ namespace trals {
 struct TcPlan {
   bool valid = false;
   int N = 0, n = 0, mode = 0;
-  std::vector<void*> allocs;
+  std::vector<void*> allocs;    // stream-ordered allocations on `stream`
+  cudaStream_t stream = nullptr;
+  size_t bytes = 0;             // device workspace held
   void* impl = nullptr;
 };
 
@@ -26,12 +28,17 @@ TcChoice tc_choose(int N, const int64_t* I, const int32_t* R, int n);
 
 // Prepare the tensor-core MTTSP of mode n for X (element type implied by `mode`).  Returns 1 when
 // the shape is supported (then tc_enqueue is used), 0 otherwise (the caller falls back to the
-// CUDA-core MTTSP).  *err is set on a CUDA failure.
+// CUDA-core MTTSP).  *err is set on a CUDA failure.  Workspace is allocated stream-ordered on s.
+// With count_bytes set nothing is allocated: the workspace bytes are added to *count_bytes.
 int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mode, const void* X, int64_t numel,
-            cudaError_t* err);
-// Enqueue M_n (FP64, I_n x R_n R_{n+1}) on stream s; returns the number of kernel launches.
-int tc_enqueue(TcPlan& p, const void* X, double* const* cores, double* M, cudaStream_t s);
+            cudaError_t* err, cudaStream_t s = nullptr, size_t* count_bytes = nullptr);
+// Enqueue M_n (FP64, I_n x R_n R_{n+1}) on stream s; returns the number of kernel launches.  When
+// given, ev0/ev1 are recorded on s directly before and after the main contraction kernel.
+int tc_enqueue(TcPlan& p, const void* X, double* const* cores, double* M, cudaStream_t s, cudaEvent_t ev0 = nullptr,
+               cudaEvent_t ev1 = nullptr);
 void tc_destroy(TcPlan& p);
+// Geometry of a valid plan (0 KM-L, 1 KM-R, 2 MM), -1 if none.
+int tc_variant(const TcPlan& p);
 // Device status word the kernel reports a bounded-wait timeout into.
 void tc_set_status(TcPlan& p, DevStatus* st);
 cudaError_t init_tc_attributes();

@@ -25,6 +25,23 @@ __global__ void finalize_explicit_residual(const double* red2, double* res_hist,
 
 __global__ void set_int_kernel(int* p, int v) { *p = v; }
 
+// Reduced-precision modes without the explicit pass: the residual identity cannot be evaluated to
+// the needed accuracy from a BF16 M_N (the subchain table is rounded too), so the sweep records NaN.
+__global__ void skip_residual_kernel(double* res_hist, int* sweep_ctr) {
+  const int s = *sweep_ctr;
+  res_hist[s] = __longlong_as_double(0x7ff8000000000000LL);
+  *sweep_ctr = s + 1;
+}
+
+// sqrt(|X - X_hat|^2 / |X|^2) into the history entry of the last sweep run
+__global__ void finalize_last_residual_kernel(const double* red2, double* res_hist, const int* sweep_ctr) {
+  const int s = *sweep_ctr;
+  if (s > 0) res_hist[s - 1] = sqrt(fmax(red2[0], 0.0) / red2[1]);
+}
+
+// sqrt(|X - X_hat|^2 / |X|^2) of the current cores into *out
+__global__ void finalize_ratio_kernel(const double* red2, double* out) { *out = sqrt(fmax(red2[0], 0.0) / red2[1]); }
+
 std::string fmt(const char* f, long long a = 0, long long b = 0, long long c = 0) {
   char buf[256];
   snprintf(buf, sizeof buf, f, a, b, c);
@@ -129,14 +146,26 @@ struct trals_plan {
   int launches = 0;
   TcPlan tc[TRALS_MAX_ORDER];
   bool use_tc[TRALS_MAX_ORDER] = {};
+  // Workspace is allocated stream-ordered (cudaMallocAsync / cudaFreeAsync on the context's
+  // stream), so creating and destroying plans never synchronises the whole device: plans of other
+  // streams keep running.  In the counting pass nothing is allocated and `bytes` sums the sizes.
+  bool counting = false;
+  size_t bytes = 0;
 
   template <typename T>
   cudaError_t alloc(T** p, size_t count) {
+    const size_t b = (std::max<size_t>(count, 1) * sizeof(T) + 255) & ~(size_t)255;
+    if (counting) {
+      *p = reinterpret_cast<T*>((uintptr_t(1) << 40) + bytes);   // never dereferenced
+      bytes += b;
+      return cudaSuccess;
+    }
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    cudaError_t e = cudaMallocAsync(&q, b, ctx->stream);
     if (e == cudaSuccess) {
       allocs.push_back(q);
       *p = static_cast<T*>(q);
+      bytes += b;
     }
     return e;
   }
@@ -165,15 +194,35 @@ int enqueue_coef(const int N, const int32_t* R, double* const* gam, int n, doubl
   return launches + 1;
 }
 
-int enqueue_mttsp(trals_plan* p, int n, cudaStream_t s) {
+int enqueue_mttsp(trals_plan* p, int n, cudaStream_t s, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
   const ModeLayout& L = p->lay[n];
   int launches = 0;
   if (p->use_tc[n]) {
-    launches += tc_enqueue(p->tc[n], p->Xk, p->cores, p->M, s);
+    launches += tc_enqueue(p->tc[n], p->Xk, p->cores, p->M, s, ev0, ev1);
     return launches;
   }
   build_tables(L, p->cores, p->I, p->R, p->ltab, p->utab, p->tscratch, s);
   launches += L.N - 1;
+  if (p->opts.mode != TRALS_MODE_FP64 && mttsp_simt_f32_fits(L)) {
+    // reduced-precision modes: FP32 arithmetic (the tables' FP32 copies go to the scratch buffer)
+    const int64_t nl = L.nL * L.Rn1 * L.Rs, nu = L.nU * L.Rs * L.Rn;
+    float* fl = reinterpret_cast<float*>(p->tscratch);
+    launch_tables_to_f32(p->ltab, nl, fl, p->utab, nu, fl + nl, s);
+    MttspSimtArgs a;
+    a.X = p->Xk;
+    a.Xlo = p->Xk_lo;
+    a.xt = p->xk_t;
+    a.offL = p->offL[n];
+    a.offU = p->offU[n];
+    a.L = L;
+    a.partials = p->partials;
+    a.M = p->M;
+    a.gridX = mttsp_simt_f32_grid(L);
+    a.ev0 = ev0;
+    a.ev1 = ev1;
+    launch_mttsp_simt_f32(a, fl, fl + nl, s);
+    return launches + 3;
+  }
   MttspSimtArgs a;
   a.X = p->Xk;
   a.Xlo = p->Xk_lo;
@@ -186,8 +235,33 @@ int enqueue_mttsp(trals_plan* p, int n, cudaStream_t s) {
   a.partials = p->partials;
   a.M = p->M;
   a.gridX = p->gridX[n];
+  a.ev0 = ev0;
+  a.ev1 = ev1;
   launch_mttsp_simt(a, s);
   return launches + 2;
+}
+
+// Explicit residual pass of the current cores against the caller's full-precision X (Sec. 4): FP64
+// reconstruction in the FP64 mode, FP32 reconstruction in the reduced-precision modes.  Leaves
+// (|X - X_hat|^2, |X|^2) in p->red2.  Returns the number of launches.
+int enqueue_explicit_residual(trals_plan* p, cudaStream_t s) {
+  const int N = p->N;
+  const int n = N - 1;
+  const ModeLayout& L = p->lay[n];
+  build_tables(L, p->cores, p->I, p->R, p->ltab, p->utab, p->tscratch, s);
+  int gridX;
+  if (p->opts.mode == TRALS_MODE_FP64) {
+    gridX = p->gridX[n];
+    launch_reconstruct(L, p->ltab, p->utab, p->offL[n], p->offU[n], p->cores[n], nullptr, TRALS_X_F64, p->X, p->xt,
+                       p->partials, gridX, s);
+  } else {
+    gridX = residual_f32_grid(L);
+    launch_residual_f32(L, p->ltab, p->utab, reinterpret_cast<float*>(p->tscratch), L.nL * L.Rn1 * L.Rs,
+                        L.nU * L.Rs * L.Rn, p->offL[n], p->offU[n], p->cores[n], p->X, p->xt, p->partials, gridX,
+                        s);
+  }
+  launch_reduce_pairs(p->partials, gridX, p->red2, s);
+  return (N - 1) + (p->opts.mode == TRALS_MODE_FP64 ? 1 : 2) + 1;
 }
 
 int enqueue_sweep(trals_plan* p) {
@@ -205,17 +279,15 @@ int enqueue_sweep(trals_plan* p) {
   }
   const int n = N - 1;
   if (p->opts.explicit_residual) {
-    // tables of the last mode still hold the other cores; regenerate to be independent of the MTTSP path
-    const ModeLayout& L = p->lay[n];
-    build_tables(L, p->cores, p->I, p->R, p->ltab, p->utab, p->tscratch, s);
-    launch_reconstruct(L, p->ltab, p->utab, p->offL[n], p->offU[n], p->cores[n], nullptr, TRALS_X_F64, p->X, p->xt,
-                       p->partials, p->gridX[n], s);
-    launch_reduce_pairs(p->partials, p->gridX[n], p->red2, s);
+    launches += enqueue_explicit_residual(p, s);
     finalize_explicit_residual<<<1, 1, 0, s>>>(p->red2, p->res_hist, p->sweep_ctr);
-    launches += (N - 1) + 3;
-  } else {
+    launches += 1;
+  } else if (p->opts.mode == TRALS_MODE_FP64) {
     launch_residual_identity(p->normX2, p->M, p->cores[n], p->S, p->gam[n], p->R[n], p->I[n], p->R[0], p->res_hist,
                              p->sweep_ctr, s);
+    launches += 1;
+  } else {
+    skip_residual_kernel<<<1, 1, 0, s>>>(p->res_hist, p->sweep_ctr);
     launches += 1;
   }
   return launches;
@@ -271,17 +343,26 @@ const char* trals_last_error(const trals_ctx* ctx) { return ctx ? ctx->last_erro
 
 void trals_plan_destroy(trals_plan* p) {
   if (!p) return;
-  if (p->ctx && p->ctx->stream) cudaStreamSynchronize(p->ctx->stream);
-  if (p->gexec) cudaGraphExecDestroy(p->gexec);
-  for (int n = 0; n < p->N; ++n) tc_destroy(p->tc[n]);
-  for (void* q : p->allocs) cudaFree(q);
+  if (!p->counting) {
+    if (p->ctx && p->ctx->stream) cudaStreamSynchronize(p->ctx->stream);
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    for (int n = 0; n < p->N; ++n) tc_destroy(p->tc[n]);
+    for (void* q : p->allocs) cudaFreeAsync(q, p->ctx->stream);
+  }
   delete p;
 }
 
-trals_status trals_plan_create(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R, const void* X_dev, int xt,
-                               const trals_opts* opts, trals_plan** out) {
-  if (!ctx || !out) return TRALS_E_ARG;
-  *out = nullptr;
+}  // extern "C"
+
+namespace {
+
+// Builds a plan, or with `counting` only sums the bytes its workspace needs (*count_out) without
+// allocating, copying or launching anything.
+trals_status plan_build(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R, const void* X_dev, int xt,
+                        const trals_opts* opts, bool counting, size_t* count_out, trals_plan** out,
+                        bool sync = true) {
+  if (!ctx || (!out && !counting)) return TRALS_E_ARG;
+  if (out) *out = nullptr;
   trals_status st = check_shape(ctx, N, I, R);
   if (st != TRALS_OK) return st;
   if (!X_dev) {
@@ -314,6 +395,7 @@ trals_status trals_plan_create(trals_ctx* ctx, int N, const int64_t* I, const in
   cudaSetDevice(ctx->device);
   trals_plan* p = new trals_plan();
   p->ctx = ctx;
+  p->counting = counting;
   p->N = N;
   for (int n = 0; n < N; ++n) {
     p->I[n] = I[n];
@@ -351,12 +433,17 @@ trals_status trals_plan_create(trals_ctx* ctx, int N, const int64_t* I, const in
     p->gridX[n] = mttsp_simt_default_grid(p->lay[n]);
     maxPart = std::max(maxPart, mttsp_simt_partials_elems(p->lay[n], p->gridX[n]));
     maxPart = std::max(maxPart, (size_t)2 * p->gridX[n]);
+    if (o.mode != TRALS_MODE_FP64)
+      maxPart = std::max(maxPart, mttsp_simt_partials_elems(p->lay[n], mttsp_simt_f32_grid(p->lay[n])));
     std::vector<int64_t> offL, offU;
     mode_offsets(N, I, p->lay[n], offL, offU);
     PLAN_TRY(p->alloc(&p->offL[n], offL.size()));
     PLAN_TRY(p->alloc(&p->offU[n], offU.size()));
-    PLAN_TRY(cudaMemcpy(p->offL[n], offL.data(), offL.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
-    PLAN_TRY(cudaMemcpy(p->offU[n], offU.data(), offU.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    if (!counting) {
+      // pageable sources: staged before the call returns
+      PLAN_TRY(cudaMemcpyAsync(p->offL[n], offL.data(), offL.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+      PLAN_TRY(cudaMemcpyAsync(p->offU[n], offU.data(), offU.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    }
   }
   PLAN_TRY(p->alloc(&p->S, (size_t)maxr * maxr));
   PLAN_TRY(p->alloc(&p->Lmat, (size_t)maxr * maxr + maxr));   // L and its reciprocal diagonal
@@ -371,7 +458,7 @@ trals_status trals_plan_create(trals_ctx* ctx, int N, const int64_t* I, const in
   PLAN_TRY(p->alloc(&p->normX2, 1));
   PLAN_TRY(p->alloc(&p->res_hist, kResCap));
   PLAN_TRY(p->alloc(&p->sweep_ctr, 1));
-  PLAN_TRY(cudaMemsetAsync(p->sweep_ctr, 0, sizeof(int), s));
+  if (!counting) PLAN_TRY(cudaMemsetAsync(p->sweep_ctr, 0, sizeof(int), s));
 
   // X as the MTTSP reads it (quantised once, K7), and |X|^2 from the full-precision source.
   p->Xk = X_dev;
@@ -379,24 +466,24 @@ trals_status trals_plan_create(trals_ctx* ctx, int N, const int64_t* I, const in
   if (o.mode == TRALS_MODE_BF16 && xt != TRALS_X_BF16) {
     __nv_bfloat16* q = nullptr;
     PLAN_TRY(p->alloc(&q, (size_t)p->numel));
-    launch_quantize(X_dev, xt, p->numel, q, nullptr, s);
+    if (!counting) launch_quantize(X_dev, xt, p->numel, q, nullptr, s);
     p->Xk = q;
     p->xk_t = TRALS_X_BF16;
   } else if (o.mode == TRALS_MODE_BF16X3) {
     __nv_bfloat16* q = nullptr;
     PLAN_TRY(p->alloc(&q, (size_t)p->numel * 2));
-    launch_quantize(X_dev, xt, p->numel, q, q + p->numel, s);
+    if (!counting) launch_quantize(X_dev, xt, p->numel, q, q + p->numel, s);
     p->Xk = q;
     p->Xk_lo = q + p->numel;
     p->xk_t = TRALS_X_BF16;
   } else if (o.mode == TRALS_MODE_FP32 && xt == TRALS_X_F64) {
     float* q = nullptr;
     PLAN_TRY(p->alloc(&q, (size_t)p->numel));
-    launch_convert_f32(X_dev, p->numel, q, s);
+    if (!counting) launch_convert_f32(X_dev, p->numel, q, s);
     p->Xk = q;
     p->xk_t = TRALS_X_F32;
   }
-  {
+  if (!counting) {
     const int g = 152 * 4;
     launch_sumsq(X_dev, xt, p->numel, p->partials, g, p->normX2, s);
   }
@@ -404,17 +491,44 @@ trals_status trals_plan_create(trals_ctx* ctx, int N, const int64_t* I, const in
   for (int n = 0; n < N; ++n) {
     p->use_tc[n] = false;
     if (o.mode != TRALS_MODE_FP64) {
-      const int ok = tc_plan(p->tc[n], N, I, R, n, o.mode, p->Xk, p->numel, &e);
+      const int ok = tc_plan(p->tc[n], N, I, R, n, o.mode, p->Xk, p->numel, &e, s, counting ? &p->bytes : nullptr);
       if (e != cudaSuccess) PLAN_TRY(e);
       p->use_tc[n] = ok != 0;
-      if (ok) tc_set_status(p->tc[n], ctx->d_status);
+      if (ok && !counting) {
+        tc_set_status(p->tc[n], ctx->d_status);
+        p->bytes += p->tc[n].bytes;
+      }
     }
   }
-  PLAN_TRY(cudaStreamSynchronize(s));
+  if (counting) {
+    *count_out = p->bytes;
+    trals_plan_destroy(p);
+    return TRALS_OK;
+  }
+  if (sync) PLAN_TRY(cudaStreamSynchronize(s));
+  else PLAN_TRY(cudaGetLastError());
 #undef PLAN_TRY
   *out = p;
   return TRALS_OK;
 }
+
+}  // namespace
+
+extern "C" {
+
+trals_status trals_plan_create(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R, const void* X_dev, int xt,
+                               const trals_opts* opts, trals_plan** out) {
+  return plan_build(ctx, N, I, R, X_dev, xt, opts, false, nullptr, out);
+}
+
+trals_status trals_plan_footprint(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R, const void* X_dev,
+                                  int xt, const trals_opts* opts, size_t* bytes) {
+  if (!bytes) return TRALS_E_ARG;
+  *bytes = 0;
+  return plan_build(ctx, N, I, R, X_dev, xt, opts, true, bytes, nullptr);
+}
+
+size_t trals_plan_bytes(const trals_plan* p) { return p ? p->bytes : 0; }
 
 trals_status trals_plan_set_cores(trals_plan* p, double* const* cores_host) {
   if (!p || !cores_host) return TRALS_E_ARG;
@@ -506,9 +620,120 @@ trals_status trals_plan_mttsp(trals_plan* p, int n, double* M_dev) {
   return TRALS_OK;
 }
 
+trals_status trals_plan_time_mttsp(trals_plan* p, int n, float* kernel_ms, float* total_ms) {
+  if (!p || n < 0 || n >= p->N) return TRALS_E_ARG;
+  trals_ctx* ctx = p->ctx;
+  cudaStream_t s = ctx->stream;
+  cudaEvent_t ev[4] = {};
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
+  if (e == cudaSuccess) {
+    enqueue_mttsp(p, n, s, ev[1], ev[2]);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(ev[3], s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+  float a = 0.f, b = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&a, ev[1], ev[2]);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[0], ev[3]);
+  for (int k = 0; k < 4; ++k)
+    if (ev[k]) cudaEventDestroy(ev[k]);
+  TRALS_CUDA_TRY(ctx, e);
+  if (kernel_ms) *kernel_ms = a;
+  if (total_ms) *total_ms = b;
+  return read_status(ctx);
+}
+
+trals_status trals_plan_explicit_residual(trals_plan* p, double* rel_res_host) {
+  if (!p || !rel_res_host) return TRALS_E_ARG;
+  trals_ctx* ctx = p->ctx;
+  cudaStream_t s = ctx->stream;
+  enqueue_explicit_residual(p, s);
+  finalize_ratio_kernel<<<1, 1, 0, s>>>(p->red2, p->red2 + 1);
+  TRALS_CUDA_TRY(ctx, cudaGetLastError());
+  TRALS_CUDA_TRY(ctx, cudaMemcpyAsync(rel_res_host, p->red2 + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+  return read_status(ctx);
+}
+
+}  // extern "C"
+
+namespace trals {
+
+trals_status plan_create_async(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R, const void* X_dev, int xt,
+                               const trals_opts* opts, trals_plan** out) {
+  return plan_build(ctx, N, I, R, X_dev, xt, opts, false, nullptr, out, false);
+}
+
+trals_status plan_set_cores_async(trals_plan* p, const double* const* cores_host) {
+  trals_ctx* ctx = p->ctx;
+  cudaStream_t s = ctx->stream;
+  for (int n = 0; n < p->N; ++n) {
+    const size_t cnt = (size_t)p->R[n] * p->I[n] * p->R[(n + 1) % p->N];
+    // pageable sources are staged before the call returns
+    TRALS_CUDA_TRY(ctx, cudaMemcpyAsync(p->cores[n], cores_host[n], cnt * sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_gamma(p->cores[n], p->R[n], p->I[n], p->R[(n + 1) % p->N], p->gam[n], s);
+  }
+  set_int_kernel<<<1, 1, 0, s>>>(p->sweep_ctr, 0);
+  TRALS_CUDA_TRY(ctx, cudaGetLastError());
+  p->host_sweeps = 0;
+  return TRALS_OK;
+}
+
+size_t plan_core_elems(const trals_plan* p) {
+  size_t t = 0;
+  for (int n = 0; n < p->N; ++n) t += (size_t)p->R[n] * p->I[n] * p->R[(n + 1) % p->N];
+  return t;
+}
+
+trals_status plan_enqueue_results(trals_plan* p, int sweeps, bool final_explicit, double* res_host,
+                                  double* cores_host, void* status_host) {
+  trals_ctx* ctx = p->ctx;
+  cudaStream_t s = ctx->stream;
+  if (final_explicit) {
+    enqueue_explicit_residual(p, s);
+    finalize_last_residual_kernel<<<1, 1, 0, s>>>(p->red2, p->res_hist, p->sweep_ctr);
+  }
+  if (sweeps > 0)
+    TRALS_CUDA_TRY(ctx, cudaMemcpyAsync(res_host, p->res_hist, sweeps * sizeof(double), cudaMemcpyDeviceToHost, s));
+  size_t off = 0;
+  for (int n = 0; n < p->N; ++n) {
+    const size_t cnt = (size_t)p->R[n] * p->I[n] * p->R[(n + 1) % p->N];
+    TRALS_CUDA_TRY(ctx, cudaMemcpyAsync(cores_host + off, p->cores[n], cnt * sizeof(double), cudaMemcpyDeviceToHost, s));
+    off += cnt;
+  }
+  TRALS_CUDA_TRY(ctx, cudaMemcpyAsync(status_host, ctx->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  launch_zero_status(ctx->d_status, s);
+  TRALS_CUDA_TRY(ctx, cudaGetLastError());
+  return TRALS_OK;
+}
+
+std::string status_message(const void* status_host) {
+  const DevStatus& st = *static_cast<const DevStatus*>(status_host);
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s at sweep %d, core %d, index %d (value %.6g)",
+           st.code == TRALS_E_NOT_SPD ? "non-positive Cholesky pivot"
+           : st.code == TRALS_E_NONFINITE ? "non-finite value in a solve"
+           : st.code == TRALS_E_TIMEOUT   ? "bounded device wait timed out"
+                                          : "device error",
+           st.sweep, st.mode, st.index, st.value);
+  return buf;
+}
+
+int status_code(const void* status_host) { return static_cast<const DevStatus*>(status_host)->code; }
+
+}  // namespace trals
+
+extern "C" {
+
 const double* trals_plan_core_dev(const trals_plan* p, int n) {
   if (!p || n < 0 || n >= p->N) return nullptr;
   return p->cores[n];
+}
+
+int trals_plan_mttsp_path(const trals_plan* p, int n) {
+  if (!p || n < 0 || n >= p->N) return -1;
+  return p->use_tc[n] ? tc_variant(p->tc[n]) + 1 : 0;
 }
 
 int trals_plan_launches_per_sweep(const trals_plan* p) {
@@ -546,6 +771,9 @@ trals_status trals_decompose(trals_ctx* ctx, int N, const int64_t* I, const int3
   if (st == TRALS_OK) st = trals_plan_set_cores(p, cores);
   if (st == TRALS_OK) st = trals_plan_run(p, sweeps, 1);
   if (st == TRALS_OK) st = trals_plan_residuals(p, rel_res, sweeps, nullptr);
+  // reduced-precision modes record no per-sweep residual unless asked to: give the final one
+  if (st == TRALS_OK && rel_res && sweeps > 0 && p->opts.mode != TRALS_MODE_FP64 && !p->opts.explicit_residual)
+    st = trals_plan_explicit_residual(p, &rel_res[sweeps - 1]);
   if (st == TRALS_OK) st = trals_plan_get_cores(p, cores);
   trals_plan_destroy(p);
   if (Xd) cudaFree(Xd);
@@ -616,7 +844,9 @@ trals_status trals_mttsp(trals_ctx* ctx, int N, const int64_t* I, const int32_t*
   e = cudaMalloc(&lt, tab * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&ut, tab * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&sc, tab * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&part, mttsp_simt_partials_elems(L, gridX) * sizeof(double));
+  if (e == cudaSuccess)
+    e = cudaMalloc(&part, std::max(mttsp_simt_partials_elems(L, gridX), mttsp_simt_partials_elems(L, mttsp_simt_f32_grid(L))) *
+                              sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&dL, offL.size() * sizeof(int64_t));
   if (e == cudaSuccess) e = cudaMalloc(&dU, offU.size() * sizeof(int64_t));
   if (e == cudaSuccess) e = cudaMemcpy(dL, offL.data(), offL.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
@@ -635,7 +865,15 @@ trals_status trals_mttsp(trals_ctx* ctx, int N, const int64_t* I, const int32_t*
     a.partials = part;
     a.M = M_dev;
     a.gridX = gridX;
-    launch_mttsp_simt(a, s);
+    if (mode != TRALS_MODE_FP64 && mttsp_simt_f32_fits(L)) {
+      const int64_t nl = L.nL * L.Rn1 * L.Rs, nu = L.nU * L.Rs * L.Rn;
+      float* fl = reinterpret_cast<float*>(sc);
+      launch_tables_to_f32(lt, nl, fl, ut, nu, fl + nl, s);
+      a.gridX = mttsp_simt_f32_grid(L);
+      launch_mttsp_simt_f32(a, fl, fl + nl, s);
+    } else {
+      launch_mttsp_simt(a, s);
+    }
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   }

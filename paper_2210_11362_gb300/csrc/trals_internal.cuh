@@ -75,8 +75,18 @@ struct MttspSimtArgs {
   double* partials;     // [gridX][I_n * r]
   double* M;            // I_n x r
   int gridX;
+  cudaEvent_t ev0 = nullptr;   // optional: recorded directly before / after the contraction kernel
+  cudaEvent_t ev1 = nullptr;
 };
 size_t mttsp_simt_partials_elems(const ModeLayout& L, int gridX);
+// FP32-arithmetic CUDA-core MTTSP for the reduced-precision modes: reads FP32 copies of the two
+// subchain tables (fl: nL*Rn1*Rs floats, fu: nU*Rs*Rn floats; see launch_tables_to_f32), visits X in
+// memory order.  Usable when mttsp_simt_f32_fits(L); grid from mttsp_simt_f32_grid(L).
+bool mttsp_simt_f32_fits(const ModeLayout& L);
+int mttsp_simt_f32_grid(const ModeLayout& L);
+void launch_mttsp_simt_f32(const MttspSimtArgs& a, const float* fl, const float* fu, cudaStream_t s);
+void launch_tables_to_f32(const double* a, int64_t na, float* fa, const double* b, int64_t nb, float* fb,
+                          cudaStream_t s);
 int mttsp_simt_default_grid(const ModeLayout& L);
 void launch_mttsp_simt(const MttspSimtArgs& a, cudaStream_t s);
 
@@ -87,6 +97,14 @@ void launch_reconstruct(const ModeLayout& L, const double* ltab, const double* u
                         double* partials, int gridX, cudaStream_t s);
 // Sum of `count` partials into out[0] (and out[1] if two interleaved series), fixed order.
 void launch_reduce_pairs(const double* partials, int count, double* out, cudaStream_t s);
+// Explicit residual with X_hat regenerated in FP32 (reduced-precision modes): converts the two FP64
+// subchain tables into `ftab` (ltab_elems + utab_elems floats), then writes per-block
+// (|X - X_hat|^2, |X|^2) pairs to partials[2 * gridX].  Shared memory: residual_f32_smem(L) bytes.
+size_t residual_f32_smem(const ModeLayout& L);
+int residual_f32_grid(const ModeLayout& L);
+void launch_residual_f32(const ModeLayout& L, const double* ltab, const double* utab, float* ftab, int64_t ltab_elems,
+                         int64_t utab_elems, const int64_t* offL, const int64_t* offU, const double* coreN,
+                         const void* X, int xt, double* partials, int gridX, cudaStream_t s);
 
 // Cholesky (K4): factor S (r x r, lower triangle) into L (r x r, then r reciprocal diagonal entries, so
 // Lmat holds r*r + r doubles); status on failure.
@@ -109,6 +127,22 @@ void launch_quantize(const void* src, int src_t, int64_t count, __nv_bfloat16* h
 // FP64 -> FP32 copy (FP32 mode fed with an FP64 X).
 void launch_convert_f32(const void* src_f64, int64_t count, float* dst, cudaStream_t s);
 void launch_zero_status(DevStatus* st, cudaStream_t s);
+
+// ---------------------------------------------------------------- asynchronous plan steps (serving)
+// As trals_plan_create / trals_plan_set_cores but without waiting on the stream (host sources may
+// be pageable: they are staged before the calls return).
+trals_status plan_create_async(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R, const void* X_dev, int xt,
+                               const trals_opts* opts, trals_plan** out);
+trals_status plan_set_cores_async(trals_plan* p, const double* const* cores_host);
+size_t plan_core_elems(const trals_plan* p);
+// Enqueue, after the sweeps: (optionally) the explicit residual of the final cores into the last
+// history entry, then copies of `sweeps` residuals, all cores (concatenated, core layout) and the
+// device status word (sizeof(DevStatus) bytes) to host buffers (pinned, for the copies to be
+// asynchronous), and a reset of the status word.
+trals_status plan_enqueue_results(trals_plan* p, int sweeps, bool final_explicit, double* res_host,
+                                  double* cores_host, void* status_host);
+std::string status_message(const void* status_host);
+int status_code(const void* status_host);
 // One-time kernel attribute setup (dynamic shared memory opt-in); called at context creation.
 cudaError_t init_small_attributes();
 cudaError_t init_simt_attributes();

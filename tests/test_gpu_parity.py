@@ -86,6 +86,26 @@ def test_mttsp_fp64_matches_oracle(ctx, I, R):
         assert rel(M.cpu().numpy().reshape(I[n], r, order="F"), ref) < 1e-12
 
 
+@pytest.mark.parametrize("I,R", SHAPES + [((40, 24, 33, 20), (4, 6, 3, 5)), ((64, 17, 50), (8, 7, 6))])
+def test_mttsp_fp32_cuda_cores_match_oracle(ctx, I, R):
+    """FP32 X on the FP32-arithmetic CUDA-core kernel (memory-order tiles): the result matches
+    X_fp32 G^{!=n} in FP64 to FP32 rounding of the factors and the per-CTA sums (1e-5)."""
+    X, _ = _problem(I, R)
+    cores = TI.gaussian_cores(9, I, R)
+    Xf = P.tensor_to_device(X, torch.float32)
+    Xq = TI.unflat_f(Xf.cpu().numpy().astype(np.float64), I)
+    cd = [P.core_to_device(G) for G in cores]
+    N = len(I)
+    for n in range(N):
+        r = R[n] * R[(n + 1) % N]
+        M = torch.zeros(I[n] * r, dtype=torch.float64, device="cuda")
+        P.trals_mttsp(ctx, I, R, Xf, "fp32", cd, n, M)
+        ref = O.unfold_mode(Xq, n) @ O.subchain_unfolded(cores, n)
+        got = M.cpu().numpy().reshape(I[n], r, order="F")
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err < 1e-5, (n, err)
+
+
 TC_SHAPES = [
     ((16, 24, 32, 20), (3, 4, 2, 5)),        # every tensor-core geometry, small ranks
     ((40, 40, 40, 40), (8, 10, 12, 10)),     # 40^4 with the ranks of the 40^5 workload
@@ -250,10 +270,14 @@ def test_reduced_precision_residual_gap(ctx, mode, I, R, eta):
     X, init = _near_truth_problem(I, R, eta, 11)
     cores = [G.copy() for G in init]
     Xd = P.tensor_to_device(X, torch.float32)
-    P.trals_decompose(ctx, I, R, Xd, cores, 6, P.make_opts(mode))
+    res = P.trals_decompose(ctx, I, R, Xd, cores, 6, P.make_opts(mode))
     _, ref_res = O.tr_als(X, init, 6, "chol")
     gap = abs(O.rel_residual(X, cores) - ref_res[-1])
     assert gap <= 1e-4, gap
+    # no per-sweep residual in the reduced modes by default; the last one is the explicit pass
+    # (FP32 regeneration against the FP32 X): equal to the oracle's residual of the same cores
+    assert np.isnan(res[:-1]).all()
+    assert abs(res[-1] - O.rel_residual(X, cores)) < 1e-6
     for n in range(len(I)):
         assert O.subchain_principal_angle(cores, O.tr_als(X, init, 6, "chol", residual=False)[0], n) < 1e-2
 
@@ -271,3 +295,38 @@ def test_tr60x4_rank10_full_size_one_sweep(ctx):
         ref[n] = O.core_fold2(O.ls_solve_normal(S, M), ref[n].shape[0], ref[n].shape[2])
     for a, b in zip(cores, ref):
         assert rel(a, b) < 1e-9
+
+
+@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+def test_explicit_per_sweep_residual_in_reduced_modes(ctx, mode):
+    """explicit_residual=1 in a reduced-precision mode: every sweep's residual comes from the FP32
+    regeneration pass and matches the oracle's residual of the cores after that sweep."""
+    I, R = (30, 26, 28, 24), (5, 4, 6, 3)
+    X, init = _near_truth_problem(I, R, 1e-2, 21)
+    Xd = P.tensor_to_device(X, torch.float32)
+    plan = P.Plan(ctx, I, R, Xd, P.make_opts(mode, explicit_residual=True))
+    try:
+        plan.set_cores(init)
+        per = []
+        for _ in range(3):
+            plan.run(1, use_graph=False)
+            per.append(O.rel_residual(X, plan.get_cores()))
+        got = plan.residuals()
+        direct = plan.explicit_residual()
+    finally:
+        plan.close()
+    np.testing.assert_allclose(got, per, rtol=0, atol=1e-6)
+    assert abs(direct - per[-1]) < 1e-6
+
+
+def test_plan_uses_the_tensor_core_geometry_it_reports(ctx):
+    """The plan of the 40^5 workload runs every mode on the tensor cores, in the geometry the host
+    query reports (no silent fallback to the CUDA cores)."""
+    I, R = (40,) * 5, (8, 10, 12, 10, 8)
+    X = torch.zeros(int(np.prod(I)), dtype=torch.bfloat16, device="cuda")
+    plan = P.Plan(ctx, I, R, X, P.make_opts("bf16"))
+    try:
+        got = [plan.mttsp_path(n) for n in range(5)]
+    finally:
+        plan.close()
+    assert got == [P.trals_mttsp_path(I, R, n, "bf16") for n in range(5)] == [3, 3, 1, 1, 2]
