@@ -197,6 +197,24 @@ trals_status trals_gamma(trals_ctx* ctx, const double* G_dev, int Rn, int64_t In
 trals_status trals_coef_matrix(trals_ctx* ctx, int N, const int32_t* R, const double* const* gammas_dev,
                                int n, double* S_dev);
 
+/* R factor of the subchain matrix G^{!=n}_[2] (Sec. 3.2: the QR factorisation TR-ALS-QR solves
+ * with), computed without forming S_n: recursive structured QR along the subchain (the mode-2 QR of
+ * G_{n+1}, then at each further core the QR of (R_t [x]_2 G_c)_[2], which Prop. slice_kron shows
+ * has the same R factor as the running product), each step by a Householder TSQR tree, all FP64.
+ * R_dev: r x r upper triangular with a positive diagonal (column-major, columns a + R_n b as in
+ * G_{n(2)}), so R^T R = S_n.  TRALS_E_NOT_SPD when a diagonal entry is zero (rank deficient).
+ * cores_dev[N] device FP64 cores.  Synchronous. */
+trals_status trals_qr_r_factor(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R,
+                               const double* const* cores_dev, int n, double* R_dev);
+
+/* Explicit-subchain coefficient matrix of mode n (regular TR-ALS, Alg. 1): the subchain matrix
+ * G^{!=n}_[2] (J_n x R_n R_{n+1}, Def. subchain tensor) is formed explicitly on the device in row
+ * blocks and S_dev (r x r, full symmetric, column-major) = (G^{!=n}_[2])^T G^{!=n}_[2] is accumulated by
+ * a blocked SYRK: in FP64 when fp64 != 0, else with FP32 rows and FP32 tile sums reduced in FP64.
+ * The comparison variant of trals_coef_matrix.  cores_dev[N] device FP64 cores.  Synchronous. */
+trals_status trals_coef_matrix_explicit(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R,
+                                        const double* const* cores_dev, int n, int fp64, double* S_dev);
+
 /* MTTSP of mode n (Alg. 2 lines 7-8): M_dev (I_n x r, FP64) = X_[n] G^{!=n}_[2], with the
  * subchain rows generated on the fly from cores_dev (FP64) in the arithmetic of `mode`
  * (X element type must match the mode: F64 for FP64, F32 for FP32, BF16 for BF16;

@@ -39,7 +39,7 @@ EXPORTED = [
     "trals_plan_run", "trals_plan_residuals", "trals_plan_mttsp", "trals_plan_time_mttsp", "trals_plan_core_dev",
     "trals_plan_explicit_residual", "trals_plan_footprint", "trals_plan_bytes",
     "trals_plan_launches_per_sweep", "trals_plan_mttsp_path",
-    "trals_gamma", "trals_coef_matrix", "trals_mttsp", "trals_mttsp_noalloc", "trals_mttsp_path", "trals_solve_chol", "trals_reconstruct",
+    "trals_gamma", "trals_coef_matrix", "trals_coef_matrix_explicit", "trals_qr_r_factor", "trals_mttsp", "trals_mttsp_noalloc", "trals_mttsp_path", "trals_solve_chol", "trals_reconstruct",
     "trals_residual_explicit", "trals_quantize_bf16",
     "trals_server_create", "trals_server_destroy", "trals_server_submit", "trals_server_poll",
     "trals_server_wait", "trals_server_stats", "trals_server_last_error",
@@ -113,6 +113,9 @@ def lib() -> ctypes.CDLL:
         "trals_plan_mttsp_path": (ctypes.c_int, [_vp, ctypes.c_int]),
         "trals_gamma": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _i64, ctypes.c_int, _vp]),
         "trals_coef_matrix": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp]),
+        "trals_qr_r_factor": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp]),
+        "trals_coef_matrix_explicit": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int,
+                                                      _vp]),
         "trals_mttsp": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp,
                                        ctypes.c_int, _vp]),
         "trals_mttsp_path": (ctypes.c_int, [ctypes.c_int, _vp, _vp, ctypes.c_int, ctypes.c_int]),
@@ -354,6 +357,20 @@ def trals_coef_matrix(ctx: Context, R, gammas_dev: Sequence, n: int, S_dev) -> N
     Ra = (_i32 * N)(*[int(v) for v in R])
     ctx.check(lib().trals_coef_matrix(ctx.handle, N, ctypes.addressof(Ra), _ptr_array([_ptr(g) for g in gammas_dev]),
                                       int(n), _ptr(S_dev)), "trals_coef_matrix")
+
+
+def trals_coef_matrix_explicit(ctx: Context, I, R, cores_dev: Sequence, n: int, S_dev, fp64: bool = True) -> None:
+    N, Ia, Ra = _shape(I, R)
+    ctx.check(lib().trals_coef_matrix_explicit(ctx.handle, N, ctypes.addressof(Ia), ctypes.addressof(Ra),
+                                               _ptr_array([_ptr(c) for c in cores_dev]), int(n), int(bool(fp64)),
+                                               _ptr(S_dev)), "trals_coef_matrix_explicit")
+
+
+def trals_qr_r_factor(ctx: Context, I, R, cores_dev: Sequence, n: int, R_dev) -> None:
+    N, Ia, Ra = _shape(I, R)
+    ctx.check(lib().trals_qr_r_factor(ctx.handle, N, ctypes.addressof(Ia), ctypes.addressof(Ra),
+                                      _ptr_array([_ptr(c) for c in cores_dev]), int(n), _ptr(R_dev)),
+              "trals_qr_r_factor")
 
 
 def trals_mttsp(ctx: Context, I, R, X_dev, mode, cores_dev: Sequence, n: int, M_dev) -> None:

@@ -10,16 +10,6 @@ namespace trals {
 
 namespace {
 
-__device__ __forceinline__ void set_status(DevStatus* st, int code, int sweep, int mode, int index, double v) {
-  if (st == nullptr) return;
-  if (atomicCAS(&st->code, 0, code) == 0) {
-    st->sweep = sweep;
-    st->mode = mode;
-    st->index = index;
-    st->value = v;
-  }
-}
-
 template <typename T>
 __device__ __forceinline__ double load_as_double(const void* p, int64_t i);
 template <>

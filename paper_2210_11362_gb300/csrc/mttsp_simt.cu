@@ -193,7 +193,8 @@ __global__ void __launch_bounds__(THREADS) reconstruct_kernel(const double* __re
                                                               const int64_t* __restrict__ offL,
                                                               const int64_t* __restrict__ offU, ModeLayout L,
                                                               const double* __restrict__ coreN, OT* __restrict__ out,
-                                                              const void* __restrict__ X, double* __restrict__ partials) {
+                                                              const void* __restrict__ X, double* __restrict__ partials,
+                                                              int out_diff) {
   extern __shared__ double smem[];
   __shared__ double red[2][THREADS / 32];
   const int r = L.Rn * L.Rn1;
@@ -218,10 +219,11 @@ __global__ void __launch_bounds__(THREADS) reconstruct_kernel(const double* __re
         xh = fma(coreN[a + (int64_t)L.Rn * (i + In * b)], Gs[kk * r + c], xh);
       }
       const int64_t off = bo + i * L.strideN;
-      if (out != nullptr) out[off] = (OT)xh;
+      if (out != nullptr && !out_diff) out[off] = (OT)xh;
       if (X != nullptr) {
         const double xv = ld<XT>(X, off);
         const double d = xv - xh;
+        if (out != nullptr && out_diff) out[off] = (OT)d;
         d2 = fma(d, d, d2);
         x2 = fma(xv, xv, x2);
       }
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(THREADS) reconstruct_kernel(const double* __re
   }
   __syncthreads();
   if (threadIdx.x == 0 && partials != nullptr) {
-    double a = 0.0, b = 0.0;
+    double a = 0.0, b = 0.0;  // per-block |X - X_hat|^2, |X|^2
     for (int w = 0; w < THREADS / 32; ++w) {
       a += red[0][w];
       b += red[1][w];
@@ -390,7 +392,8 @@ __global__ void __launch_bounds__(THREADS) residual_f32_kernel(const float* __re
                                                                const int64_t* __restrict__ offL,
                                                                const int64_t* __restrict__ offU, ModeLayout L,
                                                                const double* __restrict__ coreN,
-                                                               const void* __restrict__ X, double* __restrict__ partials) {
+                                                               const void* __restrict__ X, double* __restrict__ partials,
+                                                               float* __restrict__ Eout) {
   extern __shared__ float fsm[];
   __shared__ double red[2][THREADS / 32];
   const int r = L.Rn * L.Rn1;
@@ -466,6 +469,7 @@ __global__ void __launch_bounds__(THREADS) residual_f32_kernel(const float* __re
           if (bo < 0) continue;
           const double xv = ld<XT>(X, bo + i * L.strideN);
           const double d = xv - (double)acc[u][v];
+          if (Eout != nullptr) Eout[bo + i * L.strideN] = (float)d;
           d2 = fma(d, d, d2);
           x2 = fma(xv, xv, x2);
         }
@@ -557,18 +561,19 @@ int residual_f32_grid(const ModeLayout& L) {
 
 void launch_residual_f32(const ModeLayout& L, const double* ltab, const double* utab, float* ftab, int64_t ltab_elems,
                          int64_t utab_elems, const int64_t* offL, const int64_t* offU, const double* coreN,
-                         const void* X, int xt, double* partials, int gridX, cudaStream_t s) {
+                         const void* X, int xt, double* partials, int gridX, cudaStream_t s, float* Eout) {
   float* fl = ftab;
   float* fu = ftab + ltab_elems;
   const int g = (int)std::min<int64_t>((ltab_elems + utab_elems + 255) / 256, 152 * 4);
   tables_to_f32_kernel<<<g, 256, 0, s>>>(ltab, ltab_elems, fl, utab, utab_elems, fu);
   const size_t smem = residual_f32_smem(L);
   if (xt == TRALS_X_F32)
-    residual_f32_kernel<float><<<gridX, THREADS, smem, s>>>(fl, fu, offL, offU, L, coreN, X, partials);
+    residual_f32_kernel<float><<<gridX, THREADS, smem, s>>>(fl, fu, offL, offU, L, coreN, X, partials, Eout);
   else if (xt == TRALS_X_BF16)
-    residual_f32_kernel<__nv_bfloat16><<<gridX, THREADS, smem, s>>>(fl, fu, offL, offU, L, coreN, X, partials);
+    residual_f32_kernel<__nv_bfloat16><<<gridX, THREADS, smem, s>>>(fl, fu, offL, offU, L, coreN, X, partials,
+                                                                     Eout);
   else
-    residual_f32_kernel<double><<<gridX, THREADS, smem, s>>>(fl, fu, offL, offU, L, coreN, X, partials);
+    residual_f32_kernel<double><<<gridX, THREADS, smem, s>>>(fl, fu, offL, offU, L, coreN, X, partials, Eout);
 }
 
 size_t mttsp_simt_partials_elems(const ModeLayout& L, int gridX) {
@@ -628,11 +633,12 @@ cudaError_t init_simt_attributes() {
 
 void launch_reconstruct(const ModeLayout& L, const double* ltab, const double* utab, const int64_t* offL,
                         const int64_t* offU, const double* coreN, void* out, int out_t, const void* X, int xt,
-                        double* partials, int gridX, cudaStream_t s) {
+                        double* partials, int gridX, cudaStream_t s, bool out_diff) {
   const int r = L.Rn * L.Rn1;
   const size_t smem = (size_t)KT * r * sizeof(double) + 3 * KT * sizeof(int64_t);
-#define TRALS_RECON(XT_, OT_) \
-  reconstruct_kernel<XT_, OT_><<<gridX, THREADS, smem, s>>>(ltab, utab, offL, offU, L, coreN, (OT_*)out, X, partials)
+#define TRALS_RECON(XT_, OT_)                                                                                  \
+  reconstruct_kernel<XT_, OT_><<<gridX, THREADS, smem, s>>>(ltab, utab, offL, offU, L, coreN, (OT_*)out, X, partials, \
+                                                            out_diff ? 1 : 0)
   if (out == nullptr || out_t == TRALS_X_F64) {
     if (xt == TRALS_X_F32)
       TRALS_RECON(float, double);

@@ -16,6 +16,10 @@ using namespace trals;
 namespace {
 
 constexpr int kResCap = 1 << 14;
+// Corrected semi-normal steps after the QR solve.  Each multiplies the solution error by about
+// cond(G^{!=n}_[2])^2 u; two steps bring it to the Householder least-squares level for condition
+// numbers up to about 1e7 (one step leaves (cond^2 u)^2, e.g. 2e-6 at cond = 3.5e6).
+constexpr int kQrRefineSteps = 2;
 
 __global__ void finalize_explicit_residual(const double* red2, double* res_hist, int* sweep_ctr) {
   const int s = *sweep_ctr;
@@ -111,6 +115,7 @@ cudaError_t init_kernel_attributes() {
   cudaError_t e = init_small_attributes();
   if (e == cudaSuccess) e = init_simt_attributes();
   if (e == cudaSuccess) e = init_tc_attributes();
+  if (e == cudaSuccess) e = init_qr_attributes();
   return e;
 }
 }  // namespace trals
@@ -137,6 +142,11 @@ struct trals_plan {
   ModeLayout lay[TRALS_MAX_ORDER];
   int gridX[TRALS_MAX_ORDER] = {};
   double* partials = nullptr;
+  double *qrB = nullptr, *qrR0 = nullptr, *qrR1 = nullptr, *qrW = nullptr;   // QR solve workspace
+  void* E = nullptr;              // QR solve: residual tensor X - X_hat for the refinement step
+  double *dM = nullptr, *dG = nullptr;
+  void* Ablk = nullptr;           // explicit-Gram variant: subchain row block
+  double* gpart = nullptr;        // explicit-Gram variant: partial Gram matrices
   double* red2 = nullptr;         // [2] explicit residual reduction
   double* normX2 = nullptr;
   double* res_hist = nullptr;
@@ -264,18 +274,83 @@ int enqueue_explicit_residual(trals_plan* p, cudaStream_t s) {
   return (N - 1) + (p->opts.mode == TRALS_MODE_FP64 ? 1 : 2) + 1;
 }
 
+// One corrected semi-normal step after the QR solve (Bjorck, CSNE): with the residual tensor
+// E = X - TR(cores) taken against the caller's full-precision X, dM = E_[n] G^{!=n}_[2] (an MTTSP of
+// E) and G_{n(2)} += dM R^{-1} R^{-T}.  In the reduced-precision modes this also lifts the BF16 or
+// FP32 right-hand side to the accuracy of the source X.
+int enqueue_qr_refinement(trals_plan* p, int n, cudaStream_t s) {
+  const ModeLayout& L = p->lay[n];
+  const int N = p->N;
+  int launches = N - 1;
+  build_tables(L, p->cores, p->I, p->R, p->ltab, p->utab, p->tscratch, s);
+  MttspSimtArgs a;
+  a.X = p->E;
+  a.ltab = p->ltab;
+  a.utab = p->utab;
+  a.offL = p->offL[n];
+  a.offU = p->offU[n];
+  a.L = L;
+  a.partials = p->partials;
+  a.M = p->dM;
+  if (p->opts.mode == TRALS_MODE_FP64) {
+    launch_reconstruct(L, p->ltab, p->utab, p->offL[n], p->offU[n], p->cores[n], p->E, TRALS_X_F64, p->X, p->xt,
+                       nullptr, p->gridX[n], s, true);
+    a.xt = TRALS_X_F64;
+    a.gridX = p->gridX[n];
+    launch_mttsp_simt(a, s);
+    launches += 3;
+  } else {
+    const int64_t nl = L.nL * L.Rn1 * L.Rs, nu = L.nU * L.Rs * L.Rn;
+    float* fl = reinterpret_cast<float*>(p->tscratch);
+    launch_residual_f32(L, p->ltab, p->utab, fl, nl, nu, p->offL[n], p->offU[n], p->cores[n], p->X, p->xt,
+                        p->partials, residual_f32_grid(L), s, static_cast<float*>(p->E));
+    a.xt = TRALS_X_F32;
+    if (mttsp_simt_f32_fits(L)) {
+      a.gridX = mttsp_simt_f32_grid(L);
+      launch_mttsp_simt_f32(a, fl, fl + nl, s);   // the tables' FP32 copies are still in the scratch
+    } else {
+      a.gridX = p->gridX[n];
+      launch_mttsp_simt(a, s);
+    }
+    launches += 4;
+  }
+  launch_chol_solve(p->Lmat, p->dM, L.Rn, L.In, L.Rn1, p->dG, p->ctx->d_status, s);
+  launch_axpy((int64_t)L.Rn * L.In * L.Rn1, p->dG, p->cores[n], s);
+  return launches + 2;
+}
+
 int enqueue_sweep(trals_plan* p) {
   cudaStream_t s = p->ctx->stream;
   int launches = 0;
   const int N = p->N;
+  const bool qr = p->opts.solver == TRALS_SOLVE_QR;
   for (int n = 0; n < N; ++n) {
     const int Rn = p->R[n], Rn1 = p->R[(n + 1) % N];
-    launches += enqueue_coef(N, p->R, p->gam, n, p->chainA, p->chainB, p->S, s);
+    if (qr) {
+      // R factor of G^{!=n}_[2] by structured QR; L = R^T replaces the Cholesky factor of S_n
+      launches += launch_qr_factor(N, p->I, p->R, n, p->cores, p->qrB, p->qrR0, p->qrR1, p->qrW, p->Lmat,
+                                   p->ctx->d_status, p->sweep_ctr, s);
+    } else if (p->opts.gram == TRALS_GRAM_EXPLICIT) {
+      // regular TR-ALS normal equations: S_n from the explicitly formed subchain matrix
+      build_tables(p->lay[n], p->cores, p->I, p->R, p->ltab, p->utab, p->tscratch, s);
+      launches += (N - 1) + launch_explicit_gram(p->lay[n], p->ltab, p->utab, p->opts.mode == TRALS_MODE_FP64,
+                                                 p->Ablk, p->gpart, p->S, s);
+    } else {
+      launches += enqueue_coef(N, p->R, p->gam, n, p->chainA, p->chainB, p->S, s);
+    }
     launches += enqueue_mttsp(p, n, s);
-    launches += launch_cholesky(p->S, p->Lmat, Rn * Rn1, p->ctx->d_status, p->sweep_ctr, n, s);
+    if (!qr) launches += launch_cholesky(p->S, p->Lmat, Rn * Rn1, p->ctx->d_status, p->sweep_ctr, n, s);
     launch_chol_solve(p->Lmat, p->M, Rn, p->I[n], Rn1, p->cores[n], p->ctx->d_status, s);
+    ++launches;
+    if (qr)
+      for (int step = 0; step < kQrRefineSteps; ++step) launches += enqueue_qr_refinement(p, n, s);
     launch_gamma(p->cores[n], Rn, p->I[n], Rn1, p->gam[n], s);
-    launches += 2;
+    ++launches;
+  }
+  if (qr) {
+    // the residual identity needs S_N = L L^T
+    launch_llt(p->Lmat, p->R[N - 1] * p->R[0], p->S, s);
+    ++launches;
   }
   const int n = N - 1;
   if (p->opts.explicit_residual) {
@@ -374,11 +449,10 @@ trals_status plan_build(trals_ctx* ctx, int N, const int64_t* I, const int32_t* 
     ctx->last_error = "unknown mode or X type";
     return TRALS_E_ARG;
   }
-  if (o.solver != TRALS_SOLVE_CHOL || o.gram != TRALS_GRAM_STRUCTURED) {
-    if (!(o.solver == TRALS_SOLVE_QR || o.gram == TRALS_GRAM_EXPLICIT)) {
-      ctx->last_error = "unknown solver or gram option";
-      return TRALS_E_ARG;
-    }
+  if ((o.solver != TRALS_SOLVE_CHOL && o.solver != TRALS_SOLVE_QR) ||
+      (o.gram != TRALS_GRAM_STRUCTURED && o.gram != TRALS_GRAM_EXPLICIT)) {
+    ctx->last_error = "unknown solver or gram option";
+    return TRALS_E_ARG;
   }
   if (o.mode == TRALS_MODE_FP64 && xt != TRALS_X_F64) {
     ctx->last_error = "FP64 mode needs an FP64 X";
@@ -454,6 +528,38 @@ trals_status plan_build(trals_ctx* ctx, int N, const int64_t* I, const int32_t* 
   PLAN_TRY(p->alloc(&p->utab, (size_t)maxTab));
   PLAN_TRY(p->alloc(&p->tscratch, (size_t)maxTab));
   PLAN_TRY(p->alloc(&p->partials, std::max<size_t>(maxPart, 2 * 1024)));
+  if (o.solver == TRALS_SOLVE_QR) {
+    QrSizes qz;
+    for (int n = 0; n < N; ++n) {
+      const QrSizes z = qr_sizes(N, I, R, n);
+      qz.B_elems = std::max(qz.B_elems, z.B_elems);
+      qz.R_elems = std::max(qz.R_elems, z.R_elems);
+      qz.W_elems = std::max(qz.W_elems, z.W_elems);
+    }
+    PLAN_TRY(p->alloc(&p->qrB, (size_t)qz.B_elems));
+    PLAN_TRY(p->alloc(&p->qrR0, (size_t)qz.R_elems));
+    PLAN_TRY(p->alloc(&p->qrR1, (size_t)qz.R_elems));
+    PLAN_TRY(p->alloc(&p->qrW, (size_t)std::max<int64_t>(qz.W_elems, 1)));
+    unsigned char* e8 = nullptr;
+    PLAN_TRY(p->alloc(&e8, (size_t)p->numel * (o.mode == TRALS_MODE_FP64 ? 8 : 4)));
+    p->E = e8;
+    PLAN_TRY(p->alloc(&p->dM, (size_t)maxMr));
+    int64_t maxCore = 0;
+    for (int n = 0; n < N; ++n) maxCore = std::max<int64_t>(maxCore, (int64_t)R[n] * I[n] * R[(n + 1) % N]);
+    PLAN_TRY(p->alloc(&p->dG, (size_t)maxCore));
+  }
+  if (o.gram == TRALS_GRAM_EXPLICIT) {
+    size_t ab = 0, pe = 0;
+    for (int n = 0; n < N; ++n) {
+      const ExplicitGramSizes z = explicit_gram_sizes(p->lay[n], o.mode == TRALS_MODE_FP64);
+      ab = std::max(ab, z.A_bytes);
+      pe = std::max(pe, z.part_elems);
+    }
+    unsigned char* a = nullptr;
+    PLAN_TRY(p->alloc(&a, ab));
+    p->Ablk = a;
+    PLAN_TRY(p->alloc(&p->gpart, pe));
+  }
   PLAN_TRY(p->alloc(&p->red2, 2));
   PLAN_TRY(p->alloc(&p->normX2, 1));
   PLAN_TRY(p->alloc(&p->res_hist, kResCap));
@@ -805,6 +911,64 @@ trals_status trals_coef_matrix(trals_ctx* ctx, int N, const int32_t* R, const do
   if (b) cudaFree(b);
   TRALS_CUDA_TRY(ctx, e);
   return TRALS_OK;
+}
+
+trals_status trals_coef_matrix_explicit(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R,
+                                        const double* const* cores_dev, int n, int fp64, double* S_dev) {
+  if (!ctx || !cores_dev || !S_dev || n < 0 || n >= N) return TRALS_E_ARG;
+  trals_status st = check_shape(ctx, N, I, R);
+  if (st != TRALS_OK) return st;
+  const ModeLayout L = make_mode_layout(N, I, R, n);
+  const int64_t tab = table_level_max_elems(L, I, R);
+  const ExplicitGramSizes z = explicit_gram_sizes(L, fp64 != 0);
+  double *lt = nullptr, *ut = nullptr, *sc = nullptr, *part = nullptr;
+  void* A = nullptr;
+  cudaError_t e = cudaMalloc(&lt, tab * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&ut, tab * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&sc, tab * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&part, z.part_elems * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&A, z.A_bytes);
+  if (e == cudaSuccess) {
+    build_tables(L, cores_dev, I, R, lt, ut, sc, ctx->stream);
+    launch_explicit_gram(L, lt, ut, fp64 != 0, A, part, S_dev, ctx->stream);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  }
+  cudaFree(lt);
+  cudaFree(ut);
+  cudaFree(sc);
+  cudaFree(part);
+  cudaFree(A);
+  TRALS_CUDA_TRY(ctx, e);
+  return TRALS_OK;
+}
+
+trals_status trals_qr_r_factor(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R,
+                               const double* const* cores_dev, int n, double* R_dev) {
+  if (!ctx || !cores_dev || !R_dev || n < 0 || n >= N) return TRALS_E_ARG;
+  trals_status st = check_shape(ctx, N, I, R);
+  if (st != TRALS_OK) return st;
+  const QrSizes z = qr_sizes(N, I, R, n);
+  const int r = R[n] * R[(n + 1) % N];
+  double *B = nullptr, *R0 = nullptr, *R1 = nullptr, *W = nullptr, *Lm = nullptr;
+  cudaError_t e = cudaMalloc(&B, z.B_elems * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&R0, z.R_elems * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&R1, z.R_elems * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&W, std::max<int64_t>(z.W_elems, 1) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&Lm, ((size_t)r * r + r) * sizeof(double));
+  if (e == cudaSuccess) {
+    launch_qr_factor(N, I, R, n, cores_dev, B, R0, R1, W, Lm, ctx->d_status, nullptr, ctx->stream);
+    launch_transpose(Lm, r, R_dev, ctx->stream);
+    e = cudaGetLastError();
+  }
+  st = (e == cudaSuccess) ? read_status(ctx) : TRALS_E_CUDA;
+  if (e != cudaSuccess) ctx->last_error = cudaGetErrorString(e);
+  cudaFree(B);
+  cudaFree(R0);
+  cudaFree(R1);
+  cudaFree(W);
+  cudaFree(Lm);
+  return st;
 }
 
 trals_status trals_mttsp(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R, const void* X_dev, int xt,

@@ -1,0 +1,278 @@
+// QR-stabilised solve of the core subproblem (Sec. 3.2, TR-ALS-QR) without forming S_n.
+//
+// The R factor of the subchain matrix A = G^{!=n}_[2] is computed by a recursive structured QR along
+// the subchain c_1 = n+1, ..., c_{N-1} = n-1 (eq. subchain_new).  The first step is the mode-2 QR of
+// G_{c_1} (Def. mode-n QR).  Each later step writes the running product as
+// (R_t x_2 Q_t) [x]_2 G_{c_{t+1}} = (R_t [x]_2 G_{c_{t+1}}) x_2 (I (x) Q_t) (Prop. slice_kron).  The
+// factor I (x) Q_t has orthonormal columns, so the R factor of the product equals that of the
+// small matrix (R_t [x]_2 G_{c_{t+1}})_[2].  That matrix has at most R_{n+1} R_{c_{t+1}} I_{c_{t+1}}
+// rows and is factorised by a TSQR tree: Householder QR of row blocks, then pairwise QR of stacked
+// R factors.  The paper's Alg. 3 reaches the same R by the QR of V_n (Alg. 3 line 6), whose size
+// grows as R^{2N-2}; here every step stays R^2 I x R^2.
+//
+// With A = Q R, the normal equations G_{n(2)} A^T A = M_n read G_{n(2)} R^T R = M_n, so L = R^T
+// takes the place of the Cholesky factor of S_n.  R comes from orthogonal transformations of the
+// cores, so the squared condition number of S_n never enters the factor.
+#include <algorithm>
+
+#include "trals_internal.cuh"
+
+namespace trals {
+
+namespace {
+
+constexpr int QT = 256;   // threads per QR CTA
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[32] = v;
+  }
+  __syncthreads();
+  v = red[32];
+  __syncthreads();
+  return v;
+}
+
+// Householder QR (GvL Alg. 5.2.1) of the m x C matrix W (column-major, leading dimension ld) in place,
+// by one CTA.  On exit rows [0, min(m, C)) hold R (upper trapezoidal); everything below is zero.
+__device__ void cta_householder_qr(double* W, int m, int C, int64_t ld, double* v, double* red) {
+  const int kmax = min(m, C);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = 0; j < kmax; ++j) {
+    double s = 0.0;
+    for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
+      const double x = W[i + (int64_t)ld * j];
+      v[i] = x;
+      s = fma(x, x, s);
+    }
+    s = block_sum(s, red);
+    if (s == 0.0) continue;   // uniform: the column is already zero
+    const double x0 = v[j];
+    const double nrm = sqrt(s);
+    const double alpha = x0 >= 0.0 ? -nrm : nrm;
+    const double v0 = x0 - alpha;
+    const double tau = 2.0 / (s - x0 * x0 + v0 * v0);
+    __syncthreads();
+    if (threadIdx.x == 0) v[j] = v0;
+    __syncthreads();
+    for (int c = j + 1 + warp; c < C; c += nw) {
+      double w = 0.0;
+      for (int i = j + lane; i < m; i += 32) w = fma(v[i], W[i + (int64_t)ld * c], w);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+      const double f = tau * w;
+      for (int i = j + lane; i < m; i += 32) W[i + (int64_t)ld * c] = fma(-f, v[i], W[i + (int64_t)ld * c]);
+    }
+    if (threadIdx.x == 0) W[j + (int64_t)ld * j] = alpha;
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) W[i + (int64_t)ld * j] = 0.0;
+    __syncthreads();
+  }
+}
+
+// B[(s + m i) + M (d + Rd b)] = sum_c P[s + ldp (c + Rc b)] G[c + Rc (i + I d)]: the mode-2 unfolding of
+// (R_t [x]_2 G) with R_t given as an m x (Rc Rb) matrix (column c + Rc b).  With first != 0 the
+// running product is the identity (m = 1): B[i + I (d + Rd b)] = G[b + Rc (i + I d)] (Rc = Rb).
+__global__ void qr_form_kernel(const double* __restrict__ P, int m, int ldp, const double* __restrict__ G, int Rc,
+                               int64_t I, int Rd, int Rb, int first, double* __restrict__ B) {
+  const int64_t M = (int64_t)m * I;
+  const int64_t total = M * Rd * Rb;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = e % M;
+    const int col = (int)(e / M);
+    const int d = col % Rd, b = col / Rd;
+    const int s = (int)(row % m);
+    const int64_t i = row / m;
+    double acc;
+    if (first) {
+      acc = G[b + (int64_t)Rc * (i + I * d)];
+    } else {
+      acc = 0.0;
+      for (int c = 0; c < Rc; ++c) acc = fma(P[s + (int64_t)ldp * (c + Rc * b)], G[c + (int64_t)Rc * (i + I * d)], acc);
+    }
+    B[e] = acc;
+  }
+}
+
+// TSQR leaves: CTA b factorises rows [b Mb, min(M, (b+1) Mb)) of B (ld = M) in place and writes its
+// R factor to Rout[b] (C x C, column-major, zero below the factor).
+__global__ void __launch_bounds__(QT) tsqr_leaf_kernel(double* __restrict__ B, int64_t M, int C, int Mb,
+                                                       double* __restrict__ Rout) {
+  extern __shared__ double qsm[];
+  double* red = qsm;          // 33
+  double* v = qsm + 40;       // Mb
+  const int64_t r0 = (int64_t)blockIdx.x * Mb;
+  const int m = (int)min((int64_t)Mb, M - r0);
+  double* W = B + r0;
+  cta_householder_qr(W, m, C, M, v, red);
+  double* R = Rout + (int64_t)blockIdx.x * C * C;
+  for (int e = threadIdx.x; e < C * C; e += blockDim.x) {
+    const int i = e % C, j = e / C;
+    R[e] = (i < m && i <= j) ? W[i + M * j] : 0.0;
+  }
+}
+
+// TSQR tree level: CTA b stacks Rin[2b] over Rin[2b+1] (2C x C) in the workspace, factorises it and
+// writes the R factor to Rout[b].  An unpaired last factor is copied through.
+__global__ void __launch_bounds__(QT) tsqr_merge_kernel(const double* __restrict__ Rin, int nin, int C,
+                                                        double* __restrict__ Wk, double* __restrict__ Rout) {
+  extern __shared__ double qsm[];
+  double* red = qsm;
+  double* v = qsm + 40;       // 2C
+  const int b = blockIdx.x;
+  const double* A0 = Rin + (int64_t)(2 * b) * C * C;
+  double* R = Rout + (int64_t)b * C * C;
+  if (2 * b + 1 >= nin) {
+    for (int e = threadIdx.x; e < C * C; e += blockDim.x) R[e] = A0[e];
+    return;
+  }
+  const double* A1 = A0 + (int64_t)C * C;
+  double* W = Wk + (int64_t)b * 2 * C * C;
+  for (int e = threadIdx.x; e < 2 * C * C; e += blockDim.x) {
+    const int i = e % (2 * C), j = e / (2 * C);
+    W[e] = i < C ? A0[i + C * j] : A1[(i - C) + C * j];
+  }
+  __syncthreads();
+  cta_householder_qr(W, 2 * C, C, 2 * C, v, red);
+  for (int e = threadIdx.x; e < C * C; e += blockDim.x) {
+    const int i = e % C, j = e / C;
+    R[e] = i <= j ? W[i + 2 * C * j] : 0.0;
+  }
+}
+
+// Final factor: rows scaled to a positive diagonal, L = R^T with its reciprocal diagonal appended
+// (the layout the Cholesky solve reads).  A zero or non-finite diagonal means G^{!=n}_[2] is rank
+// deficient: reported like a failed Cholesky pivot.
+__global__ void qr_to_l_kernel(const double* __restrict__ Rf, int r, double* __restrict__ Lmat, DevStatus* st,
+                               const int* sweep_ctr, int mode) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * r; e += gridDim.x * blockDim.x) {
+    const int i = e % r, j = e / r;   // L[i, j] = sign_j R[j, i]
+    const double dj = Rf[j + (int64_t)r * j];
+    Lmat[e] = i >= j ? (dj < 0.0 ? -Rf[j + (int64_t)r * i] : Rf[j + (int64_t)r * i]) : 0.0;
+  }
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < r; j += gridDim.x * blockDim.x) {
+    const double d = fabs(Rf[j + (int64_t)r * j]);
+    if (!(d > 0.0) || !isfinite(d)) set_status(st, TRALS_E_NOT_SPD, sweep_ctr ? *sweep_ctr : -1, mode, j, d);
+    Lmat[(int64_t)r * r + j] = 1.0 / d;
+  }
+}
+
+// S = L L^T (the coefficient matrix, for the residual identity of the QR path)
+__global__ void llt_kernel(const double* __restrict__ Lmat, int r, double* __restrict__ S) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * r; e += gridDim.x * blockDim.x) {
+    const int i = e % r, j = e / r;
+    double acc = 0.0;
+    for (int k = 0; k <= min(i, j); ++k) acc = fma(Lmat[i + (int64_t)r * k], Lmat[j + (int64_t)r * k], acc);
+    S[e] = acc;
+  }
+}
+
+__global__ void transpose_kernel(const double* __restrict__ A, int r, double* __restrict__ B) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * r; e += gridDim.x * blockDim.x)
+    B[(e / r) + (int64_t)r * (e % r)] = A[e];
+}
+
+__global__ void axpy_kernel(int64_t n, const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    y[e] += x[e];
+}
+
+int grid_of(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8)); }
+
+}  // namespace
+
+// Chain steps of mode n: (rows M_t, columns C_t) of each step's matrix, and the TSQR leaf height.
+static void qr_steps(int N, const int64_t* I, const int32_t* R, int n, int64_t* Ms, int* Cs) {
+  const int Rb = R[(n + 1) % N];
+  int64_t m = 1;
+  for (int t = 1; t <= N - 1; ++t) {
+    const int c = (n + t) % N;
+    const int Rd = R[(c + 1) % N];
+    Ms[t - 1] = m * I[c];
+    Cs[t - 1] = Rd * Rb;
+    m = std::min<int64_t>(Ms[t - 1], Cs[t - 1]);
+  }
+}
+
+static int leaf_rows(int C) { return std::max(2 * C, 64); }
+
+QrSizes qr_sizes(int N, const int64_t* I, const int32_t* R, int n) {
+  QrSizes z;
+  int64_t Ms[kMaxOrder];
+  int Cs[kMaxOrder];
+  qr_steps(N, I, R, n, Ms, Cs);
+  for (int t = 0; t < N - 1; ++t) {
+    const int64_t C = Cs[t];
+    const int64_t nb = (Ms[t] + leaf_rows(Cs[t]) - 1) / leaf_rows(Cs[t]);
+    z.B_elems = std::max<int64_t>(z.B_elems, Ms[t] * C);
+    z.R_elems = std::max<int64_t>(z.R_elems, nb * C * C);
+    z.W_elems = std::max<int64_t>(z.W_elems, ((nb + 1) / 2) * 2 * C * C);
+  }
+  return z;
+}
+
+size_t qr_smem_bytes(int C) { return (40 + (size_t)std::max(leaf_rows(C), 2 * C)) * sizeof(double); }
+
+int launch_qr_factor(int N, const int64_t* I, const int32_t* R, int n, const double* const* cores, double* B,
+                     double* R0, double* R1, double* Wk, double* Lmat, DevStatus* st, const int* sweep_ctr,
+                     cudaStream_t s) {
+  int64_t Ms[kMaxOrder];
+  int Cs[kMaxOrder];
+  qr_steps(N, I, R, n, Ms, Cs);
+  const int Rb = R[(n + 1) % N];
+  int launches = 0;
+  const double* P = nullptr;
+  int m = 1, ldp = 1;
+  for (int t = 1; t <= N - 1; ++t) {
+    const int c = (n + t) % N;
+    const int Rc = R[c], Rd = R[(c + 1) % N];
+    const int64_t M = Ms[t - 1];
+    const int C = Cs[t - 1];
+    qr_form_kernel<<<grid_of(M * C), 256, 0, s>>>(P, m, ldp, cores[c], Rc, I[c], Rd, Rb, t == 1, B);
+    const int Mb = leaf_rows(C);
+    int nb = (int)((M + Mb - 1) / Mb);
+    const size_t smem = qr_smem_bytes(C);
+    tsqr_leaf_kernel<<<nb, QT, smem, s>>>(B, M, C, Mb, R0);
+    launches += 2;
+    double* in = R0;
+    double* out = R1;
+    while (nb > 1) {
+      const int nout = (nb + 1) / 2;
+      tsqr_merge_kernel<<<nout, QT, smem, s>>>(in, nb, C, Wk, out);
+      ++launches;
+      std::swap(in, out);
+      nb = nout;
+    }
+    P = in;   // C x C, rows >= min(M, C) zero
+    m = (int)std::min<int64_t>(M, C);
+    ldp = C;
+  }
+  const int r = Cs[N - 2];
+  qr_to_l_kernel<<<grid_of((int64_t)r * r), 256, 0, s>>>(P, r, Lmat, st, sweep_ctr, n);
+  return launches + 1;
+}
+
+void launch_transpose(const double* A, int r, double* B, cudaStream_t s) {
+  transpose_kernel<<<grid_of((int64_t)r * r), 256, 0, s>>>(A, r, B);
+}
+
+void launch_llt(const double* Lmat, int r, double* S, cudaStream_t s) {
+  llt_kernel<<<grid_of((int64_t)r * r), 256, 0, s>>>(Lmat, r, S);
+}
+
+void launch_axpy(int64_t n, const double* x, double* y, cudaStream_t s) { axpy_kernel<<<grid_of(n), 256, 0, s>>>(n, x, y); }
+
+cudaError_t init_qr_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(tsqr_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(tsqr_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+  return e;
+}
+
+}  // namespace trals

@@ -23,6 +23,17 @@ struct DevStatus {
   double value;
 };
 
+// Record the first failure (later ones are dropped).
+__device__ __forceinline__ void set_status(DevStatus* st, int code, int sweep, int mode, int index, double v) {
+  if (st == nullptr) return;
+  if (atomicCAS(&st->code, 0, code) == 0) {
+    st->sweep = sweep;
+    st->mode = mode;
+    st->index = index;
+    st->value = v;
+  }
+}
+
 // ---------------------------------------------------------------- per-mode MTTSP layout
 // The other modes of mode n in subchain order c_1..c_{N-1} = n+1..N,1..n-1 (eq. subchain_new)
 // are split into Left = c_1..c_m and Right = c_{m+1}..c_{N-1}.  G^{!=n}(k) = L(l) U(u) with
@@ -94,7 +105,7 @@ void launch_mttsp_simt(const MttspSimtArgs& a, cudaStream_t s);
 // xhat(i_n, k) = sum_r Z[i_n, r] G^{!=n}(k)[b, a] with Z the unfolding of core n.
 void launch_reconstruct(const ModeLayout& L, const double* ltab, const double* utab, const int64_t* offL,
                         const int64_t* offU, const double* coreN, void* out, int out_t, const void* X, int xt,
-                        double* partials, int gridX, cudaStream_t s);
+                        double* partials, int gridX, cudaStream_t s, bool out_diff = false);
 // Sum of `count` partials into out[0] (and out[1] if two interleaved series), fixed order.
 void launch_reduce_pairs(const double* partials, int count, double* out, cudaStream_t s);
 // Explicit residual with X_hat regenerated in FP32 (reduced-precision modes): converts the two FP64
@@ -104,7 +115,7 @@ size_t residual_f32_smem(const ModeLayout& L);
 int residual_f32_grid(const ModeLayout& L);
 void launch_residual_f32(const ModeLayout& L, const double* ltab, const double* utab, float* ftab, int64_t ltab_elems,
                          int64_t utab_elems, const int64_t* offL, const int64_t* offU, const double* coreN,
-                         const void* X, int xt, double* partials, int gridX, cudaStream_t s);
+                         const void* X, int xt, double* partials, int gridX, cudaStream_t s, float* Eout = nullptr);
 
 // Cholesky (K4): factor S (r x r, lower triangle) into L (r x r, then r reciprocal diagonal entries, so
 // Lmat holds r*r + r doubles); status on failure.
@@ -127,6 +138,36 @@ void launch_quantize(const void* src, int src_t, int64_t count, __nv_bfloat16* h
 // FP64 -> FP32 copy (FP32 mode fed with an FP64 X).
 void launch_convert_f32(const void* src_f64, int64_t count, float* dst, cudaStream_t s);
 void launch_zero_status(DevStatus* st, cudaStream_t s);
+
+// ---------------------------------------------------------------- explicit-subchain Gram (Alg. 1)
+struct ExplicitGramSizes {
+  int64_t block_rows = 0;   // subchain rows formed per block
+  int groups = 0;           // CTAs along the rows (partial Gram matrices)
+  size_t A_bytes = 0;       // row-block buffer
+  size_t part_elems = 0;    // partial Gram matrices (doubles)
+};
+ExplicitGramSizes explicit_gram_sizes(const ModeLayout& L, bool fp64);
+// S (r x r, full symmetric, column-major) = (G^{!=n}_[2])^T G^{!=n}_[2] with the subchain matrix formed
+// explicitly from the two FP64 partial-chain tables (build_tables).  Returns the launch count.
+int launch_explicit_gram(const ModeLayout& L, const double* ltab, const double* utab, bool fp64, void* Ablk,
+                         double* part, double* S, cudaStream_t s);
+
+// ---------------------------------------------------------------- QR-stabilised solve (Sec. 3.2)
+struct QrSizes {
+  int64_t B_elems = 0;   // largest chain-step matrix
+  int64_t R_elems = 0;   // TSQR leaf factors (each of the two ping-pong buffers)
+  int64_t W_elems = 0;   // TSQR merge workspace
+};
+QrSizes qr_sizes(int N, const int64_t* I, const int32_t* R, int n);
+// R factor of G^{!=n}_[2] by recursive structured QR (FP64), delivered as Lmat = R^T (r x r) followed by
+// its reciprocal diagonal: the layout launch_chol_solve reads.  Returns the launch count.
+int launch_qr_factor(int N, const int64_t* I, const int32_t* R, int n, const double* const* cores, double* B,
+                     double* R0, double* R1, double* Wk, double* Lmat, DevStatus* st, const int* sweep_ctr,
+                     cudaStream_t s);
+void launch_llt(const double* Lmat, int r, double* S, cudaStream_t s);
+void launch_transpose(const double* A, int r, double* B, cudaStream_t s);
+void launch_axpy(int64_t n, const double* x, double* y, cudaStream_t s);
+cudaError_t init_qr_attributes();
 
 // ---------------------------------------------------------------- asynchronous plan steps (serving)
 // As trals_plan_create / trals_plan_set_cores but without waiting on the stream (host sources may

@@ -71,6 +71,97 @@ def test_coef_matrix_equals_explicit_gram(ctx, I, R):
         assert rel(S.cpu().numpy().reshape(r, r, order="F"), ref) < 1e-12
 
 
+@pytest.mark.parametrize("I,R", SHAPES + [((60, 60, 60, 60), (10, 10, 10, 10))])
+def test_coef_matrix_explicit_subchain_gram(ctx, I, R):
+    """Explicit-subchain variant (regular TR-ALS): S_n = A^T A with A formed on the device, FP64
+    within 1e-12 of the oracle's explicit A^T A; FP32 rows within FP32 rounding (1e-5)."""
+    cores = TI.gaussian_cores(5, I, R)
+    cd = [P.core_to_device(G) for G in cores]
+    N = len(I)
+    for n in range(N):
+        r = R[n] * R[(n + 1) % N]
+        if np.prod(I) > 1e6 and n > 0:
+            continue                       # full-size shape: one mode (the oracle's A is 216000 x 100)
+        A = O.subchain_unfolded(cores, n)
+        ref = A.T @ A
+        for fp64, tol in ((True, 1e-12), (False, 1e-5)):
+            S = torch.zeros(r * r, dtype=torch.float64, device="cuda")
+            P.trals_coef_matrix_explicit(ctx, I, R, cd, n, S, fp64)
+            got = S.cpu().numpy().reshape(r, r, order="F")
+            assert np.array_equal(got, got.T)
+            assert rel(got, ref) < tol, (n, fp64, rel(got, ref))
+
+
+@pytest.mark.parametrize("I,R", SHAPES[:3])
+def test_decompose_explicit_gram_one_sweep_matches_oracle(ctx, I, R):
+    """gram = explicit (regular TR-ALS normal equations) in FP64: cores after one sweep within 1e-9
+    of the oracle's Cholesky normal equations on the explicit subchain matrix."""
+    X, init = _problem(I, R)
+    cores = [G.copy() for G in init]
+    P.trals_decompose(ctx, I, R, X, cores, 1, P.make_opts("fp64", gram=P.GRAM_EXPLICIT))
+    ref, _ = O.tr_als(X, init, 1, "chol")
+    for a, b in zip(cores, ref):
+        assert rel(a, b) < 1e-9
+
+
+@pytest.mark.parametrize("I,R", SHAPES + [((40, 40, 40, 40), (8, 10, 12, 10)), ((300, 30, 400), (3, 4, 2))])
+def test_qr_r_factor_matches_householder_qr(ctx, I, R):
+    """R factor of G^{!=n}_[2] by the structured recursive QR (never forming S_n) equals the R of a
+    Householder QR of the explicit subchain matrix (LAPACK), rows scaled to a positive diagonal."""
+    cores = TI.gaussian_cores(6, I, R)
+    cd = [P.core_to_device(G) for G in cores]
+    N = len(I)
+    for n in range(N):
+        r = R[n] * R[(n + 1) % N]
+        A = O.subchain_unfolded(cores, n)
+        Rref = np.linalg.qr(A, mode="r")
+        Rref = Rref * np.sign(np.diag(Rref))[:, None]
+        Rd = torch.zeros(r * r, dtype=torch.float64, device="cuda")
+        P.trals_qr_r_factor(ctx, I, R, cd, n, Rd)
+        got = Rd.cpu().numpy().reshape(r, r, order="F")
+        assert np.allclose(np.tril(got, -1), 0.0)
+        assert rel(got, Rref) < 1e-11, (n, rel(got, Rref))
+
+
+@pytest.mark.parametrize("I,R", SHAPES[:3] + [((40, 24, 33, 20), (4, 6, 3, 5))])
+def test_decompose_qr_one_sweep_matches_oracle(ctx, I, R):
+    """solver = QR in FP64: cores after one sweep within 1e-9 of the oracle's Householder QR least
+    squares (regular TR-ALS, which TR-ALS-QR equals in exact arithmetic)."""
+    X, init = _problem(I, R)
+    cores = [G.copy() for G in init]
+    res = P.trals_decompose(ctx, I, R, X, cores, 2, P.make_opts("fp64", solver=P.SOLVE_QR))
+    ref, ref_res = O.tr_als(X, init, 2, "qr")
+    for a, b in zip(cores, ref):
+        assert rel(a, b) < 1e-9
+    np.testing.assert_allclose(res, ref_res, rtol=1e-8)
+
+
+@pytest.mark.parametrize("eta", [1e-9, 1e-3])
+def test_qr_solver_stays_accurate_where_normal_equations_do_not(ctx, eta):
+    """Collinear cores (unit-norm unfolding columns with pairwise inner product 1 - 1e-6, the
+    construction of the paper's ill-conditioned experiments): the first core update of a sweep is a
+    least-squares problem with cond(G^{!=1}_[2]) ~ 3.5e6, whose solution LAPACK's QR and SVD solvers
+    agree on to ~1e-14.  The QR-stabilised solve matches it to 1e-8; the Cholesky normal equations
+    (cond^2 ~ 1.2e13) break down or land far off.  Only core 1 is compared: the later updates of
+    the sweep become far worse conditioned (~1e10), where no solver is reproducible."""
+    I, R = (60, 50, 40), (2, 3, 2)
+    truth = TI.collinear_cores(31, I, R, 1.0 - 1e-6)
+    X = TI.add_relative_noise(O.tr_full(truth), TI.gaussian_noise(31, I), eta)
+    init = TI.collinear_cores(32, I, R, 1.0 - 1e-6)
+    ref = O.als_update(X, [G.copy() for G in init], 0, "qr")
+    errs = {}
+    for name, solver in (("qr", P.SOLVE_QR), ("chol", P.SOLVE_CHOL)):
+        cores = [G.copy() for G in init]
+        try:
+            P.trals_decompose(ctx, I, R, X, cores, 1, P.make_opts("fp64", solver=solver))
+            errs[name] = rel(cores[0], ref)
+        except P.TralsError as e:      # the normal equations may not even be numerically SPD
+            assert name == "chol" and e.status == P.E_NOT_SPD
+            errs[name] = np.inf
+    assert errs["qr"] < 1e-8, errs
+    assert errs["chol"] > 100 * errs["qr"], errs
+
+
 @pytest.mark.parametrize("I,R", SHAPES)
 def test_mttsp_fp64_matches_oracle(ctx, I, R):
     X, _ = _problem(I, R)
@@ -262,15 +353,17 @@ def _near_truth_problem(I, R, eta, seed):
     return X, init
 
 
+@pytest.mark.parametrize("solver", ["chol", "qr"])
 @pytest.mark.parametrize("mode", ["fp32", "bf16", "bf16x3"])
 @pytest.mark.parametrize("I,R,eta", [((30, 30, 30, 30), (6, 6, 6, 6), 1e-3), ((40, 24, 32), (4, 5, 3), 1e-2)])
-def test_reduced_precision_residual_gap(ctx, mode, I, R, eta):
+def test_reduced_precision_residual_gap(ctx, mode, I, R, eta, solver):
     """Reduced-precision modes reach the FP64 oracle's residual within 1e-4 (absolute), compared at
     convergence (runs start near the truth, so both precisions sit at the noise floor)."""
     X, init = _near_truth_problem(I, R, eta, 11)
     cores = [G.copy() for G in init]
     Xd = P.tensor_to_device(X, torch.float32)
-    res = P.trals_decompose(ctx, I, R, Xd, cores, 6, P.make_opts(mode))
+    res = P.trals_decompose(ctx, I, R, Xd, cores, 6,
+                            P.make_opts(mode, solver=P.SOLVE_QR if solver == "qr" else P.SOLVE_CHOL))
     _, ref_res = O.tr_als(X, init, 6, "chol")
     gap = abs(O.rel_residual(X, cores) - ref_res[-1])
     assert gap <= 1e-4, gap

@@ -173,6 +173,31 @@ class Request:
     eta: float
 
 
+def collinear_cores(seed: int, I: Sequence[int], R: Sequence[int], gamma: float,
+                    stream: int = STREAM_TRUE_CORES) -> List[np.ndarray]:
+    """Cores whose mode-2 unfoldings (I_n x R_n R_{n+1}) have unit-norm columns with pairwise inner
+    product ``gamma`` (the collinearity-controlled construction of the paper's ill-conditioned
+    experiments, Sec. 4): column k = sqrt(gamma) u_0 + sqrt(1 - gamma) u_k with u_0, u_1, ... orthonormal.
+    Needs I_n > R_n R_{n+1}.  Pure sampling: no tensor-ring arithmetic."""
+    g = _rng(seed, stream)
+    N = len(I)
+    out = []
+    for n in range(N):
+        Rn, Rn1 = int(R[n]), int(R[(n + 1) % N])
+        r = Rn * Rn1
+        if I[n] <= r:
+            raise ValueError("collinear_cores needs I_n > R_n R_{n+1}")
+        U, _ = np.linalg.qr(g.standard_normal((int(I[n]), r + 1)))
+        cols = np.sqrt(gamma) * U[:, :1] + np.sqrt(1.0 - gamma) * U[:, 1:]
+        # column c = a + R_n b of the unfolding is the lateral fibre G[a, :, b]
+        G = np.empty((Rn, int(I[n]), Rn1))
+        for b in range(Rn1):
+            for a in range(Rn):
+                G[a, :, b] = cols[:, a + Rn * b]
+        out.append(G)
+    return out
+
+
 def request_stream(seed: int, count: int = 512, rate_hz: float = 200.0, order_range=(3, 5),
                    size_range=(16, 64), rank_range=(2, 8), sweeps: int = 15, eta: float = 1e-2) -> List[Request]:
     """Poisson arrivals at ``rate_hz``; order, mode sizes and ranks drawn uniformly per request."""
