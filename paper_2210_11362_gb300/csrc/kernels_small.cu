@@ -117,41 +117,51 @@ constexpr int kCholThreads = 1024;
 __global__ void __launch_bounds__(kCholThreads) cholesky_kernel(const double* __restrict__ S, double* __restrict__ Lmat,
                                                                  int r, DevStatus* st, const int* sweep_ctr, int mode) {
   extern __shared__ double sm[];
-  __shared__ int fail;
-  __shared__ double invd_s;
   const bool in_smem = r <= kCholSmemMax;
   double* A = in_smem ? sm : Lmat;
   const int lda = r;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int warp = tid / 32, lane = tid % 32, nw = nt / 32;
+  __shared__ double piv[2];   // sqrt and reciprocal of the current pivot
+  __shared__ int bad;
   for (int e = tid; e < r * r; e += nt) {
     const int i = e % r, j = e / r;
     A[e] = (i >= j) ? S[e] : 0.0;
   }
-  if (tid == 0) fail = 0;
+  // one thread forms each pivot's square root and reciprocal: FP64 sqrt/div are costly on this
+  // part, so they are never computed redundantly by every thread
+  auto pivot = [&](int j) {
+    const double d = A[j + lda * j];
+    if (!(d > 0.0) || !isfinite(d)) {
+      bad = 1;
+      set_status(st, isfinite(d) ? TRALS_E_NOT_SPD : TRALS_E_NONFINITE, sweep_ctr ? *sweep_ctr : -1, mode, j, d);
+    } else {
+      const double l = sqrt(d);
+      piv[0] = l;
+      piv[1] = 1.0 / l;
+    }
+  };
+  __syncthreads();
+  if (tid == 0) {
+    bad = 0;
+    pivot(0);
+  }
   __syncthreads();
   for (int j = 0; j < r; ++j) {
-    if (tid == 0) {
-      const double d = A[j + lda * j];
-      if (!(d > 0.0) || !isfinite(d)) {
-        fail = 1;
-        set_status(st, isfinite(d) ? TRALS_E_NOT_SPD : TRALS_E_NONFINITE, sweep_ctr ? *sweep_ctr : -1, mode, j, d);
-      } else {
-        const double l = sqrt(d);
-        A[j + lda * j] = l;
-        invd_s = 1.0 / l;
-        Lmat[r * r + j] = 1.0 / l;
-      }
-    }
-    __syncthreads();
-    if (fail) return;
-    const double inv = invd_s;
+    if (bad) return;
+    const double l = piv[0], inv = piv[1];
     for (int i = j + 1 + tid; i < r; i += nt) A[i + lda * j] *= inv;
     __syncthreads();
-    // A[i][k] -= A[i][j] A[k][j] for j < k <= i: column k -> warp, rows i -> lanes
+    // A[i][k] -= A[i][j] A[k][j] for j < k <= i: column k -> warp, rows i -> lanes.  Warp 0 starts
+    // with column j + 1, so its lane 0 finishes the next pivot first and forms its root at once.
     for (int k = j + 1 + warp; k < r; k += nw) {
       const double akj = A[k + lda * j];
       for (int i = k + lane; i < r; i += 32) A[i + lda * k] = fma(-A[i + lda * j], akj, A[i + lda * k]);
+      if (tid == 0 && k == j + 1) pivot(j + 1);
+    }
+    if (tid == 0) {
+      A[j + lda * j] = l;
+      Lmat[r * r + j] = inv;
     }
     __syncthreads();
   }
@@ -270,58 +280,77 @@ __global__ void chol_solve_kernel(const double* __restrict__ Lmat, const double*
     inv[j] = Lmat[r * r + j];
   }
   __syncthreads();
-  if (threadIdx.x >= 32) return;
-  const int lane = threadIdx.x;
+  // The dot products against the solved part run on all warps (FP64 throughput is per SMSP); warp 0
+  // then resolves the 32 x 32 diagonal block with shuffles.
+  double (*part)[kPanel] = reinterpret_cast<double (*)[kPanel]>(kLInSmem ? Ls + r * r : Ls);   // [8][kPanel]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = min(8, (int)(blockDim.x >> 5));
   // forward: for each panel, y_p -= L[p, 0:p0] y[0:p0], then solve L_pp y_p = rhs
   for (int p0 = 0; p0 < r; p0 += kPanel) {
     const int nb = min(kPanel, r - p0);
-    double x = 0.0;
-    if (lane < nb) {
-      const int row = p0 + lane;
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-      int k = 0;
-      for (; k + 3 < p0; k += 4) {
-        a0 = fma(L[row + r * k], y[k], a0);
-        a1 = fma(L[row + r * (k + 1)], y[k + 1], a1);
-        a2 = fma(L[row + r * (k + 2)], y[k + 2], a2);
-        a3 = fma(L[row + r * (k + 3)], y[k + 3], a3);
+    if (warp < nw) {
+      double a0 = 0.0, a1 = 0.0;
+      if (lane < nb) {
+        const int row = p0 + lane;
+        int k = warp;
+        for (; k + nw < p0; k += 2 * nw) {
+          a0 = fma(L[row + r * k], y[k], a0);
+          a1 = fma(L[row + r * (k + nw)], y[k + nw], a1);
+        }
+        for (; k < p0; k += nw) a0 = fma(L[row + r * k], y[k], a0);
       }
-      for (; k < p0; ++k) a0 = fma(L[row + r * k], y[k], a0);
-      x = y[row] - ((a0 + a1) + (a2 + a3));
+      part[warp][lane] = a0 + a1;
     }
-    for (int j = 0; j < nb; ++j) {
-      const double xj = __shfl_sync(0xffffffffu, x, j) * inv[p0 + j];
-      if (lane == j) x = xj;
-      if (lane > j && lane < nb) x = fma(-L[(p0 + lane) + r * (p0 + j)], xj, x);
+    __syncthreads();
+    if (warp == 0) {
+      double x = 0.0;
+      if (lane < nb) {
+        double acc = 0.0;
+        for (int w = 0; w < nw; ++w) acc += part[w][lane];
+        x = y[p0 + lane] - acc;
+      }
+      for (int j = 0; j < nb; ++j) {
+        const double xj = __shfl_sync(0xffffffffu, x, j) * inv[p0 + j];
+        if (lane == j) x = xj;
+        if (lane > j && lane < nb) x = fma(-L[(p0 + lane) + r * (p0 + j)], xj, x);
+      }
+      if (lane < nb) y[p0 + lane] = x;
     }
-    if (lane < nb) y[p0 + lane] = x;
-    __syncwarp();
+    __syncthreads();
   }
   // backward: for each panel from the last, y_p -= L[p1:r, p]^T z[p1:r], then solve L_pp^T z_p = rhs
   for (int p0 = ((r - 1) / kPanel) * kPanel; p0 >= 0; p0 -= kPanel) {
     const int nb = min(kPanel, r - p0), p1 = p0 + nb;
-    double x = 0.0;
-    if (lane < nb) {
-      const int col = p0 + lane;
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-      int k = p1;
-      for (; k + 3 < r; k += 4) {
-        a0 = fma(L[k + r * col], y[k], a0);
-        a1 = fma(L[(k + 1) + r * col], y[k + 1], a1);
-        a2 = fma(L[(k + 2) + r * col], y[k + 2], a2);
-        a3 = fma(L[(k + 3) + r * col], y[k + 3], a3);
+    if (warp < nw) {
+      double a0 = 0.0, a1 = 0.0;
+      if (lane < nb) {
+        const int col = p0 + lane;
+        int k = p1 + warp;
+        for (; k + nw < r; k += 2 * nw) {
+          a0 = fma(L[k + r * col], y[k], a0);
+          a1 = fma(L[(k + nw) + r * col], y[k + nw], a1);
+        }
+        for (; k < r; k += nw) a0 = fma(L[k + r * col], y[k], a0);
       }
-      for (; k < r; ++k) a0 = fma(L[k + r * col], y[k], a0);
-      x = y[col] - ((a0 + a1) + (a2 + a3));
+      part[warp][lane] = a0 + a1;
     }
-    for (int j = nb - 1; j >= 0; --j) {
-      const double xj = __shfl_sync(0xffffffffu, x, j) * inv[p0 + j];
-      if (lane == j) x = xj;
-      if (lane < j) x = fma(-L[(p0 + j) + r * (p0 + lane)], xj, x);
+    __syncthreads();
+    if (warp == 0) {
+      double x = 0.0;
+      if (lane < nb) {
+        double acc = 0.0;
+        for (int w = 0; w < nw; ++w) acc += part[w][lane];
+        x = y[p0 + lane] - acc;
+      }
+      for (int j = nb - 1; j >= 0; --j) {
+        const double xj = __shfl_sync(0xffffffffu, x, j) * inv[p0 + j];
+        if (lane == j) x = xj;
+        if (lane < j) x = fma(-L[(p0 + j) + r * (p0 + lane)], xj, x);
+      }
+      if (lane < nb) y[p0 + lane] = x;
     }
-    if (lane < nb) y[p0 + lane] = x;
-    __syncwarp();
+    __syncthreads();
   }
+  if (warp != 0) return;
   for (int c = lane; c < r; c += 32) {
     const double z = y[c];
     if (!isfinite(z)) set_status(st, TRALS_E_NONFINITE, -1, -1, (int)i, z);
@@ -544,11 +573,13 @@ int launch_cholesky(const double* S, double* Lmat, int r, DevStatus* st, const i
 void launch_chol_solve(const double* Lmat, const double* M, int Rn, int64_t In, int Rn1, double* G, DevStatus* st,
                        cudaStream_t s) {
   const int r = Rn * Rn1;
-  const size_t smem = ((size_t)r * r + 2 * (size_t)r) * sizeof(double);
+  const size_t part = 8 * kPanel * sizeof(double);   // per-warp partial dot products
+  const size_t smem = ((size_t)r * r + 2 * (size_t)r) * sizeof(double) + part;
   if (smem <= 227 * 1024)
     chol_solve_kernel<true><<<(unsigned)In, 256, smem, s>>>(Lmat, M, Rn, In, Rn1, G, st);
   else
-    chol_solve_kernel<false><<<(unsigned)In, 256, 2 * (size_t)r * sizeof(double), s>>>(Lmat, M, Rn, In, Rn1, G, st);
+    chol_solve_kernel<false><<<(unsigned)In, 256, 2 * (size_t)r * sizeof(double) + part, s>>>(Lmat, M, Rn, In, Rn1,
+                                                                                             G, st);
 }
 
 void launch_residual_identity(const double* normX2, const double* M, const double* coreN, const double* S,

@@ -880,6 +880,8 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   }
+  // one SM stays free for the FP64 coefficient-matrix branch that runs concurrently in the sweep
+  nsm = std::max(1, nsm - 1);
   const int64_t want = 4LL * nsm;
   int n_kc = (int)std::min<int64_t>(std::max<int64_t>(1, (want + n_tiles - 1) / n_tiles), std::max(1, A.ksteps / 4));
   A.kc_len = (A.ksteps + n_kc - 1) / n_kc;

@@ -153,6 +153,12 @@ struct trals_plan {
   int* sweep_ctr = nullptr;
   int host_sweeps = 0;
   cudaGraphExec_t gexec = nullptr;
+  // The coefficient-matrix branch (Gamma chain or explicit Gram or QR factor, then the Cholesky)
+  // depends only on the other cores, so it runs on `side`, concurrently with the MTTSP of the same
+  // mode, and joins before the solve.
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork[TRALS_MAX_ORDER] = {}, ev_join[TRALS_MAX_ORDER] = {};
+  double *ltab2 = nullptr, *utab2 = nullptr, *tscratch2 = nullptr;   // explicit Gram on the side branch
   int launches = 0;
   TcPlan tc[TRALS_MAX_ORDER];
   bool use_tc[TRALS_MAX_ORDER] = {};
@@ -326,20 +332,29 @@ int enqueue_sweep(trals_plan* p) {
   const bool qr = p->opts.solver == TRALS_SOLVE_QR;
   for (int n = 0; n < N; ++n) {
     const int Rn = p->R[n], Rn1 = p->R[(n + 1) % N];
+    // fork: the coefficient-matrix branch on the side stream
+    cudaStream_t b = p->side;
+    cudaEventRecord(p->ev_fork[n], s);
+    cudaStreamWaitEvent(b, p->ev_fork[n], 0);
     if (qr) {
       // R factor of G^{!=n}_[2] by structured QR; L = R^T replaces the Cholesky factor of S_n
       launches += launch_qr_factor(N, p->I, p->R, n, p->cores, p->qrB, p->qrR0, p->qrR1, p->qrW, p->Lmat,
-                                   p->ctx->d_status, p->sweep_ctr, s);
-    } else if (p->opts.gram == TRALS_GRAM_EXPLICIT) {
-      // regular TR-ALS normal equations: S_n from the explicitly formed subchain matrix
-      build_tables(p->lay[n], p->cores, p->I, p->R, p->ltab, p->utab, p->tscratch, s);
-      launches += (N - 1) + launch_explicit_gram(p->lay[n], p->ltab, p->utab, p->opts.mode == TRALS_MODE_FP64,
-                                                 p->Ablk, p->gpart, p->S, s);
+                                   p->ctx->d_status, p->sweep_ctr, b);
     } else {
-      launches += enqueue_coef(N, p->R, p->gam, n, p->chainA, p->chainB, p->S, s);
+      if (p->opts.gram == TRALS_GRAM_EXPLICIT) {
+        // regular TR-ALS normal equations: S_n from the explicitly formed subchain matrix
+        build_tables(p->lay[n], p->cores, p->I, p->R, p->ltab2, p->utab2, p->tscratch2, b);
+        launches += (N - 1) + launch_explicit_gram(p->lay[n], p->ltab2, p->utab2, p->opts.mode == TRALS_MODE_FP64,
+                                                   p->Ablk, p->gpart, p->S, b);
+      } else {
+        launches += enqueue_coef(N, p->R, p->gam, n, p->chainA, p->chainB, p->S, b);
+      }
+      launches += launch_cholesky(p->S, p->Lmat, Rn * Rn1, p->ctx->d_status, p->sweep_ctr, n, b);
     }
+    cudaEventRecord(p->ev_join[n], b);
+    // the MTTSP on the main stream, then join
     launches += enqueue_mttsp(p, n, s);
-    if (!qr) launches += launch_cholesky(p->S, p->Lmat, Rn * Rn1, p->ctx->d_status, p->sweep_ctr, n, s);
+    cudaStreamWaitEvent(s, p->ev_join[n], 0);
     launch_chol_solve(p->Lmat, p->M, Rn, p->I[n], Rn1, p->cores[n], p->ctx->d_status, s);
     ++launches;
     if (qr)
@@ -423,6 +438,14 @@ void trals_plan_destroy(trals_plan* p) {
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     for (int n = 0; n < p->N; ++n) tc_destroy(p->tc[n]);
     for (void* q : p->allocs) cudaFreeAsync(q, p->ctx->stream);
+    for (int n = 0; n < TRALS_MAX_ORDER; ++n) {
+      if (p->ev_fork[n]) cudaEventDestroy(p->ev_fork[n]);
+      if (p->ev_join[n]) cudaEventDestroy(p->ev_join[n]);
+    }
+    if (p->side) {
+      cudaStreamSynchronize(p->side);
+      cudaStreamDestroy(p->side);
+    }
   }
   delete p;
 }
@@ -559,6 +582,9 @@ trals_status plan_build(trals_ctx* ctx, int N, const int64_t* I, const int32_t* 
     PLAN_TRY(p->alloc(&a, ab));
     p->Ablk = a;
     PLAN_TRY(p->alloc(&p->gpart, pe));
+    PLAN_TRY(p->alloc(&p->ltab2, (size_t)maxTab));
+    PLAN_TRY(p->alloc(&p->utab2, (size_t)maxTab));
+    PLAN_TRY(p->alloc(&p->tscratch2, (size_t)maxTab));
   }
   PLAN_TRY(p->alloc(&p->red2, 2));
   PLAN_TRY(p->alloc(&p->normX2, 1));
@@ -610,6 +636,11 @@ trals_status plan_build(trals_ctx* ctx, int N, const int64_t* I, const int32_t* 
     *count_out = p->bytes;
     trals_plan_destroy(p);
     return TRALS_OK;
+  }
+  PLAN_TRY(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+  for (int n = 0; n < N; ++n) {
+    PLAN_TRY(cudaEventCreateWithFlags(&p->ev_fork[n], cudaEventDisableTiming));
+    PLAN_TRY(cudaEventCreateWithFlags(&p->ev_join[n], cudaEventDisableTiming));
   }
   if (sync) PLAN_TRY(cudaStreamSynchronize(s));
   else PLAN_TRY(cudaGetLastError());
