@@ -42,8 +42,17 @@ __global__ void gamma_kernel(const double* __restrict__ G, int Rn, int64_t In, i
     const int q = (int)(v % Rn), t = (int)(v / Rn);
     const double* gu = G + p + (int64_t)Rn * In * s;
     const double* gv = G + q + (int64_t)Rn * In * t;
-    double acc = 0.0;
-    for (int64_t i = 0; i < In; ++i) acc = fma(gu[Rn * i], gv[Rn * i], acc);
+    // four independent partial sums: the FP64 pipe has a long latency on this part
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int64_t i = 0;
+    for (; i + 3 < In; i += 4) {
+      a0 = fma(gu[Rn * i], gv[Rn * i], a0);
+      a1 = fma(gu[Rn * (i + 1)], gv[Rn * (i + 1)], a1);
+      a2 = fma(gu[Rn * (i + 2)], gv[Rn * (i + 2)], a2);
+      a3 = fma(gu[Rn * (i + 3)], gv[Rn * (i + 3)], a3);
+    }
+    for (; i < In; ++i) a0 = fma(gu[Rn * i], gv[Rn * i], a0);
+    const double acc = (a0 + a1) + (a2 + a3);
     Gamma[(p * Rn + q) + rows * (int64_t)(s * Rn1 + t)] = acc;
     Gamma[(q * Rn + p) + rows * (int64_t)(t * Rn1 + s)] = acc;
   }
@@ -64,8 +73,15 @@ __global__ void gemm_f64_kernel(int m, int n, int k, const double* __restrict__ 
     As[tx][ty] = (row < m && k0 + ty < k) ? A[row + (int64_t)m * (k0 + ty)] : 0.0;
     Bs[tx][ty] = (k0 + tx < k && col < n) ? B[(k0 + tx) + (int64_t)k * col] : 0.0;
     __syncthreads();
+    double a1 = 0.0, a2 = 0.0, a3 = 0.0;   // independent chains for the FP64 latency
 #pragma unroll
-    for (int kk = 0; kk < GT; ++kk) acc = fma(As[tx][kk], Bs[kk][ty], acc);
+    for (int kk = 0; kk < GT; kk += 4) {
+      acc = fma(As[tx][kk], Bs[kk][ty], acc);
+      a1 = fma(As[tx][kk + 1], Bs[kk + 1][ty], a1);
+      a2 = fma(As[tx][kk + 2], Bs[kk + 2][ty], a2);
+      a3 = fma(As[tx][kk + 3], Bs[kk + 3][ty], a3);
+    }
+    acc += (a1 + a2) + a3;
     __syncthreads();
   }
   if (row < m && col < n) C[row + (int64_t)m * col] = acc;

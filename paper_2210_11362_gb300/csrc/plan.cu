@@ -158,6 +158,10 @@ struct trals_plan {
   // mode, and joins before the solve.
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork[TRALS_MAX_ORDER] = {}, ev_join[TRALS_MAX_ORDER] = {};
+  // Gamma-chain prefixes for the next mode, formed on `side2` while the current mode is updated
+  cudaStream_t side2 = nullptr;
+  cudaEvent_t ev_pre[TRALS_MAX_ORDER] = {}, ev_pfork[TRALS_MAX_ORDER] = {};
+  double *pre[2] = {}, *preA = nullptr, *preB = nullptr;
   double *ltab2 = nullptr, *utab2 = nullptr, *tscratch2 = nullptr;   // explicit Gram on the side branch
   int launches = 0;
   TcPlan tc[TRALS_MAX_ORDER];
@@ -189,9 +193,18 @@ struct trals_plan {
 
 namespace {
 
-// Structured coefficient matrix S_n (Alg. 2 line 6): Pi_n = Gamma_{n+1} ... Gamma_{n-1}, regrouped.
+// Structured coefficient matrix S_n (Alg. 2 line 6): Pi_n = Gamma_{n+1} ... Gamma_{n-1}, regrouped.  With
+// `pre` set, it holds Gamma_{n+1} ... Gamma_{n-2} (formed while mode n-1 was being updated, from cores
+// that update did not touch), so only the product with the freshly updated Gamma_{n-1} remains.
 int enqueue_coef(const int N, const int32_t* R, double* const* gam, int n, double* chainA, double* chainB, double* S,
-                 cudaStream_t s) {
+                 cudaStream_t s, const double* pre = nullptr) {
+  if (pre) {
+    const int c = (n - 1 + N) % N;
+    const int rows = R[(n + 1) % N] * R[(n + 1) % N];
+    launch_gemm_f64(rows, R[n] * R[n], R[c] * R[c], pre, gam[c], chainA, s);
+    launch_regroup_S(chainA, R[n], R[(n + 1) % N], S, s);
+    return 2;
+  }
   int launches = 0;
   const int c0 = (n + 1) % N;
   const double* cur = gam[c0];
@@ -208,6 +221,24 @@ int enqueue_coef(const int N, const int32_t* R, double* const* gam, int n, doubl
   }
   launch_regroup_S(cur, R[n], R[(n + 1) % N], S, s);
   return launches + 1;
+}
+
+// P_n = Gamma_{n+1} ... Gamma_{n-2} (N - 2 factors, N >= 4) into `out`.
+int enqueue_prefix(const int N, const int32_t* R, double* const* gam, int n, double* tmpA, double* tmpB, double* out,
+                   cudaStream_t s) {
+  const int c0 = (n + 1) % N;
+  const double* cur = gam[c0];
+  const int rows = R[c0] * R[c0];
+  double* bufs[2] = {tmpA, tmpB};
+  int launches = 0;
+  for (int t = 2; t <= N - 2; ++t) {
+    const int c = (n + t) % N;
+    double* dst = (t == N - 2) ? out : bufs[t % 2];
+    launch_gemm_f64(rows, R[(c + 1) % N] * R[(c + 1) % N], R[c] * R[c], cur, gam[c], dst, s);
+    cur = dst;
+    ++launches;
+  }
+  return launches;
 }
 
 int enqueue_mttsp(trals_plan* p, int n, cudaStream_t s, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
@@ -346,12 +377,23 @@ int enqueue_sweep(trals_plan* p) {
         build_tables(p->lay[n], p->cores, p->I, p->R, p->ltab2, p->utab2, p->tscratch2, b);
         launches += (N - 1) + launch_explicit_gram(p->lay[n], p->ltab2, p->utab2, p->opts.mode == TRALS_MODE_FP64,
                                                    p->Ablk, p->gpart, p->S, b);
+      } else if (p->pre[0] && n >= 1) {
+        cudaStreamWaitEvent(b, p->ev_pre[n], 0);   // prefix formed during mode n-1
+        launches += enqueue_coef(N, p->R, p->gam, n, p->chainA, p->chainB, p->S, b, p->pre[n % 2]);
       } else {
         launches += enqueue_coef(N, p->R, p->gam, n, p->chainA, p->chainB, p->S, b);
       }
       launches += launch_cholesky(p->S, p->Lmat, Rn * Rn1, p->ctx->d_status, p->sweep_ctr, n, b);
     }
     cudaEventRecord(p->ev_join[n], b);
+    if (p->pre[0] && n + 1 < N) {
+      // prefix of the next mode: Gamma_{n+2} ... Gamma_{n-1}, none of which this update changes
+      cudaStream_t c = p->side2;
+      cudaEventRecord(p->ev_pfork[n], s);
+      cudaStreamWaitEvent(c, p->ev_pfork[n], 0);
+      launches += enqueue_prefix(N, p->R, p->gam, n + 1, p->preA, p->preB, p->pre[(n + 1) % 2], c);
+      cudaEventRecord(p->ev_pre[n + 1], c);
+    }
     // the MTTSP on the main stream, then join
     launches += enqueue_mttsp(p, n, s);
     cudaStreamWaitEvent(s, p->ev_join[n], 0);
@@ -441,10 +483,16 @@ void trals_plan_destroy(trals_plan* p) {
     for (int n = 0; n < TRALS_MAX_ORDER; ++n) {
       if (p->ev_fork[n]) cudaEventDestroy(p->ev_fork[n]);
       if (p->ev_join[n]) cudaEventDestroy(p->ev_join[n]);
+      if (p->ev_pre[n]) cudaEventDestroy(p->ev_pre[n]);
+      if (p->ev_pfork[n]) cudaEventDestroy(p->ev_pfork[n]);
     }
     if (p->side) {
       cudaStreamSynchronize(p->side);
       cudaStreamDestroy(p->side);
+    }
+    if (p->side2) {
+      cudaStreamSynchronize(p->side2);
+      cudaStreamDestroy(p->side2);
     }
   }
   delete p;
@@ -546,6 +594,12 @@ trals_status plan_build(trals_ctx* ctx, int N, const int64_t* I, const int32_t* 
   PLAN_TRY(p->alloc(&p->Lmat, (size_t)maxr * maxr + maxr));   // L and its reciprocal diagonal
   PLAN_TRY(p->alloc(&p->chainA, (size_t)maxR2 * maxR2));
   PLAN_TRY(p->alloc(&p->chainB, (size_t)maxR2 * maxR2));
+  if (N >= 4 && o.solver == TRALS_SOLVE_CHOL && o.gram == TRALS_GRAM_STRUCTURED) {
+    PLAN_TRY(p->alloc(&p->pre[0], (size_t)maxR2 * maxR2));
+    PLAN_TRY(p->alloc(&p->pre[1], (size_t)maxR2 * maxR2));
+    PLAN_TRY(p->alloc(&p->preA, (size_t)maxR2 * maxR2));
+    PLAN_TRY(p->alloc(&p->preB, (size_t)maxR2 * maxR2));
+  }
   PLAN_TRY(p->alloc(&p->M, (size_t)maxMr));
   PLAN_TRY(p->alloc(&p->ltab, (size_t)maxTab));
   PLAN_TRY(p->alloc(&p->utab, (size_t)maxTab));
@@ -638,9 +692,12 @@ trals_status plan_build(trals_ctx* ctx, int N, const int64_t* I, const int32_t* 
     return TRALS_OK;
   }
   PLAN_TRY(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+  PLAN_TRY(cudaStreamCreateWithFlags(&p->side2, cudaStreamNonBlocking));
   for (int n = 0; n < N; ++n) {
     PLAN_TRY(cudaEventCreateWithFlags(&p->ev_fork[n], cudaEventDisableTiming));
     PLAN_TRY(cudaEventCreateWithFlags(&p->ev_join[n], cudaEventDisableTiming));
+    PLAN_TRY(cudaEventCreateWithFlags(&p->ev_pre[n], cudaEventDisableTiming));
+    PLAN_TRY(cudaEventCreateWithFlags(&p->ev_pfork[n], cudaEventDisableTiming));
   }
   if (sync) PLAN_TRY(cudaStreamSynchronize(s));
   else PLAN_TRY(cudaGetLastError());
