@@ -127,6 +127,23 @@ __global__ void chain_level_kernel(const double* __restrict__ prev, int64_t nPre
 // else in Lmat.  Column j's trailing update is split by columns k over warps and rows i >= k over
 // lanes (no index division).  The reciprocal diagonal 1/L_jj is stored after the matrix (Lmat[r*r + j])
 // so the triangular solves never divide.
+// 1/sqrt(d) for d > 0 by Newton-Raphson on f(y) = y^-2 - d, y <- y (3 - d y^2) / 2, started from the
+// FP32 hardware estimate of the exactly rescaled argument: each step doubles the correct bits, so two
+// steps take the ~23-bit seed past the 53 of FP64.  d is first scaled by an even power of two into
+// FP32 range, which changes neither the digits nor the result beyond that exact power.  On this part
+// an FP64 instruction occupies a sub-partition's FP64 pipe for a full warp slot even with one
+// active lane, and this sequence is about a third of the length of an FP64 sqrt plus a divide.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  int e;
+  const double m = frexp(d, &e);                  // d = m 2^e, m in [0.5, 1)
+  const int h = (e >= 0 ? e : e - 1) / 2;          // floor(e / 2)
+  const double m2 = ldexp(m, e - 2 * h);           // m 2^(e - 2h) in [0.5, 2)
+  double y = (double)rsqrtf((float)m2);
+  y = y * fma(-0.5 * m2, y * y, 1.5);
+  y = y * fma(-0.5 * m2, y * y, 1.5);
+  return ldexp(y, -h);                             // (m2 2^(2h))^(-1/2)
+}
+
 constexpr int kCholSmemMax = 128;
 constexpr int kCholThreads = 1024;
 
@@ -138,7 +155,7 @@ __global__ void __launch_bounds__(kCholThreads) cholesky_kernel(const double* __
   const int lda = r;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int warp = tid / 32, lane = tid % 32, nw = nt / 32;
-  __shared__ double piv[2];   // sqrt and reciprocal of the current pivot
+  __shared__ double piv[2];   // square root and reciprocal square root of the current pivot
   __shared__ int bad;
   for (int e = tid; e < r * r; e += nt) {
     const int i = e % r, j = e / r;
@@ -152,9 +169,9 @@ __global__ void __launch_bounds__(kCholThreads) cholesky_kernel(const double* __
       bad = 1;
       set_status(st, isfinite(d) ? TRALS_E_NOT_SPD : TRALS_E_NONFINITE, sweep_ctr ? *sweep_ctr : -1, mode, j, d);
     } else {
-      const double l = sqrt(d);
-      piv[0] = l;
-      piv[1] = 1.0 / l;
+      const double y = rsqrt_newton(d);
+      piv[0] = d * y;
+      piv[1] = y;
     }
   };
   __syncthreads();
@@ -168,12 +185,21 @@ __global__ void __launch_bounds__(kCholThreads) cholesky_kernel(const double* __
     const double l = piv[0], inv = piv[1];
     for (int i = j + 1 + tid; i < r; i += nt) A[i + lda * j] *= inv;
     __syncthreads();
-    // A[i][k] -= A[i][j] A[k][j] for j < k <= i: column k -> warp, rows i -> lanes.  Warp 0 starts
-    // with column j + 1, so its lane 0 finishes the next pivot first and forms its root at once.
-    for (int k = j + 1 + warp; k < r; k += nw) {
-      const double akj = A[k + lda * j];
-      for (int i = k + lane; i < r; i += 32) A[i + lda * k] = fma(-A[i + lda * j], akj, A[i + lda * k]);
-      if (tid == 0 && k == j + 1) pivot(j + 1);
+    // A[i][k] -= A[i][j] A[k][j] for j < k <= i: column k -> warp, rows i -> lanes.  Warp 0 takes only
+    // column j + 1 and then forms the next pivot's roots; the other warps share the rest, so the
+    // serial pivot work overlaps the bulk of the update.
+    if (warp == 0) {
+      const int k = j + 1;
+      if (k < r) {
+        const double akj = A[k + lda * j];
+        for (int i = k + lane; i < r; i += 32) A[i + lda * k] = fma(-A[i + lda * j], akj, A[i + lda * k]);
+        if (lane == 0) pivot(k);
+      }
+    } else {
+      for (int k = j + 1 + warp; k < r; k += nw - 1) {
+        const double akj = A[k + lda * j];
+        for (int i = k + lane; i < r; i += 32) A[i + lda * k] = fma(-A[i + lda * j], akj, A[i + lda * k]);
+      }
     }
     if (tid == 0) {
       A[j + lda * j] = l;

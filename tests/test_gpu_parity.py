@@ -238,6 +238,25 @@ def test_solve_chol_matches_oracle(ctx):
         assert rel(P.core_from_device(G, Rn, I[n], Rn1), ref) < 1e-10
 
 
+@pytest.mark.parametrize("r", [1, 7, 64, 120, 128])
+@pytest.mark.parametrize("scale", [1.0, 2.0 ** 700, 2.0 ** -700, 3.0e150, 7.0e-160])
+def test_solve_chol_across_sizes_and_scales(ctx, r, scale):
+    """Cholesky + triangular solves on random SPD systems (cond ~ 1e3) from r = 1 to the largest
+    single-CTA size, with S and M scaled together far outside FP32 range (the pivot's reciprocal
+    square root is rescaled by exact powers of two): the solution is scale-free."""
+    rng = np.random.default_rng(r)
+    A = rng.standard_normal((3 * r + 5, r))
+    S = A.T @ A + 1e-3 * np.eye(r)
+    In = 13
+    M = rng.standard_normal((In, r))
+    ref = np.linalg.solve(S, M.T).T
+    G = torch.zeros(In * r, dtype=torch.float64, device="cuda")
+    P.trals_solve_chol(ctx, r, In, 1, torch.from_numpy((S * scale).reshape(-1, order="F").copy()).cuda(),
+                       torch.from_numpy((M * scale).reshape(-1, order="F").copy()).cuda(), G)
+    got = G.cpu().numpy().reshape(r, In, order="F").T        # core layout with R_n = r, R_{n+1} = 1
+    assert rel(got, ref) < 1e-11, rel(got, ref)
+
+
 def test_solve_chol_reports_not_spd(ctx):
     r = 6
     S = -np.eye(r)
