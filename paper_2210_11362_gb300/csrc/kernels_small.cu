@@ -496,6 +496,23 @@ __global__ void quantize_kernel(const void* __restrict__ src, int64_t count, __n
   }
 }
 
+template <typename XT>
+__global__ void quantize_padded_kernel(const void* __restrict__ src, int64_t I0, int64_t I0p, int64_t rest,
+                                       __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  const int64_t count = I0p * rest;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = e % I0p, q = e / I0p;
+    __nv_bfloat16 h = __float2bfloat16_rn(0.f), l = h;
+    if (i0 < I0) {
+      const double v = load_as_double<XT>(src, i0 + I0 * q);
+      h = __float2bfloat16_rn((float)v);
+      l = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
+    }
+    hi[e] = h;
+    if (lo != nullptr) lo[e] = l;
+  }
+}
+
 __global__ void convert_f32_kernel(const double* __restrict__ src, int64_t count, float* __restrict__ dst) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
     dst[e] = (float)src[e];
@@ -650,6 +667,17 @@ void launch_quantize(const void* src, int src_t, int64_t count, __nv_bfloat16* h
     quantize_kernel<double><<<g, 256, 0, s>>>(src, count, hi, lo);
   else
     quantize_kernel<float><<<g, 256, 0, s>>>(src, count, hi, lo);
+}
+
+void launch_quantize_padded(const void* src, int src_t, int64_t I0, int64_t I0p, int64_t rest, __nv_bfloat16* hi,
+                            __nv_bfloat16* lo, cudaStream_t s) {
+  const int g = grid_for(I0p * rest, 256, 152 * 32);
+  if (src_t == TRALS_X_F64)
+    quantize_padded_kernel<double><<<g, 256, 0, s>>>(src, I0, I0p, rest, hi, lo);
+  else if (src_t == TRALS_X_F32)
+    quantize_padded_kernel<float><<<g, 256, 0, s>>>(src, I0, I0p, rest, hi, lo);
+  else
+    quantize_padded_kernel<__nv_bfloat16><<<g, 256, 0, s>>>(src, I0, I0p, rest, hi, lo);
 }
 
 void launch_zero_status(DevStatus* st, cudaStream_t s) { zero_status_kernel<<<1, 1, 0, s>>>(st); }

@@ -9,7 +9,8 @@
 namespace trals {
 
 // ------------------------------------------------------------------ host: mode layout
-ModeLayout make_mode_layout(int N, const int64_t* I, const int32_t* R, int n) {
+ModeLayout make_mode_layout(int N, const int64_t* I, const int32_t* R, int n, const int64_t* Istore) {
+  if (!Istore) Istore = I;
   ModeLayout L{};
   L.N = N;
   L.n = n;
@@ -18,7 +19,11 @@ ModeLayout make_mode_layout(int N, const int64_t* I, const int32_t* R, int n) {
   L.Rn1 = R[(n + 1) % N];
   L.In = I[n];
   L.strideN = 1;
-  for (int j = 0; j < n; ++j) L.strideN *= I[j];
+  L.Kpre = 1;
+  for (int j = 0; j < n; ++j) {
+    L.strideN *= Istore[j];
+    L.Kpre *= I[j];
+  }
   L.J = 1;
   for (int j = 0; j < N; ++j)
     if (j != n) L.J *= I[j];
@@ -41,10 +46,11 @@ ModeLayout make_mode_layout(int N, const int64_t* I, const int32_t* R, int n) {
 }
 
 void mode_offsets(int N, const int64_t* I, const ModeLayout& L, std::vector<int64_t>& offL,
-                  std::vector<int64_t>& offU) {
+                  std::vector<int64_t>& offU, const int64_t* Istore) {
+  if (!Istore) Istore = I;
   int64_t stride[kMaxOrder];
   stride[0] = 1;
-  for (int j = 1; j < N; ++j) stride[j] = stride[j - 1] * I[j - 1];
+  for (int j = 1; j < N; ++j) stride[j] = stride[j - 1] * Istore[j - 1];
   auto fill = [&](int t0, int t1, int64_t count, std::vector<int64_t>& out) {
     out.assign((size_t)count, 0);
     for (int64_t e = 0; e < count; ++e) {
@@ -274,9 +280,12 @@ __global__ void __launch_bounds__(THREADS, 4) mttsp_simt_f32_kernel(const void* 
   const int r = L.Rn * L.Rn1;
   const int In = (int)L.In;
   const int rp = (r + 3) & ~3, inp = (In + 3) & ~3;
+  const int nLr = L.Rn1 * L.Rs, nUr = L.Rs * L.Rn;   // floats per Left / Right table row
   float* Gs = fs;                          // [FKT][rp]
   float* Xs = Gs + FKT * rp;               // [FKT][inp]
-  int64_t* base = reinterpret_cast<int64_t*>(Xs + FKT * inp);
+  float* Lt = Xs + FKT * inp;              // [FKT][nLr]: the tile columns' Left table rows
+  float* Ut = Lt + FKT * nLr;              // [FKT][nUr]: and Right table rows
+  int64_t* base = reinterpret_cast<int64_t*>(Ut + ((FKT * nUr + 1) & ~1));
   int64_t* lrow = base + FKT;              // table rows of column kk: Left l(k) and Right u(k)
   int64_t* urow = lrow + FKT;
   const int nrq = rp / 4, niq = inp / 4;
@@ -306,13 +315,23 @@ __global__ void __launch_bounds__(THREADS, 4) mttsp_simt_f32_kernel(const void* 
       }
     }
     __syncthreads();
+    // stage the two table rows of every tile column (contiguous rows: coalesced loads)
+    for (int e = threadIdx.x; e < FKT * nLr; e += blockDim.x) {
+      const int kk = e / nLr, q = e % nLr;
+      Lt[e] = base[kk] >= 0 ? ltab[lrow[kk] * (int64_t)nLr + q] : 0.f;
+    }
+    for (int e = threadIdx.x; e < FKT * nUr; e += blockDim.x) {
+      const int kk = e / nUr, q = e % nUr;
+      Ut[e] = base[kk] >= 0 ? utab[urow[kk] * (int64_t)nUr + q] : 0.f;
+    }
+    __syncthreads();
     for (int e = threadIdx.x; e < FKT * rp; e += blockDim.x) {
       const int kk = e / rp, rr = e % rp;
       float g = 0.f;
-      if (base[kk] >= 0 && rr < r) {
+      if (rr < r) {
         const int a = rr % L.Rn, b = rr / L.Rn;
-        const float* Lp = ltab + lrow[kk] * (int64_t)L.Rn1 * L.Rs;
-        const float* Up = utab + urow[kk] * (int64_t)L.Rs * L.Rn;
+        const float* Lp = Lt + kk * nLr;
+        const float* Up = Ut + kk * nUr;
         for (int c = 0; c < L.Rs; ++c) g = fmaf(Lp[b + L.Rn1 * c], Up[c + L.Rs * a], g);
       }
       Gs[e] = g;
@@ -503,7 +522,8 @@ __global__ void __launch_bounds__(THREADS) residual_f32_kernel(const float* __re
 size_t mttsp_simt_f32_smem(const ModeLayout& L) {
   const int r = L.Rn * L.Rn1;
   const int64_t rp = (r + 3) & ~3, inp = (L.In + 3) & ~3;
-  return (size_t)(FKT * (rp + inp)) * sizeof(float) + 3 * FKT * sizeof(int64_t);
+  const int64_t nLr = (int64_t)L.Rn1 * L.Rs, nUr = (int64_t)L.Rs * L.Rn;
+  return (size_t)(FKT * (rp + inp + nLr) + ((FKT * nUr + 1) & ~1)) * sizeof(float) + 3 * FKT * sizeof(int64_t);
 }
 
 bool mttsp_simt_f32_fits(const ModeLayout& L) { return L.In <= 4096 && mttsp_simt_f32_smem(L) <= 200 * 1024; }
@@ -525,7 +545,7 @@ void launch_mttsp_simt_f32(const MttspSimtArgs& a, const float* fl, const float*
   const int64_t outN = L.In * r;
   const int64_t mts = (int64_t)((r + 3) / 4) * ((L.In + 3) / 4);
   dim3 grid(a.gridX, (unsigned)((mts + THREADS - 1) / THREADS));
-  const int64_t Kpre = L.strideN;
+  const int64_t Kpre = L.Kpre;
   const int64_t Q = L.J / Kpre;
   const size_t smem = mttsp_simt_f32_smem(L);
   if (a.ev0) cudaEventRecord(a.ev0, s);

@@ -529,16 +529,21 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // M[e] = sum_g partials[g * E + e] in FP64: a block takes 32 consecutive e; warp w sums g = w, w+8, ...
 // (coalesced 128-byte rows), then the 8 warp sums are added in a fixed order.
-__global__ void tc_reduce_kernel(const float* __restrict__ partials, int G, int64_t E, double* __restrict__ M) {
+// M[i + In_out c] = sum over CTAs of partials[g][i + In c] for i < In_out (In_out < In when the rows
+// beyond In_out are the zero padding of a padded leading mode).
+__global__ void tc_reduce_kernel(const float* __restrict__ partials, int G, int64_t E, int In, int In_out,
+                                 double* __restrict__ M) {
   __shared__ double red[8][32];
   const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
-  const int64_t e = blockIdx.x * 32LL + lane;
+  const int64_t e = blockIdx.x * 32LL + lane;   // output index i + In_out c
+  const int64_t Eout = E / In * In_out;
+  const int64_t src = (e % In_out) + (int64_t)In * (e / In_out);
   double s = 0.0;
-  if (e < E)
-    for (int g = w; g < G; g += 8) s += (double)partials[(int64_t)g * E + e];
+  if (e < Eout)
+    for (int g = w; g < G; g += 8) s += (double)partials[(int64_t)g * E + src];
   red[w][lane] = s;
   __syncthreads();
-  if (w == 0 && e < E) {
+  if (w == 0 && e < Eout) {
     double t = 0.0;
     for (int k = 0; k < 8; ++k) t += red[k][lane];
     M[e] = t;
@@ -603,17 +608,28 @@ __global__ void chain_level_f32_kernel(const float* __restrict__ prev, int64_t n
 }
 
 // FP64 cores -> one FP32 copy (conversions run once per update, not once per table element).
+// FP32 copies of all cores, concatenated (offsets off[]).  Core 0 may be stored with I0p >= I0
+// slices (R0 x I0p x R1), the extra slices zero, to match a zero-padded leading mode of X.
 struct CorePtrs {
   const double* p[kMaxOrder];
   int64_t off[kMaxOrder + 1];
   int N;
+  int R0;
+  int64_t I0, I0p;
 };
 __global__ void cores_to_f32_kernel(const CorePtrs c, float* __restrict__ dst) {
   const int64_t total = c.off[c.N];
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     int j = 0;
     while (e >= c.off[j + 1]) ++j;
-    dst[e] = (float)c.p[j][e - c.off[j]];
+    const int64_t q = e - c.off[j];
+    if (j == 0 && c.I0p != c.I0) {
+      const int64_t a = q % c.R0, rest = q / c.R0;
+      const int64_t i = rest % c.I0p, b = rest / c.I0p;
+      dst[e] = i < c.I0 ? (float)c.p[0][a + c.R0 * (i + c.I0 * b)] : 0.f;
+    } else {
+      dst[e] = (float)c.p[j][q];
+    }
   }
 }
 
@@ -675,7 +691,9 @@ struct TcImpl {
   float* partials = nullptr;
   int64_t E = 0;
   const int64_t* I = nullptr;
-  int64_t Icopy[kMaxOrder];
+  int64_t Icopy[kMaxOrder];   // extents as stored (mode 0 possibly padded)
+  int64_t I0real = 0;         // the true extent of mode 0
+  int n = 0;                  // the mode this plan contracts for
   int32_t Rcopy[kMaxOrder];
   int N = 0;
 };
@@ -774,7 +792,7 @@ TcChoice tc_choose(int N, const int64_t* I, const int32_t* R, int n) {
 }
 
 int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mode, const void* X, int64_t numel,
-            cudaError_t* err, cudaStream_t s, size_t* count_bytes) {
+            cudaError_t* err, cudaStream_t s, size_t* count_bytes, int64_t I0_real) {
   if (err) *err = cudaSuccess;
   p.valid = false;
   if (mode != TRALS_MODE_BF16) return 0;
@@ -789,6 +807,8 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
 
   TcImpl* impl = new TcImpl();
   impl->N = N;
+  impl->I0real = I0_real > 0 ? I0_real : I[0];
+  impl->n = n;
   for (int j = 0; j < N; ++j) {
     impl->Icopy[j] = I[j];
     impl->Rcopy[j] = R[j];
@@ -1004,6 +1024,9 @@ int tc_enqueue(TcPlan& p, const void* X, double* const* cores, double* M, cudaSt
     CorePtrs cp;
     cp.N = N;
     for (int j = 0; j <= N; ++j) cp.off[j] = impl->core_off[j];
+    cp.R0 = R[0];
+    cp.I0 = impl->I0real;
+    cp.I0p = I[0];
     for (int j = 0; j < N; ++j) {
       cp.p[j] = cores[j];
       c32[j] = impl->cores32 + impl->core_off[j];
@@ -1037,7 +1060,12 @@ int tc_enqueue(TcPlan& p, const void* X, double* const* cores, double* M, cudaSt
   }
   ++launches;
   if (ev1) cudaEventRecord(ev1, s);
-  tc_reduce_kernel<<<(unsigned)((impl->E + 31) / 32), 256, 0, s>>>(impl->partials, impl->grid, impl->E, M);
+  {
+    const int In_out = (impl->n == 0) ? (int)impl->I0real : A.In;
+    const int64_t Eout = impl->E / A.In * In_out;
+    tc_reduce_kernel<<<(unsigned)((Eout + 31) / 32), 256, 0, s>>>(impl->partials, impl->grid, impl->E, A.In, In_out,
+                                                                  M);
+  }
   ++launches;
   return launches;
 }

@@ -140,6 +140,13 @@ struct trals_plan {
   int64_t* offL[TRALS_MAX_ORDER] = {};
   int64_t* offU[TRALS_MAX_ORDER] = {};
   ModeLayout lay[TRALS_MAX_ORDER];
+  // Layout of Xk, the copy the MTTSP reads: in the BF16 mode mode 0 is stored zero-padded to a
+  // multiple of 8 (Ist[0]) so every tensor-core geometry meets the 16-byte stride rule of TMA.
+  int64_t Ist[TRALS_MAX_ORDER] = {};
+  int64_t numel_st = 0;
+  ModeLayout layk[TRALS_MAX_ORDER];
+  int64_t* offLk[TRALS_MAX_ORDER] = {};
+  int64_t* offUk[TRALS_MAX_ORDER] = {};
   int gridX[TRALS_MAX_ORDER] = {};
   double* partials = nullptr;
   double *qrB = nullptr, *qrR0 = nullptr, *qrR1 = nullptr, *qrW = nullptr;   // QR solve workspace
@@ -242,7 +249,7 @@ int enqueue_prefix(const int N, const int32_t* R, double* const* gam, int n, dou
 }
 
 int enqueue_mttsp(trals_plan* p, int n, cudaStream_t s, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
-  const ModeLayout& L = p->lay[n];
+  const ModeLayout& L = p->layk[n];
   int launches = 0;
   if (p->use_tc[n]) {
     launches += tc_enqueue(p->tc[n], p->Xk, p->cores, p->M, s, ev0, ev1);
@@ -259,8 +266,8 @@ int enqueue_mttsp(trals_plan* p, int n, cudaStream_t s, cudaEvent_t ev0 = nullpt
     a.X = p->Xk;
     a.Xlo = p->Xk_lo;
     a.xt = p->xk_t;
-    a.offL = p->offL[n];
-    a.offU = p->offU[n];
+    a.offL = p->offLk[n];
+    a.offU = p->offUk[n];
     a.L = L;
     a.partials = p->partials;
     a.M = p->M;
@@ -276,8 +283,8 @@ int enqueue_mttsp(trals_plan* p, int n, cudaStream_t s, cudaEvent_t ev0 = nullpt
   a.xt = p->xk_t;
   a.ltab = p->ltab;
   a.utab = p->utab;
-  a.offL = p->offL[n];
-  a.offU = p->offU[n];
+  a.offL = p->offLk[n];
+  a.offU = p->offUk[n];
   a.L = L;
   a.partials = p->partials;
   a.M = p->M;
@@ -563,6 +570,10 @@ trals_status plan_build(trals_ctx* ctx, int N, const int64_t* I, const int32_t* 
     }                                                                       \
   } while (0)
 
+  for (int n = 0; n < N; ++n) p->Ist[n] = I[n];
+  if (o.mode == TRALS_MODE_BF16 && I[0] % 8 != 0) p->Ist[0] = (I[0] + 7) / 8 * 8;
+  p->numel_st = p->numel / I[0] * p->Ist[0];
+  const bool padded = p->Ist[0] != I[0];
   int maxR2 = 0, maxr = 0;
   int64_t maxMr = 0, maxTab = 0;
   size_t maxPart = 0;
@@ -588,6 +599,20 @@ trals_status plan_build(trals_ctx* ctx, int N, const int64_t* I, const int32_t* 
       // pageable sources: staged before the call returns
       PLAN_TRY(cudaMemcpyAsync(p->offL[n], offL.data(), offL.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
       PLAN_TRY(cudaMemcpyAsync(p->offU[n], offU.data(), offU.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    }
+    p->layk[n] = make_mode_layout(N, I, R, n, p->Ist);
+    if (padded) {
+      std::vector<int64_t> kL, kU;
+      mode_offsets(N, I, p->layk[n], kL, kU, p->Ist);
+      PLAN_TRY(p->alloc(&p->offLk[n], kL.size()));
+      PLAN_TRY(p->alloc(&p->offUk[n], kU.size()));
+      if (!counting) {
+        PLAN_TRY(cudaMemcpyAsync(p->offLk[n], kL.data(), kL.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        PLAN_TRY(cudaMemcpyAsync(p->offUk[n], kU.data(), kU.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+      }
+    } else {
+      p->offLk[n] = p->offL[n];
+      p->offUk[n] = p->offU[n];
     }
   }
   PLAN_TRY(p->alloc(&p->S, (size_t)maxr * maxr));
@@ -649,10 +674,15 @@ trals_status plan_build(trals_ctx* ctx, int N, const int64_t* I, const int32_t* 
   // X as the MTTSP reads it (quantised once, K7), and |X|^2 from the full-precision source.
   p->Xk = X_dev;
   p->xk_t = xt;
-  if (o.mode == TRALS_MODE_BF16 && xt != TRALS_X_BF16) {
+  if (o.mode == TRALS_MODE_BF16 && (xt != TRALS_X_BF16 || padded)) {
     __nv_bfloat16* q = nullptr;
-    PLAN_TRY(p->alloc(&q, (size_t)p->numel));
-    if (!counting) launch_quantize(X_dev, xt, p->numel, q, nullptr, s);
+    PLAN_TRY(p->alloc(&q, (size_t)p->numel_st));
+    if (!counting) {
+      if (padded)
+        launch_quantize_padded(X_dev, xt, I[0], p->Ist[0], p->numel / I[0], q, nullptr, s);
+      else
+        launch_quantize(X_dev, xt, p->numel, q, nullptr, s);
+    }
     p->Xk = q;
     p->xk_t = TRALS_X_BF16;
   } else if (o.mode == TRALS_MODE_BF16X3) {
@@ -677,7 +707,8 @@ trals_status plan_build(trals_ctx* ctx, int N, const int64_t* I, const int32_t* 
   for (int n = 0; n < N; ++n) {
     p->use_tc[n] = false;
     if (o.mode != TRALS_MODE_FP64) {
-      const int ok = tc_plan(p->tc[n], N, I, R, n, o.mode, p->Xk, p->numel, &e, s, counting ? &p->bytes : nullptr);
+      const int ok = tc_plan(p->tc[n], N, p->Ist, R, n, o.mode, p->Xk, p->numel_st, &e, s,
+                             counting ? &p->bytes : nullptr, I[0]);
       if (e != cudaSuccess) PLAN_TRY(e);
       p->use_tc[n] = ok != 0;
       if (ok && !counting) {
@@ -1142,7 +1173,11 @@ trals_status trals_mttsp(trals_ctx* ctx, int N, const int64_t* I, const int32_t*
 int trals_mttsp_path(int N, const int64_t* I, const int32_t* R, int n, int mode) {
   if (N < 3 || N > TRALS_MAX_ORDER || !I || !R || n < 0 || n >= N) return -1;
   if (mode != TRALS_MODE_BF16) return 0;
-  const TcChoice c = tc_choose(N, I, R, n);
+  // plans store the BF16 copy with mode 0 padded to a multiple of 8
+  int64_t Ist[TRALS_MAX_ORDER];
+  for (int j = 0; j < N; ++j) Ist[j] = I[j];
+  Ist[0] = (I[0] + 7) / 8 * 8;
+  const TcChoice c = tc_choose(N, Ist, R, n);
   return c.variant < 0 ? 0 : c.variant + 1;
 }
 

@@ -46,15 +46,17 @@ struct ModeLayout {
   int m;                 // number of Left modes
   int64_t nL, nU;        // table entries
   int Rn, Rn1, Rs;       // R_n, R_{n+1}, R at the split
-  int64_t In, strideN;   // I_n, prod_{j<n} I_j
+  int64_t In, strideN;   // I_n, memory stride of i_n (prod_{j<n} of the stored extents)
   int64_t J;             // prod_{j != n} I_j
+  int64_t Kpre;          // prod_{j<n} I_j (a count; equals strideN unless mode 0 is stored padded)
 };
 
-// Build the layout for mode n choosing the split that minimises nL + nU.
-ModeLayout make_mode_layout(int N, const int64_t* I, const int32_t* R, int n);
-// Host-side offsets for the layout (sizes nL and nU).
+// Build the layout for mode n choosing the split that minimises nL + nU.  With Istore given, X is
+// stored with those extents (Istore[j] >= I[j], the extra entries zero) and strides follow them.
+ModeLayout make_mode_layout(int N, const int64_t* I, const int32_t* R, int n, const int64_t* Istore = nullptr);
+// Host-side offsets for the layout (sizes nL and nU), strides from Istore when given.
 void mode_offsets(int N, const int64_t* I, const ModeLayout& L, std::vector<int64_t>& offL,
-                  std::vector<int64_t>& offU);
+                  std::vector<int64_t>& offU, const int64_t* Istore = nullptr);
 
 // ---------------------------------------------------------------- kernel launchers (stream-ordered)
 // Gamma_k (K1).
@@ -133,6 +135,10 @@ void launch_residual_identity(const double* normX2, const double* M, const doubl
 // sum of squares of X in FP64 -> partials then reduce
 void launch_sumsq(const void* X, int xt, int64_t count, double* partials, int gridX, double* out, cudaStream_t s);
 // BF16 quantisation (K7).
+// X (element type src_t, extent I0 along mode 0, `rest` = prod of the other extents) to BF16 with
+// mode 0 padded to I0p >= I0 with zeros (and, with lo != NULL, the lo halves likewise).
+void launch_quantize_padded(const void* src, int src_t, int64_t I0, int64_t I0p, int64_t rest, __nv_bfloat16* hi,
+                            __nv_bfloat16* lo, cudaStream_t s);
 void launch_quantize(const void* src, int src_t, int64_t count, __nv_bfloat16* hi, __nv_bfloat16* lo,
                      cudaStream_t s);
 // FP64 -> FP32 copy (FP32 mode fed with an FP64 X).

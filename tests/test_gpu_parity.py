@@ -225,6 +225,35 @@ def test_mttsp_bf16_tensor_cores_match_oracle(ctx, I, R):
         assert err < 4e-3, (n, P.MTTSP_PATHS[P.trals_mttsp_path(I, R, n, "bf16")], err)
 
 
+@pytest.mark.parametrize("I,R", [((41, 39, 47, 33), (3, 4, 2, 5)), ((60, 60, 60, 60), (10, 10, 10, 10)),
+                                 ((45, 53, 64, 55, 36), (7, 2, 3, 5, 4))])
+def test_plan_mttsp_bf16_with_padded_leading_mode(ctx, I, R):
+    """A plan stores the BF16 copy of X with mode 0 zero-padded to a multiple of 8 so that the
+    tensor-core geometries apply; M_n of every mode (including mode 0, whose padded rows are
+    dropped) matches X_bf16 G^{!=n} within the BF16 rounding of the factors (normwise 4e-3)."""
+    X, _ = _problem(I, R)
+    cores = TI.gaussian_cores(9, I, R)
+    Xf = P.tensor_to_device(X, torch.float32)
+    Xq = TI.unflat_f(Xf.to(torch.bfloat16).double().cpu().numpy(), I)
+    plan = P.Plan(ctx, I, R, Xf, P.make_opts("bf16"))
+    try:
+        plan.set_cores(cores)
+        N = len(I)
+        paths = [plan.mttsp_path(n) for n in range(N)]
+        assert sum(p_ > 0 for p_ in paths) >= N - 2, paths
+        for n in range(N):
+            r = R[n] * R[(n + 1) % N]
+            M = torch.zeros(I[n] * r, dtype=torch.float64, device="cuda")
+            plan.mttsp(n, M)
+            torch.cuda.synchronize()
+            ref = O.unfold_mode(Xq, n) @ O.subchain_unfolded(cores, n)
+            got = M.cpu().numpy().reshape(I[n], r, order="F")
+            err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+            assert err < 4e-3, (n, paths[n], err)
+    finally:
+        plan.close()
+
+
 def test_solve_chol_matches_oracle(ctx):
     I, R = (9, 8, 7), (3, 4, 2)
     X, init = _problem(I, R)

@@ -16,10 +16,12 @@ def test_mttsp_path_choice_fp64_is_cuda_cores():
     assert all(P.trals_mttsp_path(I, R, n, "fp64") == 0 for n in range(5))
 
 
-def test_mttsp_path_falls_back_when_unaligned_or_too_large():
-    # 60^4: mode 0's 120-byte BF16 rows cannot be described to TMA -> CUDA cores
-    assert P.trals_mttsp_path((60,) * 4, (10,) * 4, 0, "bf16") == 0
-    assert all(P.trals_mttsp_path((60,) * 4, (10,) * 4, n, "bf16") > 0 for n in (1, 2, 3))
+def test_mttsp_path_pads_the_leading_mode_and_falls_back_when_too_large():
+    # 60^4: plans store the BF16 copy with mode 0 padded to 64, so every mode meets TMA's 16-byte
+    # stride rule and runs on tensor cores
+    assert all(P.trals_mttsp_path((60,) * 4, (10,) * 4, n, "bf16") > 0 for n in range(4))
+    # a middle mode with I_n < 32 and a long K-major block: no tensor-core geometry applies
+    assert P.trals_mttsp_path((41, 39, 20, 41, 39), (2, 2, 7, 8, 3), 2, "bf16") == 0
     # rank-16 cores: stage-1 table wider than the 128-column accumulator -> CUDA cores
     assert all(P.trals_mttsp_path((256, 256, 3, 256), (16,) * 4, n, "bf16") == 0 for n in range(4))
     # tiny tensors: contraction too short for a tensor-core tile
