@@ -89,38 +89,30 @@ __device__ __forceinline__ double ld<__nv_bfloat16>(const void* p, int64_t i) {
   return (double)__bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]);
 }
 
-// Subchain rows of one tile: Gs[kk * r + (a + Rn b)] = sum_c Ltab[l][b + Rn1 c] Utab[u][c + Rs a].
-// base[] needs room for 3 KT entries: the X offsets of the tile's columns, then l and u per column.
+// Subchain rows of one tile: Gs[kk * r + (a + Rn b)] = sum_c Ltab[l][b + Rn1 c] Utab[u][c + Rs a], and
+// base[kk] = the X offset of column kk.  (The FP64 kernels are bound by the FP64 pipe, so the
+// per-element index arithmetic here runs on otherwise idle integer units.)
 __device__ __forceinline__ void gen_tile(const ModeLayout& L, const double* __restrict__ ltab,
                                          const double* __restrict__ utab, const int64_t* __restrict__ offL,
                                          const int64_t* __restrict__ offU, int64_t kbase, int64_t kend, double* Gs,
                                          int64_t* base) {
   const int r = L.Rn * L.Rn1;
-  int64_t* lrow = base + KT;
-  int64_t* urow = lrow + KT;
-  __syncthreads();   // the previous tile's readers of base are done
-  for (int kk = threadIdx.x; kk < KT; kk += blockDim.x) {
-    const int64_t k = kbase + kk;
-    if (k < kend) {
-      const int64_t l = k % L.nL, u = k / L.nL;
-      lrow[kk] = l;
-      urow[kk] = u;
-      base[kk] = offL[l] + offU[u];
-    } else {
-      base[kk] = -1;
-    }
-  }
-  __syncthreads();
   for (int e = threadIdx.x; e < KT * r; e += blockDim.x) {
     const int kk = e / r, rr = e % r;
+    const int64_t k = kbase + kk;
     double acc = 0.0;
-    if (base[kk] >= 0) {
+    if (k < kend) {
+      const int64_t l = k % L.nL, u = k / L.nL;
       const int a = rr % L.Rn, b = rr / L.Rn;
-      const double* Lp = ltab + lrow[kk] * (int64_t)L.Rn1 * L.Rs;
-      const double* Up = utab + urow[kk] * (int64_t)L.Rs * L.Rn;
+      const double* Lp = ltab + l * (int64_t)L.Rn1 * L.Rs;
+      const double* Up = utab + u * (int64_t)L.Rs * L.Rn;
       for (int c = 0; c < L.Rs; ++c) acc = fma(Lp[b + L.Rn1 * c], Up[c + L.Rs * a], acc);
     }
     Gs[e] = acc;
+  }
+  for (int kk = threadIdx.x; kk < KT; kk += blockDim.x) {
+    const int64_t k = kbase + kk;
+    base[kk] = (k < kend) ? offL[k % L.nL] + offU[k / L.nL] : -1;
   }
 }
 
