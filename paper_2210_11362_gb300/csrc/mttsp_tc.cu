@@ -467,57 +467,75 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       tmem_wait_st();
     }
-    // Combine the lanes' running sums into the CTA accumulator.  The pipeline buffers are idle now
-    // (every MMA and copy has been consumed), so lanes stage V[x][y] there and threads then own
-    // outputs (i_n, x, y), adding the rows of their i_n in a fixed order.
+    // Stage the lanes' running sums V[x][y] in the pipeline buffers, which are idle now (every MMA
+    // and copy has been consumed).
     epi_bar();
     float* S = reinterpret_cast<float*>(base);
     const int nv = a.NX * a.NY, ss = nv | 1;
-    {
-      float* myS = S + row * ss;
-      for (int x = 0; x < a.NX; ++x) {
-        uint32_t v[16];
-        tmem_ld16(vacc + 16u * x, v);
-        tmem_wait_ld();
+    float* myS = S + row * ss;
+    for (int x = 0; x < a.NX; ++x) {
+      uint32_t v[16];
+      tmem_ld16(vacc + 16u * x, v);
+      tmem_wait_ld();
 #pragma unroll
-        for (int y = 0; y < 16; ++y)
-          if (y < a.NY) myS[x * a.NY + y] = lane_ok ? __uint_as_float(v[y]) : 0.0f;
+      for (int y = 0; y < 16; ++y)
+        if (y < a.NY) myS[x * a.NY + y] = lane_ok ? __uint_as_float(v[y]) : 0.0f;
+    }
+  }
+  // Combine: all warps (the producer and MMA warps are done) own outputs (i_n, x, y) and add the rows
+  // of their i_n in a fixed order; then the CTA's partial (column-major I_n x r) goes out.
+  __syncthreads();
+  if (!*abort_flag) {
+    float* S = reinterpret_cast<float*>(base);
+    const int nv = a.NX * a.NY, ss = nv | 1;
+    int* colmap = reinterpret_cast<int*>(S + kRows * ss);   // xy -> column of M_s
+    for (int xy = threadIdx.x; xy < nv; xy += blockDim.x) {
+      const int x = xy / a.NY, y = xy % a.NY;
+      colmap[xy] = a.variant == KM_L ? (y + a.Rn * x) : (x + a.Rn * y);
+    }
+    int64_t i_lo = 0, i_hi = a.In - 1, p0 = 0, p1 = 0;
+    if (a.variant == MM) {
+      p0 = (blockIdx.x % a.pchunks) * 64;
+      p1 = min(a.P, p0 + 64);
+      i_lo = p0 / a.K_pre;
+      i_hi = (p1 - 1) / a.K_pre;
+    }
+    __syncthreads();
+    const int cnt = (int)(i_hi - i_lo + 1) * nv;
+    const int step = blockDim.x;
+    int g = (int)threadIdx.x / nv, xy = (int)threadIdx.x % nv;
+    const int dg = step / nv, dxy = step % nv;
+    for (int o = threadIdx.x; o < cnt; o += step) {
+      const int64_t i = i_lo + g;
+      float sum = 0.0f;
+      if (a.variant == KM_L) {
+        for (int rp = 0; rp < a.nrep; ++rp) sum += S[(i + a.In * rp) * ss + xy];
+      } else if (a.variant == KM_R) {
+        for (int rp = 0; rp < a.nrep; ++rp) sum += S[(rp + a.nrep * i) * ss + xy];
+      } else {
+        const int r0 = (int)(max(p0, i * a.K_pre) - p0), r1 = (int)(min(p1, (i + 1) * a.K_pre) - p0);
+        for (int at2 = 0; at2 < 2; ++at2)
+          for (int rr = r0; rr < r1; ++rr) sum += S[(at2 * 64 + rr) * ss + xy];
+      }
+      M_s[i * a.ms_stride + colmap[xy]] = sum;
+      g += dg;
+      xy += dxy;
+      if (xy >= nv) {
+        xy -= nv;
+        ++g;
       }
     }
-    epi_bar();
-    if (!*abort_flag) {
-      int64_t i_lo = 0, i_hi = a.In - 1, p0 = 0, p1 = 0;
-      if (a.variant == MM) {
-        p0 = (blockIdx.x % a.pchunks) * 64;
-        p1 = min(a.P, p0 + 64);
-        i_lo = p0 / a.K_pre;
-        i_hi = (p1 - 1) / a.K_pre;
-      }
-      const int cnt = (int)(i_hi - i_lo + 1) * nv;
-      for (int o = et; o < cnt; o += 128) {
-        const int g = o / nv, xy = o % nv;
-        const int x = xy / a.NY, y = xy % a.NY;
-        const int64_t i = i_lo + g;
-        float sum = 0.0f;
-        if (a.variant == KM_L) {
-          for (int rp = 0; rp < a.nrep; ++rp) sum += S[(i + a.In * rp) * ss + xy];
-        } else if (a.variant == KM_R) {
-          for (int rp = 0; rp < a.nrep; ++rp) sum += S[(rp + a.nrep * i) * ss + xy];
-        } else {
-          const int r0 = (int)(max(p0, i * a.K_pre) - p0), r1 = (int)(min(p1, (i + 1) * a.K_pre) - p0);
-          for (int at2 = 0; at2 < 2; ++at2)
-            for (int rr = r0; rr < r1; ++rr) sum += S[(at2 * 64 + rr) * ss + xy];
-        }
-        M_s[i * a.ms_stride + (a.variant == KM_L ? (y + a.Rn * x) : (x + a.Rn * y))] = sum;
-      }
-    }
-    epi_bar();
-    // write this CTA's partial (column-major I_n x r)
-    if (!*abort_flag) {
-      float* out = a.partials + (size_t)blockIdx.x * E;
-      for (int e = et; e < E; e += 128) {
-        const int i = e % a.In, c = e / a.In;
-        out[e] = M_s[i * a.ms_stride + c];
+    __syncthreads();
+    float* out = a.partials + (size_t)blockIdx.x * E;
+    int i = (int)threadIdx.x % a.In, c = (int)threadIdx.x / a.In;
+    const int di = step % a.In, dc = step / a.In;
+    for (int e = threadIdx.x; e < E; e += step) {
+      out[e] = M_s[i * a.ms_stride + c];
+      i += di;
+      c += dc;
+      if (i >= a.In) {
+        i -= a.In;
+        ++c;
       }
     }
   }
@@ -933,7 +951,7 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   {
     // the end-of-kernel lane staging reuses the pipeline buffers and the factor blocks
     const size_t stage_area = (size_t)ns * stage + (size_t)kRows * A.fs_stride * 4;
-    const size_t need = (size_t)kRows * ((A.NX * A.NY) | 1) * 4;
+    const size_t need = (size_t)kRows * ((A.NX * A.NY) | 1) * 4 + (size_t)A.NX * A.NY * 4;   // + column map
     if (need > stage_area) {
       delete impl;
       return 0;
