@@ -126,10 +126,18 @@ def mode_xdtype(mode, torch):
 
 
 # ----------------------------------------------------------------------------- GPU arm
-def time_mode(P, torch, w, X, mode, steps, warmup, seed, flush_buf, X_full):
+SOLVERS = {"cholesky": 0, "qr": 1}
+GRAMS = {"structured": 0, "explicit": 1}
+
+
+def opts_for(P, mode, args):
+    return P.make_opts(mode, solver=SOLVERS[args.solver], gram=GRAMS[args.gram])
+
+
+def time_mode(P, torch, w, X, mode, steps, warmup, seed, flush_buf, X_full, opts):
     stream = torch.cuda.Stream()
     ctx = P.trals_create(0, stream)
-    plan = P.Plan(ctx, w.I, w.R_fit, X, P.make_opts(mode))
+    plan = P.Plan(ctx, w.I, w.R_fit, X, opts)
     init = TI.init_cores(seed, w.I, w.R_fit)
     plan.set_cores(init)
     plan.run(warmup, use_graph=True)
@@ -173,17 +181,17 @@ def time_mode(P, torch, w, X, mode, steps, warmup, seed, flush_buf, X_full):
             "launches_per_sweep": launches, "mttsp_kernel_ms": kern, "mttsp_ms": whole, "clocks": clk}
 
 
-def e2e_run(P, torch, w, X_dev, mode, seed, sweeps):
+def e2e_run(P, torch, w, X_dev, opts, seed, sweeps):
     """End to end through trals_decompose with host buffers (pinned X, host cores)."""
     Xh = X_dev.cpu().pin_memory()
     init = TI.init_cores(seed, w.I, w.R_fit)
     ctx = P.trals_create(0)
     cores = [G.copy() for G in init]
-    P.trals_decompose(ctx, w.I, w.R_fit, Xh, cores, 1, P.make_opts(mode))   # warm (module load, graph)
+    P.trals_decompose(ctx, w.I, w.R_fit, Xh, cores, 1, opts)   # warm (module load, graph)
     cores = [G.copy() for G in init]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    res = P.trals_decompose(ctx, w.I, w.R_fit, Xh, cores, sweeps, P.make_opts(mode))
+    res = P.trals_decompose(ctx, w.I, w.R_fit, Xh, cores, sweeps, opts)
     dt = time.perf_counter() - t0
     ctx.close()
     core_bytes = sum(G.size * 8 for G in cores)
@@ -334,7 +342,8 @@ def run_ours(args):
             torch.distributed.barrier()
         # the FP64 mode beside the headline runs ~60x slower per sweep: a tenth of the steps
         steps = args.steps if mode == args.mode else max(10, args.steps // 10)
-        out[mode] = time_mode(P, torch, w, X, mode, steps, args.warmup, args.seed, flush, X_f64)
+        out[mode] = time_mode(P, torch, w, X, mode, steps, args.warmup, args.seed, flush, X_f64,
+                              opts_for(P, mode, args))
         out[mode]["X"] = X
     main = out[args.mode]
     ms = main["ms_per_step"]
@@ -344,7 +353,7 @@ def run_ours(args):
         ms = float(t.item())
     if rank != 0:
         return
-    e2e = e2e_run(P, torch, w, main["X"], args.mode, args.seed, w.sweeps)
+    e2e = e2e_run(P, torch, w, main["X"], opts_for(P, args.mode, args), args.seed, w.sweeps)
     line = {
         "metric": METRIC,
         "value": world * 1000.0 / ms, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
@@ -352,7 +361,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.mode],
         "data": "synthetic",
         "config": {"workload": w.name, "I": list(w.I), "R_fit": list(w.R_fit), "eta": w.eta, "mode": args.mode,
-                   "solver": "cholesky", "gram": "structured", "parallelism": "replicas" if world > 1 else "single",
+                   "solver": args.solver, "gram": args.gram, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed between timed sweeps (256 MB write)", "residual_after_run": main["residual"]},
         "roofline": roofline_for(w, args.mode, main["mttsp_kernel_ms"], peaks, src),
         "mttsp_ms_per_mode": main["mttsp_ms"],
@@ -422,6 +431,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--solver", default="cholesky", choices=sorted(SOLVERS))
+    ap.add_argument("--gram", default="structured", choices=sorted(GRAMS))
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)

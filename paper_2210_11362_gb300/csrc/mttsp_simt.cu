@@ -257,10 +257,10 @@ __global__ void __launch_bounds__(THREADS) reconstruct_kernel(const double* __re
 // depend on the order.  A tile holds FKT consecutive t: its X block is read coalesced, its subchain
 // rows are generated from FP32 copies of the two partial-chain tables, and each thread accumulates
 // a 4 x 4 block of M_n (rows i_n, columns a + R_n b) in FP32.  Per-CTA partials go out in FP64.
-constexpr int FKT = 64;
+constexpr int FKT = 64;        // tile width (columns); 16 when the staged tables need the room
 constexpr int kF32CtasPerSm = 6;
 
-template <typename XT>
+template <typename XT, int FKT>
 __global__ void __launch_bounds__(THREADS, 4) mttsp_simt_f32_kernel(const void* __restrict__ X,
                                                                  const void* __restrict__ Xlo,
                                                                  const float* __restrict__ ltab,
@@ -511,12 +511,17 @@ __global__ void __launch_bounds__(THREADS) residual_f32_kernel(const float* __re
 
 }  // namespace
 
-size_t mttsp_simt_f32_smem(const ModeLayout& L) {
+static size_t f32_smem_w(const ModeLayout& L, int w) {
   const int r = L.Rn * L.Rn1;
   const int64_t rp = (r + 3) & ~3, inp = (L.In + 3) & ~3;
   const int64_t nLr = (int64_t)L.Rn1 * L.Rs, nUr = (int64_t)L.Rs * L.Rn;
-  return (size_t)(FKT * (rp + inp + nLr) + ((FKT * nUr + 1) & ~1)) * sizeof(float) + 3 * FKT * sizeof(int64_t);
+  return (size_t)(w * (rp + inp + nLr) + ((w * nUr + 1) & ~1)) * sizeof(float) + 3 * w * sizeof(int64_t);
 }
+
+// tile width of the FP32 kernel for this layout: 64 columns, or 16 when that does not fit
+static int f32_width(const ModeLayout& L) { return f32_smem_w(L, FKT) <= 200 * 1024 ? FKT : 16; }
+
+size_t mttsp_simt_f32_smem(const ModeLayout& L) { return f32_smem_w(L, f32_width(L)); }
 
 bool mttsp_simt_f32_fits(const ModeLayout& L) { return L.In <= 4096 && mttsp_simt_f32_smem(L) <= 200 * 1024; }
 
@@ -525,7 +530,7 @@ int mttsp_simt_f32_grid(const ModeLayout& L) {
   const int64_t mts = (int64_t)((r + 3) / 4) * ((L.In + 3) / 4);
   const int64_t gy = (mts + THREADS - 1) / THREADS;
   // several CTAs per SM: each tile is a short chain of dependent steps, so SMs need many in flight
-  const int64_t tiles = (L.J + FKT - 1) / FKT;
+  const int64_t tiles = (L.J + f32_width(L) - 1) / f32_width(L);
   const int64_t by_partials = ((int64_t)8 << 20) / std::max<int64_t>(1, L.In * r);   // partials <= 64 MB
   return (int)std::max<int64_t>(
       1, std::min<int64_t>({tiles / 4, std::max<int64_t>(1, 152 * kF32CtasPerSm / gy), by_partials}));
@@ -540,16 +545,18 @@ void launch_mttsp_simt_f32(const MttspSimtArgs& a, const float* fl, const float*
   const int64_t Kpre = L.Kpre;
   const int64_t Q = L.J / Kpre;
   const size_t smem = mttsp_simt_f32_smem(L);
+  const bool wide = f32_width(L) == FKT;
   if (a.ev0) cudaEventRecord(a.ev0, s);
-  if (a.xt == TRALS_X_F32)
-    mttsp_simt_f32_kernel<float><<<grid, THREADS, smem, s>>>(a.X, nullptr, fl, fu, a.offL, a.offU, L, Kpre, Q,
-                                                             a.partials);
-  else if (a.xt == TRALS_X_BF16)
-    mttsp_simt_f32_kernel<__nv_bfloat16><<<grid, THREADS, smem, s>>>(a.X, a.Xlo, fl, fu, a.offL, a.offU, L, Kpre, Q,
-                                                                     a.partials);
-  else
-    mttsp_simt_f32_kernel<double><<<grid, THREADS, smem, s>>>(a.X, nullptr, fl, fu, a.offL, a.offU, L, Kpre, Q,
-                                                              a.partials);
+#define TRALS_F32(XT_, W_, LO_) \
+  mttsp_simt_f32_kernel<XT_, W_><<<grid, THREADS, smem, s>>>(a.X, LO_, fl, fu, a.offL, a.offU, L, Kpre, Q, a.partials)
+  if (a.xt == TRALS_X_F32) {
+    if (wide) TRALS_F32(float, FKT, nullptr); else TRALS_F32(float, 16, nullptr);
+  } else if (a.xt == TRALS_X_BF16) {
+    if (wide) TRALS_F32(__nv_bfloat16, FKT, a.Xlo); else TRALS_F32(__nv_bfloat16, 16, a.Xlo);
+  } else {
+    if (wide) TRALS_F32(double, FKT, nullptr); else TRALS_F32(double, 16, nullptr);
+  }
+#undef TRALS_F32
   if (a.ev1) cudaEventRecord(a.ev1, s);
   const int rg = (int)std::min<int64_t>((outN + 255) / 256, 152 * 8);
   reduce_partials_kernel<<<rg, 256, 0, s>>>(a.partials, a.gridX, outN, a.M);
@@ -622,13 +629,17 @@ void launch_mttsp_simt(const MttspSimtArgs& a, cudaStream_t s) {
 
 cudaError_t init_simt_attributes() {
   cudaError_t e = cudaFuncSetAttribute(mttsp_simt_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(mttsp_simt_f32_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(mttsp_simt_f32_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(mttsp_simt_f32_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+#define TRALS_F32_ATTR(XT_, W_)                                                                           \
+  if (e == cudaSuccess)                                                                                    \
+    e = cudaFuncSetAttribute(mttsp_simt_f32_kernel<XT_, W_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                              200 * 1024);
+  TRALS_F32_ATTR(double, FKT)
+  TRALS_F32_ATTR(float, FKT)
+  TRALS_F32_ATTR(__nv_bfloat16, FKT)
+  TRALS_F32_ATTR(double, 16)
+  TRALS_F32_ATTR(float, 16)
+  TRALS_F32_ATTR(__nv_bfloat16, 16)
+#undef TRALS_F32_ATTR
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(residual_f32_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e == cudaSuccess)
