@@ -336,12 +336,14 @@ def run_ours(args):
     out = {}
     X_f64 = make_X_device(w, args.seed, P, torch, torch.float64)
     modes = [args.mode] + ([] if args.mode == "fp64" or args.no_fp64 else ["fp64"])
+    if args.mode == "bf16" and not args.no_fp64:
+        modes.append("bf16x3")   # the compensated split-BF16 variant beside the headline
     for mode in modes:
         X = X_f64 if mode == "fp64" else X_f64.to(mode_xdtype(mode, torch))
         if world > 1:
             torch.distributed.barrier()
-        # the FP64 mode beside the headline runs ~60x slower per sweep: a tenth of the steps
-        steps = args.steps if mode == args.mode else max(10, args.steps // 10)
+        # the FP64 mode beside the headline runs ~90x slower per sweep: a tenth of the steps
+        steps = args.steps if mode != "fp64" or mode == args.mode else max(10, args.steps // 10)
         out[mode] = time_mode(P, torch, w, X, mode, steps, args.warmup, args.seed, flush, X_f64,
                               opts_for(P, mode, args))
         out[mode]["X"] = X
@@ -375,6 +377,11 @@ def run_ours(args):
                         "residual": f["residual"], "mttsp_ms_per_mode": f["mttsp_ms"],
                         "roofline": roofline_for(w, "fp64", f["mttsp_kernel_ms"], peaks, src)}
         line["speedup_vs_fp64"] = f["ms_per_step"] / main["ms_per_step"]
+    if "bf16x3" in out and args.mode != "bf16x3":
+        b = out["bf16x3"]
+        line["bf16x3"] = {"value": 1000.0 / b["ms_per_step"], "ms_per_step": b["ms_per_step"], "steps": len(b["times"]),
+                          "residual": b["residual"], "mttsp_ms_per_mode": b["mttsp_ms"],
+                          "roofline": roofline_for(w, "bf16x3", b["mttsp_kernel_ms"], peaks, src)}
     if not args.no_serve:
         for k in list(out):
             out[k].pop("X", None)

@@ -64,13 +64,15 @@ typedef enum { TRALS_X_F64 = 0, TRALS_X_F32 = 1, TRALS_X_BF16 = 2 } trals_xtype;
 /* Storage of X and arithmetic of the RHS contraction M_n (the Gram chain, S_n and the solve are
  * FP64 in every mode).
  *  FP64  : X read as FP64, MTTSP in FP64 on the CUDA cores.
- *  FP32  : X read as FP32 (converted once from FP64 if needed); MTTSP on the CUDA cores with FP64
- *          arithmetic on the FP32 values.
+ *  FP32  : X read as FP32 (converted once from FP64 if needed); MTTSP on the CUDA cores in FP32
+ *          arithmetic, per-block sums reduced in FP64.
  *  BF16  : X quantised once to BF16 (round to nearest even); MTTSP on BF16 tensor cores
  *          (tcgen05) with FP32 accumulation where trals_mttsp_path reports a tensor-core
- *          geometry, else on the CUDA cores in FP64 arithmetic.
- *  BF16X3: X split once into hi/lo BF16 pairs (hi = bf16(x), lo = bf16(x - hi)); MTTSP on the
- *          CUDA cores reading hi + lo with FP64 arithmetic. */
+ *          geometry, else on the CUDA cores in FP32 arithmetic.
+ *  BF16X3: X split once into hi/lo BF16 pairs (hi = bf16(x), lo = bf16(x - hi)), the subchain
+ *          table likewise; on the tensor cores every K step is three BF16 products
+ *          (X_hi T_hi + X_hi T_lo + X_lo T_hi) into one FP32 accumulator (the CUDA-core path reads
+ *          hi + lo in FP32 arithmetic). */
 typedef enum { TRALS_MODE_FP64 = 0, TRALS_MODE_FP32 = 1, TRALS_MODE_BF16 = 2, TRALS_MODE_BF16X3 = 3 } trals_mode;
 
 /* Solver for the R_n R_{n+1} subproblem: Cholesky on the normal equations

@@ -51,6 +51,7 @@ struct TcArgs {
   int NX, NY, Sy, Rn, r, W_pad, fs_stride, ms_stride, ns;
   uint32_t tx_bytes;
   uint32_t idesc;
+  int x3;            // bf16x3: X and the table as hi/lo BF16 pairs, three products per K step
   const float* F;    // [fac][NX][SYP]
   float* partials;   // [grid][In * r]
   DevStatus* status;
@@ -211,11 +212,13 @@ __device__ __forceinline__ bool get_unit(const TcArgs& a, int64_t j, int64_t& ti
 // row is T[y * SYP + z] (y < NY, z < SYP) and is held in registers.
 template <int SYP>
 __global__ void __launch_bounds__(kThreads, 1)
-    mttsp_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmT, const TcArgs a) {
+    mttsp_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmT,
+                    const __grid_constant__ CUtensorMap tmXl, const __grid_constant__ CUtensorMap tmTl, const TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int bBytes = ((a.W_pad * 128) + 1023) & ~1023;
-  const int stageBytes = kABytes + bBytes;
+  const int planes = a.x3 ? 2 : 1;                 // stage: X hi [, X lo], table hi [, table lo]
+  const int stageBytes = planes * (kABytes + bBytes);
   const int NS = a.ns;
   float* F_s = reinterpret_cast<float*>(base + NS * stageBytes);     // per row: its stage-2 factor block
   float* M_s = F_s + kRows * a.fs_stride;
@@ -273,18 +276,22 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           uint8_t* A = base + stage * stageBytes;
-          uint8_t* B = A + kABytes;
+          uint8_t* B = A + planes * kABytes;
           mbar_expect_tx(&full[stage], a.tx_bytes);
           const int k0 = ks * kKT;
-          if (a.variant == KM_L) {
-            tma_load_3d(A, &tmX, &full[stage], k0, 0, (int)(tile * a.nrep));
-          } else if (a.variant == KM_R) {
-            tma_load_3d(A, &tmX, &full[stage], k0, (int)(tile * a.nrep), 0);
-          } else {
-            for (int at = 0; at < 2; ++at)
-              tma_load_3d(A + at * kAtomBytes, &tmX, &full[stage], (int)(pc * 64), k0, (int)(2 * op + at));
+          for (int pl = 0; pl < planes; ++pl) {
+            const CUtensorMap* mx = pl ? &tmXl : &tmX;
+            uint8_t* Ap = A + pl * kABytes;
+            if (a.variant == KM_L) {
+              tma_load_3d(Ap, mx, &full[stage], k0, 0, (int)(tile * a.nrep));
+            } else if (a.variant == KM_R) {
+              tma_load_3d(Ap, mx, &full[stage], k0, (int)(tile * a.nrep), 0);
+            } else {
+              for (int at = 0; at < 2; ++at)
+                tma_load_3d(Ap + at * kAtomBytes, mx, &full[stage], (int)(pc * 64), k0, (int)(2 * op + at));
+            }
+            tma_load_2d(B + pl * bBytes, pl ? &tmTl : &tmT, &full[stage], k0, 0);
           }
-          tma_load_2d(B, &tmT, &full[stage], k0, 0);
           ++issued[stage];
           if (++stage == NS) {
             stage = 0;
@@ -328,13 +335,22 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           const uint32_t A = smem_u32(base + stage * stageBytes);
-          const uint32_t B = A + kABytes;
+          const uint32_t B = A + (uint32_t)(planes * kABytes);
 #pragma unroll
           for (int jj = 0; jj < kKT / 16; ++jj) {
             const uint64_t ad =
                 (a.variant == MM) ? sdesc(A + 2048u * jj, kAtomBytes, 1024) : sdesc(A + 32u * jj, 16, 1024);
             const uint64_t bd = sdesc(B + 32u * jj, 16, 1024);
             umma_bf16(d, ad, bd, a.idesc, (ks > ks0 || jj > 0) ? 1u : 0u);
+            if (a.x3) {
+              // split-BF16 products: X_hi T_lo + X_lo T_hi (X_lo T_lo is below FP32 rounding)
+              const uint32_t Al = A + (uint32_t)kABytes;
+              const uint64_t adl =
+                  (a.variant == MM) ? sdesc(Al + 2048u * jj, kAtomBytes, 1024) : sdesc(Al + 32u * jj, 16, 1024);
+              const uint64_t bdl = sdesc(B + (uint32_t)bBytes + 32u * jj, 16, 1024);
+              umma_bf16(d, ad, bdl, a.idesc, 1u);
+              umma_bf16(d, adl, bd, a.idesc, 1u);
+            }
           }
           umma_commit(&empty[stage]);
           if (++stage == NS) {
@@ -575,7 +591,8 @@ __global__ void tc_reduce_kernel(const float* __restrict__ partials, int G, int6
 // kindL (factor on the left): P = c x a (Ra = Sy rows), element (z, y); otherwise P = b x d (Ra = NY rows),
 // element (y, z).  Zero for z >= Sy, y >= NY or k >= K.
 __global__ void pack_tab_kernel(const float* __restrict__ src, int64_t K, int64_t Kpad, int Ra, int Rb, int kindL,
-                                int Sy, int SYP, int NY, int W_pad, __nv_bfloat16* __restrict__ dst) {
+                                int Sy, int SYP, int NY, int W_pad, __nv_bfloat16* __restrict__ dst,
+                                __nv_bfloat16* __restrict__ dst_lo) {
   const int64_t total = (int64_t)W_pad * Kpad;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = e % Kpad;
@@ -583,7 +600,9 @@ __global__ void pack_tab_kernel(const float* __restrict__ src, int64_t K, int64_
     const int z = w % SYP, y = w / SYP;
     float v = 0.0f;
     if (k < K && z < Sy && y < NY) v = src[(int64_t)(kindL ? (z + Ra * y) : (y + Ra * z)) * K + k];
-    dst[e] = __float2bfloat16_rn(v);
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    dst[e] = h;
+    if (dst_lo != nullptr) dst_lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));   // split-BF16 remainder
   }
 }
 
@@ -690,7 +709,7 @@ bool encode_bf16(CUtensorMap* m, const void* ptr, int rank, const uint64_t* dims
 // Host-side plan of one mode.
 struct TcImpl {
   TcArgs args{};
-  CUtensorMap tmX{}, tmT{};
+  CUtensorMap tmX{}, tmT{}, tmXl{}, tmTl{};
   int grid = 0;
   size_t smem = 0;
   // stage-1 table build: chain modes S (cyclic order), FP64 scratch, packed BF16 table
@@ -705,6 +724,7 @@ struct TcImpl {
   int64_t core_off[kMaxOrder + 1] = {};
   int SYP = 4;
   __nv_bfloat16* tab = nullptr;
+  __nv_bfloat16* tab_lo = nullptr;   // bf16x3 only
   float* F = nullptr;
   float* partials = nullptr;
   int64_t E = 0;
@@ -810,11 +830,13 @@ TcChoice tc_choose(int N, const int64_t* I, const int32_t* R, int n) {
 }
 
 int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mode, const void* X, int64_t numel,
-            cudaError_t* err, cudaStream_t s, size_t* count_bytes, int64_t I0_real) {
+            cudaError_t* err, cudaStream_t s, size_t* count_bytes, int64_t I0_real, const void* Xlo) {
   if (err) *err = cudaSuccess;
   p.valid = false;
-  if (mode != TRALS_MODE_BF16) return 0;
+  const bool x3 = mode == TRALS_MODE_BF16X3;
+  if (mode != TRALS_MODE_BF16 && !(x3 && Xlo != nullptr)) return 0;
   if ((reinterpret_cast<uintptr_t>(X) & 15) != 0) return 0;
+  if (x3 && (reinterpret_cast<uintptr_t>(Xlo) & 15) != 0) return 0;
   if (!get_encode()) return 0;
   const int Rn = R[n], Rn1 = R[(n + 1) % N];
   const int r = Rn * Rn1;
@@ -907,6 +929,8 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   A.ms_stride = A.r | 1;   // odd row stride: lanes with different i_n hit different banks
 
   A.tx_bytes += (uint32_t)(A.W_pad * 128);
+  A.x3 = x3 ? 1 : 0;
+  if (x3) A.tx_bytes *= 2;   // hi and lo planes of X and of the table
   // MMA instruction descriptor: D=F32, A=B=BF16, A major per variant, B K-major, N=W_pad, M=128
   A.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((A.variant == MM ? 1u : 0u) << 15) |
             ((uint32_t)(A.W_pad >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
@@ -940,7 +964,7 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   const int bBytes = ((A.W_pad * 128) + 1023) & ~1023;
   const size_t fixed = 1024 + (size_t)kRows * A.fs_stride * 4 +
                        (size_t)((In * A.ms_stride + 1) & ~1) * 4 + (2 * kNSMax + 4) * 8 + 64;
-  const size_t stage = (size_t)kABytes + bBytes;
+  const size_t stage = (size_t)(x3 ? 2 : 1) * ((size_t)kABytes + bBytes);
   const int ns = (int)std::min<size_t>(kNSMax, fixed < (size_t)kSmemBudget ? (kSmemBudget - fixed) / stage : 0);
   if (ns < 2) {
     delete impl;
@@ -965,7 +989,8 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   const uint64_t tstrides[1] = {(uint64_t)impl->Kpad * 2};
   const uint32_t tbox[2] = {kKT, (uint32_t)A.W_pad};
   if (!encode_bf16(&impl->tmX, X, 3, dims, strides, box) ||
-      !encode_bf16(&impl->tmT, reinterpret_cast<const void*>(uintptr_t(1) << 40), 2, tdims, tstrides, tbox)) {
+      !encode_bf16(&impl->tmT, reinterpret_cast<const void*>(uintptr_t(1) << 40), 2, tdims, tstrides, tbox) ||
+      (x3 && !encode_bf16(&impl->tmXl, Xlo, 3, dims, strides, box))) {
     delete impl;
     return 0;
   }
@@ -976,20 +1001,22 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   for (int m : impl->f_modes) nfac *= I[m];
   impl->n_fac_total = nfac;
   for (int j = 0; j < N; ++j) impl->core_off[j + 1] = impl->core_off[j] + (int64_t)R[j] * I[j] * R[(j + 1) % N];
-  const size_t sizes[6] = {(size_t)impl->core_off[N] * sizeof(float), chainMax * sizeof(float),
+  const size_t sizes[7] = {(size_t)impl->core_off[N] * sizeof(float), chainMax * sizeof(float),
                            chainMax * sizeof(float), (size_t)A.W_pad * impl->Kpad * sizeof(__nv_bfloat16),
                            (size_t)nfac * A.NX * impl->SYP * sizeof(float),
-                           (size_t)impl->grid * impl->E * sizeof(float)};
+                           (size_t)impl->grid * impl->E * sizeof(float),
+                           x3 ? (size_t)A.W_pad * impl->Kpad * sizeof(__nv_bfloat16) : 0};
+  const int nalloc = x3 ? 7 : 6;
   if (count_bytes) {
-    for (size_t b : sizes) *count_bytes += (std::max<size_t>(b, 16) + 255) & ~(size_t)255;
+    for (int k = 0; k < nalloc; ++k) *count_bytes += (std::max<size_t>(sizes[k], 16) + 255) & ~(size_t)255;
     delete impl;
     return 1;
   }
   p.stream = s;
   cudaError_t e = cudaSuccess;
-  void* q[6] = {};
+  void* q[7] = {};
   p.bytes = 0;
-  for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
+  for (int k = 0; k < nalloc && e == cudaSuccess; ++k) {
     const size_t b = (std::max<size_t>(sizes[k], 16) + 255) & ~(size_t)255;
     e = cudaMallocAsync(&q[k], b, s);
     if (e == cudaSuccess) {
@@ -1010,9 +1037,11 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   impl->tab = static_cast<__nv_bfloat16*>(q[3]);
   impl->F = static_cast<float*>(q[4]);
   impl->partials = static_cast<float*>(q[5]);
+  impl->tab_lo = x3 ? static_cast<__nv_bfloat16*>(q[6]) : nullptr;
   A.F = impl->F;
   A.partials = impl->partials;
-  if (!encode_bf16(&impl->tmT, impl->tab, 2, tdims, tstrides, tbox)) {
+  if (!encode_bf16(&impl->tmT, impl->tab, 2, tdims, tstrides, tbox) ||
+      (x3 && !encode_bf16(&impl->tmTl, impl->tab_lo, 2, tdims, tstrides, tbox))) {
     delete impl;
     for (void* a : p.allocs) cudaFreeAsync(a, s);
     p.allocs.clear();
@@ -1058,7 +1087,7 @@ int tc_enqueue(TcPlan& p, const void* X, double* const* cores, double* M, cudaSt
     const int64_t total = (int64_t)A.W_pad * impl->Kpad;
     const int g = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
     pack_tab_kernel<<<g, 256, 0, s>>>(tsrc, impl->K_S, impl->Kpad, impl->tabRa, impl->tabRb, impl->kindL, A.Sy,
-                                      impl->SYP, A.NY, A.W_pad, impl->tab);
+                                      impl->SYP, A.NY, A.W_pad, impl->tab, impl->tab_lo);
     ++launches;
   }
   const float* fsrc = build_chain(impl->f_modes, c32, I, R, N, impl->chainA, impl->chainB, s, &launches);
@@ -1070,11 +1099,13 @@ int tc_enqueue(TcPlan& p, const void* X, double* const* cores, double* M, cudaSt
     ++launches;
   }
   if (ev0) cudaEventRecord(ev0, s);
+  const CUtensorMap& xl = A.x3 ? impl->tmXl : impl->tmX;   // unread unless x3
+  const CUtensorMap& tl = A.x3 ? impl->tmTl : impl->tmT;
   switch (impl->SYP) {
-    case 4: mttsp_tc_kernel<4><<<impl->grid, kThreads, impl->smem, s>>>(impl->tmX, impl->tmT, A); break;
-    case 8: mttsp_tc_kernel<8><<<impl->grid, kThreads, impl->smem, s>>>(impl->tmX, impl->tmT, A); break;
-    case 12: mttsp_tc_kernel<12><<<impl->grid, kThreads, impl->smem, s>>>(impl->tmX, impl->tmT, A); break;
-    default: mttsp_tc_kernel<16><<<impl->grid, kThreads, impl->smem, s>>>(impl->tmX, impl->tmT, A); break;
+    case 4: mttsp_tc_kernel<4><<<impl->grid, kThreads, impl->smem, s>>>(impl->tmX, impl->tmT, xl, tl, A); break;
+    case 8: mttsp_tc_kernel<8><<<impl->grid, kThreads, impl->smem, s>>>(impl->tmX, impl->tmT, xl, tl, A); break;
+    case 12: mttsp_tc_kernel<12><<<impl->grid, kThreads, impl->smem, s>>>(impl->tmX, impl->tmT, xl, tl, A); break;
+    default: mttsp_tc_kernel<16><<<impl->grid, kThreads, impl->smem, s>>>(impl->tmX, impl->tmT, xl, tl, A); break;
   }
   ++launches;
   if (ev1) cudaEventRecord(ev1, s);

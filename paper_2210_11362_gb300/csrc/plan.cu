@@ -571,7 +571,7 @@ trals_status plan_build(trals_ctx* ctx, int N, const int64_t* I, const int32_t* 
   } while (0)
 
   for (int n = 0; n < N; ++n) p->Ist[n] = I[n];
-  if (o.mode == TRALS_MODE_BF16 && I[0] % 8 != 0) p->Ist[0] = (I[0] + 7) / 8 * 8;
+  if ((o.mode == TRALS_MODE_BF16 || o.mode == TRALS_MODE_BF16X3) && I[0] % 8 != 0) p->Ist[0] = (I[0] + 7) / 8 * 8;
   p->numel_st = p->numel / I[0] * p->Ist[0];
   const bool padded = p->Ist[0] != I[0];
   int maxR2 = 0, maxr = 0;
@@ -686,11 +686,12 @@ trals_status plan_build(trals_ctx* ctx, int N, const int64_t* I, const int32_t* 
     p->Xk = q;
     p->xk_t = TRALS_X_BF16;
   } else if (o.mode == TRALS_MODE_BF16X3) {
+    // hi and lo planes, each in the (padded) layout the MTTSP reads
     __nv_bfloat16* q = nullptr;
-    PLAN_TRY(p->alloc(&q, (size_t)p->numel * 2));
-    if (!counting) launch_quantize(X_dev, xt, p->numel, q, q + p->numel, s);
+    PLAN_TRY(p->alloc(&q, (size_t)p->numel_st * 2));
+    if (!counting) launch_quantize_padded(X_dev, xt, I[0], p->Ist[0], p->numel / I[0], q, q + p->numel_st, s);
     p->Xk = q;
-    p->Xk_lo = q + p->numel;
+    p->Xk_lo = q + p->numel_st;
     p->xk_t = TRALS_X_BF16;
   } else if (o.mode == TRALS_MODE_FP32 && xt == TRALS_X_F64) {
     float* q = nullptr;
@@ -708,7 +709,7 @@ trals_status plan_build(trals_ctx* ctx, int N, const int64_t* I, const int32_t* 
     p->use_tc[n] = false;
     if (o.mode != TRALS_MODE_FP64) {
       const int ok = tc_plan(p->tc[n], N, p->Ist, R, n, o.mode, p->Xk, p->numel_st, &e, s,
-                             counting ? &p->bytes : nullptr, I[0]);
+                             counting ? &p->bytes : nullptr, I[0], p->Xk_lo);
       if (e != cudaSuccess) PLAN_TRY(e);
       p->use_tc[n] = ok != 0;
       if (ok && !counting) {
@@ -1106,7 +1107,10 @@ trals_status trals_mttsp(trals_ctx* ctx, int N, const int64_t* I, const int32_t*
   for (int k = 0; k < N; ++k) numel *= I[k];
   TcPlan tc;
   cudaError_t e = cudaSuccess;
-  const int use_tc = (mode != TRALS_MODE_FP64) ? tc_plan(tc, N, I, R, n, mode, X_dev, numel, &e) : 0;
+  const void* Xlo = (mode == TRALS_MODE_BF16X3) ? static_cast<const void*>(static_cast<const __nv_bfloat16*>(X_dev) + numel)
+                                                 : nullptr;
+  const int use_tc =
+      (mode != TRALS_MODE_FP64) ? tc_plan(tc, N, I, R, n, mode, X_dev, numel, &e, ctx->stream, nullptr, 0, Xlo) : 0;
   TRALS_CUDA_TRY(ctx, e);
   if (use_tc) {
     tc_set_status(tc, ctx->d_status);
@@ -1172,7 +1176,7 @@ trals_status trals_mttsp(trals_ctx* ctx, int N, const int64_t* I, const int32_t*
 
 int trals_mttsp_path(int N, const int64_t* I, const int32_t* R, int n, int mode) {
   if (N < 3 || N > TRALS_MAX_ORDER || !I || !R || n < 0 || n >= N) return -1;
-  if (mode != TRALS_MODE_BF16) return 0;
+  if (mode != TRALS_MODE_BF16 && mode != TRALS_MODE_BF16X3) return 0;
   // plans store the BF16 copy with mode 0 padded to a multiple of 8
   int64_t Ist[TRALS_MAX_ORDER];
   for (int j = 0; j < N; ++j) Ist[j] = I[j];

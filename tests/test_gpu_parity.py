@@ -254,6 +254,32 @@ def test_plan_mttsp_bf16_with_padded_leading_mode(ctx, I, R):
         plan.close()
 
 
+@pytest.mark.parametrize("I,R", TC_SHAPES)
+def test_mttsp_bf16x3_tensor_cores_match_oracle(ctx, I, R):
+    """bf16x3 on the tensor cores: X and the stage-1 table split into hi/lo BF16 pairs, three BF16
+    products per K step into FP32.  The result matches X_[n] G^{!=n} (with X = hi + lo) to the
+    split-BF16 rounding, about 2^-16 relative per factor (normwise 5e-5, i.e. ~80x tighter than
+    the single-BF16 bar)."""
+    X, _ = _problem(I, R)
+    cores = TI.gaussian_cores(9, I, R)
+    numel = int(np.prod(I))
+    Xd = P.tensor_to_device(X)
+    hl = torch.zeros(2 * numel, dtype=torch.bfloat16, device="cuda")
+    P.trals_quantize_bf16(ctx, Xd, hl[:numel], hl[numel:])
+    Xq = TI.unflat_f(hl[:numel].double().cpu().numpy() + hl[numel:].double().cpu().numpy(), I)
+    cd = [P.core_to_device(G) for G in cores]
+    N = len(I)
+    for n in range(N):
+        assert P.trals_mttsp_path(I, R, n, "bf16x3") > 0
+        r = R[n] * R[(n + 1) % N]
+        M = torch.zeros(I[n] * r, dtype=torch.float64, device="cuda")
+        P.trals_mttsp(ctx, I, R, hl, "bf16x3", cd, n, M)
+        ref = O.unfold_mode(Xq, n) @ O.subchain_unfolded(cores, n)
+        got = M.cpu().numpy().reshape(I[n], r, order="F")
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err < 5e-5, (n, P.MTTSP_PATHS[P.trals_mttsp_path(I, R, n, "bf16x3")], err)
+
+
 def test_solve_chol_matches_oracle(ctx):
     I, R = (9, 8, 7), (3, 4, 2)
     X, init = _problem(I, R)
