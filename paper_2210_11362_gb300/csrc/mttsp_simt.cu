@@ -328,23 +328,33 @@ __global__ void __launch_bounds__(THREADS, 4) mttsp_simt_f32_kernel(const void* 
       }
       Gs[e] = g;
     }
-    for (int e = threadIdx.x; e < FKT * inp; e += blockDim.x) {
-      int i, kk;
-      if (Kpre == 1) {   // mode 0: memory is contiguous along i
-        i = e % inp;
-        kk = e / inp;
-      } else {           // memory is contiguous along t
-        kk = e % FKT;
-        i = e / FKT;
+    // X tile: four independent loads in flight per thread before any store
+    for (int e0 = threadIdx.x; e0 < FKT * inp; e0 += 4 * blockDim.x) {
+      float v[4];
+      int dst[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = e0 + q * blockDim.x;
+        int i = 0, kk = 0;
+        if (Kpre == 1) {   // mode 0: memory is contiguous along i
+          i = e % inp;
+          kk = e / inp;
+        } else {           // memory is contiguous along t
+          kk = e % FKT;
+          i = e / FKT;
+        }
+        dst[q] = e < FKT * inp ? kk * inp + i : -1;
+        const int64_t bo = dst[q] >= 0 ? base[kk] : -1;
+        v[q] = 0.f;
+        if (i < In && bo >= 0) {
+          const int64_t off = bo + (int64_t)i * L.strideN;
+          v[q] = (float)ld<XT>(X, off);
+          if (Xlo != nullptr) v[q] += (float)ld<XT>(Xlo, off);   // split-BF16 pair: hi + lo
+        }
       }
-      const int64_t bo = base[kk];
-      float v = 0.f;
-      if (i < In && bo >= 0) {
-        const int64_t off = bo + (int64_t)i * L.strideN;
-        v = (float)ld<XT>(X, off);
-        if (Xlo != nullptr) v += (float)ld<XT>(Xlo, off);   // split-BF16 pair: hi + lo
-      }
-      Xs[kk * inp + i] = v;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (dst[q] >= 0) Xs[dst[q]] = v[q];
     }
     __syncthreads();
     if (active) {
@@ -385,6 +395,7 @@ __global__ void __launch_bounds__(THREADS, 4) mttsp_simt_f32_kernel(const void* 
 // 1e-7 relative to |X_hat|) is far below what the residual is compared against (1e-4), while the
 // FP64 arithmetic of the reconstruction above would cost ~100x more on GB300's FP64 pipe.
 constexpr int RKT = 128;          // columns of X_[n] per tile
+constexpr int GTS = RKT + 4;      // row stride of the transposed subchain rows (16-byte aligned, banks skewed)
 constexpr int RIC = 32;           // rows of X_[n] per chunk: 8 warps x 4 rows
 
 __global__ void tables_to_f32_kernel(const double* __restrict__ a, int64_t na, float* __restrict__ fa,
@@ -409,8 +420,8 @@ __global__ void __launch_bounds__(THREADS) residual_f32_kernel(const float* __re
   __shared__ double red[2][THREADS / 32];
   const int r = L.Rn * L.Rn1;
   const int64_t In = L.In;
-  float* Gt = fsm;                         // [r][RKT]: subchain rows, transposed
-  float* Cs = Gt + (size_t)r * RKT;        // [RIC][r]: rows of G_{n(2)}
+  float* Gt = fsm;                         // [r][GTS]: subchain rows, transposed
+  float* Cs = Gt + (size_t)r * GTS;        // [RIC][r]: rows of G_{n(2)}
   int64_t* base = reinterpret_cast<int64_t*>(Cs + (size_t)RIC * r + 4);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t chunk = (L.J + gridDim.x - 1) / gridDim.x;
@@ -432,16 +443,29 @@ __global__ void __launch_bounds__(THREADS) residual_f32_kernel(const float* __re
       }
     }
     __syncthreads();
+    // lanes run along the row entries (a, b) of one column: the Left-table reads are then
+    // contiguous (lanes along the columns touched 32 cache lines per warp load)
     for (int e = threadIdx.x; e < RKT * r; e += blockDim.x) {
-      const int kk = e % RKT, rr = e / RKT;
+      const int kk = e / r, rr = e % r;
       float acc = 0.f;
       if (base[kk] >= 0) {
         const int a = rr % L.Rn, b = rr / L.Rn;
-        const float* Lp = ltab + lrow[kk] * (int64_t)L.Rn1 * L.Rs;
-        const float* Up = utab + urow[kk] * (int64_t)L.Rs * L.Rn;
-        for (int c = 0; c < L.Rs; ++c) acc = fmaf(Lp[b + L.Rn1 * c], Up[c + L.Rs * a], acc);
+        const float* Lp = ltab + lrow[kk] * (int64_t)L.Rn1 * L.Rs + b;
+        const float* Up = utab + urow[kk] * (int64_t)L.Rs * L.Rn + L.Rs * a;
+        // four independent chains: the table loads come from L2, and a single dependent chain
+        // left the SMs waiting on them
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        int c = 0;
+        for (; c + 3 < L.Rs; c += 4) {
+          a0 = fmaf(Lp[L.Rn1 * c], Up[c], a0);
+          a1 = fmaf(Lp[L.Rn1 * (c + 1)], Up[c + 1], a1);
+          a2 = fmaf(Lp[L.Rn1 * (c + 2)], Up[c + 2], a2);
+          a3 = fmaf(Lp[L.Rn1 * (c + 3)], Up[c + 3], a3);
+        }
+        for (; c < L.Rs; ++c) a0 = fmaf(Lp[L.Rn1 * c], Up[c], a0);
+        acc = (a0 + a1) + (a2 + a3);
       }
-      Gt[rr * RKT + kk] = acc;
+      Gt[rr * GTS + kk] = acc;
     }
     for (int64_t i0 = 0; i0 < In; i0 += RIC) {
       __syncthreads();   // Gt/base written; previous chunk's Cs reads done
@@ -460,7 +484,7 @@ __global__ void __launch_bounds__(THREADS) residual_f32_kernel(const float* __re
         for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
       const float* C0 = Cs + (warp * 4) * r;
       for (int c = 0; c < r; ++c) {
-        const float4 g = *reinterpret_cast<const float4*>(Gt + c * RKT + 4 * lane);
+        const float4 g = *reinterpret_cast<const float4*>(Gt + c * GTS + 4 * lane);
         const float cv[4] = {C0[c], C0[r + c], C0[2 * r + c], C0[3 * r + c]};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -470,19 +494,29 @@ __global__ void __launch_bounds__(THREADS) residual_f32_kernel(const float* __re
           acc[u][3] = fmaf(cv[u], g.w, acc[u][3]);
         }
       }
+      // issue all sixteen X loads before using any (they are independent; one DRAM latency per
+      // chunk instead of one per element)
+      double xv[4][4];
+      int64_t off[4][4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int64_t i = i0 + warp * 4 + u;
-        if (i >= In) continue;
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const int64_t bo = base[4 * lane + v];
-          if (bo < 0) continue;
-          const double xv = ld<XT>(X, bo + i * L.strideN);
-          const double d = xv - (double)acc[u][v];
-          if (Eout != nullptr) Eout[bo + i * L.strideN] = (float)d;
+          off[u][v] = (i < In && bo >= 0) ? bo + i * L.strideN : -1;
+          xv[u][v] = off[u][v] >= 0 ? ld<XT>(X, off[u][v]) : 0.0;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          if (off[u][v] < 0) continue;
+          const double d = xv[u][v] - (double)acc[u][v];
+          if (Eout != nullptr) Eout[off[u][v]] = (float)d;
           d2 = fma(d, d, d2);
-          x2 = fma(xv, xv, x2);
+          x2 = fma(xv[u][v], xv[u][v], x2);
         }
       }
     }
@@ -570,7 +604,7 @@ void launch_tables_to_f32(const double* a, int64_t na, float* fa, const double* 
 
 size_t residual_f32_smem(const ModeLayout& L) {
   const int r = L.Rn * L.Rn1;
-  return ((size_t)r * RKT + (size_t)RIC * r + 4) * sizeof(float) + 3 * RKT * sizeof(int64_t);
+  return ((size_t)r * GTS + (size_t)RIC * r + 4) * sizeof(float) + 3 * RKT * sizeof(int64_t);
 }
 
 int residual_f32_grid(const ModeLayout& L) {
