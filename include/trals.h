@@ -232,6 +232,13 @@ trals_status trals_mttsp(trals_ctx* ctx, int N, const int64_t* I, const int32_t*
 trals_status trals_solve_chol(trals_ctx* ctx, int Rn, int64_t In, int Rn1, const double* S_dev,
                               const double* M_dev, double* G_dev);
 
+/* Verification hook for the Cholesky pivots; not a step of the method.  For n positive finite doubles
+ * d_dev (device), out_dev[i] = the reciprocal square root the Cholesky kernel of trals_solve_chol uses for
+ * its pivots and ref_dev[i] = CUDA's rsqrt(d_dev[i]), both device arrays of n doubles.  Other inputs give
+ * unspecified values.  n = 0 is a no-op.  Synchronous. */
+trals_status trals_check_pivot_rsqrt(trals_ctx* ctx, const double* d_dev, int64_t n, double* out_dev,
+                                     double* ref_dev);
+
 /* trals_mttsp in FP64 mode (X FP64) without any device allocation, for callers that cannot allocate:
  * code running where cudaMalloc/cudaFree are unavailable or forbidden (a host callback, an allocator
  * hook that must not re-enter the CUDA allocator, a fixed-budget real-time loop, a runtime that owns

@@ -39,7 +39,7 @@ EXPORTED = [
     "trals_plan_run", "trals_plan_residuals", "trals_plan_mttsp", "trals_plan_time_mttsp", "trals_plan_core_dev",
     "trals_plan_explicit_residual", "trals_plan_footprint", "trals_plan_bytes",
     "trals_plan_launches_per_sweep", "trals_plan_mttsp_path",
-    "trals_gamma", "trals_coef_matrix", "trals_coef_matrix_explicit", "trals_qr_r_factor", "trals_mttsp", "trals_mttsp_noalloc", "trals_mttsp_path", "trals_solve_chol", "trals_reconstruct",
+    "trals_gamma", "trals_coef_matrix", "trals_coef_matrix_explicit", "trals_qr_r_factor", "trals_mttsp", "trals_mttsp_noalloc", "trals_mttsp_path", "trals_solve_chol", "trals_check_pivot_rsqrt", "trals_reconstruct",
     "trals_residual_explicit", "trals_quantize_bf16",
     "trals_server_create", "trals_server_destroy", "trals_server_submit", "trals_server_poll",
     "trals_server_wait", "trals_server_stats", "trals_server_last_error",
@@ -121,6 +121,7 @@ def lib() -> ctypes.CDLL:
         "trals_mttsp_path": (ctypes.c_int, [ctypes.c_int, _vp, _vp, ctypes.c_int, ctypes.c_int]),
         "trals_mttsp_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
         "trals_solve_chol": (ctypes.c_int, [_vp, ctypes.c_int, _i64, ctypes.c_int, _vp, _vp, _vp]),
+        "trals_check_pivot_rsqrt": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
         "trals_reconstruct": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int]),
         "trals_residual_explicit": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp,
                                                    ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)]),
@@ -404,6 +405,12 @@ def trals_mttsp_path(I, R, n: int, mode) -> int:
 def trals_solve_chol(ctx: Context, Rn: int, In: int, Rn1: int, S_dev, M_dev, G_dev) -> None:
     ctx.check(lib().trals_solve_chol(ctx.handle, int(Rn), int(In), int(Rn1), _ptr(S_dev), _ptr(M_dev), _ptr(G_dev)),
               "trals_solve_chol")
+
+
+def trals_check_pivot_rsqrt(ctx: Context, d_dev, out_dev, ref_dev) -> None:
+    """Verification hook: out = the Cholesky pivots' reciprocal square root of d, ref = CUDA's rsqrt(d)."""
+    ctx.check(lib().trals_check_pivot_rsqrt(ctx.handle, _ptr(d_dev), int(d_dev.numel()), _ptr(out_dev), _ptr(ref_dev)),
+              "trals_check_pivot_rsqrt")
 
 
 def trals_reconstruct(ctx: Context, I, R, cores_dev: Sequence, out_dev) -> None:

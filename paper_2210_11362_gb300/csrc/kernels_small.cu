@@ -122,17 +122,28 @@ __global__ void chain_level_kernel(const double* __restrict__ prev, int64_t nPre
 }
 
 // ------------------------------------------------------------------ K4: Cholesky (single CTA)
-// Right-looking column Cholesky of the lower triangle of S (r x r), the Golub & Van Loan Sec. 5.3.2
-// method cited for Alg. 2 line 9, in FP64.  The matrix lives in shared memory (r <= kCholSmemMax),
-// else in Lmat.  Column j's trailing update is split by columns k over warps and rows i >= k over
-// lanes (no index division).  The reciprocal diagonal 1/L_jj is stored after the matrix (Lmat[r*r + j])
-// so the triangular solves never divide.
+// Right-looking column Cholesky of the lower triangle of S (r x r, r <= kCholSmemMax), the Golub & Van
+// Loan Sec. 5.3.2 method cited for Alg. 2 line 9, in FP64 with the matrix in shared memory.  The
+// reciprocal diagonal 1/L_jj is stored after the matrix (Lmat[r*r + j]) so the triangular solves never
+// divide.
+//
+// On this part a dependent FP64 instruction costs a sub-partition's FP64 pipe a full 64-cycle warp slot
+// whatever the active lanes, so the serial part of each column (update the next column, take its pivot,
+// scale it) is latency-bound, and slows by the pipe time of every other warp sharing its sub-partition.
+// The work is therefore split by sub-partition (warp w runs on sub-partition w mod 4):
+//   * warp 0 alone on sub-partition 0 carries the chain: at step j it updates column j+1 with column j,
+//     forms the pivot of column j+1 and scales it, holding the column in registers throughout;
+//   * the 24 warps on sub-partitions 1-3 apply column j to the trailing columns k >= j+2.  Column j+2+c
+//     (length m - c, m = r - j - 2) is paired with column r-1-c (length c + 1), so every pair is m + 1
+//     entries long: a warp takes whole pairs and its lanes run down the pair, with no lanes idle beyond
+//     the last chunk and no integer division;
+//   * the other warps of sub-partition 0 only load and store the matrix.
+// One named barrier over the 800 working threads separates the steps.
+//
 // 1/sqrt(d) for d > 0 by Newton-Raphson on f(y) = y^-2 - d, y <- y (3 - d y^2) / 2, started from the
 // FP32 hardware estimate of the exactly rescaled argument: each step doubles the correct bits, so two
 // steps take the ~23-bit seed past the 53 of FP64.  d is first scaled by an even power of two into
-// FP32 range, which changes neither the digits nor the result beyond that exact power.  On this part
-// an FP64 instruction occupies a sub-partition's FP64 pipe for a full warp slot even with one
-// active lane, and this sequence is about a third of the length of an FP64 sqrt plus a divide.
+// FP32 range, which changes neither the digits nor the result beyond that exact power.
 __device__ __forceinline__ double rsqrt_newton(double d) {
   int e;
   const double m = frexp(d, &e);                  // d = m 2^e, m in [0.5, 1)
@@ -144,71 +155,134 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
   return ldexp(y, -h);                             // (m2 2^(2h))^(-1/2)
 }
 
+// 1/sqrt(d) for the pivots, d positive, finite, with a binary exponent in [-120, 120]: the FP32 hardware
+// estimate of d truncated to 24 significant bits, widened exactly, then one third-order Householder
+// step y <- y (1 + e/2 + 3e^2/8), e = 1 - d y^2, which cubes the relative error (2^-21 -> 2^-63) so the
+// result is within the final roundings of the FP64 operations.  The FP32 copy and the widening are
+// formed from the bit patterns, which keeps conversion instructions off the serial chain.  Other
+// arguments take rsqrt_newton.
+__device__ __forceinline__ double rsqrt_pivot(double d) {
+  const long long b = __double_as_longlong(d);
+  const int E = (int)((b >> 52) & 0x7ff) - 1023;
+  if (E < -120 || E > 120) return rsqrt_newton(d);
+  const unsigned fb = ((unsigned)(E + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff);
+  const unsigned yb = __float_as_uint(rsqrtf(__uint_as_float(fb)));
+  const long long yd = ((long long)((int)((yb >> 23) & 0xff) - 127 + 1023) << 52) | ((long long)(yb & 0x7fffff) << 29);
+  const double y0 = __longlong_as_double(yd);
+  const double e = fma(-d, y0 * y0, 1.0);
+  return fma(y0 * e, fma(0.375, e, 0.5), y0);
+}
+
+__global__ void pivot_rsqrt_check_kernel(const double* __restrict__ d, int64_t n, double* __restrict__ out,
+                                         double* __restrict__ ref) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    out[i] = rsqrt_pivot(d[i]);
+    ref[i] = rsqrt(d[i]);
+  }
+}
+
 constexpr int kCholSmemMax = 128;
 constexpr int kCholThreads = 1024;
+constexpr int kCholWork = 800;       // warp 0 and the 24 warps of sub-partitions 1-3
+constexpr int kCholTrail = 24;       // trailing-update warps
+
+__device__ __forceinline__ void chol_step_barrier() {
+  asm volatile("bar.sync 1, %0;" ::"r"(kCholWork) : "memory");
+}
 
 __global__ void __launch_bounds__(kCholThreads) cholesky_kernel(const double* __restrict__ S, double* __restrict__ Lmat,
                                                                  int r, DevStatus* st, const int* sweep_ctr, int mode) {
-  extern __shared__ double sm[];
-  const bool in_smem = r <= kCholSmemMax;
-  double* A = in_smem ? sm : Lmat;
-  const int lda = r;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int warp = tid / 32, lane = tid % 32, nw = nt / 32;
-  __shared__ double piv[2];   // square root and reciprocal square root of the current pivot
-  __shared__ int bad;
-  for (int e = tid; e < r * r; e += nt) {
+  extern __shared__ double A[];   // r x r, column-major
+  __shared__ int bad[2];          // failure flag of the steps of each parity
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int e = tid; e < r * r; e += kCholThreads) {
     const int i = e % r, j = e / r;
     A[e] = (i >= j) ? S[e] : 0.0;
   }
-  // one thread forms each pivot's square root and reciprocal: FP64 sqrt/div are costly on this
-  // part, so they are never computed redundantly by every thread
-  auto pivot = [&](int j) {
-    const double d = A[j + lda * j];
-    if (!(d > 0.0) || !isfinite(d)) {
-      bad = 1;
-      set_status(st, isfinite(d) ? TRALS_E_NOT_SPD : TRALS_E_NONFINITE, sweep_ctr ? *sweep_ctr : -1, mode, j, d);
-    } else {
-      const double y = rsqrt_newton(d);
-      piv[0] = d * y;
-      piv[1] = y;
+  if (tid < 2) bad[tid] = 0;
+  __syncthreads();
+  const bool chain = warp == 0, trail = (warp & 3) != 0;
+  // pivot of column k from its updated diagonal d (lane 0); on failure the flag of step parity `slot`
+  auto pivot = [&](int k, double d, int slot, double& y, double& l) -> bool {
+    int ok = 1;
+    if (lane == 0) {
+      const long long b = __double_as_longlong(d);
+      if (b > 0 && b < 0x7ff0000000000000LL) {
+        y = rsqrt_pivot(d);
+        l = d * y;
+      } else {
+        ok = 0;
+        bad[slot] = 1;
+        set_status(st, isfinite(d) ? TRALS_E_NOT_SPD : TRALS_E_NONFINITE, sweep_ctr ? *sweep_ctr : -1, mode, k, d);
+      }
     }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    y = __shfl_sync(0xffffffffu, y, 0);
+    l = __shfl_sync(0xffffffffu, l, 0);
+    return ok != 0;
   };
-  __syncthreads();
-  if (tid == 0) {
-    bad = 0;
-    pivot(0);
-  }
-  __syncthreads();
-  for (int j = 0; j < r; ++j) {
-    if (bad) return;
-    const double l = piv[0], inv = piv[1];
-    for (int i = j + 1 + tid; i < r; i += nt) A[i + lda * j] *= inv;
-    __syncthreads();
-    // A[i][k] -= A[i][j] A[k][j] for j < k <= i: column k -> warp, rows i -> lanes.  Warp 0 takes only
-    // column j + 1 and then forms the next pivot's roots; the other warps share the rest, so the
-    // serial pivot work overlaps the bulk of the update.
-    if (warp == 0) {
-      const int k = j + 1;
-      if (k < r) {
-        const double akj = A[k + lda * j];
-        for (int i = k + lane; i < r; i += 32) A[i + lda * k] = fma(-A[i + lda * j], akj, A[i + lda * k]);
-        if (lane == 0) pivot(k);
-      }
-    } else {
-      for (int k = j + 1 + warp; k < r; k += nw - 1) {
-        const double akj = A[k + lda * j];
-        for (int i = k + lane; i < r; i += 32) A[i + lda * k] = fma(-A[i + lda * j], akj, A[i + lda * k]);
+  if (chain || trail) {
+    if (chain) {
+      double y = 0.0, l = 0.0;
+      if (pivot(0, A[0], 1, y, l)) {
+        for (int i = 1 + lane; i < r; i += 32) A[i] *= y;
+        if (lane == 0) {
+          A[0] = l;
+          Lmat[(int64_t)r * r] = y;
+        }
       }
     }
-    if (tid == 0) {
-      A[j + lda * j] = l;
-      Lmat[r * r + j] = inv;
+    chol_step_barrier();
+    // the flag written in step j is read after that step's barrier; the next write to the same slot
+    // comes two barriers later, after every thread has read it
+    if (!bad[1]) {
+      const int tw = warp - (warp >> 2) - 1;   // trailing warp index 0..23
+      for (int j = 0; j + 1 < r; ++j) {
+        const double* Lj = A + r * j;
+        if (chain) {
+          const int k = j + 1;
+          double* Ak = A + r * k;
+          const double akj = Lj[k];
+          double x[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+          for (int s = 0; s < 4; ++s)
+            if (k + 32 * s < r) {
+              const int i = k + lane + 32 * s;
+              if (i < r) x[s] = fma(-Lj[i], akj, Ak[i]);
+            }
+          double y = 0.0, l = 0.0;
+          if (pivot(k, x[0], j & 1, y, l)) {
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+              if (k + 32 * s < r) {
+                const int i = k + lane + 32 * s;
+                if (i < r) Ak[i] = (i == k) ? l : x[s] * y;
+              }
+            if (lane == 0) Lmat[(int64_t)r * r + k] = y;
+          }
+        } else {
+          const int m = r - j - 2, h = m + 1, np = (m + 1) >> 1;
+          for (int c = tw; c < np; c += kCholTrail) {
+            const int k1 = j + 2 + c, k2 = r - 1 - c, len = m - c;
+            const double l1 = Lj[k1], l2 = Lj[k2];
+            for (int rho = lane; rho < h; rho += 32) {
+              const bool first = rho < len;
+              const int k = first ? k1 : k2;
+              const int i = first ? k1 + rho : k2 + rho - len;
+              // the odd middle column pairs with itself: its second half is not there
+              if (first || k2 != k1) A[i + r * k] = fma(-Lj[i], first ? l1 : l2, A[i + r * k]);
+            }
+          }
+        }
+        chol_step_barrier();
+        if (bad[j & 1]) break;
+      }
     }
-    __syncthreads();
   }
-  if (in_smem)
-    for (int e = tid; e < r * r; e += nt) Lmat[e] = A[e];
+  __syncthreads();
+  if (!bad[0] && !bad[1])
+    for (int e = tid; e < r * r; e += kCholThreads) Lmat[e] = A[e];
 }
 
 // ------------------------------------------------------------------ K4, blocked over many SMs
@@ -627,6 +701,10 @@ int launch_cholesky(const double* S, double* Lmat, int r, DevStatus* st, const i
     ++launches;
   }
   return launches;
+}
+
+void launch_pivot_rsqrt_check(const double* d, int64_t n, double* out, double* ref, cudaStream_t s) {
+  pivot_rsqrt_check_kernel<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(d, n, out, ref);
 }
 
 void launch_chol_solve(const double* Lmat, const double* M, int Rn, int64_t In, int Rn1, double* G, DevStatus* st,

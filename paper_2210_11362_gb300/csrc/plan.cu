@@ -1200,6 +1200,16 @@ trals_status trals_solve_chol(trals_ctx* ctx, int Rn, int64_t In, int Rn1, const
   return st;
 }
 
+trals_status trals_check_pivot_rsqrt(trals_ctx* ctx, const double* d_dev, int64_t n, double* out_dev,
+                                     double* ref_dev) {
+  if (!ctx || n < 0 || (n > 0 && (!d_dev || !out_dev || !ref_dev))) return TRALS_E_ARG;
+  if (n == 0) return TRALS_OK;
+  launch_pivot_rsqrt_check(d_dev, n, out_dev, ref_dev, ctx->stream);
+  TRALS_CUDA_TRY(ctx, cudaGetLastError());
+  TRALS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return TRALS_OK;
+}
+
 trals_status trals_reconstruct(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R,
                                const double* const* cores_dev, void* out_dev, int xt) {
   if (!ctx || !cores_dev || !out_dev) return TRALS_E_ARG;

@@ -125,6 +125,8 @@ void launch_residual_f32(const ModeLayout& L, const double* ltab, const double* 
 int launch_cholesky(const double* S, double* Lmat, int r, DevStatus* st, const int* sweep_ctr, int mode,
                     cudaStream_t s);
 // Triangular solves with In right-hand sides; writes core layout.
+// out[i] = the Cholesky kernel's pivot reciprocal square root of d[i], ref[i] = CUDA's rsqrt(d[i])
+void launch_pivot_rsqrt_check(const double* d, int64_t n, double* out, double* ref, cudaStream_t s);
 void launch_chol_solve(const double* Lmat, const double* M, int Rn, int64_t In, int Rn1, double* G,
                        DevStatus* st, cudaStream_t s);
 

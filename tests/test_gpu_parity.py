@@ -312,6 +312,60 @@ def test_solve_chol_across_sizes_and_scales(ctx, r, scale):
     assert rel(got, ref) < 1e-11, rel(got, ref)
 
 
+def test_pivot_rsqrt_against_cuda_rsqrt(ctx):
+    """The Cholesky pivots' reciprocal square root (FP32 estimate + one third-order Householder step,
+    rescaled path outside the FP32 exponent range) against CUDA's double rsqrt, which is documented
+    within 1 ulp: over the whole normal exponent range, exact powers of four, and both sides of the
+    fast path's exponent limits."""
+    rng = np.random.default_rng(11)
+    frac = 1.0 + rng.random(200000)
+    exps = rng.integers(-1020, 1020, size=frac.size)
+    d = np.ldexp(frac, exps)
+    edges = [np.ldexp(f, e) for e in (-122, -121, -120, -119, 119, 120, 121, 122)
+             for f in (1.0, 1.5, np.nextafter(2.0, 0.0))]
+    quads = [4.0 ** k for k in range(-200, 201)]
+    d = np.concatenate([d, edges, quads, [np.finfo(np.float64).tiny, np.finfo(np.float64).max]])
+    dd = torch.from_numpy(d).cuda()
+    out = torch.empty_like(dd)
+    ref = torch.empty_like(dd)
+    P.trals_check_pivot_rsqrt(ctx, dd, out, ref)
+    o, f = out.cpu().numpy(), ref.cpu().numpy()
+    ulp = np.spacing(np.abs(f))
+    assert np.all(np.isfinite(o))
+    assert np.max(np.abs(o - f) / ulp) <= 3.0
+    # powers of four: the exact result is a power of two
+    q = np.array(quads)
+    oq = o[-len(quads) - 2:-2]
+    exact = np.ldexp(1.0, -np.arange(-200, 201))
+    assert np.max(np.abs(oq - exact) / np.spacing(exact)) <= 1.0
+    assert np.array_equal(exact, 1.0 / np.sqrt(q))
+
+
+@pytest.mark.parametrize("r,k", [(40, 1), (40, 2), (40, 37), (40, 39), (120, 64), (120, 119), (5, 0)])
+def test_solve_chol_reports_not_spd_mid_factorization(ctx, r, k):
+    """A non-positive pivot at column k (of either step parity, including the first and the last)
+    stops the factorization with NOT_SPD; a later call on the same context still works."""
+    S = np.eye(r)
+    S[k, k] = -1.0
+    M = np.ones((3, r))
+    G = torch.zeros(r * 3, dtype=torch.float64, device="cuda")
+    with pytest.raises(P.TralsError) as e:
+        P.trals_solve_chol(ctx, r, 3, 1, torch.from_numpy(S.reshape(-1, order="F").copy()).cuda(),
+                           torch.from_numpy(M.reshape(-1, order="F").copy()).cuda(), G)
+    assert e.value.status == P.E_NOT_SPD
+    S[k, k] = np.nan
+    with pytest.raises(P.TralsError) as e:
+        P.trals_solve_chol(ctx, r, 3, 1, torch.from_numpy(S.reshape(-1, order="F").copy()).cuda(),
+                           torch.from_numpy(M.reshape(-1, order="F").copy()).cuda(), G)
+    assert e.value.status == P.E_NONFINITE
+    S[k, k] = 2.0
+    P.trals_solve_chol(ctx, r, 3, 1, torch.from_numpy(S.reshape(-1, order="F").copy()).cuda(),
+                       torch.from_numpy(M.reshape(-1, order="F").copy()).cuda(), G)
+    want = np.ones((3, r))
+    want[:, k] = 0.5
+    assert rel(G.cpu().numpy().reshape(r, 3, order="F").T, want) < 1e-14
+
+
 def test_solve_chol_reports_not_spd(ctx):
     r = 6
     S = -np.eye(r)
