@@ -374,104 +374,173 @@ __global__ void chol_panel_factor_kernel(double* __restrict__ A, int r, int p0, 
   }
 }
 
-// Two triangular solves per right-hand side (one warp per row i of M; L staged in shared memory when it
-// fits): L y = M[i,:]^T, then L^T z = y, then G[a + Rn (i + In b)] = z[a + Rn b] (classical mode-2
-// folding).  Both sweeps are blocked in kPanel-wide panels: a panel first takes the contribution of the
-// finished entries (one row of L per lane, independent partial sums), then a kPanel-step substitution
-// with shuffles.  Divisions are replaced by the stored reciprocal diagonal.
-template <bool kLInSmem>
-__global__ void chol_solve_kernel(const double* __restrict__ Lmat, const double* __restrict__ M, int Rn, int64_t In,
-                                  int Rn1, double* __restrict__ G, DevStatus* st) {
-  extern __shared__ double sh[];
-  const int r = Rn * Rn1;
-  double* y = sh;                                      // r
-  double* inv = y + r;                                 // r
-  double* Ls = inv + r;                                // r x r, column-major (when staged)
-  const double* L = kLInSmem ? Ls : Lmat;
-  const int64_t i = blockIdx.x;
-  if (kLInSmem)
-    for (int e = threadIdx.x; e < r * r; e += blockDim.x) Ls[e] = Lmat[e];
-  for (int j = threadIdx.x; j < r; j += blockDim.x) {
-    y[j] = M[i + In * (int64_t)j];
-    inv[j] = Lmat[r * r + j];
+// ------------------------------------------------------------------ K4: diagonal-block inverses
+// W_q = D_q^{-1} for the 32 x 32 diagonal blocks D_q of L, so the triangular solves below need no serial
+// substitution.  One CTA per block, by recursive doubling on the 2 x 2 block form of a lower-triangular
+// inverse, [A 0; B C]^{-1} = [A^{-1} 0; -C^{-1} B A^{-1}  C^{-1}] (Higham, Accuracy and Stability of
+// Numerical Algorithms, Sec. 14.2): level l merges pairs of 2^l x 2^l inverses, starting from the
+// reciprocal diagonal.  The upper triangles of D and of every partial inverse are exact zeros, so the
+// inner products run over whole blocks with no index tests.
+template <int l>
+__device__ __forceinline__ void block_inverse_level(double (*D)[kSolveBlock + 1], double (*W)[kSolveBlock + 1],
+                                                    double (*T)[kSolveBlock + 1], int t) {
+  constexpr int s = 1 << l;
+  const bool act = t < (kSolveBlock / 2) * s;   // (32 / 2s) merges of s x s outputs
+  const int j = t & (s - 1), i = (t >> l) & (s - 1), b = (t >> (2 * l)) * 2 * s;
+  if (act) {   // T = B A^{-1}
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < s; ++q) acc = fma(D[b + s + i][b + q], W[b + q][b + j], acc);
+    T[b + s + i][b + j] = acc;
   }
   __syncthreads();
-  // The dot products against the solved part run on all warps (FP64 throughput is per SMSP); warp 0
-  // then resolves the 32 x 32 diagonal block with shuffles.
-  double (*part)[kPanel] = reinterpret_cast<double (*)[kPanel]>(kLInSmem ? Ls + r * r : Ls);   // [8][kPanel]
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = min(8, (int)(blockDim.x >> 5));
-  // forward: for each panel, y_p -= L[p, 0:p0] y[0:p0], then solve L_pp y_p = rhs
-  for (int p0 = 0; p0 < r; p0 += kPanel) {
-    const int nb = min(kPanel, r - p0);
-    if (warp < nw) {
-      double a0 = 0.0, a1 = 0.0;
-      if (lane < nb) {
-        const int row = p0 + lane;
-        int k = warp;
-        for (; k + nw < p0; k += 2 * nw) {
-          a0 = fma(L[row + r * k], y[k], a0);
-          a1 = fma(L[row + r * (k + nw)], y[k + nw], a1);
-        }
-        for (; k < p0; k += nw) a0 = fma(L[row + r * k], y[k], a0);
+  if (act) {   // lower-left block of the merged inverse: -C^{-1} T
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < s; ++q) acc = fma(W[b + s + i][b + s + q], T[b + s + q][b + j], acc);
+    W[b + s + i][b + j] = -acc;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) chol_block_inverse_kernel(double* __restrict__ Lmat, int r) {
+  __shared__ double D[kSolveBlock][kSolveBlock + 1], W[kSolveBlock][kSolveBlock + 1], T[kSolveBlock][kSolveBlock + 1];
+  const int q = blockIdx.x, p0 = q * kSolveBlock, nb = min(kSolveBlock, r - p0);
+  const double* inv = Lmat + (size_t)r * r;
+  for (int e = threadIdx.x; e < kSolveBlock * kSolveBlock; e += blockDim.x) {
+    const int i = e % kSolveBlock, j = e / kSolveBlock;
+    double d = 0.0, w = 0.0;
+    if (i < nb && j < nb) {
+      d = (i >= j) ? Lmat[(p0 + i) + (size_t)r * (p0 + j)] : 0.0;
+      if (i == j) w = inv[p0 + i];
+    } else if (i == j) {   // identity past r
+      d = 1.0;
+      w = 1.0;
+    }
+    D[i][j] = d;
+    W[i][j] = w;
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  block_inverse_level<0>(D, W, T, t);
+  block_inverse_level<1>(D, W, T, t);
+  block_inverse_level<2>(D, W, T, t);
+  block_inverse_level<3>(D, W, T, t);
+  block_inverse_level<4>(D, W, T, t);
+  double* Wq = Lmat + (size_t)r * r + r + (size_t)q * kSolveBlock * kSolveBlock;
+  for (int e = threadIdx.x; e < kSolveBlock * kSolveBlock; e += blockDim.x)
+    Wq[e] = W[e % kSolveBlock][e / kSolveBlock];
+}
+
+// ------------------------------------------------------------------ K4: triangular solves
+// Z S = M row by row: for right-hand side i (one CTA), L y = M[i,:]^T then L^T z = y, and
+// G[a + Rn (i + In b)] = z[a + Rn b] (classical mode-2 folding).  Both sweeps go by 32-wide panels; a
+// panel first subtracts the finished unknowns (a matrix-vector product over the solved part) and then
+// multiplies by the diagonal block's inverse W_q (forward) or its transpose (backward): no serial
+// substitution and no division.  Four warps, one per sub-partition, carry the FP64 work (its throughput
+// is per sub-partition); all eight stage L (row stride r | 1, odd, so the transposed reads of the
+// backward sweep fall on distinct banks) and the W_q in shared memory when they fit.
+template <bool kInSmem>
+__global__ void __launch_bounds__(256) chol_solve_kernel(const double* __restrict__ Lmat, const double* __restrict__ M,
+                                                         int Rn, int64_t In, int Rn1, double* __restrict__ G,
+                                                         DevStatus* st) {
+  extern __shared__ double sh[];
+  constexpr int B = kSolveBlock;
+  const int r = Rn * Rn1, nblk = (r + B - 1) / B;
+  const int lda = kInSmem ? (r | 1) : r;
+  double* y = sh;                              // nblk * 32: right-hand side, then the unknowns
+  double* part = y + nblk * B;                 // 4 x 32 partial sums
+  double* Ls = part + 4 * B;                   // lda x r
+  double* Ws = Ls + (size_t)lda * r;           // nblk blocks of 32 x 33
+  const double* L = kInSmem ? Ls : Lmat;
+  const double* Wg = Lmat + (size_t)r * r + r;
+  const int64_t i0 = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (kInSmem) {
+    // element e = i + r k of L to Ls[i + lda k], two per 16-byte load, (i, k) advanced without division
+    const double2* L2 = reinterpret_cast<const double2*>(Lmat);
+    const int n2 = (r * r) >> 1;
+    int i = (2 * tid) % r, k = (2 * tid) / r;
+    const int di = (2 * nt) % r, dk = (2 * nt) / r;
+#pragma unroll 4
+    for (int e2 = tid; e2 < n2; e2 += nt) {
+      const double2 v = L2[e2];
+      Ls[i + lda * k] = v.x;
+      const bool wrap = i + 1 == r;
+      Ls[(wrap ? 0 : i + 1) + lda * (wrap ? k + 1 : k)] = v.y;
+      i += di;
+      k += dk;
+      if (i >= r) {
+        i -= r;
+        ++k;
       }
-      part[warp][lane] = a0 + a1;
+    }
+    if ((r & 1) && tid == 0) Ls[(r - 1) + lda * (r - 1)] = Lmat[(size_t)r * r - 1];
+    for (int e = tid; e < nblk * B * B; e += nt)
+      Ws[(e / (B * B)) * (B * (B + 1)) + (e % B) + (B + 1) * ((e / B) % B)] = Wg[e];
+  }
+  for (int j = tid; j < nblk * B; j += nt) y[j] = j < r ? M[i0 + In * (int64_t)j] : 0.0;
+  __syncthreads();
+  const int lane = tid & 31, warp = tid >> 5;
+  auto w_at = [&](int q, int a, int b) -> double {
+    return kInSmem ? Ws[q * (B * (B + 1)) + a + (B + 1) * b] : Wg[q * (B * B) + a + B * b];
+  };
+  auto sum_parts = [&]() { return (part[lane] + part[B + lane]) + (part[2 * B + lane] + part[3 * B + lane]); };
+  // forward: y_q = W_q (y_q - L[q, :p0] y[:p0])
+  for (int q = 0; q < nblk; ++q) {
+    const int p0 = q * B;
+    if (p0 > 0) {
+      if (warp < 4) {
+        double acc = 0.0;
+        const int i = p0 + lane;
+        if (i < r)
+          for (int k = warp; k < p0; k += 4) acc = fma(L[i + lda * k], y[k], acc);
+        part[warp * B + lane] = acc;
+      }
+      __syncthreads();
+      if (warp == 0) y[p0 + lane] -= sum_parts();
+      __syncthreads();
+    }
+    if (warp < 4) {
+      double acc = 0.0;
+#pragma unroll
+      for (int t = 8 * warp; t < 8 * warp + 8; ++t) acc = fma(w_at(q, lane, t), y[p0 + t], acc);
+      part[warp * B + lane] = acc;
     }
     __syncthreads();
-    if (warp == 0) {
-      double x = 0.0;
-      if (lane < nb) {
-        double acc = 0.0;
-        for (int w = 0; w < nw; ++w) acc += part[w][lane];
-        x = y[p0 + lane] - acc;
-      }
-      for (int j = 0; j < nb; ++j) {
-        const double xj = __shfl_sync(0xffffffffu, x, j) * inv[p0 + j];
-        if (lane == j) x = xj;
-        if (lane > j && lane < nb) x = fma(-L[(p0 + lane) + r * (p0 + j)], xj, x);
-      }
-      if (lane < nb) y[p0 + lane] = x;
-    }
+    if (warp == 0) y[p0 + lane] = sum_parts();
     __syncthreads();
   }
-  // backward: for each panel from the last, y_p -= L[p1:r, p]^T z[p1:r], then solve L_pp^T z_p = rhs
-  for (int p0 = ((r - 1) / kPanel) * kPanel; p0 >= 0; p0 -= kPanel) {
-    const int nb = min(kPanel, r - p0), p1 = p0 + nb;
-    if (warp < nw) {
-      double a0 = 0.0, a1 = 0.0;
-      if (lane < nb) {
-        const int col = p0 + lane;
-        int k = p1 + warp;
-        for (; k + nw < r; k += 2 * nw) {
-          a0 = fma(L[k + r * col], y[k], a0);
-          a1 = fma(L[(k + nw) + r * col], y[k + nw], a1);
-        }
-        for (; k < r; k += nw) a0 = fma(L[k + r * col], y[k], a0);
+  // backward: z_q = W_q^T (y_q - L[p1:, q]^T z[p1:])
+  for (int q = nblk - 1; q >= 0; --q) {
+    const int p0 = q * B, p1 = min(r, p0 + B);
+    if (p1 < r) {
+      if (warp < 4) {
+        double acc = 0.0;
+        const int i = p0 + lane;
+        if (i < r)
+          for (int k = p1 + warp; k < r; k += 4) acc = fma(L[k + lda * i], y[k], acc);
+        part[warp * B + lane] = acc;
       }
-      part[warp][lane] = a0 + a1;
+      __syncthreads();
+      if (warp == 0) y[p0 + lane] -= sum_parts();
+      __syncthreads();
+    }
+    if (warp < 4) {
+      double acc = 0.0;
+#pragma unroll
+      for (int t = 8 * warp; t < 8 * warp + 8; ++t) acc = fma(w_at(q, t, lane), y[p0 + t], acc);
+      part[warp * B + lane] = acc;
     }
     __syncthreads();
-    if (warp == 0) {
-      double x = 0.0;
-      if (lane < nb) {
-        double acc = 0.0;
-        for (int w = 0; w < nw; ++w) acc += part[w][lane];
-        x = y[p0 + lane] - acc;
-      }
-      for (int j = nb - 1; j >= 0; --j) {
-        const double xj = __shfl_sync(0xffffffffu, x, j) * inv[p0 + j];
-        if (lane == j) x = xj;
-        if (lane < j) x = fma(-L[(p0 + j) + r * (p0 + lane)], xj, x);
-      }
-      if (lane < nb) y[p0 + lane] = x;
-    }
+    if (warp == 0) y[p0 + lane] = sum_parts();
     __syncthreads();
   }
-  if (warp != 0) return;
-  for (int c = lane; c < r; c += 32) {
+  for (int c = tid; c < r; c += nt) {
     const double z = y[c];
-    if (!isfinite(z)) set_status(st, TRALS_E_NONFINITE, -1, -1, (int)i, z);
+    if (!isfinite(z)) set_status(st, TRALS_E_NONFINITE, -1, -1, (int)i0, z);
     const int a = c % Rn, b = c / Rn;
-    G[a + (int64_t)Rn * (i + In * b)] = z;
+    G[a + (int64_t)Rn * (i0 + In * b)] = z;
   }
 }
 
@@ -685,7 +754,8 @@ int launch_cholesky(const double* S, double* Lmat, int r, DevStatus* st, const i
     // one CTA, matrix in shared memory: all 32 warps share the SM's FP64 pipes with one sync pair per column
     const size_t smem = (size_t)r * r * sizeof(double);
     cholesky_kernel<<<1, kCholThreads, smem, s>>>(S, Lmat, r, st, sweep_ctr, mode);
-    return 1;
+    launch_chol_block_inverse(Lmat, r, s);
+    return 2;
   }
   int launches = 1;
   copy_lower_kernel<<<grid_for((int64_t)r * r, 256), 256, 0, s>>>(S, Lmat, r);
@@ -700,23 +770,33 @@ int launch_cholesky(const double* S, double* Lmat, int r, DevStatus* st, const i
     chol_panel_factor_kernel<<<blocks, 128, 0, s>>>(Lmat, r, p0, st, sweep_ctr, mode);
     ++launches;
   }
-  return launches;
+  launch_chol_block_inverse(Lmat, r, s);
+  return launches + 1;
 }
 
 void launch_pivot_rsqrt_check(const double* d, int64_t n, double* out, double* ref, cudaStream_t s) {
   pivot_rsqrt_check_kernel<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(d, n, out, ref);
 }
 
+size_t chol_solve_smem(int r, bool in_smem) {
+  const int nblk = (r + kSolveBlock - 1) / kSolveBlock;
+  size_t n = (size_t)nblk * kSolveBlock + 4 * kSolveBlock;
+  if (in_smem) n += (size_t)(r | 1) * r + (size_t)nblk * kSolveBlock * (kSolveBlock + 1);
+  return n * sizeof(double);
+}
+
 void launch_chol_solve(const double* Lmat, const double* M, int Rn, int64_t In, int Rn1, double* G, DevStatus* st,
                        cudaStream_t s) {
   const int r = Rn * Rn1;
-  const size_t part = 8 * kPanel * sizeof(double);   // per-warp partial dot products
-  const size_t smem = ((size_t)r * r + 2 * (size_t)r) * sizeof(double) + part;
+  const size_t smem = chol_solve_smem(r, true);
   if (smem <= 227 * 1024)
     chol_solve_kernel<true><<<(unsigned)In, 256, smem, s>>>(Lmat, M, Rn, In, Rn1, G, st);
   else
-    chol_solve_kernel<false><<<(unsigned)In, 256, 2 * (size_t)r * sizeof(double) + part, s>>>(Lmat, M, Rn, In, Rn1,
-                                                                                             G, st);
+    chol_solve_kernel<false><<<(unsigned)In, 256, chol_solve_smem(r, false), s>>>(Lmat, M, Rn, In, Rn1, G, st);
+}
+
+void launch_chol_block_inverse(double* Lmat, int r, cudaStream_t s) {
+  chol_block_inverse_kernel<<<(r + kSolveBlock - 1) / kSolveBlock, 256, 0, s>>>(Lmat, r);
 }
 
 void launch_residual_identity(const double* normX2, const double* M, const double* coreN, const double* S,

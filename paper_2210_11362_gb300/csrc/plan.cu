@@ -616,7 +616,7 @@ trals_status plan_build(trals_ctx* ctx, int N, const int64_t* I, const int32_t* 
     }
   }
   PLAN_TRY(p->alloc(&p->S, (size_t)maxr * maxr));
-  PLAN_TRY(p->alloc(&p->Lmat, (size_t)maxr * maxr + maxr));   // L and its reciprocal diagonal
+  PLAN_TRY(p->alloc(&p->Lmat, lmat_elems(maxr)));   // L, its reciprocal diagonal, diagonal-block inverses
   PLAN_TRY(p->alloc(&p->chainA, (size_t)maxR2 * maxR2));
   PLAN_TRY(p->alloc(&p->chainB, (size_t)maxR2 * maxR2));
   if (N >= 4 && o.solver == TRALS_SOLVE_CHOL && o.gram == TRALS_GRAM_STRUCTURED) {
@@ -1190,7 +1190,7 @@ trals_status trals_solve_chol(trals_ctx* ctx, int Rn, int64_t In, int Rn1, const
   if (!ctx || !S_dev || !M_dev || !G_dev || Rn < 1 || Rn1 < 1 || In < 1 || Rn * Rn1 > 256) return TRALS_E_ARG;
   const int r = Rn * Rn1;
   double* Lm = nullptr;
-  TRALS_CUDA_TRY(ctx, cudaMalloc(&Lm, ((size_t)r * r + r) * sizeof(double)));
+  TRALS_CUDA_TRY(ctx, cudaMalloc(&Lm, lmat_elems(r) * sizeof(double)));
   launch_cholesky(S_dev, Lm, r, ctx->d_status, nullptr, -1, ctx->stream);
   launch_chol_solve(Lm, M_dev, Rn, In, Rn1, G_dev, ctx->d_status, ctx->stream);
   cudaError_t e = cudaGetLastError();

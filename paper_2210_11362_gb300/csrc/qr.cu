@@ -256,7 +256,8 @@ int launch_qr_factor(int N, const int64_t* I, const int32_t* R, int n, const dou
   }
   const int r = Cs[N - 2];
   qr_to_l_kernel<<<grid_of((int64_t)r * r), 256, 0, s>>>(P, r, Lmat, st, sweep_ctr, n);
-  return launches + 1;
+  launch_chol_block_inverse(Lmat, r, s);
+  return launches + 2;
 }
 
 void launch_transpose(const double* A, int r, double* B, cudaStream_t s) {

@@ -119,11 +119,20 @@ void launch_residual_f32(const ModeLayout& L, const double* ltab, const double* 
                          int64_t utab_elems, const int64_t* offL, const int64_t* offU, const double* coreN,
                          const void* X, int xt, double* partials, int gridX, cudaStream_t s, float* Eout = nullptr);
 
-// Cholesky (K4): factor S (r x r, lower triangle) into L (r x r, then r reciprocal diagonal entries, so
-// Lmat holds r*r + r doubles); status on failure.
+// Layout of a factor buffer `Lmat` (FP64): L (r x r, column-major, lower triangle; zeros above), then
+// the r reciprocal diagonal entries 1/L_jj, then the inverses of the 32 x 32 diagonal blocks of L
+// (block q covers rows and columns [32q, 32q + 32), identity-padded past r; each column-major, 1024
+// doubles).  Every producer of a factor (Cholesky, the QR path) fills all three parts.
+constexpr int kSolveBlock = 32;
+inline size_t lmat_elems(int r) {
+  return (size_t)r * r + r + (size_t)((r + kSolveBlock - 1) / kSolveBlock) * kSolveBlock * kSolveBlock;
+}
+// Cholesky (K4): factor S (r x r, lower triangle) into Lmat; status on failure.
 // Returns the number of kernel launches.
 int launch_cholesky(const double* S, double* Lmat, int r, DevStatus* st, const int* sweep_ctr, int mode,
                     cudaStream_t s);
+// Inverses of the diagonal blocks of L into the third part of Lmat (from L and its reciprocal diagonal).
+void launch_chol_block_inverse(double* Lmat, int r, cudaStream_t s);
 // Triangular solves with In right-hand sides; writes core layout.
 // out[i] = the Cholesky kernel's pivot reciprocal square root of d[i], ref[i] = CUDA's rsqrt(d[i])
 void launch_pivot_rsqrt_check(const double* d, int64_t n, double* out, double* ref, cudaStream_t s);
