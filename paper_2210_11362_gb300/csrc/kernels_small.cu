@@ -58,33 +58,66 @@ __global__ void gamma_kernel(const double* __restrict__ G, int Rn, int64_t In, i
   }
 }
 
-// ------------------------------------------------------------------ FP64 GEMM (Gamma chain, K2)
-constexpr int GT = 16;
-__global__ void gemm_f64_kernel(int m, int n, int k, const double* __restrict__ A, const double* __restrict__ B,
-                                double* __restrict__ C) {
-  __shared__ double As[GT][GT + 1];
-  __shared__ double Bs[GT][GT + 1];
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int row = blockIdx.x * GT + tx;
-  const int col = blockIdx.y * GT + ty;
-  double acc = 0.0;
-  for (int k0 = 0; k0 < k; k0 += GT) {
-    // As[tx][ty] = A[row, k0+ty]; Bs[tx][ty] = B[k0+tx, col]
-    As[tx][ty] = (row < m && k0 + ty < k) ? A[row + (int64_t)m * (k0 + ty)] : 0.0;
-    Bs[tx][ty] = (k0 + tx < k && col < n) ? B[(k0 + tx) + (int64_t)k * col] : 0.0;
-    __syncthreads();
-    double a1 = 0.0, a2 = 0.0, a3 = 0.0;   // independent chains for the FP64 latency
-#pragma unroll
-    for (int kk = 0; kk < GT; kk += 4) {
-      acc = fma(As[tx][kk], Bs[kk][ty], acc);
-      a1 = fma(As[tx][kk + 1], Bs[kk + 1][ty], a1);
-      a2 = fma(As[tx][kk + 2], Bs[kk + 2][ty], a2);
-      a3 = fma(As[tx][kk + 3], Bs[kk + 3][ty], a3);
+// The same Gram entries with the core staged in shared memory (cores up to kGammaSmemMax doubles):
+// every block reads the core once, coalesced, instead of every thread gathering strided columns.
+constexpr int kGammaSmemMax = 12288;
+__global__ void gamma_smem_kernel(const double* __restrict__ G, int Rn, int In, int Rn1, double* __restrict__ Gamma) {
+  extern __shared__ double Gs[];
+  const int core = Rn * In * Rn1;
+  for (int e = threadIdx.x; e < core; e += blockDim.x) Gs[e] = G[e];
+  __syncthreads();
+  const int r = Rn * Rn1, rows = Rn * Rn;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * r; e += gridDim.x * blockDim.x) {
+    const int u = e % r, v = e / r;
+    if (u > v) continue;
+    const int p = u % Rn, s = u / Rn;
+    const int q = v % Rn, t = v / Rn;
+    const double* gu = Gs + p + Rn * In * s;
+    const double* gv = Gs + q + Rn * In * t;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int i = 0;
+    for (; i + 3 < In; i += 4) {
+      a0 = fma(gu[Rn * i], gv[Rn * i], a0);
+      a1 = fma(gu[Rn * (i + 1)], gv[Rn * (i + 1)], a1);
+      a2 = fma(gu[Rn * (i + 2)], gv[Rn * (i + 2)], a2);
+      a3 = fma(gu[Rn * (i + 3)], gv[Rn * (i + 3)], a3);
     }
-    acc += (a1 + a2) + a3;
-    __syncthreads();
+    for (; i < In; ++i) a0 = fma(gu[Rn * i], gv[Rn * i], a0);
+    const double acc = (a0 + a1) + (a2 + a3);
+    Gamma[(p * Rn + q) + rows * (s * Rn1 + t)] = acc;
+    Gamma[(q * Rn + p) + rows * (t * Rn1 + s)] = acc;
   }
-  if (row < m && col < n) C[row + (int64_t)m * col] = acc;
+}
+
+// ------------------------------------------------------------------ FP64 GEMM (Gamma chain, K2)
+// C = A B for the small Gamma-chain products (all dimensions <= 256).  The FP64 unit is shared by the
+// whole SM (about one warp instruction per 19 cycles) and one warp issues at most one FP64 instruction
+// per 64 cycles, so the work is spread over many blocks and short per-thread sums: a block owns an
+// 8 x 8 output tile and its four 64-thread groups take interleaved quarters of k, combined in a fixed
+// order.
+constexpr int GT = 8;
+constexpr int GK = 4;
+__global__ void __launch_bounds__(GT * GT * GK) gemm_f64_kernel(int m, int n, int k, const double* __restrict__ A,
+                                                              const double* __restrict__ B, double* __restrict__ C) {
+  __shared__ double part[GK][GT * GT];
+  const int t = threadIdx.x;
+  const int o = t % (GT * GT), g = t / (GT * GT);
+  const int row = blockIdx.x * GT + (o % GT), col = blockIdx.y * GT + (o / GT);
+  double a0 = 0.0, a1 = 0.0;
+  if (row < m && col < n) {
+    const double* Ar = A + row;
+    const double* Bc = B + (int64_t)k * col;
+    int kk = g;
+#pragma unroll 2
+    for (; kk + GK < k; kk += 2 * GK) {
+      a0 = fma(Ar[(int64_t)m * kk], Bc[kk], a0);
+      a1 = fma(Ar[(int64_t)m * (kk + GK)], Bc[kk + GK], a1);
+    }
+    if (kk < k) a0 = fma(Ar[(int64_t)m * kk], Bc[kk], a0);
+  }
+  part[g][o] = a0 + a1;
+  __syncthreads();
+  if (g == 0 && row < m && col < n) C[row + (int64_t)m * col] = (part[0][o] + part[1][o]) + (part[2][o] + part[3][o]);
 }
 
 // S[(a + Rn b) + r (a' + Rn b')] = Pi[(b Rn1 + b') + Rn1^2 (a Rn + a')]   (Prop. subchain_gram regrouping)
@@ -680,12 +713,16 @@ inline int grid_for(int64_t total, int block, int cap = 152 * 16) {
 // ------------------------------------------------------------------ launchers
 void launch_gamma(const double* G, int Rn, int64_t In, int Rn1, double* Gamma, cudaStream_t s) {
   const int64_t total = (int64_t)Rn * Rn1 * Rn * Rn1;
-  gamma_kernel<<<grid_for(total, 256), 256, 0, s>>>(G, Rn, In, Rn1, Gamma);
+  const int64_t core = (int64_t)Rn * In * Rn1;
+  if (core <= kGammaSmemMax)
+    gamma_smem_kernel<<<grid_for(total, 128), 128, (size_t)core * sizeof(double), s>>>(G, Rn, (int)In, Rn1, Gamma);
+  else
+    gamma_kernel<<<grid_for(total, 256), 256, 0, s>>>(G, Rn, In, Rn1, Gamma);
 }
 
 void launch_gemm_f64(int m, int n, int k, const double* A, const double* B, double* C, cudaStream_t s) {
   dim3 grid((m + GT - 1) / GT, (n + GT - 1) / GT);
-  gemm_f64_kernel<<<grid, dim3(GT, GT), 0, s>>>(m, n, k, A, B, C);
+  gemm_f64_kernel<<<grid, GT * GT * GK, 0, s>>>(m, n, k, A, B, C);
 }
 
 void launch_regroup_S(const double* Pi, int Rn, int Rn1, double* S, cudaStream_t s) {
@@ -850,6 +887,9 @@ cudaError_t init_small_attributes() {
   // solve: L (r x r) plus two vectors, r <= 160 (the QR path's solves use larger r from global memory)
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(chol_solve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gamma_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kGammaSmemMax * (int)sizeof(double));
   return e;
 }
 

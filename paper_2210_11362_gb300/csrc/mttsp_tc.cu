@@ -573,8 +573,20 @@ __global__ void tc_reduce_kernel(const float* __restrict__ partials, int G, int6
   const int64_t Eout = E / In * In_out;
   const int64_t src = (e % In_out) + (int64_t)In * (e / In_out);
   double s = 0.0;
-  if (e < Eout)
-    for (int g = w; g < G; g += 8) s += (double)partials[(int64_t)g * E + src];
+  if (e < Eout) {
+    // four loads in flight per thread; the sums stay in ascending g
+    const float* P = partials + src;
+    int g = w;
+    for (; g + 24 < G; g += 32) {
+      const float v0 = P[(int64_t)g * E], v1 = P[(int64_t)(g + 8) * E], v2 = P[(int64_t)(g + 16) * E],
+                  v3 = P[(int64_t)(g + 24) * E];
+      s += (double)v0;
+      s += (double)v1;
+      s += (double)v2;
+      s += (double)v3;
+    }
+    for (; g < G; g += 8) s += (double)P[(int64_t)g * E];
+  }
   red[w][lane] = s;
   __syncthreads();
   if (w == 0 && e < Eout) {
@@ -590,16 +602,17 @@ __global__ void tc_reduce_kernel(const float* __restrict__ partials, int G, int6
 // Stage-1 table: Tab[w * Kpad + k] = bf16(P_k(...)) with w = z + SYP y (z: inner/dot index, y: outer):
 // kindL (factor on the left): P = c x a (Ra = Sy rows), element (z, y); otherwise P = b x d (Ra = NY rows),
 // element (y, z).  Zero for z >= Sy, y >= NY or k >= K.
+// grid: x over k (Kpad), y over the packed column w (W_pad); no per-element division
 __global__ void pack_tab_kernel(const float* __restrict__ src, int64_t K, int64_t Kpad, int Ra, int Rb, int kindL,
                                 int Sy, int SYP, int NY, int W_pad, __nv_bfloat16* __restrict__ dst,
                                 __nv_bfloat16* __restrict__ dst_lo) {
-  const int64_t total = (int64_t)W_pad * Kpad;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t k = e % Kpad;
-    const int w = (int)(e / Kpad);
-    const int z = w % SYP, y = w / SYP;
-    float v = 0.0f;
-    if (k < K && z < Sy && y < NY) v = src[(int64_t)(kindL ? (z + Ra * y) : (y + Ra * z)) * K + k];
+  const int w = blockIdx.y;
+  const int z = w % SYP, y = w / SYP;
+  const bool live = z < Sy && y < NY;
+  const float* col = src + (int64_t)(kindL ? (z + Ra * y) : (y + Ra * z)) * K;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Kpad; k += (int64_t)gridDim.x * blockDim.x) {
+    const float v = (live && k < K) ? col[k] : 0.0f;
+    const int64_t e = (int64_t)w * Kpad + k;
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     dst[e] = h;
     if (dst_lo != nullptr) dst_lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));   // split-BF16 remainder
@@ -607,31 +620,29 @@ __global__ void pack_tab_kernel(const float* __restrict__ src, int64_t K, int64_
 }
 
 // Stage-2 factors: F[(f * NX + x) * SYP + z] = kindL ? P_f(x, z) (L[b=x][c=z]) : P_f(z, x) (Rm[d=z][a=x]).
+// grid: x over f, y over (x, z); no per-element division
 __global__ void pack_fac_kernel(const float* __restrict__ src, int64_t nf, int Ra, int Rb, int kindL, int NX, int Sy,
                                 int SYP, float* __restrict__ dst) {
-  const int64_t total = nf * NX * SYP;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int z = (int)(e % SYP);
-    const int x = (int)((e / SYP) % NX);
-    const int64_t f = e / ((int64_t)SYP * NX);
-    float v = 0.0f;
-    if (z < Sy) v = src[(int64_t)(kindL ? (x + Ra * z) : (z + Ra * x)) * nf + f];
-    dst[e] = v;
-  }
+  const int xz = blockIdx.y;
+  const int z = xz % SYP, x = xz / SYP;
+  const float* col = src + (int64_t)(kindL ? (x + Ra * z) : (z + Ra * x)) * nf;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x)
+    dst[(f * NX + x) * SYP + z] = (z < Sy) ? col[f] : 0.0f;
 }
 
 // FP32 subchain table level (reduced precision is enough here: the table is rounded to BF16 for the
 // tensor cores, and the factors feed an FP32 stage):
 // out(l + nPrev i)[x + Ra y] = sum_c prev(l)[x + Ra c] G[c + Rc (i + Ii y)]   (prev == nullptr: core slices)
+// grid: x over the output rows ent = l + nPrev i, y over the output column x + Ra y
 __global__ void chain_level_f32_kernel(const float* __restrict__ prev, int64_t nPrev, int Ra, int Rc,
                                        const float* __restrict__ G, int64_t Ii, int Rb, float* __restrict__ out) {
   const int64_t nOut = nPrev * Ii;
-  const int64_t total = nOut * Ra * Rb;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t ent = e % nOut;
-    const int xy = (int)(e / nOut);
-    const int x = xy % Ra, y = xy / Ra;
-    const int64_t l = ent % nPrev, i = ent / nPrev;
+  const int xy = blockIdx.y;
+  const int x = xy % Ra, y = xy / Ra;
+  float* o = out + (int64_t)xy * nOut;
+  for (int64_t ent = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ent < nOut;
+       ent += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = (int64_t)((uint32_t)ent / (uint32_t)nPrev), l = ent - i * nPrev;   // tables < 2^31 entries
     float acc;
     if (prev == nullptr) {
       acc = G[x + (int64_t)Rc * (i + Ii * y)];
@@ -640,7 +651,7 @@ __global__ void chain_level_f32_kernel(const float* __restrict__ prev, int64_t n
       for (int c = 0; c < Rc; ++c)
         acc = fmaf(prev[(int64_t)(x + Ra * c) * nPrev + l], G[c + (int64_t)Rc * (i + Ii * y)], acc);
     }
-    out[e] = acc;
+    o[ent] = acc;
   }
 }
 
@@ -763,8 +774,8 @@ const float* build_chain(const std::vector<int>& modes, const float* const* core
   int t = 0;
   for (int m : modes) {
     float* out = bufs[t++ % 2];
-    const int64_t total = nPrev * I[m] * Ra * R[(m + 1) % N];
-    const int g = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    const int64_t nOut = nPrev * I[m];
+    const dim3 g((unsigned)std::min<int64_t>((nOut + 255) / 256, 1024), (unsigned)(Ra * R[(m + 1) % N]));
     chain_level_f32_kernel<<<g, 256, 0, s>>>(prev, nPrev, Ra, R[m], cores[m], I[m], R[(m + 1) % N], out);
     ++*launches;
     prev = out;
@@ -1084,16 +1095,14 @@ int tc_enqueue(TcPlan& p, const void* X, double* const* cores, double* M, cudaSt
   }
   const float* tsrc = build_chain(impl->s_modes, c32, I, R, N, impl->chainA, impl->chainB, s, &launches);
   {
-    const int64_t total = (int64_t)A.W_pad * impl->Kpad;
-    const int g = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    const dim3 g((unsigned)std::min<int64_t>((impl->Kpad + 255) / 256, 1024), (unsigned)A.W_pad);
     pack_tab_kernel<<<g, 256, 0, s>>>(tsrc, impl->K_S, impl->Kpad, impl->tabRa, impl->tabRb, impl->kindL, A.Sy,
                                       impl->SYP, A.NY, A.W_pad, impl->tab, impl->tab_lo);
     ++launches;
   }
   const float* fsrc = build_chain(impl->f_modes, c32, I, R, N, impl->chainA, impl->chainB, s, &launches);
   {
-    const int64_t total = impl->n_fac_total * A.NX * impl->SYP;
-    const int g = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    const dim3 g((unsigned)std::min<int64_t>((impl->n_fac_total + 255) / 256, 1024), (unsigned)(A.NX * impl->SYP));
     pack_fac_kernel<<<g, 256, 0, s>>>(fsrc, impl->n_fac_total, impl->facRa, impl->facRb, impl->kindL, A.NX, A.Sy,
                                       impl->SYP, impl->F);
     ++launches;

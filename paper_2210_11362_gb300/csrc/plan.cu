@@ -167,7 +167,8 @@ struct trals_plan {
   cudaEvent_t ev_fork[TRALS_MAX_ORDER] = {}, ev_join[TRALS_MAX_ORDER] = {};
   // Gamma-chain prefixes for the next mode, formed on `side2` while the current mode is updated
   cudaStream_t side2 = nullptr;
-  cudaEvent_t ev_pre[TRALS_MAX_ORDER] = {}, ev_pfork[TRALS_MAX_ORDER] = {};
+  cudaEvent_t ev_pre[TRALS_MAX_ORDER] = {};
+  cudaEvent_t ev_gam[TRALS_MAX_ORDER] = {};   // Gamma_{n-1} formed on the side stream during mode n
   double *pre[2] = {}, *preA = nullptr, *preB = nullptr;
   double *ltab2 = nullptr, *utab2 = nullptr, *tscratch2 = nullptr;   // explicit Gram on the side branch
   int launches = 0;
@@ -374,6 +375,13 @@ int enqueue_sweep(trals_plan* p) {
     cudaStream_t b = p->side;
     cudaEventRecord(p->ev_fork[n], s);
     cudaStreamWaitEvent(b, p->ev_fork[n], 0);
+    // Gamma of the core the previous mode updated, on the side stream: only the coefficient branches
+    // read it, so the MTTSP of this mode does not wait for it
+    if (n >= 1) {
+      launch_gamma(p->cores[n - 1], p->R[n - 1], p->I[n - 1], Rn, p->gam[n - 1], b);
+      ++launches;
+    }
+    cudaEventRecord(p->ev_gam[n], b);
     if (qr) {
       // R factor of G^{!=n}_[2] by structured QR; L = R^T replaces the Cholesky factor of S_n
       launches += launch_qr_factor(N, p->I, p->R, n, p->cores, p->qrB, p->qrR0, p->qrR1, p->qrW, p->Lmat,
@@ -396,8 +404,7 @@ int enqueue_sweep(trals_plan* p) {
     if (p->pre[0] && n + 1 < N) {
       // prefix of the next mode: Gamma_{n+2} ... Gamma_{n-1}, none of which this update changes
       cudaStream_t c = p->side2;
-      cudaEventRecord(p->ev_pfork[n], s);
-      cudaStreamWaitEvent(c, p->ev_pfork[n], 0);
+      cudaStreamWaitEvent(c, p->ev_gam[n], 0);   // reads Gamma_{n-1}
       launches += enqueue_prefix(N, p->R, p->gam, n + 1, p->preA, p->preB, p->pre[(n + 1) % 2], c);
       cudaEventRecord(p->ev_pre[n + 1], c);
     }
@@ -408,9 +415,10 @@ int enqueue_sweep(trals_plan* p) {
     ++launches;
     if (qr)
       for (int step = 0; step < kQrRefineSteps; ++step) launches += enqueue_qr_refinement(p, n, s);
-    launch_gamma(p->cores[n], Rn, p->I[n], Rn1, p->gam[n], s);
-    ++launches;
   }
+  // Gamma of the last core on the main stream: the residual identity and the next sweep read it
+  launch_gamma(p->cores[N - 1], p->R[N - 1], p->I[N - 1], p->R[0], p->gam[N - 1], s);
+  ++launches;
   if (qr) {
     // the residual identity needs S_N = L L^T
     launch_llt(p->Lmat, p->R[N - 1] * p->R[0], p->S, s);
@@ -491,7 +499,7 @@ void trals_plan_destroy(trals_plan* p) {
       if (p->ev_fork[n]) cudaEventDestroy(p->ev_fork[n]);
       if (p->ev_join[n]) cudaEventDestroy(p->ev_join[n]);
       if (p->ev_pre[n]) cudaEventDestroy(p->ev_pre[n]);
-      if (p->ev_pfork[n]) cudaEventDestroy(p->ev_pfork[n]);
+      if (p->ev_gam[n]) cudaEventDestroy(p->ev_gam[n]);
     }
     if (p->side) {
       cudaStreamSynchronize(p->side);
@@ -729,7 +737,7 @@ trals_status plan_build(trals_ctx* ctx, int N, const int64_t* I, const int32_t* 
     PLAN_TRY(cudaEventCreateWithFlags(&p->ev_fork[n], cudaEventDisableTiming));
     PLAN_TRY(cudaEventCreateWithFlags(&p->ev_join[n], cudaEventDisableTiming));
     PLAN_TRY(cudaEventCreateWithFlags(&p->ev_pre[n], cudaEventDisableTiming));
-    PLAN_TRY(cudaEventCreateWithFlags(&p->ev_pfork[n], cudaEventDisableTiming));
+    PLAN_TRY(cudaEventCreateWithFlags(&p->ev_gam[n], cudaEventDisableTiming));
   }
   if (sync) PLAN_TRY(cudaStreamSynchronize(s));
   else PLAN_TRY(cudaGetLastError());
