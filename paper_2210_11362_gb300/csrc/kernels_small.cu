@@ -64,7 +64,8 @@ constexpr int kGammaSmemMax = 12288;
 __global__ void gamma_smem_kernel(const double* __restrict__ G, int Rn, int In, int Rn1, double* __restrict__ Gamma) {
   extern __shared__ double Gs[];
   const int core = Rn * In * Rn1;
-  for (int e = threadIdx.x; e < core; e += blockDim.x) Gs[e] = G[e];
+#pragma unroll 8
+  for (int e = threadIdx.x; e < core; e += blockDim.x) Gs[e] = G[e];   // loads batched, not one round trip each
   __syncthreads();
   const int r = Rn * Rn1, rows = Rn * Rn;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * r; e += gridDim.x * blockDim.x) {
@@ -97,8 +98,11 @@ __global__ void gamma_smem_kernel(const double* __restrict__ G, int Rn, int In, 
 // order.
 constexpr int GT = 8;
 constexpr int GK = 4;
+// With regroup_Rn > 0 the product is Pi (R_{n+1}^2 x R_n^2) and the epilogue stores it regrouped as S_n
+// (Prop. subchain_gram): S[(a + Rn b) + r (a' + Rn b')] = Pi[(b Rn1 + b') + Rn1^2 (a Rn + a')].
 __global__ void __launch_bounds__(GT * GT * GK) gemm_f64_kernel(int m, int n, int k, const double* __restrict__ A,
-                                                              const double* __restrict__ B, double* __restrict__ C) {
+                                                              const double* __restrict__ B, double* __restrict__ C,
+                                                              int regroup_Rn, int regroup_Rn1) {
   __shared__ double part[GK][GT * GT];
   const int t = threadIdx.x;
   const int o = t % (GT * GT), g = t / (GT * GT);
@@ -117,7 +121,16 @@ __global__ void __launch_bounds__(GT * GT * GK) gemm_f64_kernel(int m, int n, in
   }
   part[g][o] = a0 + a1;
   __syncthreads();
-  if (g == 0 && row < m && col < n) C[row + (int64_t)m * col] = (part[0][o] + part[1][o]) + (part[2][o] + part[3][o]);
+  if (g == 0 && row < m && col < n) {
+    const double v = (part[0][o] + part[1][o]) + (part[2][o] + part[3][o]);
+    if (regroup_Rn > 0) {
+      const int Rn = regroup_Rn, Rn1 = regroup_Rn1, r = Rn * Rn1;
+      const int b = row / Rn1, b2 = row % Rn1, a = col / Rn, a2 = col % Rn;
+      C[(a + Rn * b) + (int64_t)r * (a2 + Rn * b2)] = v;
+    } else {
+      C[row + (int64_t)m * col] = v;
+    }
+  }
 }
 
 // S[(a + Rn b) + r (a' + Rn b')] = Pi[(b Rn1 + b') + Rn1^2 (a Rn + a')]   (Prop. subchain_gram regrouping)
@@ -229,6 +242,7 @@ __global__ void __launch_bounds__(kCholThreads) cholesky_kernel(const double* __
   __shared__ int bad[2];          // failure flag of the steps of each parity
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll 4
   for (int e = tid; e < r * r; e += kCholThreads) {
     const int i = e % r, j = e / r;
     A[e] = (i >= j) ? S[e] : 0.0;
@@ -476,7 +490,7 @@ __global__ void __launch_bounds__(256) chol_block_inverse_kernel(double* __restr
 template <bool kInSmem>
 __global__ void __launch_bounds__(256) chol_solve_kernel(const double* __restrict__ Lmat, const double* __restrict__ M,
                                                          int Rn, int64_t In, int Rn1, double* __restrict__ G,
-                                                         DevStatus* st) {
+                                                         DevStatus* st, float* __restrict__ G32, int64_t Ist) {
   extern __shared__ double sh[];
   constexpr int B = kSolveBlock;
   const int r = Rn * Rn1, nblk = (r + B - 1) / B;
@@ -574,6 +588,16 @@ __global__ void __launch_bounds__(256) chol_solve_kernel(const double* __restric
     if (!isfinite(z)) set_status(st, TRALS_E_NONFINITE, -1, -1, (int)i0, z);
     const int a = c % Rn, b = c / Rn;
     G[a + (int64_t)Rn * (i0 + In * b)] = z;
+    if (G32 != nullptr) G32[a + (int64_t)Rn * (i0 + Ist * b)] = (float)z;
+  }
+}
+
+__global__ void core_to_f32_kernel(const double* __restrict__ G, int Rn, int64_t In, int64_t Ist, int Rn1,
+                                   float* __restrict__ G32) {
+  const int64_t total = (int64_t)Rn * In * Rn1;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = e % Rn, ib = e / Rn, i = ib % In, b = ib / In;
+    G32[a + Rn * (i + Ist * b)] = (float)G[e];
   }
 }
 
@@ -722,7 +746,13 @@ void launch_gamma(const double* G, int Rn, int64_t In, int Rn1, double* Gamma, c
 
 void launch_gemm_f64(int m, int n, int k, const double* A, const double* B, double* C, cudaStream_t s) {
   dim3 grid((m + GT - 1) / GT, (n + GT - 1) / GT);
-  gemm_f64_kernel<<<grid, GT * GT * GK, 0, s>>>(m, n, k, A, B, C);
+  gemm_f64_kernel<<<grid, GT * GT * GK, 0, s>>>(m, n, k, A, B, C, 0, 0);
+}
+
+void launch_gemm_f64_regroup(int k, const double* A, const double* B, int Rn, int Rn1, double* S, cudaStream_t s) {
+  const int m = Rn1 * Rn1, n = Rn * Rn;
+  dim3 grid((m + GT - 1) / GT, (n + GT - 1) / GT);
+  gemm_f64_kernel<<<grid, GT * GT * GK, 0, s>>>(m, n, k, A, B, S, Rn, Rn1);
 }
 
 void launch_regroup_S(const double* Pi, int Rn, int Rn1, double* S, cudaStream_t s) {
@@ -823,13 +853,18 @@ size_t chol_solve_smem(int r, bool in_smem) {
 }
 
 void launch_chol_solve(const double* Lmat, const double* M, int Rn, int64_t In, int Rn1, double* G, DevStatus* st,
-                       cudaStream_t s) {
+                       cudaStream_t s, float* G32, int64_t Ist) {
   const int r = Rn * Rn1;
   const size_t smem = chol_solve_smem(r, true);
   if (smem <= 227 * 1024)
-    chol_solve_kernel<true><<<(unsigned)In, 256, smem, s>>>(Lmat, M, Rn, In, Rn1, G, st);
+    chol_solve_kernel<true><<<(unsigned)In, 256, smem, s>>>(Lmat, M, Rn, In, Rn1, G, st, G32, Ist);
   else
-    chol_solve_kernel<false><<<(unsigned)In, 256, chol_solve_smem(r, false), s>>>(Lmat, M, Rn, In, Rn1, G, st);
+    chol_solve_kernel<false><<<(unsigned)In, 256, chol_solve_smem(r, false), s>>>(Lmat, M, Rn, In, Rn1, G, st, G32,
+                                                                                 Ist);
+}
+
+void launch_core_to_f32(const double* G, int Rn, int64_t In, int64_t Ist, int Rn1, float* G32, cudaStream_t s) {
+  core_to_f32_kernel<<<grid_for((int64_t)Rn * In * Rn1, 256), 256, 0, s>>>(G, Rn, In, Ist, Rn1, G32);
 }
 
 void launch_chol_block_inverse(double* Lmat, int r, cudaStream_t s) {

@@ -602,7 +602,8 @@ __global__ void tc_reduce_kernel(const float* __restrict__ partials, int G, int6
 // Stage-1 table: Tab[w * Kpad + k] = bf16(P_k(...)) with w = z + SYP y (z: inner/dot index, y: outer):
 // kindL (factor on the left): P = c x a (Ra = Sy rows), element (z, y); otherwise P = b x d (Ra = NY rows),
 // element (y, z).  Zero for z >= Sy, y >= NY or k >= K.
-// grid: x over k (Kpad), y over the packed column w (W_pad); no per-element division
+// grid: x over k (Kpad) in groups of four, y over the packed column w (W_pad); no per-element division.
+// 16-byte loads when the source columns are 16-byte aligned (K a multiple of 4).
 __global__ void pack_tab_kernel(const float* __restrict__ src, int64_t K, int64_t Kpad, int Ra, int Rb, int kindL,
                                 int Sy, int SYP, int NY, int W_pad, __nv_bfloat16* __restrict__ dst,
                                 __nv_bfloat16* __restrict__ dst_lo) {
@@ -610,12 +611,25 @@ __global__ void pack_tab_kernel(const float* __restrict__ src, int64_t K, int64_
   const int z = w % SYP, y = w / SYP;
   const bool live = z < Sy && y < NY;
   const float* col = src + (int64_t)(kindL ? (z + Ra * y) : (y + Ra * z)) * K;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Kpad; k += (int64_t)gridDim.x * blockDim.x) {
-    const float v = (live && k < K) ? col[k] : 0.0f;
-    const int64_t e = (int64_t)w * Kpad + k;
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    dst[e] = h;
-    if (dst_lo != nullptr) dst_lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));   // split-BF16 remainder
+  const bool vec = (K & 3) == 0;
+  for (int64_t k0 = 4 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x); k0 < Kpad;
+       k0 += 4 * (int64_t)gridDim.x * blockDim.x) {
+    float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (live) {
+      if (vec && k0 + 3 < K) {
+        const float4 q = *reinterpret_cast<const float4*>(col + k0);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+      } else {
+        for (int t = 0; t < 4; ++t) v[t] = (k0 + t < K) ? col[k0 + t] : 0.0f;
+      }
+    }
+    const int64_t e = (int64_t)w * Kpad + k0;   // Kpad is a multiple of 8
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(v[t]);
+      dst[e + t] = h;
+      if (dst_lo != nullptr) dst_lo[e + t] = __float2bfloat16_rn(v[t] - __bfloat162float(h));   // split-BF16 remainder
+    }
   }
 }
 
@@ -633,9 +647,9 @@ __global__ void pack_fac_kernel(const float* __restrict__ src, int64_t nf, int R
 // FP32 subchain table level (reduced precision is enough here: the table is rounded to BF16 for the
 // tensor cores, and the factors feed an FP32 stage):
 // out(l + nPrev i)[x + Ra y] = sum_c prev(l)[x + Ra c] G[c + Rc (i + Ii y)]   (prev == nullptr: core slices)
-// grid: x over the output rows ent = l + nPrev i, y over the output column x + Ra y
-__global__ void chain_level_f32_kernel(const float* __restrict__ prev, int64_t nPrev, int Ra, int Rc,
-                                       const float* __restrict__ G, int64_t Ii, int Rb, float* __restrict__ out) {
+// Small levels: grid x over the output rows ent = l + nPrev i, y over the output column x + Ra y.
+__global__ void chain_level_f32_small_kernel(const float* __restrict__ prev, int64_t nPrev, int Ra, int Rc,
+                                             const float* __restrict__ G, int64_t Ii, int Rb, float* __restrict__ out) {
   const int64_t nOut = nPrev * Ii;
   const int xy = blockIdx.y;
   const int x = xy % Ra, y = xy / Ra;
@@ -652,6 +666,81 @@ __global__ void chain_level_f32_kernel(const float* __restrict__ prev, int64_t n
         acc = fmaf(prev[(int64_t)(x + Ra * c) * nPrev + l], G[c + (int64_t)Rc * (i + Ii * y)], acc);
     }
     o[ent] = acc;
+  }
+}
+
+// Large levels: grid x over the output rows, y over x; each thread keeps prev(l)[x + Ra c] (c < Rc) in
+// registers and forms all Rb outputs of its row, so prev is read once per x rather than once per (x, y).
+constexpr int kChainMaxR = 16;
+__global__ void chain_level_f32_kernel(const float* __restrict__ prev, int64_t nPrev, int Ra, int Rc,
+                                       const float* __restrict__ G, int64_t Ii, int Rb, float* __restrict__ out) {
+  const int64_t nOut = nPrev * Ii;
+  const int x = blockIdx.y;
+  for (int64_t ent = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ent < nOut;
+       ent += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = (int64_t)((uint32_t)ent / (uint32_t)nPrev), l = ent - i * nPrev;   // tables < 2^31 entries
+    if (prev == nullptr) {
+      for (int y = 0; y < Rb; ++y) out[(int64_t)(x + Ra * y) * nOut + ent] = G[x + (int64_t)Rc * (i + Ii * y)];
+      continue;
+    }
+    float pv[kChainMaxR];
+#pragma unroll
+    for (int c = 0; c < kChainMaxR; ++c) pv[c] = c < Rc ? prev[(int64_t)(x + Ra * c) * nPrev + l] : 0.0f;
+    const float* Gi = G + (int64_t)Rc * i;
+    for (int y = 0; y < Rb; ++y) {
+      const float* g = Gi + (int64_t)Rc * Ii * y;
+      float acc = 0.0f;
+#pragma unroll
+      for (int c = 0; c < kChainMaxR; ++c)
+        if (c < Rc) acc = fmaf(pv[c], g[c], acc);
+      out[(int64_t)(x + Ra * y) * nOut + ent] = acc;
+    }
+  }
+}
+
+// The last level of a chain fused with its packing (for the core the previous mode updated): the level's
+// sums run in the order of chain_level_f32_kernel, and each result goes straight to the packed stage-1
+// table (kTab: BF16 hi and optional lo planes, row w = z + SYP y, column k = the level's row) or to the
+// packed stage-2 factor (F[(f NX + x) SYP + z], f = the level's row).  Padding entries are never
+// written: the plan zeroes those buffers once.
+template <bool kTab>
+__global__ void chain_last_pack_kernel(const float* __restrict__ prev, int64_t nPrev, int Ra, int Rc,
+                                       const float* __restrict__ G, int64_t Ii, int Rb, int kindL,
+                                       int SYP, int Sy, int NY, int64_t Kpad, int NX, __nv_bfloat16* __restrict__ tab,
+                                       __nv_bfloat16* __restrict__ tab_lo, float* __restrict__ F) {
+  const int64_t nOut = nPrev * Ii;
+  const int x = blockIdx.y;
+  for (int64_t ent = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ent < nOut;
+       ent += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = (int64_t)((uint32_t)ent / (uint32_t)nPrev), l = ent - i * nPrev;
+    float pv[kChainMaxR];
+#pragma unroll
+    for (int c = 0; c < kChainMaxR; ++c)
+      pv[c] = (prev != nullptr && c < Rc) ? prev[(int64_t)(x + Ra * c) * nPrev + l] : 0.0f;
+    for (int y = 0; y < Rb; ++y) {
+      const float* g = G + (int64_t)Rc * (i + Ii * y);
+      float v;
+      if (prev == nullptr) {
+        v = g[x];
+      } else {
+        v = 0.0f;
+#pragma unroll
+        for (int c = 0; c < kChainMaxR; ++c)
+          if (c < Rc) v = fmaf(pv[c], g[c], v);
+      }
+      if (kTab) {
+        const int z = kindL ? x : y, yy = kindL ? y : x;
+        if (z < Sy && yy < NY) {
+          const int64_t e = (int64_t)(z + SYP * yy) * Kpad + ent;
+          const __nv_bfloat16 h = __float2bfloat16_rn(v);
+          tab[e] = h;
+          if (tab_lo != nullptr) tab_lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+        }
+      } else {
+        const int z = kindL ? y : x, xx = kindL ? x : y;
+        if (z < Sy) F[(ent * NX + xx) * SYP + z] = v;
+      }
+    }
   }
 }
 
@@ -745,6 +834,10 @@ struct TcImpl {
   int n = 0;                  // the mode this plan contracts for
   int32_t Rcopy[kMaxOrder];
   int N = 0;
+  // the core the previous mode of a sweep updates is the last link of one chain: everything else is
+  // built by tc_enqueue_pre, that link (fused with its packing) by tc_enqueue_main
+  int late = 0;
+  bool late_in_s = false;
 };
 
 int64_t prod_range(const int64_t* I, int lo, int hi) {  // prod I[lo..hi-1]
@@ -775,13 +868,30 @@ const float* build_chain(const std::vector<int>& modes, const float* const* core
   for (int m : modes) {
     float* out = bufs[t++ % 2];
     const int64_t nOut = nPrev * I[m];
-    const dim3 g((unsigned)std::min<int64_t>((nOut + 255) / 256, 1024), (unsigned)(Ra * R[(m + 1) % N]));
-    chain_level_f32_kernel<<<g, 256, 0, s>>>(prev, nPrev, Ra, R[m], cores[m], I[m], R[(m + 1) % N], out);
+    if (nOut * Ra >= (int64_t)152 * 2048) {   // enough rows to fill the GPU with one thread per (row, x)
+      const dim3 g((unsigned)std::min<int64_t>((nOut + 255) / 256, 4096), (unsigned)Ra);
+      chain_level_f32_kernel<<<g, 256, 0, s>>>(prev, nPrev, Ra, R[m], cores[m], I[m], R[(m + 1) % N], out);
+    } else {
+      const dim3 g((unsigned)((nOut + 255) / 256), (unsigned)(Ra * R[(m + 1) % N]));
+      chain_level_f32_small_kernel<<<g, 256, 0, s>>>(prev, nPrev, Ra, R[m], cores[m], I[m], R[(m + 1) % N], out);
+    }
     ++*launches;
     prev = out;
     nPrev *= I[m];
   }
   return prev;
+}
+
+// The first `count` levels of a chain; *nPrev_out gets the row count of the last level built.
+const float* build_chain_levels(const std::vector<int>& modes, int count, const float* const* cores, const int64_t* I,
+                                const int32_t* R, int N, float* bufA, float* bufB, cudaStream_t s, int* launches,
+                                int64_t* nPrev_out) {
+  std::vector<int> sub(modes.begin(), modes.begin() + count);
+  int64_t nPrev = 1;
+  for (int m : sub) nPrev *= I[m];
+  *nPrev_out = nPrev;
+  if (count == 0) return nullptr;
+  return build_chain(sub, cores, I, R, N, bufA, bufB, s, launches);
 }
 
 }  // namespace
@@ -934,6 +1044,12 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
     A.tx_bytes = (uint32_t)(2 * kAtomBytes);
   }
   impl->SYP = (A.Sy + 3) / 4 * 4;
+  impl->late = (n + N - 1) % N;
+  impl->late_in_s = !impl->s_modes.empty() && impl->s_modes.back() == impl->late;
+  if (!impl->late_in_s && (impl->f_modes.empty() || impl->f_modes.back() != impl->late)) {
+    delete impl;   // every geometry ends one chain with the previous mode; anything else is not planned for
+    return 0;
+  }
   const int W = impl->SYP * A.NY;
   A.W_pad = (W + 15) / 16 * 16;
   A.fs_stride = (A.NX * impl->SYP + 7) / 8 * 8 + 4;
@@ -1051,6 +1167,17 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   impl->tab_lo = x3 ? static_cast<__nv_bfloat16*>(q[6]) : nullptr;
   A.F = impl->F;
   A.partials = impl->partials;
+  // padding of the packed table and factor stays zero: the fused last-link kernel writes live entries only
+  e = cudaMemsetAsync(impl->tab, 0, sizes[3], s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(impl->F, 0, sizes[4], s);
+  if (e == cudaSuccess && x3) e = cudaMemsetAsync(impl->tab_lo, 0, sizes[6], s);
+  if (e != cudaSuccess) {
+    if (err) *err = e;
+    delete impl;
+    for (void* a : p.allocs) cudaFreeAsync(a, s);
+    p.allocs.clear();
+    return 0;
+  }
   if (!encode_bf16(&impl->tmT, impl->tab, 2, tdims, tstrides, tbox) ||
       (x3 && !encode_bf16(&impl->tmTl, impl->tab_lo, 2, tdims, tstrides, tbox))) {
     delete impl;
@@ -1067,18 +1194,17 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   return 1;
 }
 
-int tc_enqueue(TcPlan& p, const void* X, double* const* cores, double* M, cudaStream_t s, cudaEvent_t ev0,
-               cudaEvent_t ev1) {
+int tc_enqueue_pre(TcPlan& p, double* const* cores, cudaStream_t s, const float* const* c32_ext) {
   TcImpl* impl = static_cast<TcImpl*>(p.impl);
-  (void)X;
   int launches = 0;
   const int64_t* I = impl->Icopy;
   const int32_t* R = impl->Rcopy;
   const int N = impl->N;
   TcArgs A = impl->args;
-  // stage-1 table (Alg. 2 line 8's subchain factors over S) and stage-2 factors
   const float* c32[kMaxOrder];
-  {
+  if (c32_ext != nullptr) {
+    for (int j = 0; j < N; ++j) c32[j] = c32_ext[j];
+  } else {
     CorePtrs cp;
     cp.N = N;
     for (int j = 0; j <= N; ++j) cp.off[j] = impl->core_off[j];
@@ -1093,18 +1219,56 @@ int tc_enqueue(TcPlan& p, const void* X, double* const* cores, double* M, cudaSt
                                                                                                      impl->cores32);
     ++launches;
   }
-  const float* tsrc = build_chain(impl->s_modes, c32, I, R, N, impl->chainA, impl->chainB, s, &launches);
-  {
-    const dim3 g((unsigned)std::min<int64_t>((impl->Kpad + 255) / 256, 1024), (unsigned)A.W_pad);
+  // the chain without the late core, whole, and its packing
+  if (impl->late_in_s) {
+    const float* fsrc = build_chain(impl->f_modes, c32, I, R, N, impl->chainA, impl->chainB, s, &launches);
+    const dim3 g((unsigned)std::min<int64_t>((impl->n_fac_total + 255) / 256, 1024), (unsigned)(A.NX * impl->SYP));
+    pack_fac_kernel<<<g, 256, 0, s>>>(fsrc, impl->n_fac_total, impl->facRa, impl->facRb, impl->kindL, A.NX, A.Sy,
+                                      impl->SYP, impl->F);
+    ++launches;
+  } else {
+    const float* tsrc = build_chain(impl->s_modes, c32, I, R, N, impl->chainA, impl->chainB, s, &launches);
+    const dim3 g((unsigned)std::min<int64_t>((impl->Kpad / 4 + 255) / 256, 1024), (unsigned)A.W_pad);
     pack_tab_kernel<<<g, 256, 0, s>>>(tsrc, impl->K_S, impl->Kpad, impl->tabRa, impl->tabRb, impl->kindL, A.Sy,
                                       impl->SYP, A.NY, A.W_pad, impl->tab, impl->tab_lo);
     ++launches;
   }
-  const float* fsrc = build_chain(impl->f_modes, c32, I, R, N, impl->chainA, impl->chainB, s, &launches);
+  // the other chain up to its last link (left in chainA / chainB for tc_enqueue_main)
+  const std::vector<int>& lc = impl->late_in_s ? impl->s_modes : impl->f_modes;
+  int64_t nPrev = 1;
+  build_chain_levels(lc, (int)lc.size() - 1, c32, I, R, N, impl->chainA, impl->chainB, s, &launches, &nPrev);
+  return launches;
+}
+
+int tc_enqueue_main(TcPlan& p, double* const* cores, double* M, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
+                    const float* const* c32_ext) {
+  (void)cores;
+  TcImpl* impl = static_cast<TcImpl*>(p.impl);
+  int launches = 0;
+  const int64_t* I = impl->Icopy;
+  const int32_t* R = impl->Rcopy;
+  const int N = impl->N;
+  TcArgs A = impl->args;
   {
-    const dim3 g((unsigned)std::min<int64_t>((impl->n_fac_total + 255) / 256, 1024), (unsigned)(A.NX * impl->SYP));
-    pack_fac_kernel<<<g, 256, 0, s>>>(fsrc, impl->n_fac_total, impl->facRa, impl->facRb, impl->kindL, A.NX, A.Sy,
-                                      impl->SYP, impl->F);
+    // the last link: the level built by tc_enqueue_pre sits in chainA or chainB by the parity of its levels
+    const std::vector<int>& lc = impl->late_in_s ? impl->s_modes : impl->f_modes;
+    const int nl = (int)lc.size() - 1;
+    int64_t nPrev = 1;
+    for (int j = 0; j < nl; ++j) nPrev *= I[lc[j]];
+    const float* prev = nl == 0 ? nullptr : ((nl - 1) % 2 == 0 ? impl->chainA : impl->chainB);
+    const int m = lc.back();
+    const int Ra = R[lc[0]], Rc = R[m], Rb = R[(m + 1) % N];
+    const float* G = c32_ext != nullptr ? c32_ext[m] : impl->cores32 + impl->core_off[m];
+    const int64_t nOut = nPrev * I[m];
+    const dim3 g((unsigned)std::min<int64_t>((nOut + 255) / 256, 4096), (unsigned)Ra);
+    if (impl->late_in_s)
+      chain_last_pack_kernel<true><<<g, 256, 0, s>>>(prev, nPrev, Ra, Rc, G, I[m], Rb, impl->kindL,
+                                                      impl->SYP, A.Sy, A.NY, impl->Kpad, A.NX, impl->tab,
+                                                      impl->tab_lo, nullptr);
+    else
+      chain_last_pack_kernel<false><<<g, 256, 0, s>>>(prev, nPrev, Ra, Rc, G, I[m], Rb, impl->kindL,
+                                                       impl->SYP, A.Sy, A.NY, impl->Kpad, A.NX, nullptr, nullptr,
+                                                       impl->F);
     ++launches;
   }
   if (ev0) cudaEventRecord(ev0, s);
@@ -1126,6 +1290,27 @@ int tc_enqueue(TcPlan& p, const void* X, double* const* cores, double* M, cudaSt
   }
   ++launches;
   return launches;
+}
+
+int tc_enqueue(TcPlan& p, const void* X, double* const* cores, double* M, cudaStream_t s, cudaEvent_t ev0,
+               cudaEvent_t ev1) {
+  (void)X;
+  return tc_enqueue_pre(p, cores, s, nullptr) + tc_enqueue_main(p, cores, M, s, ev0, ev1, nullptr);
+}
+
+void launch_cores_to_f32(double* const* cores, int N, const int32_t* R, const int64_t* Ist, int64_t I0real,
+                         float* dst, cudaStream_t s) {
+  CorePtrs cp;
+  cp.N = N;
+  cp.off[0] = 0;
+  for (int j = 0; j < N; ++j) {
+    cp.p[j] = cores[j];
+    cp.off[j + 1] = cp.off[j] + (int64_t)R[j] * Ist[j] * R[(j + 1) % N];
+  }
+  cp.R0 = R[0];
+  cp.I0 = I0real;
+  cp.I0p = Ist[0];
+  cores_to_f32_kernel<<<(unsigned)std::min<int64_t>((cp.off[N] + 255) / 256, 152 * 4), 256, 0, s>>>(cp, dst);
 }
 
 int tc_variant(const TcPlan& p) { return p.impl ? static_cast<const TcImpl*>(p.impl)->args.variant : -1; }

@@ -40,6 +40,20 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
 // given, ev0/ev1 are recorded on s directly before and after the main contraction kernel.
 int tc_enqueue(TcPlan& p, const void* X, double* const* cores, double* M, cudaStream_t s, cudaEvent_t ev0 = nullptr,
                cudaEvent_t ev1 = nullptr);
+// tc_enqueue in two parts.  The core of the mode before p.n (the one a sweep updates just before this
+// MTTSP) ends one of the two subchain products.  tc_enqueue_pre builds everything that does not read
+// it (so it may run while that core is being updated, on another stream); tc_enqueue_main builds the
+// last link from that core, then runs the MTTSP and its reduction.  Both return their launch counts.
+// c32 (optional): FP32 copies of the cores kept by the caller, laid out as launch_cores_to_f32 writes
+// them; without it, tc_enqueue_pre converts the cores into the plan's own copy (all of them, so the
+// two parts must then see the same cores).
+int tc_enqueue_pre(TcPlan& p, double* const* cores, cudaStream_t s, const float* const* c32 = nullptr);
+int tc_enqueue_main(TcPlan& p, double* const* cores, double* M, cudaStream_t s, cudaEvent_t ev0 = nullptr,
+                    cudaEvent_t ev1 = nullptr, const float* const* c32 = nullptr);
+// FP32 copies of all N cores into dst, concatenated in order; core j holds R_j x Ist[j] x R_{j+1} values,
+// the slices of core 0 from I0real to Ist[0] zero (a zero-padded leading mode of the BF16 copy of X).
+void launch_cores_to_f32(double* const* cores, int N, const int32_t* R, const int64_t* Ist, int64_t I0real,
+                         float* dst, cudaStream_t s);
 void tc_destroy(TcPlan& p);
 // Geometry of a valid plan (0 KM-L, 1 KM-R, 2 MM), -1 if none.
 int tc_variant(const TcPlan& p);

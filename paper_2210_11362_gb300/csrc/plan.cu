@@ -169,11 +169,19 @@ struct trals_plan {
   cudaStream_t side2 = nullptr;
   cudaEvent_t ev_pre[TRALS_MAX_ORDER] = {};
   cudaEvent_t ev_gam[TRALS_MAX_ORDER] = {};   // Gamma_{n-1} formed on the side stream during mode n
+  // the parts of the next mode's tensor-core subchain tables that do not read the core being updated,
+  // built on `side3` during the current mode
+  cudaStream_t side3 = nullptr;
+  cudaEvent_t ev_tcpre[TRALS_MAX_ORDER] = {};
   double *pre[2] = {}, *preA = nullptr, *preB = nullptr;
   double *ltab2 = nullptr, *utab2 = nullptr, *tscratch2 = nullptr;   // explicit Gram on the side branch
   int launches = 0;
   TcPlan tc[TRALS_MAX_ORDER];
   bool use_tc[TRALS_MAX_ORDER] = {};
+  // FP32 copies of the cores for the tensor-core subchain tables (core 0 with Ist[0] slices, the padded
+  // ones zero): refreshed at the start of every run and by each core update inside the sweep
+  float* c32buf = nullptr;
+  float* c32[TRALS_MAX_ORDER] = {};
   // Workspace is allocated stream-ordered (cudaMallocAsync / cudaFreeAsync on the context's
   // stream), so creating and destroying plans never synchronises the whole device: plans of other
   // streams keep running.  In the counting pass nothing is allocated and `bytes` sums the sizes.
@@ -208,10 +216,8 @@ int enqueue_coef(const int N, const int32_t* R, double* const* gam, int n, doubl
                  cudaStream_t s, const double* pre = nullptr) {
   if (pre) {
     const int c = (n - 1 + N) % N;
-    const int rows = R[(n + 1) % N] * R[(n + 1) % N];
-    launch_gemm_f64(rows, R[n] * R[n], R[c] * R[c], pre, gam[c], chainA, s);
-    launch_regroup_S(chainA, R[n], R[(n + 1) % N], S, s);
-    return 2;
+    launch_gemm_f64_regroup(R[c] * R[c], pre, gam[c], R[n], R[(n + 1) % N], S, s);
+    return 1;
   }
   int launches = 0;
   const int c0 = (n + 1) % N;
@@ -249,11 +255,16 @@ int enqueue_prefix(const int N, const int32_t* R, double* const* gam, int n, dou
   return launches;
 }
 
-int enqueue_mttsp(trals_plan* p, int n, cudaStream_t s, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
+// tc_pre_done: the tensor-core tables' first part was enqueued already (tc_enqueue_pre on side3)
+int enqueue_mttsp(trals_plan* p, int n, cudaStream_t s, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr,
+                  bool tc_pre_done = false) {
   const ModeLayout& L = p->layk[n];
   int launches = 0;
   if (p->use_tc[n]) {
-    launches += tc_enqueue(p->tc[n], p->Xk, p->cores, p->M, s, ev0, ev1);
+    if (tc_pre_done)
+      launches += tc_enqueue_main(p->tc[n], p->cores, p->M, s, ev0, ev1, p->c32);
+    else
+      launches += tc_enqueue(p->tc[n], p->Xk, p->cores, p->M, s, ev0, ev1);
     return launches;
   }
   build_tables(L, p->cores, p->I, p->R, p->ltab, p->utab, p->tscratch, s);
@@ -382,6 +393,12 @@ int enqueue_sweep(trals_plan* p) {
       ++launches;
     }
     cudaEventRecord(p->ev_gam[n], b);
+    // the next mode's tensor-core tables, all but the link through core n (updated below)
+    if (n + 1 < N && p->use_tc[n + 1]) {
+      cudaStreamWaitEvent(p->side3, p->ev_fork[n], 0);
+      launches += tc_enqueue_pre(p->tc[n + 1], p->cores, p->side3, p->c32);
+      cudaEventRecord(p->ev_tcpre[n + 1], p->side3);
+    }
     if (qr) {
       // R factor of G^{!=n}_[2] by structured QR; L = R^T replaces the Cholesky factor of S_n
       launches += launch_qr_factor(N, p->I, p->R, n, p->cores, p->qrB, p->qrR0, p->qrR1, p->qrW, p->Lmat,
@@ -409,12 +426,20 @@ int enqueue_sweep(trals_plan* p) {
       cudaEventRecord(p->ev_pre[n + 1], c);
     }
     // the MTTSP on the main stream, then join
-    launches += enqueue_mttsp(p, n, s);
+    const bool tc_pre = n >= 1 && p->use_tc[n];
+    if (tc_pre) cudaStreamWaitEvent(s, p->ev_tcpre[n], 0);
+    launches += enqueue_mttsp(p, n, s, nullptr, nullptr, tc_pre);
     cudaStreamWaitEvent(s, p->ev_join[n], 0);
-    launch_chol_solve(p->Lmat, p->M, Rn, p->I[n], Rn1, p->cores[n], p->ctx->d_status, s);
+    launch_chol_solve(p->Lmat, p->M, Rn, p->I[n], Rn1, p->cores[n], p->ctx->d_status, s,
+                      qr ? nullptr : p->c32[n], p->Ist[n]);
     ++launches;
-    if (qr)
+    if (qr) {
       for (int step = 0; step < kQrRefineSteps; ++step) launches += enqueue_qr_refinement(p, n, s);
+      if (p->c32buf) {
+        launch_core_to_f32(p->cores[n], Rn, p->I[n], p->Ist[n], Rn1, p->c32[n], s);
+        ++launches;
+      }
+    }
   }
   // Gamma of the last core on the main stream: the residual identity and the next sweep read it
   launch_gamma(p->cores[N - 1], p->R[N - 1], p->I[N - 1], p->R[0], p->gam[N - 1], s);
@@ -500,6 +525,7 @@ void trals_plan_destroy(trals_plan* p) {
       if (p->ev_join[n]) cudaEventDestroy(p->ev_join[n]);
       if (p->ev_pre[n]) cudaEventDestroy(p->ev_pre[n]);
       if (p->ev_gam[n]) cudaEventDestroy(p->ev_gam[n]);
+      if (p->ev_tcpre[n]) cudaEventDestroy(p->ev_tcpre[n]);
     }
     if (p->side) {
       cudaStreamSynchronize(p->side);
@@ -508,6 +534,10 @@ void trals_plan_destroy(trals_plan* p) {
     if (p->side2) {
       cudaStreamSynchronize(p->side2);
       cudaStreamDestroy(p->side2);
+    }
+    if (p->side3) {
+      cudaStreamSynchronize(p->side3);
+      cudaStreamDestroy(p->side3);
     }
   }
   delete p;
@@ -726,18 +756,40 @@ trals_status plan_build(trals_ctx* ctx, int N, const int64_t* I, const int32_t* 
       }
     }
   }
+  {
+    bool any_tc = false;
+    for (int n = 0; n < N; ++n) any_tc = any_tc || p->use_tc[n];
+    if (any_tc) {
+      int64_t tot = 0;
+      for (int n = 0; n < N; ++n) tot += (int64_t)R[n] * p->Ist[n] * R[(n + 1) % N];
+      PLAN_TRY(p->alloc(&p->c32buf, (size_t)tot));
+      int64_t off = 0;
+      for (int n = 0; n < N; ++n) {
+        p->c32[n] = p->c32buf + off;
+        off += (int64_t)R[n] * p->Ist[n] * R[(n + 1) % N];
+      }
+    }
+  }
   if (counting) {
     *count_out = p->bytes;
     trals_plan_destroy(p);
     return TRALS_OK;
   }
-  PLAN_TRY(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
-  PLAN_TRY(cudaStreamCreateWithFlags(&p->side2, cudaStreamNonBlocking));
+  {
+    // the coefficient branch (Gram, Cholesky) is the critical path of the modes with large R_n R_{n+1}:
+    // its blocks go first; the next mode's table pre-phase fills whatever is left
+    int least = 0, greatest = 0;
+    PLAN_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    PLAN_TRY(cudaStreamCreateWithPriority(&p->side, cudaStreamNonBlocking, greatest));
+    PLAN_TRY(cudaStreamCreateWithFlags(&p->side2, cudaStreamNonBlocking));
+    PLAN_TRY(cudaStreamCreateWithPriority(&p->side3, cudaStreamNonBlocking, least));
+  }
   for (int n = 0; n < N; ++n) {
     PLAN_TRY(cudaEventCreateWithFlags(&p->ev_fork[n], cudaEventDisableTiming));
     PLAN_TRY(cudaEventCreateWithFlags(&p->ev_join[n], cudaEventDisableTiming));
     PLAN_TRY(cudaEventCreateWithFlags(&p->ev_pre[n], cudaEventDisableTiming));
     PLAN_TRY(cudaEventCreateWithFlags(&p->ev_gam[n], cudaEventDisableTiming));
+    PLAN_TRY(cudaEventCreateWithFlags(&p->ev_tcpre[n], cudaEventDisableTiming));
   }
   if (sync) PLAN_TRY(cudaStreamSynchronize(s));
   else PLAN_TRY(cudaGetLastError());
@@ -804,6 +856,11 @@ trals_status trals_plan_run(trals_plan* p, int sweeps, int use_graph) {
     return TRALS_E_ARG;
   }
   cudaStream_t s = ctx->stream;
+  if (p->c32buf && sweeps > 0) {
+    // the cores may have been set or written since the last run
+    launch_cores_to_f32(p->cores, p->N, p->R, p->Ist, p->I[0], p->c32buf, s);
+    TRALS_CUDA_TRY(ctx, cudaGetLastError());
+  }
   for (int k = 0; k < sweeps; ++k) {
     if (use_graph) {
       if (!p->gexec) {
@@ -815,7 +872,8 @@ trals_status trals_plan_run(trals_plan* p, int sweeps, int use_graph) {
           ctx->last_error = std::string("graph capture: ") + cudaGetErrorString(e);
           return TRALS_E_CUDA;
         }
-        e = cudaGraphInstantiate(&p->gexec, g, 0);
+        // kernel nodes keep the priority of the stream they were captured from
+        e = cudaGraphInstantiate(&p->gexec, g, cudaGraphInstantiateFlagUseNodePriority);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) {
           ctx->last_error = std::string("graph instantiate: ") + cudaGetErrorString(e);

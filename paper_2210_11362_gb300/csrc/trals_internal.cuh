@@ -63,6 +63,8 @@ void mode_offsets(int N, const int64_t* I, const ModeLayout& L, std::vector<int6
 void launch_gamma(const double* G, int Rn, int64_t In, int Rn1, double* Gamma, cudaStream_t s);
 // C (m x n) = A (m x k) * B (k x n), column-major FP64.
 void launch_gemm_f64(int m, int n, int k, const double* A, const double* B, double* C, cudaStream_t s);
+// Pi = A B (R_{n+1}^2 x R_n^2, inner dimension k) stored directly as the regrouped S_n (r x r).
+void launch_gemm_f64_regroup(int k, const double* A, const double* B, int Rn, int Rn1, double* S, cudaStream_t s);
 // S_n regroup of Pi (R_{n+1}^2 x R_n^2) -> S (r x r).
 void launch_regroup_S(const double* Pi, int Rn, int Rn1, double* S, cudaStream_t s);
 // Chain table: out[l + nPrev * i][x + Ra * y] = sum_c prev[l][x + Ra c] * G[c + Rc (i + I y)]
@@ -136,8 +138,12 @@ void launch_chol_block_inverse(double* Lmat, int r, cudaStream_t s);
 // Triangular solves with In right-hand sides; writes core layout.
 // out[i] = the Cholesky kernel's pivot reciprocal square root of d[i], ref[i] = CUDA's rsqrt(d[i])
 void launch_pivot_rsqrt_check(const double* d, int64_t n, double* out, double* ref, cudaStream_t s);
+// With G32 set, the core is also stored in FP32 there (R_n x Ist x R_{n+1}, Ist >= In slices; the
+// slices past In are left as they are).
 void launch_chol_solve(const double* Lmat, const double* M, int Rn, int64_t In, int Rn1, double* G,
-                       DevStatus* st, cudaStream_t s);
+                       DevStatus* st, cudaStream_t s, float* G32 = nullptr, int64_t Ist = 0);
+// FP32 copy of one core (R_n x In x R_{n+1}) into G32 laid out with Ist >= In slices.
+void launch_core_to_f32(const double* G, int Rn, int64_t In, int64_t Ist, int Rn1, float* G32, cudaStream_t s);
 
 // Residual identity (K6): res2 = normX2 - 2<M, Z> + <S, Z^T Z>; Gamma holds the regrouped Z^T Z.
 void launch_residual_identity(const double* normX2, const double* M, const double* coreN, const double* S,
