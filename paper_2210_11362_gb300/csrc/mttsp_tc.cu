@@ -41,8 +41,9 @@ enum { KM_L = 0, KM_R = 1, MM = 2 };
 
 struct TcArgs {
   int variant;
-  int ksteps, n_kc, kc_len;
-  int64_t n_units;
+  int ksteps;
+  int64_t n_tiles;   // KM: row tiles (each ksteps K steps)
+  int whole;         // split the work at tile boundaries only (shares of several tiles)
   int In;
   int nrep;          // KM: factor values per tile
   int64_t n_fac;     // KM: factor entries along the tiled mode (K_post or K_mid)
@@ -159,13 +160,6 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-// Unit u of this CTA (u counts this CTA's own units).  K-major tiles: a static round robin over all
-// units.  MN-major tiles: CTA c keeps one p-chunk (pc = c % pchunks) for its whole life so that each
-// lane's i_n never changes; the CTAs sharing a p-chunk split its (o-pair, K-chunk) units.
-struct UnitSched {
-  int64_t first, step, count;   // unit ids first + j*step, j < count (K-major); j-th unit of the chunk (MN-major)
-};
-
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 __device__ __forceinline__ void raise_timeout(DevStatus* st, int where) {
@@ -183,28 +177,45 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// The j-th unit of this CTA: K-major tiles take units blockIdx.x + j * gridDim.x of all (tile, K-chunk)
-// units; MN-major tiles pin the CTA to p-chunk pc = blockIdx.x % pchunks and take every G-th of that
-// chunk's (o-pair, K-chunk) units, so each lane keeps the same rows (hence the same i_n) throughout.
+// Work split: a CTA owns one contiguous, equal share of the K steps of all its tiles (tile-major), so
+// every CTA streams the same amount of X; the share is cut at tile boundaries into units, the j-th
+// being (tile, K steps [ks0, ks1)).  When the shares span several tiles (a.whole) they are rounded to
+// whole tiles instead: each unit costs an epilogue, and splitting would add one per CTA.  Every unit's contribution is additive, so a tile may be split
+// between CTAs anywhere in K.  K-major tiles are shared by the whole grid; MN-major tiles pin CTA c
+// to p-chunk pc = c % pchunks (each lane keeps its rows, hence its i_n, for the whole launch) and the
+// CTAs of a p-chunk share that chunk's o-pairs.  Producer, MMA issuer and epilogue call this alike.
 __device__ __forceinline__ bool get_unit(const TcArgs& a, int64_t j, int64_t& tile, int64_t& op, int64_t& pc,
-                                         int& kc) {
+                                         int& ks0, int& ks1) {
+  int64_t ntile, g, G;
   if (a.variant != MM) {
-    const int64_t u = blockIdx.x + j * (int64_t)gridDim.x;
-    if (u >= a.n_units) return false;
-    tile = u / a.n_kc;
-    kc = (int)(u % a.n_kc);
-    op = 0;
+    ntile = a.n_tiles;
+    g = blockIdx.x;
+    G = gridDim.x;
     pc = 0;
+  } else {
+    pc = blockIdx.x % a.pchunks;
+    g = blockIdx.x / a.pchunks;
+    G = (gridDim.x - pc + a.pchunks - 1) / a.pchunks;   // CTAs sharing this p-chunk
+    ntile = a.opairs;
+  }
+  if (a.whole) {   // contiguous whole tiles: no tile is split, so every unit carries a full K range
+    const int64_t t = g * ntile / G + j;
+    if (t >= (g + 1) * ntile / G) return false;
+    ks0 = 0;
+    ks1 = a.ksteps;
+    tile = (a.variant != MM) ? t : 0;
+    op = (a.variant != MM) ? 0 : t;
     return true;
   }
-  pc = blockIdx.x % a.pchunks;
-  const int64_t g = blockIdx.x / a.pchunks;
-  const int64_t G = (gridDim.x - pc + a.pchunks - 1) / a.pchunks;   // CTAs sharing this p-chunk
-  const int64_t w = g + j * G;
-  if (w >= a.opairs * a.n_kc) return false;
-  op = w / a.n_kc;
-  kc = (int)(w % a.n_kc);
-  tile = 0;
+  const int64_t W = ntile * a.ksteps;
+  const int64_t s0 = g * W / G, s1 = (g + 1) * W / G;   // this CTA's K steps
+  const int64_t t = s0 / a.ksteps + j;
+  const int64_t ts = t * a.ksteps;
+  if (s0 >= s1 || ts >= s1) return false;
+  ks0 = (int)(max(s0, ts) - ts);
+  ks1 = (int)(min(s1, ts + a.ksteps) - ts);
+  tile = (a.variant != MM) ? t : 0;
+  op = (a.variant != MM) ? 0 : t;
   return true;
 }
 
@@ -266,9 +277,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0;
       int issued[kNSMax] = {0, 0, 0, 0, 0, 0};
       int64_t tile, op, pc;
-      int kc;
-      for (int64_t j = 0; get_unit(a, j, tile, op, pc, kc) && !*abort_flag; ++j) {
-        const int ks0 = kc * a.kc_len, ks1 = min(a.ksteps, ks0 + a.kc_len);
+      int ks0, ks1;
+      for (int64_t j = 0; get_unit(a, j, tile, op, pc, ks0, ks1) && !*abort_flag; ++j) {
         for (int ks = ks0; ks < ks1; ++ks) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
             *abort_flag = 1;
@@ -314,9 +324,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       int stage = 0;
       uint32_t phase = 0;
       int64_t tile, op, pc;
-      int kc;
-      for (int64_t j = 0; get_unit(a, j, tile, op, pc, kc) && !*abort_flag; ++j) {
-        const int ks0 = kc * a.kc_len, ks1 = min(a.ksteps, ks0 + a.kc_len);
+      int ks0, ks1;
+      for (int64_t j = 0; get_unit(a, j, tile, op, pc, ks0, ks1) && !*abort_flag; ++j) {
         const int buf = (int)(j & 1);
         if (!mbar_wait(&acce[buf], (uint32_t)(((j >> 1) & 1) ^ 1), abort_flag)) {
           *abort_flag = 1;
@@ -401,8 +410,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       tmem_wait_st();
     }
     int64_t tile, op, pc;
-    int kc;
-    for (int64_t j = 0; get_unit(a, j, tile, op, pc, kc); ++j) {
+    int ks0, ks1;
+    for (int64_t j = 0; get_unit(a, j, tile, op, pc, ks0, ks1); ++j) {
       const int buf = (int)(j & 1);
       bool valid;
       int64_t fi;
@@ -1071,11 +1080,14 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   }
   // one SM stays free for the FP64 coefficient-matrix branch that runs concurrently in the sweep
   nsm = std::max(1, nsm - 1);
-  const int64_t want = 4LL * nsm;
-  int n_kc = (int)std::min<int64_t>(std::max<int64_t>(1, (want + n_tiles - 1) / n_tiles), std::max(1, A.ksteps / 4));
-  A.kc_len = (A.ksteps + n_kc - 1) / n_kc;
-  A.n_kc = (A.ksteps + A.kc_len - 1) / A.kc_len;
-  A.n_units = n_tiles * A.n_kc;
+  A.n_tiles = n_tiles;
+  {
+    // shares of at least four tiles: whole tiles (at most a quarter of imbalance, one epilogue fewer)
+    const int64_t per_chunk = (A.variant == MM) ? A.opairs : n_tiles;
+    const int64_t ctas = (A.variant == MM) ? std::max<int64_t>(1, nsm / std::max<int64_t>(1, A.pchunks))
+                                           : std::min<int64_t>(n_tiles * A.ksteps, nsm);
+    A.whole = per_chunk >= 4 * ctas ? 1 : 0;
+  }
   if (A.variant == MM) {
     if (A.pchunks > nsm) {   // each CTA keeps a single p-chunk
       delete impl;
@@ -1083,7 +1095,7 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
     }
     impl->grid = nsm;
   } else {
-    impl->grid = (int)std::min<int64_t>(A.n_units, nsm);
+    impl->grid = (int)std::min<int64_t>(n_tiles * A.ksteps, nsm);
   }
   impl->E = In * r;
 
