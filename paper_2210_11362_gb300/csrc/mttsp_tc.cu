@@ -1253,7 +1253,7 @@ int tc_enqueue_pre(TcPlan& p, double* const* cores, cudaStream_t s, const float*
 }
 
 int tc_enqueue_main(TcPlan& p, double* const* cores, double* M, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
-                    const float* const* c32_ext) {
+                    const float* const* c32_ext, cudaEvent_t before_kernel) {
   (void)cores;
   TcImpl* impl = static_cast<TcImpl*>(p.impl);
   int launches = 0;
@@ -1283,6 +1283,7 @@ int tc_enqueue_main(TcPlan& p, double* const* cores, double* M, cudaStream_t s, 
                                                        impl->F);
     ++launches;
   }
+  if (before_kernel) cudaStreamWaitEvent(s, before_kernel, 0);
   if (ev0) cudaEventRecord(ev0, s);
   const CUtensorMap& xl = A.x3 ? impl->tmXl : impl->tmX;   // unread unless x3
   const CUtensorMap& tl = A.x3 ? impl->tmTl : impl->tmT;

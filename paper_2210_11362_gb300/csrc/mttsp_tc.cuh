@@ -48,8 +48,11 @@ int tc_enqueue(TcPlan& p, const void* X, double* const* cores, double* M, cudaSt
 // them; without it, tc_enqueue_pre converts the cores into the plan's own copy (all of them, so the
 // two parts must then see the same cores).
 int tc_enqueue_pre(TcPlan& p, double* const* cores, cudaStream_t s, const float* const* c32 = nullptr);
+// before_kernel (optional): an event the MTTSP kernel itself waits for.  Its persistent CTAs fill every
+// SM but one, so work that must not be squeezed onto that SM is better finished first.
 int tc_enqueue_main(TcPlan& p, double* const* cores, double* M, cudaStream_t s, cudaEvent_t ev0 = nullptr,
-                    cudaEvent_t ev1 = nullptr, const float* const* c32 = nullptr);
+                    cudaEvent_t ev1 = nullptr, const float* const* c32 = nullptr,
+                    cudaEvent_t before_kernel = nullptr);
 // FP32 copies of all N cores into dst, concatenated in order; core j holds R_j x Ist[j] x R_{j+1} values,
 // the slices of core 0 from I0real to Ist[0] zero (a zero-padded leading mode of the BF16 copy of X).
 void launch_cores_to_f32(double* const* cores, int N, const int32_t* R, const int64_t* Ist, int64_t I0real,

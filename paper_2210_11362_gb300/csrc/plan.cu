@@ -173,6 +173,9 @@ struct trals_plan {
   // built on `side3` during the current mode
   cudaStream_t side3 = nullptr;
   cudaEvent_t ev_tcpre[TRALS_MAX_ORDER] = {};
+  // S_n formed (structured Gram): the tensor-core MTTSP kernel waits for it, so that the FP64 Gamma and
+  // GEMM steps run on the whole GPU instead of the one SM that kernel leaves free
+  cudaEvent_t ev_coef[TRALS_MAX_ORDER] = {};
   double *pre[2] = {}, *preA = nullptr, *preB = nullptr;
   double *ltab2 = nullptr, *utab2 = nullptr, *tscratch2 = nullptr;   // explicit Gram on the side branch
   int launches = 0;
@@ -257,12 +260,12 @@ int enqueue_prefix(const int N, const int32_t* R, double* const* gam, int n, dou
 
 // tc_pre_done: the tensor-core tables' first part was enqueued already (tc_enqueue_pre on side3)
 int enqueue_mttsp(trals_plan* p, int n, cudaStream_t s, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr,
-                  bool tc_pre_done = false) {
+                  bool tc_pre_done = false, cudaEvent_t before_kernel = nullptr) {
   const ModeLayout& L = p->layk[n];
   int launches = 0;
   if (p->use_tc[n]) {
     if (tc_pre_done)
-      launches += tc_enqueue_main(p->tc[n], p->cores, p->M, s, ev0, ev1, p->c32);
+      launches += tc_enqueue_main(p->tc[n], p->cores, p->M, s, ev0, ev1, p->c32, before_kernel);
     else
       launches += tc_enqueue(p->tc[n], p->Xk, p->cores, p->M, s, ev0, ev1);
     return launches;
@@ -393,6 +396,7 @@ int enqueue_sweep(trals_plan* p) {
       ++launches;
     }
     cudaEventRecord(p->ev_gam[n], b);
+    cudaEvent_t coef_ev = nullptr;
     // the next mode's tensor-core tables, all but the link through core n (updated below)
     if (n + 1 < N && p->use_tc[n + 1]) {
       cudaStreamWaitEvent(p->side3, p->ev_fork[n], 0);
@@ -412,9 +416,12 @@ int enqueue_sweep(trals_plan* p) {
       } else if (p->pre[0] && n >= 1) {
         cudaStreamWaitEvent(b, p->ev_pre[n], 0);   // prefix formed during mode n-1
         launches += enqueue_coef(N, p->R, p->gam, n, p->chainA, p->chainB, p->S, b, p->pre[n % 2]);
+        coef_ev = p->ev_coef[n];
       } else {
         launches += enqueue_coef(N, p->R, p->gam, n, p->chainA, p->chainB, p->S, b);
+        coef_ev = p->ev_coef[n];
       }
+      if (coef_ev) cudaEventRecord(coef_ev, b);
       launches += launch_cholesky(p->S, p->Lmat, Rn * Rn1, p->ctx->d_status, p->sweep_ctr, n, b);
     }
     cudaEventRecord(p->ev_join[n], b);
@@ -428,7 +435,7 @@ int enqueue_sweep(trals_plan* p) {
     // the MTTSP on the main stream, then join
     const bool tc_pre = n >= 1 && p->use_tc[n];
     if (tc_pre) cudaStreamWaitEvent(s, p->ev_tcpre[n], 0);
-    launches += enqueue_mttsp(p, n, s, nullptr, nullptr, tc_pre);
+    launches += enqueue_mttsp(p, n, s, nullptr, nullptr, tc_pre, tc_pre ? coef_ev : nullptr);
     cudaStreamWaitEvent(s, p->ev_join[n], 0);
     launch_chol_solve(p->Lmat, p->M, Rn, p->I[n], Rn1, p->cores[n], p->ctx->d_status, s,
                       qr ? nullptr : p->c32[n], p->Ist[n]);
@@ -526,6 +533,7 @@ void trals_plan_destroy(trals_plan* p) {
       if (p->ev_pre[n]) cudaEventDestroy(p->ev_pre[n]);
       if (p->ev_gam[n]) cudaEventDestroy(p->ev_gam[n]);
       if (p->ev_tcpre[n]) cudaEventDestroy(p->ev_tcpre[n]);
+      if (p->ev_coef[n]) cudaEventDestroy(p->ev_coef[n]);
     }
     if (p->side) {
       cudaStreamSynchronize(p->side);
@@ -790,6 +798,7 @@ trals_status plan_build(trals_ctx* ctx, int N, const int64_t* I, const int32_t* 
     PLAN_TRY(cudaEventCreateWithFlags(&p->ev_pre[n], cudaEventDisableTiming));
     PLAN_TRY(cudaEventCreateWithFlags(&p->ev_gam[n], cudaEventDisableTiming));
     PLAN_TRY(cudaEventCreateWithFlags(&p->ev_tcpre[n], cudaEventDisableTiming));
+    PLAN_TRY(cudaEventCreateWithFlags(&p->ev_coef[n], cudaEventDisableTiming));
   }
   if (sync) PLAN_TRY(cudaStreamSynchronize(s));
   else PLAN_TRY(cudaGetLastError());
