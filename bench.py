@@ -313,7 +313,8 @@ def roofline_for(w, mode, kernel_ms, peaks, src):
         achieved = sum(flops) / t / 1e12
         return {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
                 "frac": achieved / 1.25, "traffic": None,
-                "note": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz = 1.26 TFLOP/s (nominal 1.25)"}
+                "note": "nominal FP64 1.25 TFLOP/s; the SM's shared FP64 unit issues one warp instruction per "
+                        "19 cycles (measured), i.e. 152 x 32/19 x 2 FLOP x 2.07 GHz = 1.06 TFLOP/s"}
     achieved = N * bytes_per / t / 1e9
     peak = peaks["hbm_gbs"]
     tr = _recorded_traffic(w.name, mode)
