@@ -177,6 +177,9 @@ struct trals_plan {
   // GEMM steps run on the whole GPU instead of the one SM that kernel leaves free
   cudaEvent_t ev_coef[TRALS_MAX_ORDER] = {};
   double *pre[2] = {}, *preA = nullptr, *preB = nullptr;
+  // mode 0's prefix Gamma_1 ... Gamma_{N-2}: formed during mode N-1 for the next sweep (and by every run's
+  // prologue), in a buffer of its own since mode N-1 may be reading pre[(N-1) % 2] = pre[0] meanwhile
+  double* pre0 = nullptr;
   double *ltab2 = nullptr, *utab2 = nullptr, *tscratch2 = nullptr;   // explicit Gram on the side branch
   int launches = 0;
   TcPlan tc[TRALS_MAX_ORDER];
@@ -185,6 +188,9 @@ struct trals_plan {
   // ones zero): refreshed at the start of every run and by each core update inside the sweep
   float* c32buf = nullptr;
   float* c32[TRALS_MAX_ORDER] = {};
+  // set when the cores may have changed outside a run (set from the host, or their device pointer
+  // handed out): the next run refreshes the FP32 copies and mode 0's prepared inputs first
+  bool prep_stale = true;
   // Workspace is allocated stream-ordered (cudaMallocAsync / cudaFreeAsync on the context's
   // stream), so creating and destroying plans never synchronises the whole device: plans of other
   // streams keep running.  In the counting pass nothing is allocated and `bytes` sums the sizes.
@@ -397,11 +403,13 @@ int enqueue_sweep(trals_plan* p) {
     }
     cudaEventRecord(p->ev_gam[n], b);
     cudaEvent_t coef_ev = nullptr;
-    // the next mode's tensor-core tables, all but the link through core n (updated below)
-    if (n + 1 < N && p->use_tc[n + 1]) {
+    // the next mode's tensor-core tables, all but the link through core n (updated below); after the
+    // last mode, mode 0's for the next sweep (cores 1 .. N-2 do not change before it)
+    const int nx = (n + 1) % N;
+    if (p->use_tc[nx]) {
       cudaStreamWaitEvent(p->side3, p->ev_fork[n], 0);
-      launches += tc_enqueue_pre(p->tc[n + 1], p->cores, p->side3, p->c32);
-      cudaEventRecord(p->ev_tcpre[n + 1], p->side3);
+      launches += tc_enqueue_pre(p->tc[nx], p->cores, p->side3, p->c32);
+      cudaEventRecord(p->ev_tcpre[nx], p->side3);
     }
     if (qr) {
       // R factor of G^{!=n}_[2] by structured QR; L = R^T replaces the Cholesky factor of S_n
@@ -413,9 +421,10 @@ int enqueue_sweep(trals_plan* p) {
         build_tables(p->lay[n], p->cores, p->I, p->R, p->ltab2, p->utab2, p->tscratch2, b);
         launches += (N - 1) + launch_explicit_gram(p->lay[n], p->ltab2, p->utab2, p->opts.mode == TRALS_MODE_FP64,
                                                    p->Ablk, p->gpart, p->S, b);
-      } else if (p->pre[0] && n >= 1) {
-        cudaStreamWaitEvent(b, p->ev_pre[n], 0);   // prefix formed during mode n-1
-        launches += enqueue_coef(N, p->R, p->gam, n, p->chainA, p->chainB, p->S, b, p->pre[n % 2]);
+      } else if (p->pre[0]) {
+        // prefix formed during mode n-1 (mode 0's: during the previous sweep's last mode, or the prologue)
+        if (n >= 1) cudaStreamWaitEvent(b, p->ev_pre[n], 0);
+        launches += enqueue_coef(N, p->R, p->gam, n, p->chainA, p->chainB, p->S, b, n == 0 ? p->pre0 : p->pre[n % 2]);
         coef_ev = p->ev_coef[n];
       } else {
         launches += enqueue_coef(N, p->R, p->gam, n, p->chainA, p->chainB, p->S, b);
@@ -425,16 +434,17 @@ int enqueue_sweep(trals_plan* p) {
       launches += launch_cholesky(p->S, p->Lmat, Rn * Rn1, p->ctx->d_status, p->sweep_ctr, n, b);
     }
     cudaEventRecord(p->ev_join[n], b);
-    if (p->pre[0] && n + 1 < N) {
-      // prefix of the next mode: Gamma_{n+2} ... Gamma_{n-1}, none of which this update changes
+    if (p->pre[0]) {
+      // prefix of the next mode: Gamma_{n+2} ... Gamma_{n-1}, none of which this update changes (after the
+      // last mode: mode 0's prefix Gamma_1 ... Gamma_{N-2} for the next sweep)
       cudaStream_t c = p->side2;
       cudaStreamWaitEvent(c, p->ev_gam[n], 0);   // reads Gamma_{n-1}
-      launches += enqueue_prefix(N, p->R, p->gam, n + 1, p->preA, p->preB, p->pre[(n + 1) % 2], c);
-      cudaEventRecord(p->ev_pre[n + 1], c);
+      launches += enqueue_prefix(N, p->R, p->gam, nx, p->preA, p->preB, nx == 0 ? p->pre0 : p->pre[nx % 2], c);
+      cudaEventRecord(p->ev_pre[nx], c);
     }
     // the MTTSP on the main stream, then join
-    const bool tc_pre = n >= 1 && p->use_tc[n];
-    if (tc_pre) cudaStreamWaitEvent(s, p->ev_tcpre[n], 0);
+    const bool tc_pre = p->use_tc[n];
+    if (tc_pre && n >= 1) cudaStreamWaitEvent(s, p->ev_tcpre[n], 0);   // mode 0's came before this sweep
     launches += enqueue_mttsp(p, n, s, nullptr, nullptr, tc_pre, tc_pre ? coef_ev : nullptr);
     cudaStreamWaitEvent(s, p->ev_join[n], 0);
     launch_chol_solve(p->Lmat, p->M, Rn, p->I[n], Rn1, p->cores[n], p->ctx->d_status, s,
@@ -451,6 +461,9 @@ int enqueue_sweep(trals_plan* p) {
   // Gamma of the last core on the main stream: the residual identity and the next sweep read it
   launch_gamma(p->cores[N - 1], p->R[N - 1], p->I[N - 1], p->R[0], p->gam[N - 1], s);
   ++launches;
+  // join what was prepared for the next sweep's mode 0
+  if (p->pre[0]) cudaStreamWaitEvent(s, p->ev_pre[0], 0);
+  if (p->use_tc[0]) cudaStreamWaitEvent(s, p->ev_tcpre[0], 0);
   if (qr) {
     // the residual identity needs S_N = L L^T
     launch_llt(p->Lmat, p->R[N - 1] * p->R[0], p->S, s);
@@ -668,6 +681,7 @@ trals_status plan_build(trals_ctx* ctx, int N, const int64_t* I, const int32_t* 
   if (N >= 4 && o.solver == TRALS_SOLVE_CHOL && o.gram == TRALS_GRAM_STRUCTURED) {
     PLAN_TRY(p->alloc(&p->pre[0], (size_t)maxR2 * maxR2));
     PLAN_TRY(p->alloc(&p->pre[1], (size_t)maxR2 * maxR2));
+    PLAN_TRY(p->alloc(&p->pre0, (size_t)maxR2 * maxR2));
     PLAN_TRY(p->alloc(&p->preA, (size_t)maxR2 * maxR2));
     PLAN_TRY(p->alloc(&p->preB, (size_t)maxR2 * maxR2));
   }
@@ -838,6 +852,7 @@ trals_status trals_plan_set_cores(trals_plan* p, double* const* cores_host) {
     TRALS_CUDA_TRY(ctx, cudaMemcpyAsync(p->cores[n], cores_host[n], cnt * sizeof(double), cudaMemcpyHostToDevice, s));
     launch_gamma(p->cores[n], p->R[n], p->I[n], p->R[(n + 1) % p->N], p->gam[n], s);
   }
+  p->prep_stale = true;
   set_int_kernel<<<1, 1, 0, s>>>(p->sweep_ctr, 0);
   TRALS_CUDA_TRY(ctx, cudaGetLastError());
   // host copies are pageable: make them complete before returning
@@ -865,10 +880,14 @@ trals_status trals_plan_run(trals_plan* p, int sweeps, int use_graph) {
     return TRALS_E_ARG;
   }
   cudaStream_t s = ctx->stream;
-  if (p->c32buf && sweeps > 0) {
-    // the cores may have been set or written since the last run
-    launch_cores_to_f32(p->cores, p->N, p->R, p->Ist, p->I[0], p->c32buf, s);
+  if (sweeps > 0 && p->prep_stale) {
+    // the cores may have been set or written since the last run: refresh their FP32 copies and what
+    // each sweep's mode 0 expects from the sweep before it (a sweep leaves both current)
+    if (p->c32buf) launch_cores_to_f32(p->cores, p->N, p->R, p->Ist, p->I[0], p->c32buf, s);
+    if (p->pre[0]) enqueue_prefix(p->N, p->R, p->gam, 0, p->preA, p->preB, p->pre0, s);
+    if (p->use_tc[0]) tc_enqueue_pre(p->tc[0], p->cores, s, p->c32);
     TRALS_CUDA_TRY(ctx, cudaGetLastError());
+    p->prep_stale = false;
   }
   for (int k = 0; k < sweeps; ++k) {
     if (use_graph) {
@@ -975,6 +994,7 @@ trals_status plan_set_cores_async(trals_plan* p, const double* const* cores_host
     TRALS_CUDA_TRY(ctx, cudaMemcpyAsync(p->cores[n], cores_host[n], cnt * sizeof(double), cudaMemcpyHostToDevice, s));
     launch_gamma(p->cores[n], p->R[n], p->I[n], p->R[(n + 1) % p->N], p->gam[n], s);
   }
+  p->prep_stale = true;
   set_int_kernel<<<1, 1, 0, s>>>(p->sweep_ctr, 0);
   TRALS_CUDA_TRY(ctx, cudaGetLastError());
   p->host_sweeps = 0;
