@@ -90,6 +90,38 @@ __global__ void gamma_smem_kernel(const double* __restrict__ G, int Rn, int In, 
   }
 }
 
+// The Gram entries as a small tiled product, for the sweep: Gamma is the Gram matrix of the mode-2
+// unfolding G_[2] (I_n x r), (G_[2]^T G_[2])[(p + Rn s), (q + Rn t)] = sum_i G[p, i, s] G[q, i, t],
+// stored regrouped.  Each block owns an 8 x 8 tile of (u, v) and its four 64-thread groups take
+// interleaved quarters of i, summed in a fixed order; the whole square is formed (twice the work of
+// the symmetric half, which is negligible) so no block idles.
+__global__ void __launch_bounds__(256) gamma_tiled_kernel(const double* __restrict__ G, int Rn, int In, int Rn1,
+                                                          double* __restrict__ Gamma) {
+  __shared__ double part[4][64];
+  const int t = threadIdx.x, o = t % 64, g = t / 64;
+  const int r = Rn * Rn1;
+  const int u = blockIdx.x * 8 + (o % 8), v = blockIdx.y * 8 + (o / 8);
+  double a0 = 0.0, a1 = 0.0;
+  if (u < r && v < r) {
+    const int p = u % Rn, s = u / Rn, q = v % Rn, tt = v / Rn;
+    const double* gu = G + p + (int64_t)Rn * In * s;
+    const double* gv = G + q + (int64_t)Rn * In * tt;
+    int i = g;
+#pragma unroll 4
+    for (; i + 4 < In; i += 8) {
+      a0 = fma(gu[(int64_t)Rn * i], gv[(int64_t)Rn * i], a0);
+      a1 = fma(gu[(int64_t)Rn * (i + 4)], gv[(int64_t)Rn * (i + 4)], a1);
+    }
+    if (i < In) a0 = fma(gu[(int64_t)Rn * i], gv[(int64_t)Rn * i], a0);
+  }
+  part[g][o] = a0 + a1;
+  __syncthreads();
+  if (g == 0 && u < r && v < r) {
+    const int p = u % Rn, s = u / Rn, q = v % Rn, tt = v / Rn;
+    Gamma[(p * Rn + q) + (int64_t)Rn * Rn * (s * Rn1 + tt)] = (part[0][o] + part[1][o]) + (part[2][o] + part[3][o]);
+  }
+}
+
 // ------------------------------------------------------------------ FP64 GEMM (Gamma chain, K2)
 // C = A B for the small Gamma-chain products (all dimensions <= 256).  The FP64 unit is shared by the
 // whole SM (about one warp instruction per 19 cycles) and one warp issues at most one FP64 instruction
@@ -112,7 +144,7 @@ __global__ void __launch_bounds__(GT * GT * GK) gemm_f64_kernel(int m, int n, in
     const double* Ar = A + row;
     const double* Bc = B + (int64_t)k * col;
     int kk = g;
-#pragma unroll 2
+#pragma unroll 8
     for (; kk + GK < k; kk += 2 * GK) {
       a0 = fma(Ar[(int64_t)m * kk], Bc[kk], a0);
       a1 = fma(Ar[(int64_t)m * (kk + GK)], Bc[kk + GK], a1);
@@ -738,7 +770,11 @@ inline int grid_for(int64_t total, int block, int cap = 152 * 16) {
 void launch_gamma(const double* G, int Rn, int64_t In, int Rn1, double* Gamma, cudaStream_t s) {
   const int64_t total = (int64_t)Rn * Rn1 * Rn * Rn1;
   const int64_t core = (int64_t)Rn * In * Rn1;
-  if (core <= kGammaSmemMax)
+  const int r = Rn * Rn1;
+  if (In <= 4096) {
+    const dim3 grid((r + 7) / 8, (r + 7) / 8);
+    gamma_tiled_kernel<<<grid, 256, 0, s>>>(G, Rn, (int)In, Rn1, Gamma);
+  } else if (core <= kGammaSmemMax)
     gamma_smem_kernel<<<grid_for(total, 128), 128, (size_t)core * sizeof(double), s>>>(G, Rn, (int)In, Rn1, Gamma);
   else
     gamma_kernel<<<grid_for(total, 256), 256, 0, s>>>(G, Rn, In, Rn1, Gamma);
