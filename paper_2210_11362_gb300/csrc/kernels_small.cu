@@ -536,17 +536,15 @@ __global__ void __launch_bounds__(256) chol_solve_kernel(const double* __restric
   const int64_t i0 = blockIdx.x;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (kInSmem) {
-    // element e = i + r k of L to Ls[i + lda k], two per 16-byte load, (i, k) advanced without division
-    const double2* L2 = reinterpret_cast<const double2*>(Lmat);
-    const int n2 = (r * r) >> 1;
-    int i = (2 * tid) % r, k = (2 * tid) / r;
-    const int di = (2 * nt) % r, dk = (2 * nt) / r;
-#pragma unroll 4
-    for (int e2 = tid; e2 < n2; e2 += nt) {
-      const double2 v = L2[e2];
-      Ls[i + lda * k] = v.x;
-      const bool wrap = i + 1 == r;
-      Ls[(wrap ? 0 : i + 1) + lda * (wrap ? k + 1 : k)] = v.y;
+    // element e = i + r k of L to Ls[i + lda k] and the W_q entries, by 8-byte asynchronous copies:
+    // every copy is in flight at once instead of a round trip per batch of loads; (i, k) advanced
+    // without division
+    int i = tid % r, k = tid / r;
+    const int di = nt % r, dk = nt / r;
+    for (int e = tid; e < r * r; e += nt) {
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(Ls + i + lda * k)),
+                   "l"(Lmat + e)
+                   : "memory");
       i += di;
       k += dk;
       if (i >= r) {
@@ -554,11 +552,16 @@ __global__ void __launch_bounds__(256) chol_solve_kernel(const double* __restric
         ++k;
       }
     }
-    if ((r & 1) && tid == 0) Ls[(r - 1) + lda * (r - 1)] = Lmat[(size_t)r * r - 1];
-    for (int e = tid; e < nblk * B * B; e += nt)
-      Ws[(e / (B * B)) * (B * (B + 1)) + (e % B) + (B + 1) * ((e / B) % B)] = Wg[e];
+    for (int e = tid; e < nblk * B * B; e += nt) {
+      double* dst = Ws + (e / (B * B)) * (B * (B + 1)) + (e % B) + (B + 1) * ((e / B) % B);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                   "l"(Wg + e)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
   }
   for (int j = tid; j < nblk * B; j += nt) y[j] = j < r ? M[i0 + In * (int64_t)j] : 0.0;
+  if (kInSmem) asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
   const int lane = tid & 31, warp = tid >> 5;
   auto w_at = [&](int q, int a, int b) -> double {

@@ -389,6 +389,7 @@ int enqueue_sweep(trals_plan* p) {
   int launches = 0;
   const int N = p->N;
   const bool qr = p->opts.solver == TRALS_SOLVE_QR;
+  const bool gam_last_deferred = p->opts.mode != TRALS_MODE_FP64;
   for (int n = 0; n < N; ++n) {
     const int Rn = p->R[n], Rn1 = p->R[(n + 1) % N];
     // fork: the coefficient-matrix branch on the side stream
@@ -396,9 +397,12 @@ int enqueue_sweep(trals_plan* p) {
     cudaEventRecord(p->ev_fork[n], s);
     cudaStreamWaitEvent(b, p->ev_fork[n], 0);
     // Gamma of the core the previous mode updated, on the side stream: only the coefficient branches
-    // read it, so the MTTSP of this mode does not wait for it
-    if (n >= 1) {
-      launch_gamma(p->cores[n - 1], p->R[n - 1], p->I[n - 1], Rn, p->gam[n - 1], b);
+    // read it, so the MTTSP of this mode does not wait for it.  Mode 0 forms the last core's, left by
+    // the previous sweep, except in the FP64 mode, whose residual identity needs it at the end of
+    // the sweep itself.
+    if (n >= 1 || gam_last_deferred) {
+      const int c = (n + N - 1) % N;
+      launch_gamma(p->cores[c], p->R[c], p->I[c], Rn, p->gam[c], b);
       ++launches;
     }
     cudaEventRecord(p->ev_gam[n], b);
@@ -458,9 +462,12 @@ int enqueue_sweep(trals_plan* p) {
       }
     }
   }
-  // Gamma of the last core on the main stream: the residual identity and the next sweep read it
-  launch_gamma(p->cores[N - 1], p->R[N - 1], p->I[N - 1], p->R[0], p->gam[N - 1], s);
-  ++launches;
+  // Gamma of the last core on the main stream when the residual identity below reads it (else the next
+  // sweep's mode 0 forms it)
+  if (!gam_last_deferred) {
+    launch_gamma(p->cores[N - 1], p->R[N - 1], p->I[N - 1], p->R[0], p->gam[N - 1], s);
+    ++launches;
+  }
   // join what was prepared for the next sweep's mode 0
   if (p->pre[0]) cudaStreamWaitEvent(s, p->ev_pre[0], 0);
   if (p->use_tc[0]) cudaStreamWaitEvent(s, p->ev_tcpre[0], 0);
