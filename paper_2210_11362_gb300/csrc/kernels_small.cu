@@ -260,6 +260,10 @@ __global__ void pivot_rsqrt_check_kernel(const double* __restrict__ d, int64_t n
 }
 
 constexpr int kCholSmemMax = 128;
+// from this order on the blocked, many-SM factorization is used.  Measured warm on GB300, one-CTA kernel
+// plus its block inverses against the blocked path: r = 64: 62.6 / 61.5 us; 80: 86.0 / 86.0;
+// 96: 110.7 / 94.3; 120: 170.9 / 125.1; 128: 192.5 / 127.1.
+constexpr int kCholBlockedMin = 88;
 constexpr int kCholThreads = 1024;
 constexpr int kCholWork = 800;       // warp 0 and the 24 warps of sub-partitions 1-3
 constexpr int kCholTrail = 24;       // trailing-update warps
@@ -364,95 +368,6 @@ __global__ void __launch_bounds__(kCholThreads) cholesky_kernel(const double* __
     for (int e = tid; e < r * r; e += kCholThreads) Lmat[e] = A[e];
 }
 
-// ------------------------------------------------------------------ K4, blocked over many SMs
-// FP64 throughput per SM is small on this GPU, so larger systems use a right-looking blocked Cholesky
-// in kPanel-wide panels, two kernels per panel (Golub & Van Loan Sec. 4.2, the same factorization):
-//   update: A[i][j] -= sum_{k < p0} L[i][k] L[j][k]   for the panel's columns j and rows i >= j
-//   factor: every CTA factors the panel's diagonal block redundantly in shared memory, then solves
-//           its share of the rows below: L[i][p0:p1] = A[i][p0:p1] L_pp^{-T}.
-// L is the lower triangle of Lmat (column-major, leading dimension r); 1/L_jj goes to Lmat[r*r + j].
-constexpr int kPanel = 32;
-
-__global__ void chol_panel_update_kernel(double* __restrict__ A, int r, int p0) {
-  // one thread per (i, j) with j in [p0, p0 + kPanel), i in [j, r)
-  const int p1 = min(r, p0 + kPanel);
-  const int nj = p1 - p0;
-  const int total = (r - p0) * nj;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-    const int i = p0 + e % (r - p0), j = p0 + e / (r - p0);
-    if (i < j) continue;
-    double acc = 0.0;
-    for (int k = 0; k < p0; ++k) acc = fma(A[i + (int64_t)r * k], A[j + (int64_t)r * k], acc);
-    A[i + (int64_t)r * j] -= acc;
-  }
-}
-
-__global__ void chol_panel_factor_kernel(double* __restrict__ A, int r, int p0, DevStatus* st, const int* sweep_ctr,
-                                         int mode) {
-  __shared__ double D[kPanel][kPanel + 1];
-  __shared__ double invd[kPanel];
-  __shared__ int fail;
-  const int p1 = min(r, p0 + kPanel);
-  const int nb = p1 - p0;
-  const int tid = threadIdx.x;
-  for (int e = tid; e < nb * nb; e += blockDim.x) {
-    const int i = e % nb, j = e / nb;
-    D[i][j] = (i >= j) ? A[(p0 + i) + (int64_t)r * (p0 + j)] : 0.0;
-  }
-  if (tid == 0) fail = 0;
-  __syncthreads();
-  // factor the diagonal block (one warp, column by column)
-  if (tid < 32) {
-    for (int j = 0; j < nb; ++j) {
-      if (tid == 0) {
-        const double d = D[j][j];
-        if (!(d > 0.0) || !isfinite(d)) {
-          fail = 1;
-          if (blockIdx.x == 0)
-            set_status(st, isfinite(d) ? TRALS_E_NOT_SPD : TRALS_E_NONFINITE, sweep_ctr ? *sweep_ctr : -1, mode,
-                       p0 + j, d);
-          D[j][j] = 1.0;
-          invd[j] = 1.0;
-        } else {
-          const double l = sqrt(d);
-          D[j][j] = l;
-          invd[j] = 1.0 / l;
-        }
-      }
-      __syncwarp();
-      const double inv = invd[j];
-      if (tid > j && tid < nb) D[tid][j] *= inv;
-      __syncwarp();
-      // trailing update inside the block: lane i updates its row i >= k > j
-      if (tid > j && tid < nb) {
-        const double lij = D[tid][j];
-        for (int k = j + 1; k <= tid; ++k) D[tid][k] = fma(-lij, D[k][j], D[tid][k]);
-      }
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-  if (fail) return;
-  if (blockIdx.x == 0) {
-    for (int e = tid; e < nb * nb; e += blockDim.x) {
-      const int i = e % nb, j = e / nb;
-      if (i >= j) A[(p0 + i) + (int64_t)r * (p0 + j)] = D[i][j];
-    }
-    for (int j = tid; j < nb; j += blockDim.x) A[(int64_t)r * r + p0 + j] = invd[j];
-  }
-  // rows below the block: x L_pp^T = a  (forward substitution per row, one warp per row)
-  const int warp = tid / 32, lane = tid % 32, nw = blockDim.x / 32;
-  for (int i = p1 + blockIdx.x * nw + warp; i < r; i += gridDim.x * nw) {
-    double x = (lane < nb) ? A[i + (int64_t)r * (p0 + lane)] : 0.0;
-    for (int j = 0; j < nb; ++j) {
-      const double xj = __shfl_sync(0xffffffffu, x, j) * invd[j];
-      if (lane == j) x = xj;
-      if (lane > j && lane < nb) x = fma(-D[lane][j], xj, x);
-    }
-    if (lane < nb) A[i + (int64_t)r * (p0 + lane)] = x;
-  }
-}
-
 // ------------------------------------------------------------------ K4: diagonal-block inverses
 // W_q = D_q^{-1} for the 32 x 32 diagonal blocks D_q of L, so the triangular solves below need no serial
 // substitution.  One CTA per block, by recursive doubling on the 2 x 2 block form of a lower-triangular
@@ -509,6 +424,148 @@ __global__ void __launch_bounds__(256) chol_block_inverse_kernel(double* __restr
   double* Wq = Lmat + (size_t)r * r + r + (size_t)q * kSolveBlock * kSolveBlock;
   for (int e = threadIdx.x; e < kSolveBlock * kSolveBlock; e += blockDim.x)
     Wq[e] = W[e % kSolveBlock][e / kSolveBlock];
+}
+
+// ------------------------------------------------------------------ K4, blocked over many SMs
+// Left-looking blocked Cholesky in 32-column panels (Golub & Van Loan Sec. 4.2, the same factorization),
+// two kernels per panel so the FP64 work is spread over many SMs (the FP64 unit of a single SM is the
+// bound of the one-CTA kernel above):
+//   update: A[i][j] -= sum_{k < p0} L[i][k] L[j][k] for the panel's columns j and rows i >= j;
+//   factor: every CTA factors the panel's diagonal block D redundantly in shared memory (the split
+//           chain of cholesky_kernel at 32 x 32), inverts it by recursive doubling, and forms its share
+//           of the rows below as L[i][p0:p1] = A[i][p0:p1] D^{-T}, a product with the inverse rather than
+//           a substitution.  CTA 0 stores D, its reciprocal diagonal and W_q = D^{-1}: the factor's whole
+//           layout, so no separate block-inverse pass follows.
+constexpr int kPanel = kSolveBlock;
+
+__global__ void __launch_bounds__(256) chol_panel_update_kernel(double* __restrict__ A, int r, int p0, int p1,
+                                                                int move_prev) {
+  __shared__ double part[4][64];
+  const int t = threadIdx.x, o = t & 63, g = t >> 6;
+  if (move_prev && blockIdx.x == 0 && blockIdx.y == 0) {
+    // the previous panel's factored diagonal block, parked in the scratch after W by its factor kernel
+    // (whose CTAs all read that block as input, so none of them could write it in place)
+    const int q0 = p0 - kPanel;
+    const double* scratch = A + lmat_scratch_offset(r);
+    for (int e = t; e < kPanel * kPanel; e += blockDim.x) {
+      const int i = e % kPanel, j = e / kPanel;
+      if (i >= j) A[(q0 + i) + (int64_t)r * (q0 + j)] = scratch[e];
+    }
+  }
+  const int i = p0 + blockIdx.x * 8 + (o & 7), j = p0 + blockIdx.y * 8 + (o >> 3);
+  const bool live = i < r && j < p1 && i >= j;
+  double a0 = 0.0, a1 = 0.0;
+  if (live) {
+    const double* Li = A + i;
+    const double* Lj = A + j;
+    int k = g;
+#pragma unroll 4
+    for (; k + 4 < p0; k += 8) {
+      a0 = fma(Li[(int64_t)r * k], Lj[(int64_t)r * k], a0);
+      a1 = fma(Li[(int64_t)r * (k + 4)], Lj[(int64_t)r * (k + 4)], a1);
+    }
+    if (k < p0) a0 = fma(Li[(int64_t)r * k], Lj[(int64_t)r * k], a0);
+  }
+  part[g][o] = a0 + a1;
+  __syncthreads();
+  if (g == 0 && live) A[i + (int64_t)r * j] -= (part[0][o] + part[1][o]) + (part[2][o] + part[3][o]);
+}
+
+__global__ void __launch_bounds__(256) chol_panel_factor_kernel(double* __restrict__ A, int r, int p0, DevStatus* st,
+                                                                const int* sweep_ctr, int mode) {
+  constexpr int B = kPanel;
+  __shared__ double D[B][B + 1], W[B][B + 1], T[B][B + 1];
+  __shared__ double yv[B];
+  __shared__ int fail[2];   // failure flag of the steps of each parity
+  const int p1 = min(r, p0 + B), nb = p1 - p0;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int e = tid; e < B * B; e += blockDim.x) {
+    const int i = e % B, j = e / B;
+    double v;
+    if (i < nb && j < nb) v = (i >= j) ? A[(p0 + i) + (int64_t)r * (p0 + j)] : 0.0;
+    else v = (i == j) ? 1.0 : 0.0;   // identity past the panel
+    D[i][j] = v;
+  }
+  if (tid < 2) fail[tid] = 0;
+  __syncthreads();
+  // pivot of column k of the block from its updated diagonal d (every lane of warp 0 alike); a failure
+  // goes to the flag of parity `slot`, read by everyone after that step's barrier
+  auto pivot = [&](int k, double d, int slot, double& y) -> bool {
+    const long long b = __double_as_longlong(d);
+    if (b > 0 && b < 0x7ff0000000000000LL) {
+      y = rsqrt_pivot(d);
+      return true;
+    }
+    if (lane == 0) {
+      fail[slot] = 1;
+      if (blockIdx.x == 0)
+        set_status(st, isfinite(d) ? TRALS_E_NOT_SPD : TRALS_E_NONFINITE, sweep_ctr ? *sweep_ctr : -1, mode, p0 + k, d);
+    }
+    return false;
+  };
+  if (warp == 0) {
+    double y = 0.0;
+    if (pivot(0, D[0][0], 1, y)) {
+      if (lane < nb) D[lane][0] *= y;
+      if (lane == 0) yv[0] = y;
+    }
+  }
+  __syncthreads();
+  // right-looking over the block: warp 0 carries column c+1 (update with column c, pivot, scale); warps
+  // 1..7 apply column c to the columns after it.  One barrier per column; `fail` is read after it.
+  for (int c = 0; c + 1 < nb; ++c) {
+    // the flag of the previous step (slot 1 for the first column); the next write to that slot comes two
+    // barriers later, after every thread has read it
+    if (fail[(c + 1) & 1]) break;
+    if (warp == 0) {
+      const int k = c + 1;
+      const double lkc = D[k][c];
+      const double x = (lane >= k && lane < nb) ? fma(-D[lane][c], lkc, D[lane][k]) : 0.0;
+      double y = 0.0;
+      if (pivot(k, __shfl_sync(0xffffffffu, x, k), c & 1, y)) {
+        if (lane >= k && lane < nb) D[lane][k] = x * y;
+        if (lane == 0) yv[k] = y;
+      }
+    } else {
+      for (int kk = c + 1 + warp; kk < nb; kk += 7) {
+        const double lkc = D[kk][c];
+        if (lane >= kk && lane < nb) D[lane][kk] = fma(-D[lane][c], lkc, D[lane][kk]);
+      }
+    }
+    __syncthreads();
+  }
+  if (fail[0] || fail[1]) return;   // uniform: read after the last barrier
+  for (int e = tid; e < B * B; e += blockDim.x) {
+    const int i = e % B, j = e / B;
+    W[i][j] = (i == j) ? (i < nb ? yv[i] : 1.0) : 0.0;
+  }
+  __syncthreads();
+  block_inverse_level<0>(D, W, T, tid);
+  block_inverse_level<1>(D, W, T, tid);
+  block_inverse_level<2>(D, W, T, tid);
+  block_inverse_level<3>(D, W, T, tid);
+  block_inverse_level<4>(D, W, T, tid);
+  if (blockIdx.x == 0) {
+    if (gridDim.x == 1) {   // no other CTA reads the block: in place
+      for (int e = tid; e < nb * nb; e += blockDim.x) {
+        const int i = e % nb, j = e / nb;
+        if (i >= j) A[(p0 + i) + (int64_t)r * (p0 + j)] = D[i][j];
+      }
+    } else {                // parked; the next panel's update kernel moves it in place
+      double* scratch = A + lmat_scratch_offset(r);
+      for (int e = tid; e < B * B; e += blockDim.x) scratch[e] = D[e % B][e / B];
+    }
+    for (int c = tid; c < nb; c += blockDim.x) A[(int64_t)r * r + p0 + c] = yv[c];
+    double* Wq = A + (int64_t)r * r + r + (int64_t)(p0 / B) * B * B;
+    for (int e = tid; e < B * B; e += blockDim.x) Wq[e] = W[e % B][e / B];
+  }
+  // rows below: L[i][p0 + c] = sum_{t <= c} A[i][p0 + t] W[c][t], one warp per row
+  for (int i = p1 + blockIdx.x * 8 + warp; i < r; i += gridDim.x * 8) {
+    const double a = (lane < nb) ? A[i + (int64_t)r * (p0 + lane)] : 0.0;
+    double acc = 0.0;
+    for (int t = 0; t < nb; ++t) acc = fma(__shfl_sync(0xffffffffu, a, t), W[lane][t], acc);
+    if (lane < nb) A[i + (int64_t)r * (p0 + lane)] = acc;
+  }
 }
 
 // ------------------------------------------------------------------ K4: triangular solves
@@ -854,30 +911,39 @@ __global__ void copy_lower_kernel(const double* __restrict__ S, double* __restri
   }
 }
 
+int launch_cholesky_blocked(const double* S, double* Lmat, int r, DevStatus* st, const int* sweep_ctr, int mode,
+                            cudaStream_t s) {
+  int launches = 1;
+  copy_lower_kernel<<<grid_for((int64_t)r * r, 256), 256, 0, s>>>(S, Lmat, r);
+  int prev_blocks = 0;
+  for (int p0 = 0; p0 < r; p0 += kPanel) {
+    const int p1 = std::min(r, p0 + kPanel);
+    if (p0 > 0) {
+      const dim3 g((r - p0 + 7) / 8, (p1 - p0 + 7) / 8);
+      chol_panel_update_kernel<<<g, 256, 0, s>>>(Lmat, r, p0, p1, prev_blocks > 1 ? 1 : 0);
+      ++launches;
+    }
+    const int rows_below = r - p1;
+    const int blocks = std::max(1, std::min(16, (rows_below + 7) / 8));
+    chol_panel_factor_kernel<<<blocks, 256, 0, s>>>(Lmat, r, p0, st, sweep_ctr, mode);
+    ++launches;
+    prev_blocks = blocks;
+  }
+  return launches;
+}
+
+bool cholesky_is_blocked(int r) { return !(r <= kCholSmemMax && r < kCholBlockedMin); }
+
 int launch_cholesky(const double* S, double* Lmat, int r, DevStatus* st, const int* sweep_ctr, int mode,
                     cudaStream_t s) {
-  if (r <= kCholSmemMax) {
-    // one CTA, matrix in shared memory: all 32 warps share the SM's FP64 pipes with one sync pair per column
+  if (!cholesky_is_blocked(r)) {
+    // one CTA, matrix in shared memory: the split chain of cholesky_kernel
     const size_t smem = (size_t)r * r * sizeof(double);
     cholesky_kernel<<<1, kCholThreads, smem, s>>>(S, Lmat, r, st, sweep_ctr, mode);
     launch_chol_block_inverse(Lmat, r, s);
     return 2;
   }
-  int launches = 1;
-  copy_lower_kernel<<<grid_for((int64_t)r * r, 256), 256, 0, s>>>(S, Lmat, r);
-  for (int p0 = 0; p0 < r; p0 += kPanel) {
-    if (p0 > 0) {
-      const int total = (r - p0) * std::min(kPanel, r - p0);
-      chol_panel_update_kernel<<<(total + 63) / 64, 64, 0, s>>>(Lmat, r, p0);
-      ++launches;
-    }
-    const int rows_below = std::max(0, r - std::min(r, p0 + kPanel));
-    const int blocks = std::max(1, std::min(64, (rows_below + 3) / 4));
-    chol_panel_factor_kernel<<<blocks, 128, 0, s>>>(Lmat, r, p0, st, sweep_ctr, mode);
-    ++launches;
-  }
-  launch_chol_block_inverse(Lmat, r, s);
-  return launches + 1;
+  return launch_cholesky_blocked(S, Lmat, r, st, sweep_ctr, mode, s);
 }
 
 void launch_pivot_rsqrt_check(const double* d, int64_t n, double* out, double* ref, cudaStream_t s) {

@@ -960,7 +960,7 @@ TcChoice tc_choose(int N, const int64_t* I, const int32_t* R, int n) {
 }
 
 int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mode, const void* X, int64_t numel,
-            cudaError_t* err, cudaStream_t s, size_t* count_bytes, int64_t I0_real, const void* Xlo) {
+            cudaError_t* err, cudaStream_t s, size_t* count_bytes, int64_t I0_real, const void* Xlo, int free_sms) {
   if (err) *err = cudaSuccess;
   p.valid = false;
   const bool x3 = mode == TRALS_MODE_BF16X3;
@@ -1078,8 +1078,9 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   }
-  // one SM stays free for the FP64 coefficient-matrix branch that runs concurrently in the sweep
-  nsm = std::max(1, nsm - 1);
+  // SMs left free for the FP64 coefficient-matrix branch that runs concurrently in the sweep (its
+  // one-CTA Cholesky needs one; the blocked factorization's panel kernels need more)
+  nsm = std::max(1, nsm - std::max(0, free_sms));
   A.n_tiles = n_tiles;
   {
     // shares of at least four tiles: whole tiles (at most a quarter of imbalance, one epilogue fewer)

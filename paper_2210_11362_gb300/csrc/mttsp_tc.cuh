@@ -32,10 +32,11 @@ TcChoice tc_choose(int N, const int64_t* I, const int32_t* R, int n);
 // With count_bytes set nothing is allocated: the workspace bytes are added to *count_bytes.
 // I are the extents of X as stored; I0_real (0: I[0]) is the true extent of mode 0 when X is stored
 // with mode 0 zero-padded to I[0] (the rows of M_0 beyond it are dropped).
-// In the bf16x3 mode Xlo is the lo plane of the split-BF16 X (same layout as X).
+// In the bf16x3 mode Xlo is the lo plane of the split-BF16 X (same layout as X).  The grid leaves
+// free_sms SMs free for concurrent work (the coefficient branch of the sweep).
 int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mode, const void* X, int64_t numel,
             cudaError_t* err, cudaStream_t s = nullptr, size_t* count_bytes = nullptr, int64_t I0_real = 0,
-            const void* Xlo = nullptr);
+            const void* Xlo = nullptr, int free_sms = 1);
 // Enqueue M_n (FP64, I_n x R_n R_{n+1}) on stream s; returns the number of kernel launches.  When
 // given, ev0/ev1 are recorded on s directly before and after the main contraction kernel.
 int tc_enqueue(TcPlan& p, const void* X, double* const* cores, double* M, cudaStream_t s, cudaEvent_t ev0 = nullptr,

@@ -775,8 +775,11 @@ trals_status plan_build(trals_ctx* ctx, int N, const int64_t* I, const int32_t* 
   for (int n = 0; n < N; ++n) {
     p->use_tc[n] = false;
     if (o.mode != TRALS_MODE_FP64) {
+      // the blocked Cholesky's panel kernels run beside this MTTSP: leave them SMs (its factor kernels
+      // use up to 16 CTAs); the one-CTA Cholesky needs one
+      const bool blocked = o.solver == TRALS_SOLVE_CHOL && cholesky_is_blocked(R[n] * R[(n + 1) % N]);
       const int ok = tc_plan(p->tc[n], N, p->Ist, R, n, o.mode, p->Xk, p->numel_st, &e, s,
-                             counting ? &p->bytes : nullptr, I[0], p->Xk_lo);
+                             counting ? &p->bytes : nullptr, I[0], p->Xk_lo, blocked ? 17 : 1);
       if (e != cudaSuccess) PLAN_TRY(e);
       p->use_tc[n] = ok != 0;
       if (ok && !counting) {

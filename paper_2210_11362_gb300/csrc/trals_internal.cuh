@@ -124,15 +124,22 @@ void launch_residual_f32(const ModeLayout& L, const double* ltab, const double* 
 // Layout of a factor buffer `Lmat` (FP64): L (r x r, column-major, lower triangle; zeros above), then
 // the r reciprocal diagonal entries 1/L_jj, then the inverses of the 32 x 32 diagonal blocks of L
 // (block q covers rows and columns [32q, 32q + 32), identity-padded past r; each column-major, 1024
-// doubles).  Every producer of a factor (Cholesky, the QR path) fills all three parts.
+// doubles), then 1024 doubles of scratch for the blocked factorization.  Every producer of a factor
+// (Cholesky, the QR path) fills the first three parts.
 constexpr int kSolveBlock = 32;
-inline size_t lmat_elems(int r) {
+__host__ __device__ inline size_t lmat_scratch_offset(int r) {
   return (size_t)r * r + r + (size_t)((r + kSolveBlock - 1) / kSolveBlock) * kSolveBlock * kSolveBlock;
 }
+inline size_t lmat_elems(int r) { return lmat_scratch_offset(r) + (size_t)kSolveBlock * kSolveBlock; }
 // Cholesky (K4): factor S (r x r, lower triangle) into Lmat; status on failure.
 // Returns the number of kernel launches.
 int launch_cholesky(const double* S, double* Lmat, int r, DevStatus* st, const int* sweep_ctr, int mode,
                     cudaStream_t s);
+// Whether launch_cholesky takes the blocked, many-SM path for order r (else one CTA on one SM).
+bool cholesky_is_blocked(int r);
+// The same factor by the blocked, many-SM path (any r).
+int launch_cholesky_blocked(const double* S, double* Lmat, int r, DevStatus* st, const int* sweep_ctr, int mode,
+                            cudaStream_t s);
 // Inverses of the diagonal blocks of L into the third part of Lmat (from L and its reciprocal diagonal).
 void launch_chol_block_inverse(double* Lmat, int r, cudaStream_t s);
 // Triangular solves with In right-hand sides; writes core layout.
