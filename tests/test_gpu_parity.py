@@ -293,12 +293,13 @@ def test_solve_chol_matches_oracle(ctx):
         assert rel(P.core_from_device(G, Rn, I[n], Rn1), ref) < 1e-10
 
 
-@pytest.mark.parametrize("r", [1, 7, 64, 120, 128])
+@pytest.mark.parametrize("r", [1, 7, 64, 97, 120, 128, 200])
 @pytest.mark.parametrize("scale", [1.0, 2.0 ** 700, 2.0 ** -700, 3.0e150, 7.0e-160])
 def test_solve_chol_across_sizes_and_scales(ctx, r, scale):
-    """Cholesky + triangular solves on random SPD systems (cond ~ 1e3) from r = 1 to the largest
-    single-CTA size, with S and M scaled together far outside FP32 range (the pivot's reciprocal
-    square root is rescaled by exact powers of two): the solution is scale-free."""
+    """Cholesky + triangular solves on random SPD systems (cond ~ 1e3) from r = 1 through the blocked
+    many-SM factorization (r = 97: a one-column last panel; 200: the solve reading L from global
+    memory), with S and M scaled together far outside FP32 range (the pivot's reciprocal square root
+    is rescaled by exact powers of two): the solution is scale-free."""
     rng = np.random.default_rng(r)
     A = rng.standard_normal((3 * r + 5, r))
     S = A.T @ A + 1e-3 * np.eye(r)
@@ -341,7 +342,8 @@ def test_pivot_rsqrt_against_cuda_rsqrt(ctx):
     assert np.array_equal(exact, 1.0 / np.sqrt(q))
 
 
-@pytest.mark.parametrize("r,k", [(40, 1), (40, 2), (40, 37), (40, 39), (120, 64), (120, 119), (5, 0)])
+@pytest.mark.parametrize("r,k", [(40, 1), (40, 2), (40, 37), (40, 39), (120, 64), (120, 119), (5, 0), (97, 96),
+                                 (200, 150), (200, 0)])
 def test_solve_chol_reports_not_spd_mid_factorization(ctx, r, k):
     """A non-positive pivot at column k (of either step parity, including the first and the last)
     stops the factorization with NOT_SPD; a later call on the same context still works."""
