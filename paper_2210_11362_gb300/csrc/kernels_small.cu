@@ -205,17 +205,18 @@ __global__ void chain_level_kernel(const double* __restrict__ prev, int64_t nPre
 // reciprocal diagonal 1/L_jj is stored after the matrix (Lmat[r*r + j]) so the triangular solves never
 // divide.
 //
-// On this part a dependent FP64 instruction costs a sub-partition's FP64 pipe a full 64-cycle warp slot
-// whatever the active lanes, so the serial part of each column (update the next column, take its pivot,
-// scale it) is latency-bound, and slows by the pipe time of every other warp sharing its sub-partition.
-// The work is therefore split by sub-partition (warp w runs on sub-partition w mod 4):
-//   * warp 0 alone on sub-partition 0 carries the chain: at step j it updates column j+1 with column j,
-//     forms the pivot of column j+1 and scales it, holding the column in registers throughout;
-//   * the 24 warps on sub-partitions 1-3 apply column j to the trailing columns k >= j+2.  Column j+2+c
-//     (length m - c, m = r - j - 2) is paired with column r-1-c (length c + 1), so every pair is m + 1
-//     entries long: a warp takes whole pairs and its lanes run down the pair, with no lanes idle beyond
-//     the last chunk and no integer division;
-//   * the other warps of sub-partition 0 only load and store the matrix.
+// On this part the SM's FP64 unit is shared by all its warps: it completes about one warp instruction per
+// 19 cycles whatever the active lanes, and one warp issues at most one FP64 instruction per 64 cycles.
+// The serial part of each column (update the next column, take its pivot, scale it) is a chain of
+// dependent FP64 instructions, so it is latency-bound, and every FP64 instruction queued by other warps
+// delays it.  The work is split so that few warps contend with it:
+//   * warp 0 carries the chain: at step j it updates column j+1 with column j, forms the pivot of column
+//     j+1 and scales it, holding the column in registers throughout;
+//   * 24 warps (those with w mod 4 != 0, the arrangement measured fastest) apply column j to the
+//     trailing columns k >= j+2.  Column j+2+c (length m - c, m = r - j - 2) is paired with column
+//     r-1-c (length c + 1), so every pair is m + 1 entries long: a warp takes whole pairs and its lanes
+//     run down the pair, with no lanes idle beyond the last chunk and no integer division;
+//   * the remaining warps only load and store the matrix.
 // One named barrier over the 800 working threads separates the steps.
 //
 // 1/sqrt(d) for d > 0 by Newton-Raphson on f(y) = y^-2 - d, y <- y (3 - d y^2) / 2, started from the
@@ -265,7 +266,7 @@ constexpr int kCholSmemMax = 128;
 // 96: 110.7 / 94.3; 120: 170.9 / 125.1; 128: 192.5 / 127.1.
 constexpr int kCholBlockedMin = 88;
 constexpr int kCholThreads = 1024;
-constexpr int kCholWork = 800;       // warp 0 and the 24 warps of sub-partitions 1-3
+constexpr int kCholWork = 800;       // warp 0 and the 24 trailing-update warps
 constexpr int kCholTrail = 24;       // trailing-update warps
 
 __device__ __forceinline__ void chol_step_barrier() {
@@ -573,8 +574,9 @@ __global__ void __launch_bounds__(256) chol_panel_factor_kernel(double* __restri
 // G[a + Rn (i + In b)] = z[a + Rn b] (classical mode-2 folding).  Both sweeps go by 32-wide panels; a
 // panel first subtracts the finished unknowns (a matrix-vector product over the solved part) and then
 // multiplies by the diagonal block's inverse W_q (forward) or its transpose (backward): no serial
-// substitution and no division.  Four warps, one per sub-partition, carry the FP64 work (its throughput
-// is per sub-partition); all eight stage L (row stride r | 1, odd, so the transposed reads of the
+// substitution and no division.  Four warps carry the FP64 work: one warp issues at most one FP64
+// instruction per 64 cycles, and four keep the SM's shared FP64 unit (about one per 19 cycles) busy
+// with short reductions.  All eight stage L (row stride r | 1, odd, so the transposed reads of the
 // backward sweep fall on distinct banks) and the W_q in shared memory when they fit.
 template <bool kInSmem>
 __global__ void __launch_bounds__(256) chol_solve_kernel(const double* __restrict__ Lmat, const double* __restrict__ M,
