@@ -427,6 +427,33 @@ def test_plan_graph_replay_is_bitwise_equal_to_eager(ctx):
         np.testing.assert_array_equal(res, outs[0][1])
 
 
+def test_plan_bf16_split_runs_match_one_run(ctx):
+    """A reduced-precision sweep prepares the next sweep's mode 0 (its tensor-core table pre-phase and
+    Gamma-chain prefix); a run after set_cores prepares it in a prologue.  Three sweeps in one run, in
+    three runs, and again after set_cores, all give the same cores bit for bit."""
+    I, R = (40, 40, 40, 40), (8, 10, 12, 10)
+    X, init = _problem(I, R)
+    Xd = P.tensor_to_device(X, torch.float32)
+    outs = []
+    for split in (False, True):
+        plan = P.Plan(ctx, I, R, Xd, P.make_opts("bf16"))
+        plan.set_cores(init)
+        if split:
+            for _ in range(3):
+                plan.run(1, use_graph=True)
+        else:
+            plan.run(3, use_graph=True)
+        outs.append(plan.get_cores())
+        if split:
+            plan.set_cores(init)
+            plan.run(3, use_graph=True)
+            outs.append(plan.get_cores())
+        plan.close()
+    for other in outs[1:]:
+        for a, b in zip(other, outs[0]):
+            np.testing.assert_array_equal(a, b)
+
+
 def test_reconstruct_and_explicit_residual(ctx):
     for I, R in SHAPES:
         cores = TI.gaussian_cores(4, I, R)
