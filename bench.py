@@ -101,6 +101,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value, device):
+    """The largest per-rank value (the job's step time is its slowest rank's), by an all-reduce over the
+    default process group; tensors on `device` ("cuda" under NCCL, "cpu" under gloo)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ms_max, world):
+    """Whole-job sweeps/s: every rank runs its own replica of the workload (weak scaling), so the job
+    completes `world` sweeps per slowest-rank step."""
+    return world * 1000.0 / ms_max
+
+
 # ----------------------------------------------------------------------------- data
 def make_X_device(w, seed, P, torch, dtype):
     """Observed tensor on the device: X_true = TR(true cores) by the library's reconstruction
@@ -351,15 +367,13 @@ def run_ours(args):
     main = out[args.mode]
     ms = main["ms_per_step"]
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, "cuda")
     if rank != 0:
         return
     e2e = e2e_run(P, torch, w, main["X"], opts_for(P, args.mode, args), args.seed, w.sweeps)
     line = {
         "metric": METRIC,
-        "value": world * 1000.0 / ms, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
+        "value": job_rate(ms, world), "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.mode],
         "data": "synthetic",
