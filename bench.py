@@ -197,6 +197,68 @@ def time_mode(P, torch, w, X, mode, steps, warmup, seed, flush_buf, X_full, opts
             "launches_per_sweep": launches, "mttsp_kernel_ms": kern, "mttsp_ms": whole, "clocks": clk}
 
 
+def mixed_subchain_gram(cores_a, cores_b, n):
+    """C = (G_a^{!=n}_[2])^T G_b^{!=n}_[2] (r_a x r_b, columns a + R_n b) from the mixed Gram chain
+    Pi = prod over the subchain modes of sum_i A_k(i) (x) B_k(i) (the inner-product structure of the
+    paper's by-product proposition), without forming either subchain matrix."""
+    N = len(cores_a)
+    Pi = None
+    for m in [(n + t) % N for t in range(1, N)]:
+        A, B = cores_a[m], cores_b[m]
+        g = np.einsum("pis,qit->pqst", A, B).reshape(A.shape[0] * B.shape[0], A.shape[2] * B.shape[2])
+        Pi = g if Pi is None else Pi @ g
+    Ra1, Rb1 = cores_a[n].shape[2], cores_b[n].shape[2]
+    Ra0, Rb0 = cores_a[n].shape[0], cores_b[n].shape[0]
+    T = Pi.reshape(Ra1, Rb1, Ra0, Rb0).transpose(2, 0, 3, 1)      # (a, b, a', b')
+    return T.reshape(Ra0 * Ra1, Rb0 * Rb1, order="F")
+
+
+def subspace_angle(cores_a, cores_b, n):
+    """Largest principal angle (radians) between range(G^{!=n}_[2]) of two TR solutions: with the
+    Cholesky factors L_a, L_b of the two Gram matrices, the cosines are the singular values of
+    L_a^{-1} C_ab L_b^{-T}.  Gauge invariant; angles below ~1e-8 are not resolved."""
+    La = np.linalg.cholesky(mixed_subchain_gram(cores_a, cores_a, n))
+    Lb = np.linalg.cholesky(mixed_subchain_gram(cores_b, cores_b, n))
+    C = mixed_subchain_gram(cores_a, cores_b, n)
+    K = np.linalg.solve(La, np.linalg.solve(Lb, C.T).T)
+    s = np.linalg.svd(K, compute_uv=False)
+    return float(np.arccos(np.clip(s.min(), -1.0, 1.0)))
+
+
+def oracle_reference(workload, seed):
+    """The FP64 oracle's stored run of a workload (tests/golden/make_oracle_reference.py): per-sweep
+    residuals and final cores, or None when no file was written for it."""
+    path = os.path.join(ROOT, "tests", "golden", f"oracle_{workload}_seed{seed}.npz")
+    if not os.path.exists(path):
+        return None
+    z = np.load(path)
+    N = len(z["I"])
+    return {"residuals": z["residuals"], "cores": [z[f"core{n}"] for n in range(N)], "sweeps": int(z["sweeps"])}
+
+
+def accuracy_run(P, torch, w, X, X_full, mode, opts, seed, ref):
+    """The workload's own sweep count from the seeded init in `mode`, then the final relative residual
+    (explicit, against the FP64 X) and its gap to the FP64 oracle's, and the largest principal angle
+    between the subchain ranges of the two solutions over all modes."""
+    ctx = P.trals_create(0)
+    plan = P.Plan(ctx, w.I, w.R_fit, X, opts)
+    try:
+        plan.set_cores(TI.init_cores(seed, w.I, w.R_fit))
+        plan.run(ref["sweeps"], use_graph=True)
+        torch.cuda.synchronize()
+        cores = plan.get_cores()
+        r2, x2 = P.trals_residual_explicit(ctx, w.I, w.R_fit, X_full,
+                                           [plan.core_dev(n) for n in range(len(w.I))])
+    finally:
+        plan.close()
+        ctx.close()
+    res = float(np.sqrt(max(r2, 0.0) / x2))
+    angles = [subspace_angle(cores, ref["cores"], n) for n in range(len(w.I))]
+    gap = abs(res - float(ref["residuals"][-1]))
+    return {"mode": mode, "sweeps": ref["sweeps"], "residual": res, "oracle_residual": float(ref["residuals"][-1]),
+            "gap": gap, "gap_within_1e-4": gap <= 1e-4, "angle_max_rad": max(angles), "angle_per_mode_rad": angles}
+
+
 def e2e_run(P, torch, w, X_dev, opts, seed, sweeps):
     """End to end through trals_decompose with host buffers (pinned X, host cores)."""
     Xh = X_dev.cpu().pin_memory()
@@ -318,7 +380,12 @@ def _recorded_traffic(config, mode):
     return rec["bytes"]
 
 
-def roofline_for(w, mode, kernel_ms, peaks, src):
+def roofline_for(w, mode, kernel_ms, peaks, src, step_ms=None):
+    """Roofline of the RHS contraction.  ``frac`` is the main contraction kernel alone (the dominant
+    kernel: its CUDA-event time per launch); ``frac_contraction`` is the whole contraction step of a
+    core update as ``trals_plan_time_mttsp`` times it (the link of the subchain tables through the
+    core updated just before, the kernel, and the FP64 reduction of the per-CTA partials), which is
+    the figure the >= 0.60 target of the RHS contraction is compared with."""
     numel = w.numel
     N = len(w.I)
     esize = {"fp64": 8, "fp32": 4, "bf16": 2, "bf16x3": 4}[mode]
@@ -334,9 +401,17 @@ def roofline_for(w, mode, kernel_ms, peaks, src):
     achieved = N * bytes_per / t / 1e9
     peak = peaks["hbm_gbs"]
     tr = _recorded_traffic(w.name, mode)
-    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": (sum(tr) / len(tr)) if tr else None, "peak_source": f"{src} hbm_gbs (burst copy)",
-            "algorithmic_bytes_per_launch": bytes_per, "launch_ms_per_mode": kernel_ms}
+    out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "traffic": (sum(tr) / len(tr)) if tr else None, "peak_source": f"{src} hbm_gbs (burst copy)",
+           "algorithmic_bytes_per_launch": bytes_per, "launch_ms_per_mode": kernel_ms,
+           "frac_of": "the main contraction kernel alone (mttsp_tc_kernel), CUDA events on its stream"}
+    if step_ms:
+        ach_step = N * bytes_per / (sum(step_ms) * 1e-3) / 1e9
+        out.update({"achieved_contraction": ach_step, "frac_contraction": ach_step / peak,
+                    "contraction_ms_per_mode": step_ms,
+                    "frac_contraction_of": "the whole contraction step (last table link + kernel + FP64 "
+                                           "partial reduction); the >= 0.60 target applies to this one"})
+    return out
 
 
 def run_ours(args):
@@ -364,6 +439,15 @@ def run_ours(args):
         out[mode] = time_mode(P, torch, w, X, mode, steps, args.warmup, args.seed, flush, X_f64,
                               opts_for(P, mode, args))
         out[mode]["X"] = X
+    # per-config accuracy against the FP64 oracle's stored run, every mode measured above
+    ref = oracle_reference(w.name, args.seed)
+    accuracy = {}
+    for mode in out:
+        if ref is None:
+            accuracy[mode] = {"unavailable": f"no stored oracle run for {w.name} seed {args.seed}"}
+            continue
+        accuracy[mode] = accuracy_run(P, torch, w, out[mode]["X"], X_f64, mode, opts_for(P, mode, args), args.seed,
+                                      ref)
     main = out[args.mode]
     ms = main["ms_per_step"]
     if world > 1:
@@ -380,11 +464,12 @@ def run_ours(args):
         "config": {"workload": w.name, "I": list(w.I), "R_fit": list(w.R_fit), "eta": w.eta, "mode": args.mode,
                    "solver": args.solver, "gram": args.gram, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed between timed sweeps (256 MB write)", "residual_after_run": main["residual"]},
-        "roofline": roofline_for(w, args.mode, main["mttsp_kernel_ms"], peaks, src),
+        "roofline": roofline_for(w, args.mode, main["mttsp_kernel_ms"], peaks, src, main["mttsp_ms"]),
         "mttsp_ms_per_mode": main["mttsp_ms"],
         "gpu_launches": main["launches_per_sweep"] * args.steps,
         "clocks": main["clocks"],
         "e2e": e2e,
+        "accuracy": {w.name: accuracy},
     }
     if "fp64" in out and args.mode != "fp64":
         f = out["fp64"]
@@ -396,7 +481,7 @@ def run_ours(args):
         b = out["bf16x3"]
         line["bf16x3"] = {"value": 1000.0 / b["ms_per_step"], "ms_per_step": b["ms_per_step"], "steps": len(b["times"]),
                           "residual": b["residual"], "mttsp_ms_per_mode": b["mttsp_ms"],
-                          "roofline": roofline_for(w, "bf16x3", b["mttsp_kernel_ms"], peaks, src)}
+                          "roofline": roofline_for(w, "bf16x3", b["mttsp_kernel_ms"], peaks, src, b["mttsp_ms"])}
     if not args.no_serve:
         for k in list(out):
             out[k].pop("X", None)
@@ -428,12 +513,13 @@ def run_reference(args):
         t.append(time.perf_counter() - t0)
     per_update = sum(t) / len(t)
     value = 1.0 / (N * per_update)
+    # one timed step is one core update: ms_per_step x steps is the timed region
     line = {"impl": "reference", "metric": METRIC,
             "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * N * per_update, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1000.0 * per_update, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "I": list(w.I), "R_fit": list(w.R_fit), "eta": w.eta,
-                       "step": "one core update of the CPU oracle per timed step (sweeps/s = 1 / (N x mean)"},
+                       "step": "one core update of the CPU oracle per timed step (sweeps/s = 1 / (N x mean update time))"},
             "cpu_baseline": {"value": value, "unit": "sweeps/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"{args.steps} timed core updates after {args.warmup} warm-up updates"},
             "e2e": {"value": value, "unit": "sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

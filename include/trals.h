@@ -164,16 +164,16 @@ trals_status trals_plan_residuals(trals_plan* plan, double* rel_res_host, int ca
  * workspace, writing M_n (I_n x R_n R_{n+1}, FP64) to M_dev (NULL: the plan's internal buffer).
  * Allocates nothing; used to time and test the RHS contraction in isolation. */
 trals_status trals_plan_mttsp(trals_plan* plan, int n, double* M_dev);
-/* Measurement hook (the paper has no counterpart): enqueue the MTTSP of mode n once, exactly as a
- * sweep does, with CUDA events around the whole step (table builds, contraction, reduction) and
- * around its main contraction kernel alone; waits for it and returns both durations in
- * milliseconds.  The caller may flush L2 on the context's stream beforehand.  Not for use while
- * the stream is being captured. */
 /* Relative residual |X - TR(cores)|_F / |X|_F of the plan's current cores against the caller's X
  * (the explicit error of Sec. 4), by one pass over X that regenerates X_hat: in FP64 in the FP64
  * mode, in FP32 (differences and sums in FP64) in the reduced-precision modes, where the
  * regeneration error (~1e-7 relative) is far below the residuals being compared.  Synchronous. */
 trals_status trals_plan_explicit_residual(trals_plan* plan, double* rel_res_host);
+/* Measurement hook (the paper has no counterpart): enqueue the MTTSP of mode n once, exactly as a
+ * sweep does, with CUDA events around the whole step (table builds, contraction, reduction) and
+ * around its main contraction kernel alone; waits for it and returns both durations in
+ * milliseconds.  The caller may flush L2 on the context's stream beforehand.  Not for use while
+ * the stream is being captured. */
 trals_status trals_plan_time_mttsp(trals_plan* plan, int n, float* kernel_ms, float* total_ms);
 /* Device pointer of core n (FP64, layout above), valid until the plan is destroyed. */
 const double* trals_plan_core_dev(const trals_plan* plan, int n);
@@ -240,17 +240,25 @@ trals_status trals_check_pivot_rsqrt(trals_ctx* ctx, const double* d_dev, int64_
                                      double* ref_dev);
 
 /* trals_mttsp in FP64 mode (X FP64) without any device allocation, for callers that cannot allocate:
- * code running where cudaMalloc/cudaFree are unavailable or forbidden (a host callback, an allocator
- * hook that must not re-enter the CUDA allocator, a fixed-budget real-time loop, a runtime that owns
- * all device memory).  The paper has no counterpart; it is an interface convenience.  Its subchain
- * tables, offsets and per-block partial sums live in one static 32 MiB device array that every GPU
- * loading the library holds until process exit; shapes whose tables plus one block's partial sums do
- * not fit return TRALS_E_ARG with a message.  The array's address is looked up on the first call made
- * on each device (make that call before any stream capture).  All calls share the array, so calls
- * that overlap on the GPU race: serialise them on one stream.  Synchronous.  Arguments and result
- * layout as trals_mttsp. */
+ * an allocator hook that must not re-enter the CUDA allocator, a fixed-budget real-time loop whose
+ * device memory may not grow, or a runtime that owns all device memory and hands the library only
+ * its inputs and outputs.  The paper has no counterpart; it is an interface convenience.  Its
+ * subchain tables, offsets and per-block partial sums live in one static 32 MiB device array that
+ * every GPU loading the library holds until process exit; shapes whose tables plus one block's
+ * partial sums do not fit return TRALS_E_ARG with a message, as do the shapes trals_mttsp rejects.
+ * The array's device address is looked up on the first call made on each device.  The call is
+ * synchronous (it copies index offsets from host memory and waits for its stream), so it must not be
+ * made from a stream callback (cudaLaunchHostFunc, where CUDA calls are not allowed) nor while any
+ * stream is being captured.  All calls share the array, so calls that overlap on the GPU race:
+ * serialise them.  Arguments and result layout as trals_mttsp. */
 trals_status trals_mttsp_noalloc(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R, const void* X_dev,
                                  const double* const* cores_dev, int n, double* M_dev);
+
+/* Which kernel the last successful trals_mttsp call on ctx actually ran (codes of trals_mttsp_path;
+ * -1 before any call or after a failed one).  trals_mttsp takes the tensor-core kernel where
+ * trals_mttsp_path reports a geometry and the TMA descriptor encoder and X's 16-byte alignment
+ * allow it, else the CUDA cores; this query tells which happened.  Host only. */
+int trals_last_mttsp_path(const trals_ctx* ctx);
 
 /* Which kernel computes the MTTSP of mode n in `mode` (host-only query, needs no GPU):
  * 0 = CUDA cores (the FP64 path, and shapes the tensor-core kernel does not take);

@@ -207,6 +207,20 @@ def normal_equation_terms(X: np.ndarray, cores: Sequence[np.ndarray], n: int,
     return S, M
 
 
+def mttsp(X: np.ndarray, cores: Sequence[np.ndarray], n: int, block: int = 1 << 17) -> np.ndarray:
+    """M_n = X_[n] G^{!=n}_[2] (Alg. 2 lines 7-8, the tensor-times-subchain product, by its
+    definition), accumulated over row blocks of the explicit subchain matrix so that it never sits
+    in memory whole."""
+    Xn = unfold_mode(X, n)
+    J = Xn.shape[1]
+    r = cores[n].shape[0] * cores[n].shape[2]
+    M = np.zeros((Xn.shape[0], r))
+    for k0 in range(0, J, block):
+        k1 = min(J, k0 + block)
+        M += Xn[:, k0:k1] @ subchain_rows(cores, n, k0, k1)
+    return M
+
+
 def als_update(X: np.ndarray, cores: List[np.ndarray], n: int, solver: str = "qr") -> np.ndarray:
     """One TR-ALS core update (Alg. 1 lines 4-5): G_n = argmin |G^{!=n}_[2] Z^T - X_[n]^T|_F."""
     Rn, Rn1 = cores[n].shape[0], cores[n].shape[2]
@@ -372,11 +386,16 @@ def multi_ttm_mode_unfolded(X: np.ndarray, Qs: Sequence[np.ndarray], n: int) -> 
 
 def tr_als_qr(X: np.ndarray, init: Sequence[np.ndarray], sweeps: int,
               residual: bool = True) -> Tuple[List[np.ndarray], List[float]]:
-    """TR-ALS-QR (Alg. 3), literally, for small shapes only (its V_n QR costs O(R^{2N+2})).
+    """TR-ALS-QR (Alg. 3) for small shapes only (the QR of V_n costs O(R^{2N+2})).
 
-    Per core: mode-2 QR of every core; V_n = R_{n+1} [x] ... [x] R_{n-1}; mode-2 QR
-    V_n = R x_2 Q_0; Y_[n] by Multi-TTM; W_n = Y_[n] Q_0; solve G_{n(2)} R_[2]^T = W_n.
-    The solve works in the column order of G^{!=n}_[2] (r_n + R_n r_{n+1}).
+    Derivation from the least-squares problem of Sec. 3.2, min |G^{!=n}_[2] Z^T - X_[n]^T|_F:
+    with each core factored as G_j = R_j x_2 Q_j (mode-2 QR), Prop. slice_kron moves every Q_j out
+    of the subchain, G^{!=n}_[2] = (Q_{n-1} (x) ... (x) Q_{n+1}) V_n[2] with V_n the subchain of the
+    R_j; a QR V_n[2] = Q_0 R makes G^{!=n}_[2] = Q R with Q = (Q_{n-1} (x) ... (x) Q_{n+1}) Q_0
+    orthonormal.  The least-squares solution then solves R Z^T = Q^T X_[n]^T = W_n^T, where
+    W_n = (X_[n] (Q_{n-1} (x) ... (x) Q_{n+1})) Q_0 = Y_[n] Q_0 and Y = X x_{j!=n} Q_j^T (Prop. ttm).
+    Columns follow G^{!=n}_[2] (r_n + R_n r_{n+1}).  tests/test_oracle_pins.py checks the result
+    against the Householder least-squares solution on the explicit subchain matrix.
     """
     cores = [np.array(G, dtype=np.float64, copy=True) for G in init]
     N = len(cores)

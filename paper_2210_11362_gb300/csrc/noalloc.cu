@@ -1,18 +1,19 @@
 // trals_mttsp_noalloc: the FP64 MTTSP (the CUDA-core kernel behind trals_mttsp in FP64 mode) for
 // callers that must not allocate device memory.
 //
-// Who needs it: code that runs where cudaMalloc/cudaFree are unavailable or forbidden, for example a
-// host callback or a custom allocator hook that must not re-enter the CUDA allocator, a real-time
-// loop with a fixed memory budget that may not grow, or an embedding runtime that owns all device
-// memory itself.  trals_mttsp allocates its subchain tables, offsets and per-block partial sums on
-// every call; this variant places them in one static device array instead.
+// Who needs it: code that may not call cudaMalloc/cudaFree, for example a custom allocator hook
+// that must not re-enter the CUDA allocator, a real-time loop with a fixed memory budget that may
+// not grow, or an embedding runtime that owns all device memory itself and passes the library only
+// its inputs and outputs.  trals_mttsp allocates its subchain tables, offsets and per-block partial
+// sums on every call; this variant places them in one static device array instead.
 //
 // The scratch array (kNoAllocScratchBytes) exists on every GPU that loads the library, from load to
 // process exit.  Its device address is looked up once per device with cudaGetSymbolAddress on the
-// first call made while that device is current; make that first call before any stream capture.
-// Every call shares the array: concurrent or overlapping calls on the GPU race, so issue calls on one
-// stream (or otherwise serialise them).  Nothing in the array needs to start at zero: each call
-// rewrites every table entry, offset and partial sum it reads.
+// first call made while that device is current.  The call is synchronous: it copies the index
+// offsets from host memory and waits for its stream, so it is not for stream callbacks (where CUDA
+// calls are not allowed) nor for a stream that is being captured.  Every call shares the array:
+// calls that overlap on the GPU race, so serialise them.  Nothing in the array needs to start at
+// zero: each call rewrites every table entry, offset and partial sum it reads.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -28,7 +29,11 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 void* g_scratch_addr[kMaxDevices] = {};
 
-size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+constexpr size_t kSat = ~(size_t)0;
+// products and sums that stick at SIZE_MAX instead of wrapping
+size_t mul_sat(size_t a, size_t b) { return (a != 0 && b > kSat / a) ? kSat : a * b; }
+size_t add_sat(size_t a, size_t b) { return b > kSat - a ? kSat : a + b; }
+size_t align256(size_t b) { return b > kSat - 255 ? kSat : (b + 255) & ~(size_t)255; }
 
 }  // namespace
 
@@ -36,26 +41,33 @@ extern "C" trals_status trals_mttsp_noalloc(trals_ctx* ctx, int N, const int64_t
                                             const void* X_dev, const double* const* cores_dev, int n,
                                             double* M_dev) {
   using namespace trals;
-  if (!ctx || !I || !R || !X_dev || !cores_dev || !M_dev || N < 3 || N > TRALS_MAX_ORDER || n < 0 || n >= N)
+  if (!ctx) return TRALS_E_ARG;
+  if (!X_dev || !cores_dev || !M_dev) {
+    ctx->last_error = "trals_mttsp_noalloc: null buffer";
     return TRALS_E_ARG;
-  for (int k = 0; k < N; ++k) {
-    if (I[k] < 1 || R[k] < 1 || R[k] > 64) {
-      ctx->last_error = "trals_mttsp_noalloc: invalid mode size or rank";
-      return TRALS_E_ARG;
-    }
   }
-  if (ctx->device < 0 || ctx->device >= kMaxDevices) return TRALS_E_ARG;
-  // size check first: a shape that does not fit is rejected before any CUDA call
+  // the shapes trals_mttsp accepts, no others (this also caps prod I_n at 2^46)
+  const trals_status st = check_shape(ctx, N, I, R);
+  if (st != TRALS_OK) return st;
+  if (n < 0 || n >= N) {
+    ctx->last_error = "trals_mttsp_noalloc: mode index out of range";
+    return TRALS_E_ARG;
+  }
+  if (ctx->device < 0 || ctx->device >= kMaxDevices) {
+    ctx->last_error = "trals_mttsp_noalloc: device index beyond the supported range";
+    return TRALS_E_ARG;
+  }
+  // size check first, in saturating arithmetic: a shape that does not fit is rejected before any
+  // CUDA call, and no wrapped product can pass the comparison
   const ModeLayout L = make_mode_layout(N, I, R, n);
-  const int64_t tab = table_level_max_elems(L, I, R);
-  const size_t tab_b = align256((size_t)tab * sizeof(double));
-  const size_t offL_b = align256((size_t)L.nL * sizeof(int64_t));
-  const size_t offU_b = align256((size_t)L.nU * sizeof(int64_t));
-  const size_t fixed = 3 * tab_b + offL_b + offU_b;
-  const size_t per_block = (size_t)(L.In * L.Rn * L.Rn1) * sizeof(double);
-  if (fixed + per_block > kNoAllocScratchBytes) {
+  const size_t tab_b = align256(mul_sat((size_t)table_level_max_elems(L, I, R), sizeof(double)));
+  const size_t offL_b = align256(mul_sat((size_t)L.nL, sizeof(int64_t)));
+  const size_t offU_b = align256(mul_sat((size_t)L.nU, sizeof(int64_t)));
+  const size_t fixed = add_sat(add_sat(mul_sat(3, tab_b), offL_b), offU_b);
+  const size_t per_block = mul_sat(mul_sat((size_t)L.In, (size_t)L.Rn * L.Rn1), sizeof(double));
+  if (add_sat(fixed, per_block) > kNoAllocScratchBytes) {
     ctx->last_error = "trals_mttsp_noalloc: the subchain tables and one block's partial sums need " +
-                      std::to_string(fixed + per_block) + " bytes, more than the " +
+                      std::to_string(add_sat(fixed, per_block)) + " bytes, more than the " +
                       std::to_string(kNoAllocScratchBytes) + "-byte static scratch (use trals_mttsp)";
     return TRALS_E_ARG;
   }

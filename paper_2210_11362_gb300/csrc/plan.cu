@@ -52,38 +52,6 @@ std::string fmt(const char* f, long long a = 0, long long b = 0, long long c = 0
   return buf;
 }
 
-trals_status check_shape(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R) {
-  if (N < 3 || N > TRALS_MAX_ORDER) {
-    ctx->last_error = fmt("order N=%lld outside [3, %lld]", N, TRALS_MAX_ORDER);
-    return TRALS_E_ARG;
-  }
-  if (!I || !R) {
-    ctx->last_error = "null shape or rank array";
-    return TRALS_E_ARG;
-  }
-  for (int n = 0; n < N; ++n) {
-    if (I[n] < 1 || R[n] < 1 || R[n] > 64) {
-      ctx->last_error = fmt("mode %lld: I=%lld R=%lld (need I>=1, 1<=R<=64)", n, I[n], R[n]);
-      return TRALS_E_ARG;
-    }
-  }
-  for (int n = 0; n < N; ++n) {
-    int64_t J = 1;
-    for (int j = 0; j < N; ++j)
-      if (j != n) J *= I[j];
-    const int64_t r = (int64_t)R[n] * R[(n + 1) % N];
-    if (r > 256) {
-      ctx->last_error = fmt("mode %lld: R_n R_{n+1} = %lld exceeds 256", n, r);
-      return TRALS_E_ARG;
-    }
-    if (J < r) {
-      ctx->last_error = fmt("mode %lld: J_n=%lld < R_n R_{n+1}=%lld (underdetermined subproblem)", n, J, r);
-      return TRALS_E_ARG;
-    }
-  }
-  return TRALS_OK;
-}
-
 trals_status read_status(trals_ctx* ctx) {
   DevStatus st{};
   cudaError_t e = cudaMemcpyAsync(&st, ctx->d_status, sizeof st, cudaMemcpyDeviceToHost, ctx->stream);
@@ -111,6 +79,50 @@ trals_status read_status(trals_ctx* ctx) {
 
 // ------------------------------------------------------------------ plan
 namespace trals {
+trals_status check_shape(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R) {
+  if (N < 3 || N > TRALS_MAX_ORDER) {
+    ctx->last_error = fmt("order N=%lld outside [3, %lld]", N, TRALS_MAX_ORDER);
+    return TRALS_E_ARG;
+  }
+  if (!I || !R) {
+    ctx->last_error = "null shape or rank array";
+    return TRALS_E_ARG;
+  }
+  for (int n = 0; n < N; ++n) {
+    if (I[n] < 1 || R[n] < 1 || R[n] > 64) {
+      ctx->last_error = fmt("mode %lld: I=%lld R=%lld (need I>=1, 1<=R<=64)", n, I[n], R[n]);
+      return TRALS_E_ARG;
+    }
+  }
+  {
+    // every size computed from the shape (element counts, table and workspace bytes) stays far from
+    // int64 overflow: prod I_n is capped at 2^46 elements, beyond any device memory
+    int64_t numel = 1;
+    for (int n = 0; n < N; ++n) {
+      if (I[n] > ((int64_t)1 << 46) / numel) {
+        ctx->last_error = "prod I_n exceeds 2^46 elements";
+        return TRALS_E_ARG;
+      }
+      numel *= I[n];
+    }
+  }
+  for (int n = 0; n < N; ++n) {
+    int64_t J = 1;
+    for (int j = 0; j < N; ++j)
+      if (j != n) J *= I[j];
+    const int64_t r = (int64_t)R[n] * R[(n + 1) % N];
+    if (r > 256) {
+      ctx->last_error = fmt("mode %lld: R_n R_{n+1} = %lld exceeds 256", n, r);
+      return TRALS_E_ARG;
+    }
+    if (J < r) {
+      ctx->last_error = fmt("mode %lld: J_n=%lld < R_n R_{n+1}=%lld (underdetermined subproblem)", n, J, r);
+      return TRALS_E_ARG;
+    }
+  }
+  return TRALS_OK;
+}
+
 cudaError_t init_kernel_attributes() {
   cudaError_t e = init_small_attributes();
   if (e == cudaSuccess) e = init_simt_attributes();
@@ -1199,6 +1211,7 @@ trals_status trals_qr_r_factor(trals_ctx* ctx, int N, const int64_t* I, const in
 trals_status trals_mttsp(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R, const void* X_dev, int xt,
                          int mode, const double* const* cores_dev, int n, double* M_dev) {
   if (!ctx || !X_dev || !cores_dev || !M_dev || n < 0 || n >= N) return TRALS_E_ARG;
+  ctx->last_mttsp_path = -1;
   trals_status st = check_shape(ctx, N, I, R);
   if (st != TRALS_OK) return st;
   const bool ok_type = (mode == TRALS_MODE_FP64 && xt == TRALS_X_F64) || (mode == TRALS_MODE_FP32 && xt == TRALS_X_F32) ||
@@ -1218,12 +1231,16 @@ trals_status trals_mttsp(trals_ctx* ctx, int N, const int64_t* I, const int32_t*
       (mode != TRALS_MODE_FP64) ? tc_plan(tc, N, I, R, n, mode, X_dev, numel, &e, ctx->stream, nullptr, 0, Xlo) : 0;
   TRALS_CUDA_TRY(ctx, e);
   if (use_tc) {
+    const int variant = tc_variant(tc);
     tc_set_status(tc, ctx->d_status);
     tc_enqueue(tc, X_dev, const_cast<double* const*>(cores_dev), M_dev, s);
     e = cudaStreamSynchronize(s);
     tc_destroy(tc);
     TRALS_CUDA_TRY(ctx, e);
     TRALS_CUDA_TRY(ctx, cudaGetLastError());
+    st = read_status(ctx);
+    if (st != TRALS_OK) return st;
+    ctx->last_mttsp_path = variant + 1;
     return TRALS_OK;
   }
   const ModeLayout L = make_mode_layout(N, I, R, n);
@@ -1276,8 +1293,11 @@ trals_status trals_mttsp(trals_ctx* ctx, int N, const int64_t* I, const int32_t*
   cudaFree(dL);
   cudaFree(dU);
   TRALS_CUDA_TRY(ctx, e);
+  ctx->last_mttsp_path = 0;
   return TRALS_OK;
 }
+
+int trals_last_mttsp_path(const trals_ctx* ctx) { return ctx ? ctx->last_mttsp_path : -1; }
 
 int trals_mttsp_path(int N, const int64_t* I, const int32_t* R, int n, int mode) {
   if (N < 3 || N > TRALS_MAX_ORDER || !I || !R || n < 0 || n >= N) return -1;

@@ -34,6 +34,10 @@ __device__ __forceinline__ void set_status(DevStatus* st, int code, int sweep, i
   }
 }
 
+// Validate a shape for every entry point: 3 <= N <= TRALS_MAX_ORDER, I_n >= 1, 1 <= R_n <= 64,
+// prod I_n <= 2^46, R_n R_{n+1} <= 256 and J_n >= R_n R_{n+1}.  Sets ctx->last_error on failure.
+trals_status check_shape(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R);
+
 // ---------------------------------------------------------------- per-mode MTTSP layout
 // The other modes of mode n in subchain order c_1..c_{N-1} = n+1..N,1..n-1 (eq. subchain_new)
 // are split into Left = c_1..c_m and Right = c_{m+1}..c_{N-1}.  G^{!=n}(k) = L(l) U(u) with
@@ -229,6 +233,7 @@ struct trals_ctx {
   std::string last_error;
   trals::DevStatus* d_status = nullptr;   // per-context device status word
   int* d_zero_ctr = nullptr;              // a device int holding 0 (sweep counter for one-off calls)
+  int last_mttsp_path = -1;               // kernel the last trals_mttsp call ran (trals_mttsp_path codes)
 };
 
 #define TRALS_CUDA_TRY(ctx, call)                                                        \

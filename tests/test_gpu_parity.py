@@ -203,81 +203,164 @@ TC_SHAPES = [
     ((40, 40, 40, 32, 4), (4, 5, 6, 5, 4)),    # order 5: K-major tiles with a large table and with mid modes
 ]
 
-
-@pytest.mark.parametrize("I,R", TC_SHAPES)
-def test_mttsp_bf16_tensor_cores_match_oracle(ctx, I, R):
-    """BF16 X, subchain factors in BF16 (stage 1) / FP32 (stage 2), FP32 accumulation: the result
-    matches X_bf16 G^{!=n} in FP64 to within the BF16 rounding of the factors (normwise 4e-3)."""
-    X, _ = _problem(I, R)
-    cores = TI.gaussian_cores(9, I, R)
-    Xb = P.tensor_to_device(X, torch.bfloat16)
-    Xq = TI.unflat_f(Xb.float().cpu().numpy().astype(np.float64), I)
-    cd = [P.core_to_device(G) for G in cores]
-    N = len(I)
-    for n in range(N):
-        assert P.trals_mttsp_path(I, R, n, "bf16") > 0
-        r = R[n] * R[(n + 1) % N]
-        M = torch.zeros(I[n] * r, dtype=torch.float64, device="cuda")
-        P.trals_mttsp(ctx, I, R, Xb, "bf16", cd, n, M)
-        ref = O.unfold_mode(Xq, n) @ O.subchain_unfolded(cores, n)
-        got = M.cpu().numpy().reshape(I[n], r, order="F")
-        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-        assert err < 4e-3, (n, P.MTTSP_PATHS[P.trals_mttsp_path(I, R, n, "bf16")], err)
+# Componentwise error bound of the reduced-precision MTTSP against M_ref = X_q G^{!=n}_[2] in FP64
+# (X_q: the BF16, or hi + lo, values the kernel reads):
+#   |M - M_ref| <= (c u + (N - 2)(R_max + 1) 2^-24 + lambda sqrt(J_n) 2^-24) (|X_q,[n]| |G|^{!=n}_[2])
+# where |G|^{!=n} is the subchain of the elementwise absolute cores, an upper bound of |F| |Tab| for any
+# split of the chain into the stage-1 table Tab and the stage-2 factor F.
+#  - c u: the storage rounding of the stage-1 table: RNE to BF16 (2^-9 relative) with u = 2^-8 and
+#    c = 1; for the split-BF16 mode the dropped lo x lo product and the rounding of the lo planes
+#    (2 x 2^-18) with u = 2^-16 and c = 1;
+#  - (N - 2)(R_max + 1) 2^-24: the FP32 chain products that build the table and the factor;
+#  - lambda sqrt(J_n) 2^-24: the FP32 accumulation over the J_n terms, by the probabilistic bound of
+#    Higham & Mary (SIAM J. Sci. Comput. 2019) with lambda = 10 (failure probability below 1e-15).
+U_BF16, U_BF16X3, LAMBDA_FP32 = 2.0 ** -8, 2.0 ** -16, 10.0
 
 
-@pytest.mark.parametrize("I,R", [((41, 39, 47, 33), (3, 4, 2, 5)), ((60, 60, 60, 60), (10, 10, 10, 10)),
-                                 ((45, 53, 64, 55, 36), (7, 2, 3, 5, 4))])
-def test_plan_mttsp_bf16_with_padded_leading_mode(ctx, I, R):
-    """A plan stores the BF16 copy of X with mode 0 zero-padded to a multiple of 8 so that the
-    tensor-core geometries apply; M_n of every mode (including mode 0, whose padded rows are
-    dropped) matches X_bf16 G^{!=n} within the BF16 rounding of the factors (normwise 4e-3)."""
-    X, _ = _problem(I, R)
-    cores = TI.gaussian_cores(9, I, R)
-    Xf = P.tensor_to_device(X, torch.float32)
-    Xq = TI.unflat_f(Xf.to(torch.bfloat16).double().cpu().numpy(), I)
-    plan = P.Plan(ctx, I, R, Xf, P.make_opts("bf16"))
-    try:
-        plan.set_cores(cores)
-        N = len(I)
-        paths = [plan.mttsp_path(n) for n in range(N)]
-        assert sum(p_ > 0 for p_ in paths) >= N - 2, paths
-        for n in range(N):
-            r = R[n] * R[(n + 1) % N]
-            M = torch.zeros(I[n] * r, dtype=torch.float64, device="cuda")
-            plan.mttsp(n, M)
-            torch.cuda.synchronize()
-            ref = O.unfold_mode(Xq, n) @ O.subchain_unfolded(cores, n)
-            got = M.cpu().numpy().reshape(I[n], r, order="F")
-            err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-            assert err < 4e-3, (n, paths[n], err)
-    finally:
-        plan.close()
+def componentwise_tol(Xq, cores, n, u, c=1.0):
+    N = len(cores)
+    J = Xq.size // Xq.shape[n]
+    Rmax = max(G.shape[0] for G in cores)
+    B = O.mttsp(np.abs(Xq), [np.abs(G) for G in cores], n)
+    return (c * u + (N - 2) * (Rmax + 1) * 2.0 ** -24 + LAMBDA_FP32 * np.sqrt(J) * 2.0 ** -24) * B
 
 
-@pytest.mark.parametrize("I,R", TC_SHAPES)
-def test_mttsp_bf16x3_tensor_cores_match_oracle(ctx, I, R):
-    """bf16x3 on the tensor cores: X and the stage-1 table split into hi/lo BF16 pairs, three BF16
-    products per K step into FP32.  The result matches X_[n] G^{!=n} (with X = hi + lo) to the
-    split-BF16 rounding, about 2^-16 relative per factor (normwise 5e-5, i.e. ~80x tighter than
-    the single-BF16 bar)."""
-    X, _ = _problem(I, R)
-    cores = TI.gaussian_cores(9, I, R)
+def _integer_problem(I, R, seed=5):
+    """Small-integer X and signed-selection cores: every product and sum of the reduced-precision
+    MTTSP is an exact integer in BF16/FP32, so the result must equal the FP64 oracle exactly."""
+    return TI.small_integer_tensor(seed, I), TI.signed_selection_cores(seed, I, R)
+
+
+def _mode_input(ctx, X, mode):
+    """The device X a mode reads: BF16, or the hi and lo BF16 halves of split-BF16 (2 prod(I) values),
+    with the FP64 values they hold."""
+    I = X.shape
     numel = int(np.prod(I))
+    if mode == "bf16":
+        Xb = P.tensor_to_device(X, torch.bfloat16)
+        return Xb, TI.unflat_f(Xb.double().cpu().numpy(), I)
     Xd = P.tensor_to_device(X)
     hl = torch.zeros(2 * numel, dtype=torch.bfloat16, device="cuda")
     P.trals_quantize_bf16(ctx, Xd, hl[:numel], hl[numel:])
-    Xq = TI.unflat_f(hl[:numel].double().cpu().numpy() + hl[numel:].double().cpu().numpy(), I)
-    cd = [P.core_to_device(G) for G in cores]
-    N = len(I)
-    for n in range(N):
-        assert P.trals_mttsp_path(I, R, n, "bf16x3") > 0
-        r = R[n] * R[(n + 1) % N]
-        M = torch.zeros(I[n] * r, dtype=torch.float64, device="cuda")
-        P.trals_mttsp(ctx, I, R, hl, "bf16x3", cd, n, M)
-        ref = O.unfold_mode(Xq, n) @ O.subchain_unfolded(cores, n)
-        got = M.cpu().numpy().reshape(I[n], r, order="F")
+    return hl, TI.unflat_f(hl[:numel].double().cpu().numpy() + hl[numel:].double().cpu().numpy(), I)
+
+
+def _run_mttsp(ctx, I, R, Xdev, mode, cores, n):
+    r = R[n] * R[(n + 1) % len(I)]
+    M = torch.full((I[n] * r,), float("nan"), dtype=torch.float64, device="cuda")
+    P.trals_mttsp(ctx, I, R, Xdev, mode, [P.core_to_device(G) for G in cores], n, M)
+    return M.cpu().numpy().reshape(I[n], r, order="F"), P.trals_last_mttsp_path(ctx)
+
+
+@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("I,R", TC_SHAPES)
+def test_mttsp_tensor_cores_exact_on_integer_data(ctx, I, R, mode):
+    """On data where every intermediate is exact (small-integer X, subchain entries in {-1, 0, 1})
+    the tensor-core MTTSP must give the FP64 oracle's M_n bit for bit: any wrong row, column,
+    factor or K step shows as an integer difference.  The kernel that ran is the tensor-core one."""
+    X, cores = _integer_problem(I, R)
+    Xdev, Xq = _mode_input(ctx, X, mode)
+    assert np.array_equal(Xq, X)
+    for n in range(len(I)):
+        got, path = _run_mttsp(ctx, I, R, Xdev, mode, cores, n)
+        assert path == P.trals_mttsp_path(I, R, n, mode) > 0, (n, path)
+        ref = O.mttsp(X, cores, n)
+        assert np.array_equal(got, ref), (n, P.MTTSP_PATHS[path], np.abs(got - ref).max())
+
+
+@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("I,R", TC_SHAPES)
+def test_mttsp_tensor_cores_componentwise_bound(ctx, I, R, mode):
+    """Gaussian data: every element of M_n within the componentwise bound above (and normwise
+    within 4e-3 for BF16, 5e-5 for split-BF16), on the tensor-core kernel."""
+    X, _ = _problem(I, R)
+    cores = TI.gaussian_cores(9, I, R)
+    Xdev, Xq = _mode_input(ctx, X, mode)
+    u, normwise = (U_BF16, 4e-3) if mode == "bf16" else (U_BF16X3, 5e-5)
+    for n in range(len(I)):
+        got, path = _run_mttsp(ctx, I, R, Xdev, mode, cores, n)
+        assert path == P.trals_mttsp_path(I, R, n, mode) > 0, (n, path)
+        ref = O.mttsp(Xq, cores, n)
+        tol = componentwise_tol(Xq, cores, n, u)
+        ratio = float((np.abs(got - ref) / tol).max())
+        assert ratio <= 1.0, (n, P.MTTSP_PATHS[path], ratio)
         err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-        assert err < 5e-5, (n, P.MTTSP_PATHS[P.trals_mttsp_path(I, R, n, "bf16x3")], err)
+        assert err < normwise, (n, P.MTTSP_PATHS[path], err)
+
+
+PADDED_SHAPES = [((41, 39, 47, 33), (3, 4, 2, 5)), ((60, 60, 60, 60), (10, 10, 10, 10)),
+                 ((45, 53, 64, 55, 36), (7, 2, 3, 5, 4))]
+
+
+@pytest.mark.parametrize("I,R", PADDED_SHAPES)
+def test_plan_mttsp_bf16_with_padded_leading_mode(ctx, I, R):
+    """A plan stores the BF16 copy of X with mode 0 zero-padded to a multiple of 8 so that the
+    tensor-core geometries apply; M_n of every mode (including mode 0, whose padded rows are
+    dropped) is within the componentwise bound of X_bf16 G^{!=n} element by element, and exactly
+    equal to it on integer data."""
+    N = len(I)
+    for exact in (False, True):
+        if exact:
+            X, cores = _integer_problem(I, R)
+        else:
+            X, _ = _problem(I, R)
+            cores = TI.gaussian_cores(9, I, R)
+        Xf = P.tensor_to_device(X, torch.float32)
+        Xq = TI.unflat_f(Xf.to(torch.bfloat16).double().cpu().numpy(), I)
+        plan = P.Plan(ctx, I, R, Xf, P.make_opts("bf16"))
+        try:
+            plan.set_cores(cores)
+            paths = [plan.mttsp_path(n) for n in range(N)]
+            assert paths == [P.trals_mttsp_path(I, R, n, "bf16") for n in range(N)]
+            assert sum(p_ > 0 for p_ in paths) >= N - 2, paths
+            for n in range(N):
+                r = R[n] * R[(n + 1) % N]
+                M = torch.full((I[n] * r,), float("nan"), dtype=torch.float64, device="cuda")
+                plan.mttsp(n, M)
+                torch.cuda.synchronize()
+                got = M.cpu().numpy().reshape(I[n], r, order="F")
+                ref = O.mttsp(Xq, cores, n)
+                if exact:
+                    assert np.array_equal(got, ref), (n, paths[n], np.abs(got - ref).max())
+                else:
+                    ratio = float((np.abs(got - ref) / componentwise_tol(Xq, cores, n, U_BF16)).max())
+                    assert ratio <= 1.0, (n, paths[n], ratio)
+        finally:
+            plan.close()
+
+
+def test_plan_mttsp_full_size_40x5(ctx):
+    """The 40^5 workload shape, R = (8,10,12,10,8), through the plan exactly as a sweep runs it,
+    every mode on its tensor-core geometry (mode 0 MN-major with whole-tile work shares):
+    integer data must match the FP64 oracle exactly; Gaussian data must stay within the
+    componentwise bound in the MN-major (0) and K-major-right (4) modes."""
+    I, R = (40,) * 5, (8, 10, 12, 10, 8)
+    for exact, modes in ((True, range(5)), (False, (0, 4))):
+        if exact:
+            X, cores = _integer_problem(I, R, seed=6)
+        else:
+            X = TI.gaussian_noise(6, I)
+            cores = TI.gaussian_cores(6, I, R)
+        Xf = P.tensor_to_device(X, torch.float32)
+        Xq = TI.unflat_f(Xf.to(torch.bfloat16).double().cpu().numpy(), I)
+        plan = P.Plan(ctx, I, R, Xf, P.make_opts("bf16"))
+        try:
+            plan.set_cores(cores)
+            assert [plan.mttsp_path(n) for n in range(5)] == [3, 3, 1, 1, 2]
+            for n in modes:
+                r = R[n] * R[(n + 1) % 5]
+                M = torch.full((I[n] * r,), float("nan"), dtype=torch.float64, device="cuda")
+                plan.mttsp(n, M)
+                torch.cuda.synchronize()
+                got = M.cpu().numpy().reshape(I[n], r, order="F")
+                ref = O.mttsp(Xq, cores, n)
+                if exact:
+                    assert np.array_equal(got, ref), (n, np.abs(got - ref).max())
+                else:
+                    ratio = float((np.abs(got - ref) / componentwise_tol(Xq, cores, n, U_BF16)).max())
+                    assert ratio <= 1.0, (n, ratio)
+        finally:
+            plan.close()
 
 
 def test_solve_chol_matches_oracle(ctx):

@@ -31,3 +31,26 @@ def test_mttsp_path_pads_the_leading_mode_and_falls_back_when_too_large():
 def test_mttsp_path_rejects_bad_arguments():
     assert P.trals_mttsp_path((4, 4), (2, 2), 0, "bf16") < 0
     assert P.trals_mttsp_path((4, 4, 4), (2, 2, 2), 3, "bf16") < 0
+
+
+def test_bench_subspace_angle_matches_the_oracle():
+    """The bench's gauge-invariant angle (mixed Gram chains, no subchain matrix) against the oracle's
+    explicit QR-based principal angle, and its mixed Gram against the explicit A^T B."""
+    import numpy as np
+
+    import bench
+    import oracle as O
+    import trals_inputs as TI
+
+    I, R = (6, 5, 7, 4), (2, 3, 2, 3)
+    a = TI.gaussian_cores(1, I, R)
+    rng = np.random.default_rng(2)
+    b = [G + 0.05 * rng.standard_normal(G.shape) for G in a]
+    for n in range(4):
+        C = bench.mixed_subchain_gram(a, b, n)
+        np.testing.assert_allclose(C, O.subchain_unfolded(a, n).T @ O.subchain_unfolded(b, n), rtol=1e-12,
+                                   atol=1e-12 * np.abs(C).max())
+        ang = bench.subspace_angle(a, b, n)
+        assert ang > 1e-4
+        assert abs(ang - O.subchain_principal_angle(a, b, n)) < 1e-9
+        assert bench.subspace_angle(a, a, n) < 1e-6

@@ -249,6 +249,38 @@ def test_normal_equations_blockwise_match_explicit():
         np.testing.assert_allclose(M, O.unfold_mode(X, n) @ A, rtol=1e-12, atol=1e-10)
 
 
+def test_mttsp_blockwise_matches_model_identity():
+    """O.mttsp (blockwise over subchain rows) against two independent facts: the explicit product
+    X_[n] G^{!=n}_[2] for any X, and, for an exact TR tensor X = TR(cores), the ALS model identity
+    X_[n] = G_{n(2)} (G^{!=n}_[2])^T, which gives M_n = G_{n(2)} S_n with S_n the structured
+    coefficient matrix of Prop. subchain_gram (chained Gram tensors, no subchain matrix)."""
+    X, init = _small_problem()
+    for n in range(4):
+        A = O.subchain_unfolded(init, n)
+        np.testing.assert_allclose(O.mttsp(X, init, n, block=7), O.unfold_mode(X, n) @ A, rtol=1e-12, atol=1e-10)
+        Xt = O.tr_full(init)
+        S = O.paper_coefficient_matrix(init, n)
+        want = O.core_unfold2(init[n]) @ S
+        np.testing.assert_allclose(O.mttsp(Xt, init, n, block=5), want, rtol=1e-10, atol=1e-9 * np.abs(want).max())
+
+
+def test_signed_selection_cores_keep_subchain_entries_ternary():
+    """The exact-arithmetic GPU tests rely on every subchain entry of these cores being -1, 0 or +1
+    with at most one nonzero per row of each G^{!=n}(k) (brute force through the oracle)."""
+    I, R = (5, 4, 6, 3), (3, 4, 2, 5)
+    cores = TI.signed_selection_cores(3, I, R)
+    for G in cores:
+        assert set(np.unique(G)) <= {-1.0, 0.0, 1.0}
+        assert (np.abs(G).sum(axis=2) <= 1).all()
+    for n in range(4):
+        T = O.subchain_tensor(cores, n)          # (R_{n+1}, J, R_n)
+        assert set(np.unique(T)) <= {-1.0, 0.0, 1.0}
+        assert (np.abs(T).sum(axis=2) <= 1).all()
+        assert np.count_nonzero(T) > 0
+    X = TI.small_integer_tensor(3, I, amp=8)
+    assert np.array_equal(X, np.round(X)) and np.abs(X).max() <= 8
+
+
 def test_ne_and_qr_agree_after_one_sweep():
     X, init = _small_problem()
     c_qr, _ = O.tr_als(X, init, 1, "qr", residual=False)

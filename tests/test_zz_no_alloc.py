@@ -57,3 +57,20 @@ def test_noalloc_rejects_shapes_beyond_the_scratch():
         P.trals_mttsp_noalloc(ctx, I, R, Xd, cd, 0, M)
     assert e.value.status == P.E_ARG and "static scratch" in str(e.value)
     ctx.close()
+
+
+def test_noalloc_rejects_what_the_allocating_entry_point_rejects():
+    """R_n R_{n+1} = 400 > 256 (and other invalid shapes): trals_mttsp refuses them, and so does the
+    no-allocation variant, with the same status, before any CUDA call."""
+    ctx = P.trals_create(0)
+    Xd = torch.zeros(1, dtype=torch.float64, device="cuda")
+    cd = [torch.zeros(1, dtype=torch.float64, device="cuda") for _ in range(3)]
+    M = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for I, R, n in (((30, 30, 30), (20, 20, 20), 0), ((2, 2, 2), (3, 3, 3), 1), ((4, 4), (2, 2), 0),
+                    ((1 << 20, 1 << 20, 1 << 20), (2, 2, 2), 0), ((8, 8, 8), (2, 2, 2), 3)):
+        for call in (lambda: P.trals_mttsp(ctx, I, R, Xd, "fp64", cd[:len(I)], n, M),
+                     lambda: P.trals_mttsp_noalloc(ctx, I, R, Xd, cd[:len(I)], n, M)):
+            with pytest.raises(P.TralsError) as e:
+                call()
+            assert e.value.status == P.E_ARG, (I, R, n)
+    ctx.close()

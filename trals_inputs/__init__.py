@@ -198,6 +198,35 @@ def collinear_cores(seed: int, I: Sequence[int], R: Sequence[int], gamma: float,
     return out
 
 
+def signed_selection_cores(seed: int, I: Sequence[int], R: Sequence[int], dead: float = 0.15,
+                           stream: int = STREAM_TRUE_CORES) -> List[np.ndarray]:
+    """Cores whose lateral slices G_n(i) (R_n x R_{n+1}) hold at most one nonzero per row, +1 or -1
+    at a uniformly drawn column; a row is all zero with probability ``dead``.  Every product of such
+    slices has the same form, so all subchain entries are -1, 0 or +1: exact in BF16 and FP32.  With
+    small-integer data every sum of the RHS contraction is then an exact integer in FP32, which makes
+    reduced-precision kernels comparable element by element, without tolerance, to an FP64
+    reference.  Pure sampling: no tensor-ring arithmetic."""
+    g = _rng(seed, stream)
+    N = len(I)
+    out = []
+    for n in range(N):
+        Rn, In, Rn1 = int(R[n]), int(I[n]), int(R[(n + 1) % N])
+        G = np.zeros((Rn, In, Rn1))
+        col = g.integers(0, Rn1, size=(Rn, In))
+        sign = np.where(g.random((Rn, In)) < 0.5, -1.0, 1.0)
+        live = g.random((Rn, In)) >= dead
+        a, i = np.nonzero(live)
+        G[a, i, col[a, i]] = sign[a, i]
+        out.append(G)
+    return out
+
+
+def small_integer_tensor(seed: int, I: Sequence[int], amp: int = 8) -> np.ndarray:
+    """iid integers uniform in [-amp, amp] (float64, shape I): exactly representable in BF16 for
+    amp <= 256."""
+    return _rng(seed, STREAM_NOISE).integers(-amp, amp + 1, size=tuple(int(i) for i in I)).astype(np.float64)
+
+
 def request_stream(seed: int, count: int = 512, rate_hz: float = 200.0, order_range=(3, 5),
                    size_range=(16, 64), rank_range=(2, 8), sweeps: int = 15, eta: float = 1e-2) -> List[Request]:
     """Poisson arrivals at ``rate_hz``; order, mode sizes and ranks drawn uniformly per request."""
