@@ -137,6 +137,12 @@ def make_X_device(w, seed, P, torch, dtype):
     return X.to(dtype)
 
 
+def workload_config(w):
+    """The workload both arms run (the same dict in both JSON lines)."""
+    return {"workload": w.name, "I": list(w.I), "R_fit": list(w.R_fit), "eta": w.eta, "sweeps": w.sweeps,
+            "noise": "relative Frobenius" if w.kind == "tr" else "absolute std"}
+
+
 def mode_xdtype(mode, torch):
     return {"fp64": torch.float64, "fp32": torch.float32, "bf16": torch.float32, "bf16x3": torch.float32}[mode]
 
@@ -461,9 +467,10 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.mode],
         "data": "synthetic",
-        "config": {"workload": w.name, "I": list(w.I), "R_fit": list(w.R_fit), "eta": w.eta, "mode": args.mode,
-                   "solver": args.solver, "gram": args.gram, "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "flushed between timed sweeps (256 MB write)", "residual_after_run": main["residual"]},
+        "config": workload_config(w),
+        "variant": {"mode": args.mode, "solver": args.solver, "gram": args.gram,
+                    "parallelism": "replicas" if world > 1 else "single"},
+        "l2": "flushed between timed sweeps (256 MB write)", "residual_after_run": main["residual"],
         "roofline": roofline_for(w, args.mode, main["mttsp_kernel_ms"], peaks, src, main["mttsp_ms"]),
         "mttsp_ms_per_mode": main["mttsp_ms"],
         "gpu_launches": main["launches_per_sweep"] * args.steps,
@@ -518,8 +525,8 @@ def run_reference(args):
             "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * per_update, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "I": list(w.I), "R_fit": list(w.R_fit), "eta": w.eta,
-                       "step": "one core update of the CPU oracle per timed step (sweeps/s = 1 / (N x mean update time))"},
+            "config": workload_config(w),
+            "step": "one core update of the CPU oracle per timed step (sweeps/s = 1 / (N x mean update time))",
             "cpu_baseline": {"value": value, "unit": "sweeps/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"{args.steps} timed core updates after {args.warmup} warm-up updates"},
             "e2e": {"value": value, "unit": "sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -426,6 +426,37 @@ def tr_als_qr(X: np.ndarray, init: Sequence[np.ndarray], sweeps: int,
     return cores, res
 
 
+def tr_als_qrne(X: np.ndarray, init: Sequence[np.ndarray], sweeps: int,
+                residual: bool = True) -> Tuple[List[np.ndarray], List[float]]:
+    """TR-ALS-QRNE (Alg. 4, Sec. 3.3): the normal equations of the QR-compressed problem.
+
+    The mode-2 QR G_j = R_j x_2 Q_j of every core compresses the least-squares problem: with
+    Y = X x_{j!=n} Q_j^T (Multi-TTM) and V_n the subchain of the R_j, the compressed problem
+    min |Y_[n] - G_{n(2)} V_n[2]^T|_F (eq. qrhalf_ls) is solved through its normal equations:
+    M_n = Y_[n] V_n[2], S_n = the structured coefficient matrix chained from the Gram tensors of
+    the R_j (Prop. subchain_gram applied to V_n), then G_{n(2)} S_n = M_n by Cholesky.  After each
+    update the new core's QR and Gram tensor are recomputed.  Small shapes only (the Multi-TTM is
+    formed through an explicit Kronecker product).
+    """
+    cores = [np.array(G, dtype=np.float64, copy=True) for G in init]
+    N = len(cores)
+    QR = [mode2_qr(G) for G in cores]
+    res = []
+    for _ in range(sweeps):
+        for n in range(N):
+            Rs = [q[0] for q in QR]
+            S = paper_coefficient_matrix(Rs, n)                     # from the Gram tensors of the R_j
+            V2 = subchain_unfolded(Rs, n)                           # V_n[2]
+            Yn = multi_ttm_mode_unfolded(X, [q[1] for q in QR], n)  # Y_[n]
+            M = Yn @ V2
+            Rn, Rn1 = cores[n].shape[0], cores[n].shape[2]
+            cores[n] = core_fold2(ls_solve_normal(S, M), Rn, Rn1)
+            QR[n] = mode2_qr(cores[n])
+        if residual:
+            res.append(rel_residual(X, cores))
+    return cores, res
+
+
 # ---------------------------------------------------------------------------
 # Gauge-invariant comparison of two solutions (subspace angle) and Gamma-chain helpers
 # ---------------------------------------------------------------------------

@@ -54,3 +54,26 @@ def test_bench_subspace_angle_matches_the_oracle():
         assert ang > 1e-4
         assert abs(ang - O.subchain_principal_angle(a, b, n)) < 1e-9
         assert bench.subspace_angle(a, a, n) < 1e-6
+
+
+def test_multivariate_t_cores_correlation_and_layout():
+    """Rows of the mode-2 unfolding follow the correlation theta^|i-j| (checked by sampling with a
+    large degree of freedom, where the t distribution approaches the Gaussian), and the unfolding's
+    column a + R_n b is the lateral fibre G[a, :, b]."""
+    import numpy as np
+
+    import oracle as O
+    import trals_inputs as TI
+
+    G = TI.multivariate_t_cores(1, (40000, 6, 6), (5, 5, 5), 0.8, dof=1e12)[0]
+    Z = O.core_unfold2(G)                                       # I x R_n R_{n+1}, column a + R_n b
+    assert np.array_equal(Z[:, 2 + 5 * 3], G[2, :, 3])
+    want = 0.8 ** np.abs(np.subtract.outer(np.arange(25), np.arange(25)))
+    assert np.abs(np.corrcoef(Z.T) - want).max() < 0.03
+    # d = 1: heavy tails (Cauchy-like marginals), still finite
+    H = TI.multivariate_t_cores(2, (100, 100, 100), (5, 5, 5), 1 - 1e-7, dof=1.0)
+    assert all(np.isfinite(h).all() for h in H)
+    # near-perfect correlation: neighbouring unfolding columns nearly parallel
+    Z = O.core_unfold2(H[0])
+    cos = abs(Z[:, 0] @ Z[:, 1]) / (np.linalg.norm(Z[:, 0]) * np.linalg.norm(Z[:, 1]))
+    assert cos > 1 - 1e-5

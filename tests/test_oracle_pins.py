@@ -361,6 +361,35 @@ def test_tr_als_qr_matches_regular_als(I, R):
     np.testing.assert_allclose(r_qr, r_ref, rtol=1e-10)
 
 
+@pytest.mark.parametrize("I,R", [((9, 8, 10), (2, 2, 2)), ((12, 3, 11, 10), (2, 3, 2, 2))])
+def test_tr_als_qrne_matches_regular_als(I, R):
+    """TR-ALS-QRNE solves the same least-squares problems as TR-ALS (Sec. 3.3): the cores after a
+    sweep agree with Householder least squares on the explicit subchain matrix.  Modes 1 and 3 of
+    the second shape compress (I_j > R_j R_{j+1}); mode 2 (I = 3 < 6) keeps its square Q."""
+    X, init = _small_problem(seed=23, I=I, R=R, eta=0.05)
+    a, ra = O.tr_als_qrne(X, init, 2)
+    b, rb = O.tr_als(X, init, 2, "qr")
+    for Ga, Gb in zip(a, b):
+        np.testing.assert_allclose(Ga, Gb, rtol=1e-9, atol=1e-10 * np.abs(Gb).max())
+    np.testing.assert_allclose(ra, rb, rtol=1e-10)
+
+
+def test_qrne_compressed_terms_equal_the_uncompressed_ones():
+    """M_n = Y_[n] V_n[2] with Y = X x_{j!=n} Q_j^T equals X_[n] G^{!=n}_[2] (Prop. slice_kron and
+    Prop. ttm), and the coefficient matrix from the Gram tensors of the R factors equals the explicit
+    (G^{!=n}_[2])^T G^{!=n}_[2]."""
+    I, R = (7, 3, 9, 8), (2, 2, 3, 2)
+    X, cores = _small_problem(seed=24, I=I, R=R, eta=0.1)
+    QR = [O.mode2_qr(G) for G in cores]
+    for n in range(4):
+        Yn = O.multi_ttm_mode_unfolded(X, [q[1] for q in QR], n)
+        V2 = O.subchain_unfolded([q[0] for q in QR], n)
+        A = O.subchain_unfolded(cores, n)          # pinned to brute force in test_subchain_rows_brute_force
+        np.testing.assert_allclose(Yn @ V2, O.unfold_mode(X, n) @ A, rtol=1e-11, atol=1e-11 * np.abs(X).max())
+        S = O.paper_coefficient_matrix([q[0] for q in QR], n)
+        np.testing.assert_allclose(S, A.T @ A, rtol=1e-11, atol=1e-11 * np.abs(A.T @ A).max())
+
+
 def test_subspace_angle_gauge_invariance():
     X, init = _small_problem()
     cores, _ = O.tr_als(X, init, 2, "qr", residual=False)

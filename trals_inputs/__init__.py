@@ -198,6 +198,38 @@ def collinear_cores(seed: int, I: Sequence[int], R: Sequence[int], gamma: float,
     return out
 
 
+def multivariate_t_cores(seed: int, I: Sequence[int], R: Sequence[int], theta: float, dof: float = 1.0,
+                         stream: int = STREAM_TRUE_CORES) -> List[np.ndarray]:
+    """Cores whose mode-2 unfoldings (I_n x R_n R_{n+1}) have rows drawn from the multivariate t
+    distribution with ``dof`` degrees of freedom and correlation matrix C_ij = theta^|i-j| (the
+    correlated-core construction of the paper's second ill-conditioned experiment, Sec. 4).  Each row
+    is z / sqrt(w / dof) with z ~ N(0, C) and w ~ chi^2_dof.  z is sampled as the stationary AR(1)
+    sequence z_0 = g_0, z_k = theta z_{k-1} + sqrt(1 - theta^2) g_k (g iid N(0,1)), whose covariance is
+    exactly theta^|i-j|, so no factorization of the nearly singular C is needed.  Column
+    c = a + R_n b of the unfolding is the lateral fibre G[a, :, b].  Pure sampling: no tensor-ring
+    arithmetic."""
+    g = _rng(seed, stream)
+    N = len(I)
+    c = math.sqrt(max(0.0, 1.0 - theta * theta))
+    out = []
+    for n in range(N):
+        Rn, In, Rn1 = int(R[n]), int(I[n]), int(R[(n + 1) % N])
+        r = Rn * Rn1
+        gau = g.standard_normal((In, r))
+        z = np.empty((In, r))
+        z[:, 0] = gau[:, 0]
+        for k in range(1, r):
+            z[:, k] = theta * z[:, k - 1] + c * gau[:, k]
+        w = g.chisquare(dof, size=In)
+        rows = z / np.sqrt(w / dof)[:, None]
+        G = np.empty((Rn, In, Rn1))
+        for b in range(Rn1):
+            for a in range(Rn):
+                G[a, :, b] = rows[:, a + Rn * b]
+        out.append(G)
+    return out
+
+
 def signed_selection_cores(seed: int, I: Sequence[int], R: Sequence[int], dead: float = 0.15,
                            stream: int = STREAM_TRUE_CORES) -> List[np.ndarray]:
     """Cores whose lateral slices G_n(i) (R_n x R_{n+1}) hold at most one nonzero per row, +1 or -1
