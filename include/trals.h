@@ -170,10 +170,12 @@ trals_status trals_plan_mttsp(trals_plan* plan, int n, double* M_dev);
  * regeneration error (~1e-7 relative) is far below the residuals being compared.  Synchronous. */
 trals_status trals_plan_explicit_residual(trals_plan* plan, double* rel_res_host);
 /* Measurement hook (the paper has no counterpart): enqueue the MTTSP of mode n once, exactly as a
- * sweep does, with CUDA events around the whole step (table builds, contraction, reduction) and
- * around its main contraction kernel alone; waits for it and returns both durations in
- * milliseconds.  The caller may flush L2 on the context's stream beforehand.  Not for use while
- * the stream is being captured. */
+ * sweep does, with CUDA events around the part of the step a sweep has on its critical path (for the
+ * tensor-core kernel: the link of the subchain tables through the core updated just before, the
+ * contraction and the reduction of its per-CTA partials; the other table builds, which a sweep runs
+ * during the previous mode on a side stream, are enqueued before the first event) and around the
+ * main contraction kernel alone; waits for it and returns both durations in milliseconds.  The caller
+ * may evict L2 on the context's stream beforehand.  Not for use while the stream is being captured. */
 trals_status trals_plan_time_mttsp(trals_plan* plan, int n, float* kernel_ms, float* total_ms);
 /* Device pointer of core n (FP64, layout above), valid until the plan is destroyed. */
 const double* trals_plan_core_dev(const trals_plan* plan, int n);
@@ -264,7 +266,9 @@ int trals_last_mttsp_path(const trals_ctx* ctx);
  * 0 = CUDA cores (the FP64 path, and shapes the tensor-core kernel does not take);
  * 1 = tensor cores, X K-major with the stage-2 factor on the left;
  * 2 = tensor cores, X K-major with the stage-2 factor on the right;
- * 3 = tensor cores, X MN-major.  Negative on invalid arguments. */
+ * 3 = tensor cores, X MN-major with the stage-2 factor on the right;
+ * 4 = tensor cores, X MN-major with the stage-2 factor on the left (mode 0: a tile's rows are consecutive
+ *     elements of X).  Negative on invalid arguments. */
 int trals_mttsp_path(int N, const int64_t* I, const int32_t* R, int n, int mode);
 
 /* X_hat = TR(cores) written to out_dev (column-major, element type xt) (Sec. 1 element formula). */

@@ -14,6 +14,10 @@
 //   KM-L : S = modes 0..n-1 (K-major X), F = G_{n+1}...G_N on the left   (n < N-1)
 //   KM-R : S = modes 0..s,    (K-major X), F = G_{s+1}...G_{N-1} on the right (n = N-1)
 //   MM   : S = modes n+1..m  (MN-major X), F = G_{m+1}...G_N G_1...G_{n-1} on the right
+//   MM-L : n = 0, S = modes m..N-1 (MN-major X), F = G_1...G_{m-1} on the left; a tile is 128
+//          consecutive elements of X in memory, (i_0, i_1 .. i_{m-1}), so every TMA row is one aligned
+//          pair of 128-byte lines even when I_0 < 64; the row -> i_0 map then changes from tile to tile,
+//          so each unit's rows are combined into a shared-memory I_0 x r accumulator in a fixed order
 // Rows of a tile map to distinct (i_n, factor) pairs; stage 2 reduces rows with equal i_n in a
 // fixed order into a per-CTA FP32 accumulator; CTA partials are summed in FP64 by a second kernel.
 #include <cuda.h>
@@ -29,7 +33,7 @@ namespace {
 
 constexpr int kRows = 128;                    // MMA M (TMEM lanes)
 constexpr int kKT = 64;                       // K elements per stage (one 128-byte swizzle row of BF16)
-constexpr int kNSMax = 6;                     // pipeline stages (upper bound; the host picks what fits)
+constexpr int kNSMax = 8;                     // pipeline stages (upper bound; the host picks what fits)
 constexpr int kThreads = 192;                 // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr int kABytes = kRows * 128;          // X tile: 128 rows x 128 B
 constexpr int kAtomBytes = 64 * 128;          // MN-major atom: 64 K rows x 128 B (64 MN elements)
@@ -37,7 +41,7 @@ constexpr int kMaxW = 128;                    // stage-1 table width (MMA N) lim
 constexpr int kSmemBudget = 227 * 1024;
 constexpr long long kSpinLimit = 4000000000LL;  // ~2 s at 2 GHz
 
-enum { KM_L = 0, KM_R = 1, MM = 2 };
+enum { KM_L = 0, KM_R = 1, MM = 2, MM_L = 3 };
 
 struct TcArgs {
   int variant;
@@ -50,6 +54,11 @@ struct TcArgs {
   int64_t P, K_pre, K_hi, pchunks;   // MM
   int64_t opairs;                    // MM: ceil(K_hi / 2) o-pairs per p-chunk
   int NX, NY, Sy, Rn, r, W_pad, fs_stride, ms_stride, ns;
+  int fac_shared;    // KM-L, KM-R, MM-L: the factor blocks of a tile are staged once (double buffered);
+                     // MM: one block per row
+  int nslot;         // factor blocks per tile (KM: nrep; MM-L: distinct i_1.. values in 128 elements)
+  int64_t Pp;        // MM-L: elements per K row (I_0 ... I_{m-1})
+  int ksync;         // K-synchronous work split (see get_unit)
   uint32_t tx_bytes;
   uint32_t idesc;
   int x3;            // bf16x3: X and the table as hi/lo BF16 pairs, three products per K step
@@ -91,19 +100,33 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   }
 }
 
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+// TMA tile loads with an L2 cache policy: X is read once per launch (evict first), the stage-1 table
+// by every tile (evict last), so the stream of X does not push the table out of L2.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
+                                            uint64_t policy) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-          smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%3, "
+      "%4}], [%2], %5;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "l"(policy)
       : "memory");
 }
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z,
+                                            uint64_t policy) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
-          "r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%3, "
+      "%4, %5}], [%2], %6;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z), "l"(policy)
       : "memory");
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -186,6 +209,19 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // CTAs of a p-chunk share that chunk's o-pairs.  Producer, MMA issuer and epilogue call this alike.
 __device__ __forceinline__ bool get_unit(const TcArgs& a, int64_t j, int64_t& tile, int64_t& op, int64_t& pc,
                                          int& ks0, int& ks1) {
+  if (a.ksync) {
+    // K-synchronous split (grid = n_tiles x groups): CTA c takes tile c % n_tiles and the (c / n_tiles)-th
+    // K range of it, one unit per CTA, so the CTAs of all tiles walk the same K rows of X together and
+    // jointly read whole DRAM rows (each tile holds only a 256-byte piece of a K row)
+    if (j > 0) return false;
+    const int64_t T = a.n_tiles, groups = gridDim.x / T, g = blockIdx.x / T;
+    tile = blockIdx.x % T;
+    op = 0;
+    pc = 0;
+    ks0 = (int)(g * a.ksteps / groups);
+    ks1 = (int)((g + 1) * a.ksteps / groups);
+    return ks0 < ks1;
+  }
   int64_t ntile, g, G;
   if (a.variant != MM) {
     ntile = a.n_tiles;
@@ -231,9 +267,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int planes = a.x3 ? 2 : 1;                 // stage: X hi [, X lo], table hi [, table lo]
   const int stageBytes = planes * (kABytes + bBytes);
   const int NS = a.ns;
-  float* F_s = reinterpret_cast<float*>(base + NS * stageBytes);     // per row: its stage-2 factor block
-  float* M_s = F_s + kRows * a.fs_stride;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(M_s + ((a.In * a.ms_stride + 1) & ~1));
+  // stage-2 factor blocks: per row (MM), or the blocks of a tile, double buffered
+  float* F_s = reinterpret_cast<float*>(base + NS * stageBytes);
+  const int fs_rows = a.fac_shared ? 2 * a.nslot : kRows;
+  // MM-L: one x-column of every row's stage-2 result (rows 128, stride NY | 1), and the CTA's I_0 x r sums
+  float* U_s = F_s + ((fs_rows * a.fs_stride + 1) & ~1);
+  const int us = a.NY | 1;
+  float* Macc = U_s + (a.variant == MM_L ? ((kRows * us + 1) & ~1) : 0);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(Macc + (a.variant == MM_L ? ((a.In * a.ms_stride + 1) & ~1) : 0));
   uint64_t* full = bars;
   uint64_t* empty = bars + kNSMax;
   uint64_t* accf = bars + 2 * kNSMax;
@@ -245,7 +286,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int E = a.In * a.r;
 
-  for (int e = threadIdx.x; e < a.In * a.ms_stride; e += blockDim.x) M_s[e] = 0.0f;
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
       mbar_init(&full[s], 1);
@@ -275,7 +315,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      int issued[kNSMax] = {0, 0, 0, 0, 0, 0};
+      int issued[kNSMax] = {};
+      const uint64_t pol_x = policy_evict_first(), pol_tab = policy_evict_last();
       int64_t tile, op, pc;
       int ks0, ks1;
       for (int64_t j = 0; get_unit(a, j, tile, op, pc, ks0, ks1) && !*abort_flag; ++j) {
@@ -293,14 +334,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             const CUtensorMap* mx = pl ? &tmXl : &tmX;
             uint8_t* Ap = A + pl * kABytes;
             if (a.variant == KM_L) {
-              tma_load_3d(Ap, mx, &full[stage], k0, 0, (int)(tile * a.nrep));
+              tma_load_3d(Ap, mx, &full[stage], k0, 0, (int)(tile * a.nrep), pol_x);
             } else if (a.variant == KM_R) {
-              tma_load_3d(Ap, mx, &full[stage], k0, (int)(tile * a.nrep), 0);
+              tma_load_3d(Ap, mx, &full[stage], k0, (int)(tile * a.nrep), 0, pol_x);
+            } else if (a.variant == MM_L) {
+              for (int at = 0; at < 2; ++at)
+                tma_load_2d(Ap + at * kAtomBytes, mx, &full[stage], (int)(tile * kRows + 64 * at), k0, pol_x);
             } else {
               for (int at = 0; at < 2; ++at)
-                tma_load_3d(Ap + at * kAtomBytes, mx, &full[stage], (int)(pc * 64), k0, (int)(2 * op + at));
+                tma_load_3d(Ap + at * kAtomBytes, mx, &full[stage], (int)(pc * 64), k0, (int)(2 * op + at), pol_x);
             }
-            tma_load_2d(B + pl * bBytes, pl ? &tmTl : &tmT, &full[stage], k0, 0);
+            tma_load_2d(B + pl * bBytes, pl ? &tmTl : &tmT, &full[stage], k0, 0, pol_tab);
           }
           ++issued[stage];
           if (++stage == NS) {
@@ -347,15 +391,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t B = A + (uint32_t)(planes * kABytes);
 #pragma unroll
           for (int jj = 0; jj < kKT / 16; ++jj) {
-            const uint64_t ad =
-                (a.variant == MM) ? sdesc(A + 2048u * jj, kAtomBytes, 1024) : sdesc(A + 32u * jj, 16, 1024);
+            const bool mn = a.variant == MM || a.variant == MM_L;
+            const uint64_t ad = mn ? sdesc(A + 2048u * jj, kAtomBytes, 1024) : sdesc(A + 32u * jj, 16, 1024);
             const uint64_t bd = sdesc(B + 32u * jj, 16, 1024);
             umma_bf16(d, ad, bd, a.idesc, (ks > ks0 || jj > 0) ? 1u : 0u);
             if (a.x3) {
               // split-BF16 products: X_hi T_lo + X_lo T_hi (X_lo T_lo is below FP32 rounding)
               const uint32_t Al = A + (uint32_t)kABytes;
-              const uint64_t adl =
-                  (a.variant == MM) ? sdesc(Al + 2048u * jj, kAtomBytes, 1024) : sdesc(Al + 32u * jj, 16, 1024);
+              const uint64_t adl = mn ? sdesc(Al + 2048u * jj, kAtomBytes, 1024) : sdesc(Al + 32u * jj, 16, 1024);
               const uint64_t bdl = sdesc(B + (uint32_t)bBytes + 32u * jj, 16, 1024);
               umma_bf16(d, ad, bdl, a.idesc, 1u);
               umma_bf16(d, adl, bd, a.idesc, 1u);
@@ -376,9 +419,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------------------ epilogue (stage 2)
     const int q = warp & 3;            // TMEM lane quarter of this warp
     const int row = 32 * q + lane;
-    const int et = threadIdx.x - 64;   // 0..127 among the epilogue threads
     const int fblk = a.NX * SYP;       // floats per factor block
-    float* myF = F_s + row * a.fs_stride;
+    float* myF = F_s + row * a.fs_stride;   // MM; the shared blocks are picked per unit below
     const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
     const uint32_t vacc = lane_base + 256u;   // this lane's running V[x][y] at column 256 + 16 x + y
     // Fixed row geometry: the i_n of this lane never changes (see get_unit).
@@ -386,7 +428,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int my_i, rep = 0;
     int64_t k_pre = 0;
     int at = 0;
-    if (a.variant == KM_L) {
+    if (a.variant == KM_L || a.variant == MM_L) {
       rep = row / a.In;
       my_i = row % a.In;
       lane_ok = rep < a.nrep;
@@ -402,7 +444,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       my_i = lane_ok ? (int)(p / a.K_pre) : 0;
       k_pre = p % a.K_pre;
     }
-    {
+    const bool accum_rows = a.variant == MM_L;   // per-unit row combine instead of per-lane running sums
+    if (accum_rows) {
+      for (int e = row; e < a.In * a.ms_stride; e += kRows) Macc[e] = 0.0f;
+    } else {
       uint32_t z[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) z[j] = 0u;
@@ -415,16 +460,32 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int buf = (int)(j & 1);
       bool valid;
       int64_t fi;
+      int slot = rep;
+      bool copier = my_i == 0;
       if (a.variant == MM) {
         const int64_t o = 2 * op + at;
         valid = lane_ok && o < a.K_hi;
         fi = o + a.K_hi * k_pre;
+      } else if (accum_rows) {
+        const int64_t e = tile * kRows + row;
+        valid = e < a.Pp;
+        my_i = (int)(e % a.In);
+        fi = e / a.In;
+        slot = (int)(fi - (tile * kRows) / a.In);
+        copier = row == 0 || my_i == 0;
       } else {
         fi = tile * a.nrep + rep;
         valid = lane_ok && fi < a.n_fac;
       }
-      // prefetch this row's factor block into shared memory while the MMAs run
-      if (valid) {
+      // prefetch the factor blocks into shared memory while the MMAs run: each row its own (MM), or
+      // the first row of each repetition its repetition's block into the buffer of this unit's parity
+      if (a.fac_shared) {
+        myF = F_s + (2 * slot + (int)(j & 1)) * a.fs_stride;
+        if (valid && copier) {
+          const float* src = a.F + (size_t)fi * fblk;
+          for (int c = 0; c < fblk; c += 4) cp_async16(myF + c, src + c);
+        }
+      } else if (valid) {
         const float* src = a.F + (size_t)fi * fblk;
         for (int c = 0; c < fblk; c += 4) cp_async16(myF + c, src + c);
       }
@@ -460,6 +521,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_before();
       mbar_arrive(&acce[buf]);
       cp_async_wait_all();
+      if (a.fac_shared) epi_bar();   // the copying row's block is visible to the other rows
       // stage 2: V[x][y] += f_x . T[y]  (independent accumulators over y), kept per lane in TMEM
       constexpr int YMAX = (128 / SYP) < 16 ? (128 / SYP) : 16;
       for (int x = 0; x < a.NX; ++x) {
@@ -473,8 +535,6 @@ __global__ void __launch_bounds__(kThreads, 1)
           f[4 * jj + 2] = t.z;
           f[4 * jj + 3] = t.w;
         }
-        uint32_t v[16];
-        tmem_ld16(vacc + 16u * x, v);
         float acc[YMAX];
 #pragma unroll
         for (int y = 0; y < YMAX; ++y) acc[y] = 0.0f;
@@ -485,6 +545,26 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int y = 0; y < YMAX; ++y) acc[y] = fmaf(f[z], T[y * SYP + z], acc[y]);
           }
         }
+        if (accum_rows) {
+          // this x-column of every row to shared memory, then each output (i_0, y) adds the rows of
+          // its i_0 in ascending order into the CTA's sums
+#pragma unroll
+          for (int y = 0; y < YMAX; ++y)
+            if (y < a.NY) U_s[row * us + y] = acc[y];
+          epi_bar();
+          const int base_i = (int)((tile * kRows) % a.In);
+          const int64_t rows_left = a.Pp - tile * kRows;
+          for (int o = row; o < a.In * a.NY; o += kRows) {
+            const int i = o / a.NY, y = o - i * a.NY;
+            float sum = 0.0f;
+            for (int r = (i - base_i + a.In) % a.In; r < kRows && r < rows_left; r += a.In) sum += U_s[r * us + y];
+            Macc[i * a.ms_stride + y + a.Rn * x] += sum;
+          }
+          epi_bar();
+          continue;
+        }
+        uint32_t v[16];
+        tmem_ld16(vacc + 16u * x, v);
         tmem_wait_ld();
 #pragma unroll
         for (int y = 0; y < YMAX; ++y) v[y] = __float_as_uint(__uint_as_float(v[y]) + acc[y]);
@@ -495,6 +575,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // Stage the lanes' running sums V[x][y] in the pipeline buffers, which are idle now (every MMA
     // and copy has been consumed).
     epi_bar();
+    if (!accum_rows) {
     float* S = reinterpret_cast<float*>(base);
     const int nv = a.NX * a.NY, ss = nv | 1;
     float* myS = S + row * ss;
@@ -506,18 +587,29 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int y = 0; y < 16; ++y)
         if (y < a.NY) myS[x * a.NY + y] = lane_ok ? __uint_as_float(v[y]) : 0.0f;
     }
+    }
   }
   // Combine: all warps (the producer and MMA warps are done) own outputs (i_n, x, y) and add the rows
   // of their i_n in a fixed order; then the CTA's partial (column-major I_n x r) goes out.
   __syncthreads();
-  if (!*abort_flag) {
+  if (!*abort_flag && a.variant == MM_L) {
+    // MM-L: the sums are already combined
+    float* out = a.partials + (size_t)blockIdx.x * E;
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+      const int i = e % a.In, c = e / a.In;
+      out[e] = Macc[i * a.ms_stride + c];
+    }
+  } else if (!*abort_flag) {
     float* S = reinterpret_cast<float*>(base);
     const int nv = a.NX * a.NY, ss = nv | 1;
     int* colmap = reinterpret_cast<int*>(S + kRows * ss);   // xy -> column of M_s
+    float* M_s = reinterpret_cast<float*>(colmap + ((nv + 3) & ~3));
+    const bool left = a.variant == KM_L || a.variant == MM_L;
     for (int xy = threadIdx.x; xy < nv; xy += blockDim.x) {
       const int x = xy / a.NY, y = xy % a.NY;
-      colmap[xy] = a.variant == KM_L ? (y + a.Rn * x) : (x + a.Rn * y);
+      colmap[xy] = left ? (y + a.Rn * x) : (x + a.Rn * y);
     }
+    for (int e = threadIdx.x; e < a.In * a.ms_stride; e += blockDim.x) M_s[e] = 0.0f;
     int64_t i_lo = 0, i_hi = a.In - 1, p0 = 0, p1 = 0;
     if (a.variant == MM) {
       p0 = (blockIdx.x % a.pchunks) * 64;
@@ -533,7 +625,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int o = threadIdx.x; o < cnt; o += step) {
       const int64_t i = i_lo + g;
       float sum = 0.0f;
-      if (a.variant == KM_L) {
+      if (left) {
         for (int rp = 0; rp < a.nrep; ++rp) sum += S[(i + a.In * rp) * ss + xy];
       } else if (a.variant == KM_R) {
         for (int rp = 0; rp < a.nrep; ++rp) sum += S[(rp + a.nrep * i) * ss + xy];
@@ -797,8 +889,12 @@ EncodeTiledFn get_encode() {
   return fn;
 }
 
+// 128-byte promotion for X: tiles whose rows start off a 256-byte boundary (mode 0 with the factor on
+// the left) would otherwise fetch lines they do not read (measured: 77 -> 68 us on that mode).
+constexpr CUtensorMapL2promotion kXPromotion = CU_TENSOR_MAP_L2_PROMOTION_L2_128B;
+
 bool encode_bf16(CUtensorMap* m, const void* ptr, int rank, const uint64_t* dims, const uint64_t* strides_bytes,
-                 const uint32_t* box) {
+                 const uint32_t* box, CUtensorMapL2promotion promotion = CU_TENSOR_MAP_L2_PROMOTION_L2_256B) {
   EncodeTiledFn fn = get_encode();
   if (!fn) return false;
   cuuint64_t gd[5], gs[4];
@@ -810,7 +906,7 @@ bool encode_bf16(CUtensorMap* m, const void* ptr, int rank, const uint64_t* dims
   }
   for (int i = 0; i + 1 < rank; ++i) gs[i] = strides_bytes[i];
   const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(ptr), gd, gs, bd, es,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, promotion,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -913,13 +1009,18 @@ TcChoice tc_choose(int N, const int64_t* I, const int32_t* R, int n) {
   const int r = Rn * Rn1;
   const int64_t In = I[n];
   if (maxR > 16 || r > 256 || In * r > 8192) return best;
-  auto consider = [&](TcChoice c, int W) {
+  auto consider = [&](TcChoice c, int W, int64_t extra_cost = 0) {
     if (c.K_S < 256 || W > kMaxW) return;
     const int64_t tabBytes = c.K_S * (int64_t)((W + 15) / 16 * 16) * 2;
     if (tabBytes > (int64_t)64 << 20) return;
     c.cost = (c.variant == MM) ? tabBytes + tabBytes / 4 + 1 : tabBytes;   // prefer K-major X unless MN-major is clearly cheaper
+    c.cost += extra_cost;
     if (best.variant < 0 || c.cost < best.cost) best = c;
   };
+  // MN-major tiles over a contiguous run P = I_0 ... I_n shorter than a 64-element TMA row read part
+  // of every 128-byte row out of bounds, which the copy engine streams at about half the rate of full
+  // rows (measured): such an MM tile counts as costly as a 1 GB table.
+  constexpr int64_t kShortRunPenalty = (int64_t)1 << 30;
   // KM-L: S = modes 0..n-1 (needs post modes)
   if (n >= 1 && n <= N - 2) {
     TcChoice c;
@@ -952,8 +1053,29 @@ TcChoice tc_choose(int N, const int64_t* I, const int32_t* R, int n) {
         c.s_lo = n + 1;
         c.s_hi = m;
         c.K_S = prod_range(I, n + 1, m + 1);
-        consider(c, (R[(m + 1) % N] + 3) / 4 * 4 * Rn1);
+        consider(c, (R[(m + 1) % N] + 3) / 4 * 4 * Rn1, P < 64 ? kShortRunPenalty : 0);
       }
+    }
+  }
+  // MM-L (n = 0): S = modes m..N-1, a tile = 128 consecutive elements (i_0, l), l over modes 1..m-1,
+  // the left factor G_1(i_1)...G_{m-1}(i_{m-1}); K rows are P' = I_0 ... I_{m-1} elements apart (a
+  // multiple of 8 for the 16-byte stride rule).
+  if (n == 0 && In <= kRows) {
+    for (int m = 2; m <= N - 1; ++m) {
+      const int64_t Pp = prod_range(I, 0, m);
+      if ((Pp * 2) % 16 != 0 || Pp > ((int64_t)1 << 30)) continue;
+      TcChoice c;
+      c.variant = MM_L;
+      c.s_lo = m;
+      c.s_hi = N - 1;
+      c.K_S = prod_range(I, m, N);
+      // only the smallest m whose table fits: K rows of X are P' elements apart, and with a short P'
+      // the CTAs of all tiles read each K row together (whole DRAM rows); a larger m makes the table
+      // smaller but scatters every tile's 256-byte pieces over K rows megabytes apart
+      const int W = (R[m] + 3) / 4 * 4 * R[0];
+      if (c.K_S < 256 || W > kMaxW || c.K_S * (int64_t)((W + 15) / 16 * 16) * 2 > ((int64_t)64 << 20)) continue;
+      consider(c, W);
+      break;
     }
   }
   return best;
@@ -1031,6 +1153,26 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
     strides[0] = best.K_S * 2; strides[1] = best.K_S * K_mid * 2;
     box[0] = kKT; box[1] = (uint32_t)A.nrep; box[2] = (uint32_t)In;
     A.tx_bytes = (uint32_t)(kKT * 2 * In * A.nrep);
+  } else if (A.variant == MM_L) {
+    // T = c x a (c = dot index, Sy = R_m); F = L = G_1..G_{m-1} (R_1 x R_m) on the left; a tile = 128
+    // consecutive elements e = i_0 + I_0 l of a K row
+    impl->kindL = 1;
+    for (int m = 1; m < best.s_lo; ++m) impl->f_modes.push_back(m);
+    impl->facRa = R[1];
+    impl->facRb = R[best.s_lo];
+    A.NX = R[1];
+    A.NY = Rn;
+    A.Sy = R[best.s_lo];
+    const int64_t Lf = prod_range(I, 1, best.s_lo);
+    A.nrep = 1;
+    A.nslot = (int)((kRows + In - 1) / In) + 1;   // values of l that 128 consecutive elements can touch
+    A.Pp = In * Lf;
+    A.n_fac = Lf;
+    n_tiles = (A.Pp + kRows - 1) / kRows;
+    dims[0] = In * Lf; dims[1] = best.K_S; dims[2] = 1;
+    strides[0] = In * Lf * 2; strides[1] = In * Lf * best.K_S * 2;
+    box[0] = 64; box[1] = kKT; box[2] = 1;
+    A.tx_bytes = (uint32_t)(2 * kAtomBytes);
   } else {
     // T = b x d (d = dot index, Sy = R_{m+1}); F = Rm = G_{m+1}..G_{N-1} G_0..G_{n-1} (R_{m+1} x R_n) on the right
     impl->kindL = 0;
@@ -1053,6 +1195,8 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
     A.tx_bytes = (uint32_t)(2 * kAtomBytes);
   }
   impl->SYP = (A.Sy + 3) / 4 * 4;
+  A.fac_shared = (A.variant == MM) ? 0 : 1;
+  if (A.variant == KM_L || A.variant == KM_R) A.nslot = A.nrep;
   impl->late = (n + N - 1) % N;
   impl->late_in_s = !impl->s_modes.empty() && impl->s_modes.back() == impl->late;
   if (!impl->late_in_s && (impl->f_modes.empty() || impl->f_modes.back() != impl->late)) {
@@ -1068,7 +1212,7 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   A.x3 = x3 ? 1 : 0;
   if (x3) A.tx_bytes *= 2;   // hi and lo planes of X and of the table
   // MMA instruction descriptor: D=F32, A=B=BF16, A major per variant, B K-major, N=W_pad, M=128
-  A.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((A.variant == MM ? 1u : 0u) << 15) |
+  A.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((A.variant == MM || A.variant == MM_L ? 1u : 0u) << 15) |
             ((uint32_t)(A.W_pad >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
 
   // units: split K so that the grid gets a few units per SM
@@ -1089,12 +1233,17 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
                                            : std::min<int64_t>(n_tiles * A.ksteps, nsm);
     A.whole = per_chunk >= 4 * ctas ? 1 : 0;
   }
+  A.ksync = 0;
   if (A.variant == MM) {
     if (A.pchunks > nsm) {   // each CTA keeps a single p-chunk
       delete impl;
       return 0;
     }
     impl->grid = nsm;
+  } else if (A.variant == MM_L && n_tiles <= nsm && A.ksteps >= nsm / n_tiles) {
+    A.ksync = 1;
+    A.whole = 0;
+    impl->grid = (int)(n_tiles * (nsm / n_tiles));
   } else {
     impl->grid = (int)std::min<int64_t>(n_tiles * A.ksteps, nsm);
   }
@@ -1102,8 +1251,10 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
 
   // ---- shared-memory plan (checked before anything is allocated)
   const int bBytes = ((A.W_pad * 128) + 1023) & ~1023;
-  const size_t fixed = 1024 + (size_t)kRows * A.fs_stride * 4 +
-                       (size_t)((In * A.ms_stride + 1) & ~1) * 4 + (2 * kNSMax + 4) * 8 + 64;
+  const int fs_rows = A.fac_shared ? 2 * A.nslot : kRows;
+  size_t fixed = 1024 + (size_t)((fs_rows * A.fs_stride + 1) & ~1) * 4 + (2 * kNSMax + 4) * 8 + 64;
+  if (A.variant == MM_L)   // one x-column of every row, and the I_0 x r sums
+    fixed += (size_t)((kRows * (A.NY | 1) + 1) & ~1) * 4 + (size_t)((In * A.ms_stride + 1) & ~1) * 4;
   const size_t stage = (size_t)(x3 ? 2 : 1) * ((size_t)kABytes + bBytes);
   const int ns = (int)std::min<size_t>(kNSMax, fixed < (size_t)kSmemBudget ? (kSmemBudget - fixed) / stage : 0);
   if (ns < 2) {
@@ -1113,9 +1264,11 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   A.ns = ns;
   impl->smem = fixed + (size_t)ns * stage;
   {
-    // the end-of-kernel lane staging reuses the pipeline buffers and the factor blocks
-    const size_t stage_area = (size_t)ns * stage + (size_t)kRows * A.fs_stride * 4;
-    const size_t need = (size_t)kRows * ((A.NX * A.NY) | 1) * 4 + (size_t)A.NX * A.NY * 4;   // + column map
+    // the end-of-kernel lane staging, its column map and the CTA's I_n x r sums reuse the pipeline
+    // buffers (idle by then)
+    const size_t stage_area = (size_t)ns * stage;
+    const int nv = A.NX * A.NY;
+    const size_t need = (size_t)kRows * (nv | 1) * 4 + (size_t)((nv + 3) & ~3) * 4 + (size_t)In * A.ms_stride * 4;
     if (need > stage_area) {
       delete impl;
       return 0;
@@ -1128,9 +1281,10 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   const uint64_t tdims[2] = {(uint64_t)impl->Kpad, (uint64_t)A.W_pad};
   const uint64_t tstrides[1] = {(uint64_t)impl->Kpad * 2};
   const uint32_t tbox[2] = {kKT, (uint32_t)A.W_pad};
-  if (!encode_bf16(&impl->tmX, X, 3, dims, strides, box) ||
+  const int xrank = (A.variant == MM_L) ? 2 : 3;
+  if (!encode_bf16(&impl->tmX, X, xrank, dims, strides, box, kXPromotion) ||
       !encode_bf16(&impl->tmT, reinterpret_cast<const void*>(uintptr_t(1) << 40), 2, tdims, tstrides, tbox) ||
-      (x3 && !encode_bf16(&impl->tmXl, Xlo, 3, dims, strides, box))) {
+      (x3 && !encode_bf16(&impl->tmXl, Xlo, xrank, dims, strides, box, kXPromotion))) {
     delete impl;
     return 0;
   }

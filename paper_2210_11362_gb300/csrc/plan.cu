@@ -969,9 +969,17 @@ trals_status trals_plan_time_mttsp(trals_plan* p, int n, float* kernel_ms, float
   cudaEvent_t ev[4] = {};
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
+  // the tensor-core tables' first part runs during the previous mode in a sweep (on a side stream):
+  // it is enqueued before the first event, so the total covers what a sweep has on its critical path
+  const bool tc = p->use_tc[n];
+  if (e == cudaSuccess && tc) {
+    launch_cores_to_f32(p->cores, p->N, p->R, p->Ist, p->I[0], p->c32buf, s);   // current FP32 core copies
+    tc_enqueue_pre(p->tc[n], p->cores, s, p->c32);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
   if (e == cudaSuccess) {
-    enqueue_mttsp(p, n, s, ev[1], ev[2]);
+    enqueue_mttsp(p, n, s, ev[1], ev[2], tc);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaEventRecord(ev[3], s);

@@ -331,11 +331,12 @@ def test_plan_mttsp_bf16_with_padded_leading_mode(ctx, I, R):
 
 def test_plan_mttsp_full_size_40x5(ctx):
     """The 40^5 workload shape, R = (8,10,12,10,8), through the plan exactly as a sweep runs it,
-    every mode on its tensor-core geometry (mode 0 MN-major with whole-tile work shares):
-    integer data must match the FP64 oracle exactly; Gaussian data must stay within the
-    componentwise bound in the MN-major (0) and K-major-right (4) modes."""
+    every mode on its tensor-core geometry (mode 0 MN-major with the factor on the left, mode 1
+    MN-major with the factor on the right and whole-tile work shares): integer data must match the
+    FP64 oracle exactly; Gaussian data must stay within the componentwise bound in the MN-major
+    modes (0, 1) and the K-major-right mode (4)."""
     I, R = (40,) * 5, (8, 10, 12, 10, 8)
-    for exact, modes in ((True, range(5)), (False, (0, 4))):
+    for exact, modes in ((True, range(5)), (False, (0, 1, 4))):
         if exact:
             X, cores = _integer_problem(I, R, seed=6)
         else:
@@ -346,7 +347,7 @@ def test_plan_mttsp_full_size_40x5(ctx):
         plan = P.Plan(ctx, I, R, Xf, P.make_opts("bf16"))
         try:
             plan.set_cores(cores)
-            assert [plan.mttsp_path(n) for n in range(5)] == [3, 3, 1, 1, 2]
+            assert [plan.mttsp_path(n) for n in range(5)] == [4, 3, 1, 1, 2]
             for n in modes:
                 r = R[n] * R[(n + 1) % 5]
                 M = torch.full((I[n] * r,), float("nan"), dtype=torch.float64, device="cuda")
@@ -662,4 +663,4 @@ def test_plan_uses_the_tensor_core_geometry_it_reports(ctx):
         got = [plan.mttsp_path(n) for n in range(5)]
     finally:
         plan.close()
-    assert got == [P.trals_mttsp_path(I, R, n, "bf16") for n in range(5)] == [3, 3, 1, 1, 2]
+    assert got == [P.trals_mttsp_path(I, R, n, "bf16") for n in range(5)] == [4, 3, 1, 1, 2]

@@ -7,8 +7,9 @@ import paper_2210_11362_gb300 as P
 def test_mttsp_path_choice_40x5():
     I, R = (40,) * 5, (8, 10, 12, 10, 8)
     paths = [P.trals_mttsp_path(I, R, n, "bf16") for n in range(5)]
-    # every mode of the 40^5 workload runs on tensor cores; modes 0-1 need the MN-major tile
-    assert paths == [3, 3, 1, 1, 2]
+    # every mode of the 40^5 workload runs on tensor cores; modes 0-1 need MN-major tiles (mode 0 with
+    # the factor on the left, so that its rows are consecutive elements of X)
+    assert paths == [4, 3, 1, 1, 2]
 
 
 def test_mttsp_path_choice_fp64_is_cuda_cores():
