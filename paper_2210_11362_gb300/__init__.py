@@ -39,7 +39,7 @@ EXPORTED = [
     "trals_plan_run", "trals_plan_residuals", "trals_plan_mttsp", "trals_plan_time_mttsp", "trals_plan_core_dev",
     "trals_plan_explicit_residual", "trals_plan_footprint", "trals_plan_bytes",
     "trals_plan_launches_per_sweep", "trals_plan_mttsp_path",
-    "trals_gamma", "trals_coef_matrix", "trals_coef_matrix_explicit", "trals_qr_r_factor", "trals_mttsp", "trals_mttsp_noalloc", "trals_mttsp_path", "trals_last_mttsp_path", "trals_solve_chol", "trals_check_pivot_rsqrt", "trals_reconstruct",
+    "trals_gamma", "trals_coef_matrix", "trals_coef_matrix_explicit", "trals_qr_r_factor", "trals_mttsp", "trals_mttsp_noalloc", "trals_mttsp_path", "trals_last_mttsp_path", "trals_testing_mttsp_withheld_copy", "trals_solve_chol", "trals_check_pivot_rsqrt", "trals_reconstruct",
     "trals_residual_explicit", "trals_quantize_bf16",
     "trals_server_create", "trals_server_destroy", "trals_server_submit", "trals_server_poll",
     "trals_server_wait", "trals_server_stats", "trals_server_last_error",
@@ -120,6 +120,8 @@ def lib() -> ctypes.CDLL:
                                        ctypes.c_int, _vp]),
         "trals_mttsp_path": (ctypes.c_int, [ctypes.c_int, _vp, _vp, ctypes.c_int, ctypes.c_int]),
         "trals_last_mttsp_path": (ctypes.c_int, [_vp]),
+        "trals_testing_mttsp_withheld_copy": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp,
+                                                             ctypes.c_int, _vp, ctypes.c_longlong]),
         "trals_mttsp_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
         "trals_solve_chol": (ctypes.c_int, [_vp, ctypes.c_int, _i64, ctypes.c_int, _vp, _vp, _vp]),
         "trals_check_pivot_rsqrt": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
@@ -398,6 +400,20 @@ MTTSP_PATHS = {0: "cuda-cores", 1: "tc-kmajor-left", 2: "tc-kmajor-right", 3: "t
 def trals_last_mttsp_path(ctx: Context) -> int:
     """Kernel the last successful trals_mttsp on ctx ran (MTTSP_PATHS codes; -1 if none)."""
     return lib().trals_last_mttsp_path(ctx.handle)
+
+
+def trals_testing_mttsp_withheld_copy(ctx: Context, I, R, X_dev, mode, cores_dev: Sequence, n: int, M_dev,
+                                      spin_cycles: int) -> None:
+    """Fault injection (include/trals_testing.h): the tensor-core MTTSP with its first copy withheld and
+    every wait bounded by spin_cycles; raises TralsError(E_TIMEOUT) as the kernel reports."""
+    N, Ia, Ra = _shape(I, R)
+    if isinstance(mode, str):
+        mode = MODE_NAMES[mode]
+    ctx.check(lib().trals_testing_mttsp_withheld_copy(ctx.handle, N, ctypes.addressof(Ia), ctypes.addressof(Ra),
+                                                      _ptr(X_dev), int(mode),
+                                                      _ptr_array([_ptr(c) for c in cores_dev]), int(n),
+                                                      _ptr(M_dev), int(spin_cycles)),
+              "trals_testing_mttsp_withheld_copy")
 
 
 def trals_mttsp_path(I, R, n: int, mode) -> int:

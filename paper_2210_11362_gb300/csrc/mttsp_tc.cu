@@ -39,7 +39,7 @@ constexpr int kABytes = kRows * 128;          // X tile: 128 rows x 128 B
 constexpr int kAtomBytes = 64 * 128;          // MN-major atom: 64 K rows x 128 B (64 MN elements)
 constexpr int kMaxW = 128;                    // stage-1 table width (MMA N) limit
 constexpr int kSmemBudget = 227 * 1024;
-constexpr long long kSpinLimit = 4000000000LL;  // ~2 s at 2 GHz
+constexpr long long kSpinLimit = 4000000000LL;  // ~2 s at 2 GHz: the default bound of every wait
 
 enum { KM_L = 0, KM_R = 1, MM = 2, MM_L = 3 };
 
@@ -59,6 +59,8 @@ struct TcArgs {
   int nslot;         // factor blocks per tile (KM: nrep; MM-L: distinct i_1.. values in 128 elements)
   int64_t Pp;        // MM-L: elements per K row (I_0 ... I_{m-1})
   int ksync;         // K-synchronous work split (see get_unit)
+  long long spin_limit;   // bound of every mbarrier wait, in clock cycles
+  int withhold;      // fault injection for tests: the producer skips its first copy (see tc_set_fault)
   uint32_t tx_bytes;
   uint32_t idesc;
   int x3;            // bf16x3: X and the table as hi/lo BF16 pairs, three products per K step
@@ -90,13 +92,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait: false when the limit passes or another role raised the abort flag.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          long long limit) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (clock64() - t0 > kSpinLimit) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 
@@ -321,32 +324,36 @@ __global__ void __launch_bounds__(kThreads, 1)
       int ks0, ks1;
       for (int64_t j = 0; get_unit(a, j, tile, op, pc, ks0, ks1) && !*abort_flag; ++j) {
         for (int ks = ks0; ks < ks1; ++ks) {
-          if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, a.spin_limit)) {
             *abort_flag = 1;
             raise_timeout(a.status, 1);
             break;
           }
-          uint8_t* A = base + stage * stageBytes;
-          uint8_t* B = A + planes * kABytes;
-          mbar_expect_tx(&full[stage], a.tx_bytes);
-          const int k0 = ks * kKT;
-          for (int pl = 0; pl < planes; ++pl) {
-            const CUtensorMap* mx = pl ? &tmXl : &tmX;
-            uint8_t* Ap = A + pl * kABytes;
-            if (a.variant == KM_L) {
-              tma_load_3d(Ap, mx, &full[stage], k0, 0, (int)(tile * a.nrep), pol_x);
-            } else if (a.variant == KM_R) {
-              tma_load_3d(Ap, mx, &full[stage], k0, (int)(tile * a.nrep), 0, pol_x);
-            } else if (a.variant == MM_L) {
-              for (int at = 0; at < 2; ++at)
-                tma_load_2d(Ap + at * kAtomBytes, mx, &full[stage], (int)(tile * kRows + 64 * at), k0, pol_x);
-            } else {
-              for (int at = 0; at < 2; ++at)
-                tma_load_3d(Ap + at * kAtomBytes, mx, &full[stage], (int)(pc * 64), k0, (int)(2 * op + at), pol_x);
+          // fault injection (tests only): the first copy of the CTA's first unit is never issued, so the
+          // MMA issuer's wait for it runs out and the kernel reports TRALS_E_TIMEOUT
+          if (!(a.withhold && j == 0 && ks == ks0)) {
+            uint8_t* A = base + stage * stageBytes;
+            uint8_t* B = A + planes * kABytes;
+            mbar_expect_tx(&full[stage], a.tx_bytes);
+            const int k0 = ks * kKT;
+            for (int pl = 0; pl < planes; ++pl) {
+              const CUtensorMap* mx = pl ? &tmXl : &tmX;
+              uint8_t* Ap = A + pl * kABytes;
+              if (a.variant == KM_L) {
+                tma_load_3d(Ap, mx, &full[stage], k0, 0, (int)(tile * a.nrep), pol_x);
+              } else if (a.variant == KM_R) {
+                tma_load_3d(Ap, mx, &full[stage], k0, (int)(tile * a.nrep), 0, pol_x);
+              } else if (a.variant == MM_L) {
+                for (int at = 0; at < 2; ++at)
+                  tma_load_2d(Ap + at * kAtomBytes, mx, &full[stage], (int)(tile * kRows + 64 * at), k0, pol_x);
+              } else {
+                for (int at = 0; at < 2; ++at)
+                  tma_load_3d(Ap + at * kAtomBytes, mx, &full[stage], (int)(pc * 64), k0, (int)(2 * op + at), pol_x);
+              }
+              tma_load_2d(B + pl * bBytes, pl ? &tmTl : &tmT, &full[stage], k0, 0, pol_tab);
             }
-            tma_load_2d(B + pl * bBytes, pl ? &tmTl : &tmT, &full[stage], k0, 0, pol_tab);
+            ++issued[stage];
           }
-          ++issued[stage];
           if (++stage == NS) {
             stage = 0;
             phase ^= 1u;
@@ -358,7 +365,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // load issued into every stage.
         volatile int never = 0;
         for (int st = 0; st < NS; ++st)
-          if (issued[st] > 0) mbar_wait(&full[st], (uint32_t)((issued[st] - 1) & 1), &never);
+          if (issued[st] > 0) mbar_wait(&full[st], (uint32_t)((issued[st] - 1) & 1), &never, kSpinLimit);
       }
     }
     __syncwarp();
@@ -371,7 +378,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       int ks0, ks1;
       for (int64_t j = 0; get_unit(a, j, tile, op, pc, ks0, ks1) && !*abort_flag; ++j) {
         const int buf = (int)(j & 1);
-        if (!mbar_wait(&acce[buf], (uint32_t)(((j >> 1) & 1) ^ 1), abort_flag)) {
+        if (!mbar_wait(&acce[buf], (uint32_t)(((j >> 1) & 1) ^ 1), abort_flag, a.spin_limit)) {
           *abort_flag = 1;
           raise_timeout(a.status, 2);
           break;
@@ -380,7 +387,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t d = tmem + (uint32_t)(buf * 128);
         bool ok = true;
         for (int ks = ks0; ks < ks1; ++ks) {
-          if (!mbar_wait(&full[stage], phase, abort_flag)) {
+          if (!mbar_wait(&full[stage], phase, abort_flag, a.spin_limit)) {
             *abort_flag = 1;
             raise_timeout(a.status, 3);
             ok = false;
@@ -490,7 +497,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int c = 0; c < fblk; c += 4) cp_async16(myF + c, src + c);
       }
       cp_async_commit();
-      const bool got = mbar_wait(&accf[buf], (uint32_t)((j >> 1) & 1), abort_flag);
+      const bool got = mbar_wait(&accf[buf], (uint32_t)((j >> 1) & 1), abort_flag, a.spin_limit);
       if (!got) {
         *abort_flag = 1;
         epi_stop[j & 1] = 1;
@@ -1234,6 +1241,8 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
     A.whole = per_chunk >= 4 * ctas ? 1 : 0;
   }
   A.ksync = 0;
+  A.spin_limit = kSpinLimit;
+  A.withhold = 0;
   if (A.variant == MM) {
     if (A.pchunks > nsm) {   // each CTA keeps a single p-chunk
       delete impl;
@@ -1485,6 +1494,13 @@ int tc_variant(const TcPlan& p) { return p.impl ? static_cast<const TcImpl*>(p.i
 
 void tc_set_status(TcPlan& p, DevStatus* st) {
   if (p.impl) static_cast<TcImpl*>(p.impl)->args.status = st;
+}
+
+void tc_set_fault(TcPlan& p, int withhold_first_copy, long long spin_limit_cycles) {
+  if (!p.impl) return;
+  TcArgs& A = static_cast<TcImpl*>(p.impl)->args;
+  A.withhold = withhold_first_copy ? 1 : 0;
+  A.spin_limit = spin_limit_cycles > 0 ? spin_limit_cycles : kSpinLimit;
 }
 
 void tc_destroy(TcPlan& p) {

@@ -17,7 +17,8 @@ struct TcPlan {
 
 // Geometry the tensor-core MTTSP would use for mode n (host only; variant -1 = not supported):
 // 0 = K-major X with the factor on the left, 1 = K-major X with the factor on the right,
-// 2 = MN-major X.  S = modes [s_lo, s_hi] is contracted on the tensor cores.
+// 2 = MN-major X with the factor on the right, 3 = MN-major X with the factor on the left (mode 0).
+// S = modes [s_lo, s_hi] is contracted on the tensor cores.
 struct TcChoice {
   int variant = -1;
   int s_lo = 0, s_hi = 0;
@@ -59,10 +60,15 @@ int tc_enqueue_main(TcPlan& p, double* const* cores, double* M, cudaStream_t s, 
 void launch_cores_to_f32(double* const* cores, int N, const int32_t* R, const int64_t* Ist, int64_t I0real,
                          float* dst, cudaStream_t s);
 void tc_destroy(TcPlan& p);
-// Geometry of a valid plan (0 KM-L, 1 KM-R, 2 MM), -1 if none.
+// Geometry of a valid plan (0 KM-L, 1 KM-R, 2 MM, 3 MM-L), -1 if none.
 int tc_variant(const TcPlan& p);
 // Device status word the kernel reports a bounded-wait timeout into.
 void tc_set_status(TcPlan& p, DevStatus* st);
+// Fault injection for tests: with withhold_first_copy set, the producer of every CTA skips the first
+// copy of its first unit, so the MMA issuer's wait for it gives up after spin_limit_cycles clock cycles
+// (<= 0: the default of about 2 s); the kernel then stops every role, drains the copies it did issue,
+// frees its tensor memory and reports TRALS_E_TIMEOUT in the status word.
+void tc_set_fault(TcPlan& p, int withhold_first_copy, long long spin_limit_cycles);
 cudaError_t init_tc_attributes();
 
 }  // namespace trals

@@ -10,6 +10,7 @@
 
 #include "trals_internal.cuh"
 #include "mttsp_tc.cuh"
+#include "../../include/trals_testing.h"
 
 using namespace trals;
 
@@ -65,6 +66,7 @@ trals_status read_status(trals_ctx* ctx) {
     snprintf(buf, sizeof buf, "%s at sweep %d, core %d, index %d (value %.6g)",
              st.code == TRALS_E_NOT_SPD ? "non-positive Cholesky pivot"
              : st.code == TRALS_E_NONFINITE ? "non-finite value in a solve"
+             : st.code == TRALS_E_TIMEOUT   ? "a bounded wait of the tensor-core kernel gave up"
                                             : "device error",
              st.sweep, st.mode, st.index, st.value);
     ctx->last_error = buf;
@@ -1306,6 +1308,35 @@ trals_status trals_mttsp(trals_ctx* ctx, int N, const int64_t* I, const int32_t*
 }
 
 int trals_last_mttsp_path(const trals_ctx* ctx) { return ctx ? ctx->last_mttsp_path : -1; }
+
+trals_status trals_testing_mttsp_withheld_copy(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R,
+                                               const void* X_dev, int mode, const double* const* cores_dev, int n,
+                                               double* M_dev, long long spin_cycles) {
+  if (!ctx || !X_dev || !cores_dev || !M_dev || n < 0 || n >= N || spin_cycles <= 0) return TRALS_E_ARG;
+  trals_status st = check_shape(ctx, N, I, R);
+  if (st != TRALS_OK) return st;
+  if (mode != TRALS_MODE_BF16) {
+    ctx->last_error = "trals_testing_mttsp_withheld_copy: BF16 mode only";
+    return TRALS_E_ARG;
+  }
+  int64_t numel = 1;
+  for (int k = 0; k < N; ++k) numel *= I[k];
+  TcPlan tc;
+  cudaError_t e = cudaSuccess;
+  if (!tc_plan(tc, N, I, R, n, mode, X_dev, numel, &e, ctx->stream)) {
+    TRALS_CUDA_TRY(ctx, e);
+    ctx->last_error = "trals_testing_mttsp_withheld_copy: no tensor-core geometry for this mode";
+    return TRALS_E_ARG;
+  }
+  tc_set_status(tc, ctx->d_status);
+  tc_set_fault(tc, 1, spin_cycles);
+  tc_enqueue(tc, X_dev, const_cast<double* const*>(cores_dev), M_dev, ctx->stream);
+  e = cudaStreamSynchronize(ctx->stream);
+  tc_destroy(tc);
+  TRALS_CUDA_TRY(ctx, e);
+  TRALS_CUDA_TRY(ctx, cudaGetLastError());
+  return read_status(ctx);
+}
 
 int trals_mttsp_path(int N, const int64_t* I, const int32_t* R, int n, int mode) {
   if (N < 3 || N > TRALS_MAX_ORDER || !I || !R || n < 0 || n >= N) return -1;

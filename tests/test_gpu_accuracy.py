@@ -1,0 +1,113 @@
+"""Accuracy of every workload against the FP64 oracle (through the C ABI): the final relative residual
+gap (the mixed-precision bar is 1e-4 absolute) and the largest principal angle between the subchain
+ranges of the two solutions (gauge invariant), at the workloads' own sizes and sweep counts.
+
+The 60^4 and 40^5 references are the oracle's stored runs (tests/golden/make_oracle_reference.py, which
+calls only oracle/); the smooth 256x256x3x256 workload is checked on a reduced 64x64x3x64 instance, where
+the oracle's Householder least squares runs in seconds.
+"""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+import oracle as O
+import trals_inputs as TI
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU hosts
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2210_11362_gb300 as P  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402  (the gauge-invariant angle from mixed Gram chains, pinned in test_host_logic)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return P.trals_create(0)
+
+
+def _run(ctx, w, X_host, Xdev, opts, sweeps, seed=0):
+    cores = TI.init_cores(seed, w.I, w.R_fit)
+    P.trals_decompose(ctx, w.I, w.R_fit, Xdev, cores, sweeps, opts)
+    return cores, O.rel_residual(X_host, cores)
+
+
+def _stored(name):
+    ref = bench.oracle_reference(name, 0)
+    assert ref is not None, f"stored oracle run for {name} missing"
+    return ref
+
+
+@pytest.mark.parametrize("mode,gram", [("fp64", P.GRAM_STRUCTURED), ("fp32", P.GRAM_STRUCTURED),
+                                       ("fp64", P.GRAM_EXPLICIT), ("bf16", P.GRAM_STRUCTURED)])
+def test_tr60x4_rank10_twenty_sweeps_against_stored_oracle(ctx, mode, gram):
+    """60^4, TR ranks 10, 1e-2 noise, 20 sweeps from the seeded init: FP64 (structured or explicit
+    Gram) follows the oracle's trajectory (residual within 1e-9 relative, angle below 1e-6); FP32 and
+    BF16 land within 1e-4 of its final residual."""
+    w = TI.WORKLOADS["tr60x4_r10"]
+    ref = _stored(w.name)
+    X = TI.make_tensor_host(w, 0, O.tr_full)
+    Xdev = P.tensor_to_device(X, torch.float64 if mode == "fp64" else torch.float32)
+    cores, res = _run(ctx, w, X, Xdev, P.make_opts(mode, gram=gram), ref["sweeps"])
+    want = float(ref["residuals"][-1])
+    angle = max(bench.subspace_angle(cores, ref["cores"], n) for n in range(4))
+    if mode == "fp64":
+        assert abs(res - want) <= 1e-9 * want, (res, want)
+        assert angle < 1e-6, angle
+    else:
+        assert abs(res - want) <= 1e-4, (res, want)
+        assert angle < 1e-2, angle
+
+
+@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+def test_tr40x5_thirty_sweeps_against_stored_oracle(ctx, mode):
+    """40^5, ranks (8,10,12,10,8), 1e-3 noise, 30 sweeps from the seeded init with X stored in BF16
+    (or split-BF16): the final residual measured against the FP64 X is within 1e-4 of the FP64 oracle's
+    (split-BF16 within 1e-6), and the subchain ranges agree to within a small angle."""
+    w = TI.WORKLOADS["tr40x5_r8-12"]
+    ref = _stored(w.name)
+    X = TI.make_tensor_host(w, 0, O.tr_full)
+    Xdev = P.tensor_to_device(X, torch.float32)
+    cores, res = _run(ctx, w, X, Xdev, P.make_opts(mode), ref["sweeps"])
+    want = float(ref["residuals"][-1])
+    angle = max(bench.subspace_angle(cores, ref["cores"], n) for n in range(5))
+    assert abs(res - want) <= (1e-4 if mode == "bf16" else 1e-6), (res, want)
+    assert angle < (1e-2 if mode == "bf16" else 1e-4), angle
+
+
+def _smooth_reduced():
+    I, R = (64, 64, 3, 64), (16,) * 4
+    f, phi = TI.sinusoid_params(0, 64, 4)
+    X = TI.sinusoid_tensor(I, f, phi) + 0.05 * TI.gaussian_noise(0, I)
+    return I, R, X, TI.init_cores(0, I, R)
+
+
+def test_smooth_reduced_qr_solver_matches_oracle_least_squares(ctx):
+    """The smooth workload's shape class at 64x64x3x64, rank 16 (a mode of size 3 against
+    R_n R_{n+1} = 256): the FP64 QR-stabilised solve follows the oracle's Householder least squares
+    for two sweeps (cores within 1e-9 relative, residuals within 1e-10 relative)."""
+    I, R, X, init = _smooth_reduced()
+    cores = [G.copy() for G in init]
+    res = P.trals_decompose(ctx, I, R, X, cores, 2, P.make_opts("fp64", solver=P.SOLVE_QR))
+    ref, ref_res = O.tr_als(X, init, 2, "qr")
+    for a, b in zip(cores, ref):
+        assert np.abs(a - b).max() <= 1e-9 * np.abs(b).max()
+    np.testing.assert_allclose(res, ref_res, rtol=1e-10)
+
+
+def test_smooth_reduced_bf16_qr_gap(ctx):
+    """The same reduced problem with X in BF16 and the QR-stabilised solve (its corrected semi-normal
+    steps read the FP32 source X): the residual after 6 sweeps is within 1e-4 of the oracle's."""
+    I, R, X, init = _smooth_reduced()
+    cores = [G.copy() for G in init]
+    P.trals_decompose(ctx, I, R, P.tensor_to_device(X, torch.float32), cores, 6,
+                      P.make_opts("bf16", solver=P.SOLVE_QR))
+    _, ref_res = O.tr_als(X, init, 6, "qr")
+    assert abs(O.rel_residual(X, cores) - ref_res[-1]) <= 1e-4

@@ -653,6 +653,25 @@ def test_explicit_per_sweep_residual_in_reduced_modes(ctx, mode):
     assert abs(direct - per[-1]) < 1e-6
 
 
+@pytest.mark.parametrize("I,R,n", [((40, 40, 40, 40), (8, 10, 12, 10), 1), ((40, 40, 40, 40), (8, 10, 12, 10), 0)])
+def test_tensor_core_wait_timeout_returns_status(ctx, I, R, n):
+    """A copy the TMA producer never issues (fault injection on the host side of the launch): the MMA
+    issuer's bounded wait gives up after ~1 ms, the kernel drains what it did issue, frees its tensor
+    memory and reports TRALS_E_TIMEOUT; the same context then computes the MTTSP correctly."""
+    X, cores = _integer_problem(I, R)
+    Xb = P.tensor_to_device(X, torch.bfloat16)
+    cd = [P.core_to_device(G) for G in cores]
+    r = R[n] * R[(n + 1) % len(I)]
+    M = torch.zeros(I[n] * r, dtype=torch.float64, device="cuda")
+    with pytest.raises(P.TralsError) as e:
+        P.trals_testing_mttsp_withheld_copy(ctx, I, R, Xb, "bf16", cd, n, M, 2_000_000)
+    assert e.value.status == P.E_TIMEOUT
+    assert "bounded wait" in str(e.value)
+    got, path = _run_mttsp(ctx, I, R, Xb, "bf16", cores, n)
+    assert path > 0
+    assert np.array_equal(got, O.mttsp(X, cores, n))
+
+
 def test_plan_uses_the_tensor_core_geometry_it_reports(ctx):
     """The plan of the 40^5 workload runs every mode on the tensor cores, in the geometry the host
     query reports (no silent fallback to the CUDA cores)."""

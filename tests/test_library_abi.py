@@ -1,4 +1,4 @@
-"""The C-ABI library builds, loads without a GPU and exports every entry point include/trals.h declares."""
+"""The C-ABI library builds, loads without a GPU and exports every entry point include/*.h declares."""
 import ctypes
 import os
 import re
@@ -9,7 +9,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "trals.h")).read()
+    import glob
+    src = "".join(open(h).read() for h in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(trals_[a-z0-9_]+)\s*\(", src)))
 
