@@ -581,7 +581,8 @@ __global__ void __launch_bounds__(256) chol_panel_factor_kernel(double* __restri
 template <bool kInSmem>
 __global__ void __launch_bounds__(256) chol_solve_kernel(const double* __restrict__ Lmat, const double* __restrict__ M,
                                                          int Rn, int64_t In, int Rn1, double* __restrict__ G,
-                                                         DevStatus* st, float* __restrict__ G32, int64_t Ist) {
+                                                         DevStatus* st, float* __restrict__ G32, int64_t Ist,
+                                                         int fwd_only) {
   extern __shared__ double sh[];
   constexpr int B = kSolveBlock;
   const int r = Rn * Rn1, nblk = (r + B - 1) / B;
@@ -652,8 +653,8 @@ __global__ void __launch_bounds__(256) chol_solve_kernel(const double* __restric
     if (warp == 0) y[p0 + lane] = sum_parts();
     __syncthreads();
   }
-  // backward: z_q = W_q^T (y_q - L[p1:, q]^T z[p1:])
-  for (int q = nblk - 1; q >= 0; --q) {
+  // backward: z_q = W_q^T (y_q - L[p1:, q]^T z[p1:])  (skipped for a forward solve alone: z = y)
+  for (int q = fwd_only ? -1 : nblk - 1; q >= 0; --q) {
     const int p0 = q * B, p1 = min(r, p0 + B);
     if (p1 < r) {
       if (warp < 4) {
@@ -960,14 +961,14 @@ size_t chol_solve_smem(int r, bool in_smem) {
 }
 
 void launch_chol_solve(const double* Lmat, const double* M, int Rn, int64_t In, int Rn1, double* G, DevStatus* st,
-                       cudaStream_t s, float* G32, int64_t Ist) {
+                       cudaStream_t s, float* G32, int64_t Ist, bool fwd_only) {
   const int r = Rn * Rn1;
   const size_t smem = chol_solve_smem(r, true);
   if (smem <= 227 * 1024)
-    chol_solve_kernel<true><<<(unsigned)In, 256, smem, s>>>(Lmat, M, Rn, In, Rn1, G, st, G32, Ist);
+    chol_solve_kernel<true><<<(unsigned)In, 256, smem, s>>>(Lmat, M, Rn, In, Rn1, G, st, G32, Ist, fwd_only ? 1 : 0);
   else
     chol_solve_kernel<false><<<(unsigned)In, 256, chol_solve_smem(r, false), s>>>(Lmat, M, Rn, In, Rn1, G, st, G32,
-                                                                                 Ist);
+                                                                                 Ist, fwd_only ? 1 : 0);
 }
 
 void launch_core_to_f32(const double* G, int Rn, int64_t In, int64_t Ist, int Rn1, float* G32, cudaStream_t s) {

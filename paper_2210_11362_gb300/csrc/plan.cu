@@ -1119,6 +1119,17 @@ trals_status trals_decompose(trals_ctx* ctx, int N, const int64_t* I, const int3
     }
     Xuse = Xd;
   }
+  if (opts && opts->solver == TRALS_SOLVE_QRNE) {
+    // TR-ALS-QRNE (Alg. 4): its own driver, FP64 only
+    if (opts->mode != TRALS_MODE_FP64 || xt != TRALS_X_F64 || opts->gram != TRALS_GRAM_STRUCTURED) {
+      ctx->last_error = "the QRNE solver runs in the FP64 mode with an FP64 X and the structured Gram";
+      st = TRALS_E_ARG;
+    } else {
+      st = qrne_decompose(ctx, N, I, R, static_cast<const double*>(Xuse), cores, sweeps, rel_res);
+    }
+    if (Xd) cudaFree(Xd);
+    return st;
+  }
   trals_plan* p = nullptr;
   st = trals_plan_create(ctx, N, I, R, Xuse, xt, opts, &p);
   if (st == TRALS_OK) st = trals_plan_set_cores(p, cores);

@@ -1,0 +1,288 @@
+// TR-ALS-QRNE (Alg. 4, Sec. 3.3) on the GPU, FP64: the normal equations of the QR-compressed
+// least-squares problem.
+//
+// Every core is factored G_j = R_j x_2 Q_j (mode-2 QR).  A mode-n update then
+//   * compresses X along every other mode, Y = X x_{j != n} Q_j^T (Multi-TTM, Alg. 4 line 8),
+//   * contracts Y with the subchain of the R factors, M_n = Y_[n] V_n[2] (line 9; the FP64 MTTSP of
+//     the NE path, run on Y and the R cores),
+//   * forms S_n from the Gram tensors of the R factors (lines 3, 6, 12; the Gamma chain of the NE
+//     path) and solves G_{n(2)} S_n = M_n by Cholesky (line 10),
+//   * refactors the updated core (line 11).
+// The mode-2 QR of a core whose unfolding G_{j(2)} (I_j x R_j R_{j+1}) is tall is computed by
+// CholeskyQR2 (Fukaya, Nakatsukasa, Yanagisawa & Yamamoto, 2014): R_1 from the Cholesky factor of
+// G_{(2)}^T G_{(2)}, Q_1 = G_{(2)} R_1^{-1}, then once more on Q_1, R = R_2 R_1 and Q = Q_1 R_2^{-1};
+// two passes give orthonormal columns to working accuracy for any condition number below about
+// u^{-1/2}.  A mode with I_j <= R_j R_{j+1} has nothing to compress (case (2) of the mode-2 QR
+// definition: Q_j square); it keeps Q_j = I and R_j = G_j, which leaves M_n and S_n unchanged, since
+// the method needs only G_j = R_j x_2 Q_j with Q_j orthonormal.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "trals_internal.cuh"
+
+namespace trals {
+namespace {
+
+int grid_of(int64_t n, int threads, int cap = 152 * 16) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, cap));
+}
+
+// core G (R x I x R1, element a + R (i + I b)) -> G2 = G_(2) (I x R R1, column-major, column a + R b)
+__global__ void unfold2_kernel(const double* __restrict__ G, int R, int64_t I, int R1, double* __restrict__ G2) {
+  const int64_t total = (int64_t)R * I * R1;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = e % R, ib = e / R, i = ib % I, b = ib / I;
+    G2[i + I * (a + (int64_t)R * b)] = G[e];
+  }
+}
+
+// P = R^T (lower, r x r, column-major) -> the R core (R x r x R1): Rc[a + R (c + r b)] = R[c, a + R b]
+__global__ void rcore_from_lower_kernel(const double* __restrict__ P, int R, int R1, double* __restrict__ Rc) {
+  const int r = R * R1;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * r; e += gridDim.x * blockDim.x) {
+    const int a = e % R, cb = e / R, c = cb % r, b = cb / r;
+    Rc[e] = P[(a + R * b) + (int64_t)r * c];
+  }
+}
+
+// mode-j TTM with Q^T: out[a + A (c + C b)] = sum_d Q[d + D c] in[a + A (d + D b)].  Each thread owns one
+// (a, b) pair and up to 8 consecutive c, and streams its column of `in` in order of d.
+__global__ void ttm_kernel(const double* __restrict__ in, int64_t A, int64_t D, int64_t B, const double* __restrict__ Q,
+                           int C, double* __restrict__ out) {
+  const int c0 = blockIdx.y * 8;
+  const int nc = min(8, C - c0);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < A * B; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = t % A, b = t / A;
+    const double* x = in + a + A * D * b;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t d = 0; d < D; ++d) {
+      const double v = x[A * d];
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (k < nc) acc[k] = fma(Q[d + D * (c0 + k)], v, acc[k]);
+    }
+    for (int k = 0; k < nc; ++k) out[a + A * ((c0 + k) + (int64_t)C * b)] = acc[k];
+  }
+}
+
+__global__ void finalize_ratio_kernel(const double* red2, double* out) { *out = sqrt(fmax(red2[0], 0.0) / red2[1]); }
+
+struct Buf {
+  std::vector<void*> all;
+  cudaError_t e = cudaSuccess;
+  template <class T>
+  T* get(size_t n) {
+    void* p = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T));
+    if (e == cudaSuccess) all.push_back(p);
+    return static_cast<T*>(p);
+  }
+  ~Buf() {
+    for (void* p : all) cudaFree(p);
+  }
+};
+
+}  // namespace
+
+trals_status qrne_decompose(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R, const double* X,
+                            double* const* cores_host, int sweeps, double* rel_res) {
+  cudaStream_t s = ctx->stream;
+  Buf buf;
+  int rr[kMaxOrder];
+  bool comp[kMaxOrder];
+  int64_t Yd[kMaxOrder];   // extents of the compressed modes (mode n keeps I_n)
+  int64_t core_el[kMaxOrder], rcore_el[kMaxOrder];
+  int rmax = 1;
+  int64_t Imax = 1;
+  for (int j = 0; j < N; ++j) {
+    rr[j] = R[j] * R[(j + 1) % N];
+    comp[j] = I[j] > rr[j];
+    Yd[j] = comp[j] ? rr[j] : I[j];
+    core_el[j] = (int64_t)R[j] * I[j] * R[(j + 1) % N];
+    rcore_el[j] = (int64_t)R[j] * Yd[j] * R[(j + 1) % N];
+    rmax = std::max(rmax, rr[j]);
+    Imax = std::max(Imax, I[j]);
+  }
+  // ---- workspace
+  double* G[kMaxOrder];
+  double* Rc[kMaxOrder];
+  double* Qm[kMaxOrder];
+  double* gam[kMaxOrder];
+  for (int j = 0; j < N; ++j) {
+    G[j] = buf.get<double>(core_el[j]);
+    Rc[j] = comp[j] ? buf.get<double>(rcore_el[j]) : G[j];
+    Qm[j] = comp[j] ? buf.get<double>((size_t)I[j] * rr[j]) : nullptr;
+    gam[j] = buf.get<double>((size_t)R[j] * R[j] * R[(j + 1) % N] * R[(j + 1) % N]);
+  }
+  double* G2 = buf.get<double>((size_t)Imax * rmax);
+  double* Q1 = buf.get<double>((size_t)Imax * rmax);
+  double* C = buf.get<double>((size_t)rmax * rmax);
+  double* L1 = buf.get<double>(lmat_elems(rmax));
+  double* L2 = buf.get<double>(lmat_elems(rmax));
+  double* Pm = buf.get<double>((size_t)rmax * rmax);
+  int64_t rsq = 1;
+  for (int j = 0; j < N; ++j) rsq = std::max<int64_t>(rsq, (int64_t)R[j] * R[j]);
+  double* chainA = buf.get<double>(rsq * rsq);   // Gamma-chain products: R_{n+1}^2 x R_c^2
+  double* chainB = buf.get<double>(rsq * rsq);
+  double* S = buf.get<double>((size_t)rmax * rmax);
+  double* Lm = buf.get<double>(lmat_elems(rmax));
+  // the Multi-TTM of mode n applies the most compressing modes first
+  auto ttm_order = [&](int n) {
+    std::vector<int> order;
+    for (int j = 0; j < N; ++j)
+      if (j != n && comp[j]) order.push_back(j);
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return (double)rr[a] / I[a] < (double)rr[b] / I[b]; });
+    return order;
+  };
+  // Multi-TTM ping-pong buffers: the largest intermediate of any mode's sequence
+  int64_t ymax = 1;
+  for (int n = 0; n < N; ++n) {
+    int64_t cur[kMaxOrder];
+    for (int j = 0; j < N; ++j) cur[j] = I[j];
+    for (int j : ttm_order(n)) {
+      cur[j] = rr[j];
+      int64_t t = 1;
+      for (int m = 0; m < N; ++m) t *= cur[m];
+      ymax = std::max(ymax, t);
+    }
+  }
+  double* Ya = buf.get<double>(ymax);
+  double* Yb = buf.get<double>(ymax);
+  // MTTSP of Y with the R cores: layouts, offsets and tables per mode
+  ModeLayout LY[kMaxOrder];
+  int64_t* offL[kMaxOrder];
+  int64_t* offU[kMaxOrder];
+  int64_t tab = 1;
+  size_t part = 1;
+  for (int n = 0; n < N; ++n) {
+    int64_t d[kMaxOrder];
+    for (int j = 0; j < N; ++j) d[j] = (j == n) ? I[j] : Yd[j];
+    LY[n] = make_mode_layout(N, d, R, n);
+    tab = std::max(tab, table_level_max_elems(LY[n], d, R));
+    part = std::max(part, mttsp_simt_partials_elems(LY[n], mttsp_simt_default_grid(LY[n])));
+    std::vector<int64_t> oL, oU;
+    mode_offsets(N, d, LY[n], oL, oU);
+    offL[n] = buf.get<int64_t>(oL.size());
+    offU[n] = buf.get<int64_t>(oU.size());
+    if (buf.e == cudaSuccess) buf.e = cudaMemcpy(offL[n], oL.data(), oL.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (buf.e == cudaSuccess) buf.e = cudaMemcpy(offU[n], oU.data(), oU.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+  }
+  // explicit residual of the G cores against X (layout of the last mode of X)
+  const ModeLayout LX = make_mode_layout(N, I, R, N - 1);
+  tab = std::max(tab, table_level_max_elems(LX, I, R));
+  std::vector<int64_t> xoL, xoU;
+  mode_offsets(N, I, LX, xoL, xoU);
+  int64_t* xdL = buf.get<int64_t>(xoL.size());
+  int64_t* xdU = buf.get<int64_t>(xoU.size());
+  if (buf.e == cudaSuccess) buf.e = cudaMemcpy(xdL, xoL.data(), xoL.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+  if (buf.e == cudaSuccess) buf.e = cudaMemcpy(xdU, xoU.data(), xoU.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+  const int gridR = mttsp_simt_default_grid(LX);
+  double* lt = buf.get<double>(tab);
+  double* ut = buf.get<double>(tab);
+  double* sc = buf.get<double>(tab);
+  double* partials = buf.get<double>(std::max<size_t>(part, 2 * (size_t)gridR));
+  double* M = buf.get<double>((size_t)Imax * rmax);
+  double* red = buf.get<double>(2);
+  double* res_dev = buf.get<double>(std::max(1, sweeps));
+  TRALS_CUDA_TRY(ctx, buf.e);
+  for (int j = 0; j < N; ++j)
+    TRALS_CUDA_TRY(ctx, cudaMemcpyAsync(G[j], cores_host[j], core_el[j] * sizeof(double), cudaMemcpyHostToDevice, s));
+
+  // mode-2 QR of core j (Alg. 4 lines 2 and 11) and the Gram tensor of its R factor (lines 3 and 12)
+  auto factor_core = [&](int j) {
+    const int Rj = R[j], Rj1 = R[(j + 1) % N], r = rr[j];
+    if (comp[j]) {
+      const int64_t Ij = I[j];
+      unfold2_kernel<<<grid_of(core_el[j], 256), 256, 0, s>>>(G[j], Rj, Ij, Rj1, G2);
+      // pass 1: C = G2^T G2 (the Gram of a 1 x I_j x r "core"), L1 L1^T = C, Q1 = G2 L1^{-T}
+      launch_gamma(G2, 1, Ij, r, C, s);
+      launch_cholesky(C, L1, r, ctx->d_status, nullptr, j, s);
+      launch_chol_solve(L1, G2, 1, Ij, r, Q1, ctx->d_status, s, nullptr, 0, true);
+      // pass 2 on Q1
+      launch_gamma(Q1, 1, Ij, r, C, s);
+      launch_cholesky(C, L2, r, ctx->d_status, nullptr, j, s);
+      launch_chol_solve(L2, Q1, 1, Ij, r, Qm[j], ctx->d_status, s, nullptr, 0, true);
+      // R = R2 R1 = (L1 L2)^T
+      launch_gemm_f64(r, r, r, L1, L2, Pm, s);
+      rcore_from_lower_kernel<<<grid_of((int64_t)r * r, 256), 256, 0, s>>>(Pm, Rj, Rj1, Rc[j]);
+    }
+    launch_gamma(Rc[j], Rj, Yd[j], Rj1, gam[j], s);
+  };
+  for (int j = 0; j < N; ++j) factor_core(j);
+
+  for (int sw = 0; sw < sweeps; ++sw) {
+    for (int n = 0; n < N; ++n) {
+      const int Rn = R[n], Rn1 = R[(n + 1) % N], r = rr[n];
+      // S_n from the Gram tensors of the R factors: Pi_n = Gamma_{n+1} ... Gamma_{n-1}, regrouped (line 7)
+      {
+        const int c0 = (n + 1) % N;
+        const double* cur = gam[c0];
+        const int rows = R[c0] * R[c0];
+        double* bufs[2] = {chainA, chainB};
+        for (int t = 2; t < N; ++t) {
+          const int c = (n + t) % N;
+          launch_gemm_f64(rows, R[(c + 1) % N] * R[(c + 1) % N], R[c] * R[c], cur, gam[c], bufs[t % 2], s);
+          cur = bufs[t % 2];
+        }
+        launch_regroup_S(cur, Rn, Rn1, S, s);
+      }
+      // Y = X x_{j != n} Q_j^T, the most compressing modes first (line 8)
+      int64_t cur[kMaxOrder];
+      for (int j = 0; j < N; ++j) cur[j] = I[j];
+      const std::vector<int> order = ttm_order(n);
+      const double* src = X;
+      double* dst = Ya;
+      for (int j : order) {
+        int64_t A = 1, B = 1;
+        for (int m = 0; m < j; ++m) A *= cur[m];
+        for (int m = j + 1; m < N; ++m) B *= cur[m];
+        const dim3 g((unsigned)grid_of(A * B, 128), (unsigned)((rr[j] + 7) / 8));
+        ttm_kernel<<<g, 128, 0, s>>>(src, A, I[j], B, Qm[j], rr[j], dst);
+        cur[j] = rr[j];
+        src = dst;
+        dst = (dst == Ya) ? Yb : Ya;
+      }
+      // M_n = Y_[n] V_n[2]: the FP64 MTTSP of Y with the R cores (line 9)
+      {
+        int64_t d[kMaxOrder];
+        for (int j = 0; j < N; ++j) d[j] = (j == n) ? I[j] : Yd[j];
+        const double* rc[kMaxOrder];
+        for (int j = 0; j < N; ++j) rc[j] = Rc[j];
+        build_tables(LY[n], rc, d, R, lt, ut, sc, s);
+        MttspSimtArgs a;
+        a.X = src;
+        a.xt = TRALS_X_F64;
+        a.ltab = lt;
+        a.utab = ut;
+        a.offL = offL[n];
+        a.offU = offU[n];
+        a.L = LY[n];
+        a.partials = partials;
+        a.M = M;
+        a.gridX = mttsp_simt_default_grid(LY[n]);
+        launch_mttsp_simt(a, s);
+      }
+      // G_{n(2)} S_n = M_n by Cholesky (line 10), then the new core's QR and Gram tensor (lines 11-12)
+      launch_cholesky(S, Lm, r, ctx->d_status, nullptr, n, s);
+      launch_chol_solve(Lm, M, Rn, I[n], Rn1, G[n], ctx->d_status, s);
+      factor_core(n);
+    }
+    // explicit relative residual of the G cores against X (Sec. 4 error formula)
+    const double* gc[kMaxOrder];
+    for (int j = 0; j < N; ++j) gc[j] = G[j];
+    build_tables(LX, gc, I, R, lt, ut, sc, s);
+    launch_reconstruct(LX, lt, ut, xdL, xdU, G[N - 1], nullptr, TRALS_X_F64, X, TRALS_X_F64, partials, gridR, s);
+    launch_reduce_pairs(partials, gridR, red, s);
+    finalize_ratio_kernel<<<1, 1, 0, s>>>(red, res_dev + sw);
+    TRALS_CUDA_TRY(ctx, cudaGetLastError());
+  }
+  for (int j = 0; j < N; ++j)
+    TRALS_CUDA_TRY(ctx, cudaMemcpyAsync(cores_host[j], G[j], core_el[j] * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (rel_res && sweeps > 0)
+    TRALS_CUDA_TRY(ctx, cudaMemcpyAsync(rel_res, res_dev, sweeps * sizeof(double), cudaMemcpyDeviceToHost, s));
+  TRALS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  return TRALS_OK;
+}
+
+}  // namespace trals

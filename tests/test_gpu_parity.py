@@ -683,3 +683,28 @@ def test_plan_uses_the_tensor_core_geometry_it_reports(ctx):
     finally:
         plan.close()
     assert got == [P.trals_mttsp_path(I, R, n, "bf16") for n in range(5)] == [4, 3, 1, 1, 2]
+
+
+@pytest.mark.parametrize("I,R", [((300, 30, 400), (3, 4, 2)), ((40, 3, 50, 36), (2, 3, 2, 2)),
+                                 ((20, 20, 20), (3, 3, 3)), ((13, 3, 5, 2, 4), (2, 3, 2, 2, 3))])
+def test_decompose_qrne_matches_oracle(ctx, I, R):
+    """TR-ALS-QRNE (Alg. 4) on the GPU: CholeskyQR2 of every compressible core, the Multi-TTM of X with
+    the Q factors, the FP64 MTTSP of the compressed tensor with the R cores, the structured Gram chain of
+    the R cores and the Cholesky solve.  Two sweeps from the same init give the cores of the oracle's
+    literal Alg. 4 (which equals regular TR-ALS) within 1e-9 relative, and the same residuals.  The
+    shapes mix compressible modes (I_j > R_j R_{j+1}) with modes kept whole (I_j <= R_j R_{j+1})."""
+    X, init = _problem(I, R)
+    cores = [G.copy() for G in init]
+    res = P.trals_decompose(ctx, I, R, X, cores, 2, P.make_opts("fp64", solver=P.SOLVE_QRNE))
+    ref, ref_res = O.tr_als_qrne(X, init, 2)
+    for a, b in zip(cores, ref):
+        assert rel(a, b) < 1e-9, rel(a, b)
+    np.testing.assert_allclose(res, ref_res, rtol=1e-9)
+
+
+def test_qrne_rejects_reduced_precision(ctx):
+    X, init = _problem((20, 20, 20), (3, 3, 3))
+    with pytest.raises(P.TralsError) as e:
+        P.trals_decompose(ctx, (20, 20, 20), (3, 3, 3), P.tensor_to_device(X, torch.float32), [G.copy() for G in init],
+                          1, P.make_opts("fp32", solver=P.SOLVE_QRNE))
+    assert e.value.status == P.E_ARG

@@ -118,3 +118,30 @@ def test_oversized_request_rejected_and_host_X_matches_device_X(ctx, problems):
         srv.close()
     for ga, gb in zip(a[1], b[1]):
         np.testing.assert_array_equal(ga, gb)
+
+
+@pytest.mark.parametrize("mode", ["fp32", "bf16"])
+def test_served_results_match_the_oracle_on_a_subsample(ctx, problems, mode):
+    """A subsample of served requests (orders 3 and 4) against the FP64 oracle run alone from the same
+    init for the serving workload's 15 sweeps: the final relative residual, measured against the
+    request's own X, is within 1e-4 of the oracle's.  The runs start near the generating cores (plus a
+    1e-2 perturbation), so both precisions are compared at convergence: trajectories of different
+    precisions from a random start part ways before they converge."""
+    import oracle as O
+    rng = np.random.default_rng(7)
+    picks = [0, 1, 3]
+    inits = {k: [G + 1e-2 * rng.standard_normal(G.shape) for G in TI.gaussian_cores(100 + k, *SHAPES[k])]
+             for k in picks}
+    srv = P.Server(0, hbm_budget_bytes=8 << 30, max_slots=4)
+    try:
+        tickets = [srv.submit(SHAPES[k][0], SHAPES[k][1], problems[k][0], inits[k], 15, P.make_opts(mode))
+                   for k in picks]
+        out = [srv.wait(t, timeout=300.0) for t in tickets]
+    finally:
+        srv.close()
+    for k, got in zip(picks, out):
+        I, R = SHAPES[k]
+        X = TI.unflat_f(problems[k][0].double().cpu().numpy(), I)
+        assert got is not None and got[0]["status"] == P.OK
+        _, ref_res = O.tr_als(X, inits[k], 15, "chol")
+        assert abs(O.rel_residual(X, got[1]) - ref_res[-1]) <= 1e-4, (k, O.rel_residual(X, got[1]), ref_res[-1])
