@@ -75,11 +75,23 @@ typedef enum { TRALS_X_F64 = 0, TRALS_X_F32 = 1, TRALS_X_BF16 = 2 } trals_xtype;
  *          hi + lo in FP32 arithmetic). */
 typedef enum { TRALS_MODE_FP64 = 0, TRALS_MODE_FP32 = 1, TRALS_MODE_BF16 = 2, TRALS_MODE_BF16X3 = 3 } trals_mode;
 
-/* Solver for the R_n R_{n+1} subproblem: Cholesky on the normal equations (Alg. 2 line 9), the
- * QR-stabilised solve (Sec. 3.2), or TR-ALS-QRNE (Alg. 4, Sec. 3.3: the normal equations of the problem
- * compressed by the mode-2 QR of every core, with the Multi-TTM Y = X x_{j!=n} Q_j^T; FP64 mode and
- * trals_decompose only). */
-typedef enum { TRALS_SOLVE_CHOL = 0, TRALS_SOLVE_QR = 1, TRALS_SOLVE_QRNE = 2 } trals_solver;
+/* Solver for the R_n R_{n+1} subproblem:
+ *  CHOL          Cholesky on the normal equations (Alg. 2 line 9);
+ *  QR            the QR-stabilised solve (Sec. 3.2): R factor of G^{!=n}_[2] by structured recursive QR and
+ *                corrected semi-normal steps, for any shape;
+ *  QRNE          TR-ALS-QRNE (Alg. 4, Sec. 3.3): the normal equations of the problem compressed by the mode-2
+ *                QR of every core (CholeskyQR2), with the Multi-TTM Y = X x_{j!=n} Q_j^T;
+ *  QR_COMPRESSED the literal TR-ALS-QR (Alg. 3) for the compressible regime (I_j > R_j R_{j+1}): Householder
+ *                mode-2 QRs of the cores, the Multi-TTM, the explicit subchain V_n of the R factors and its
+ *                Householder QR V_n[2] = Q_0 R, W_n = Y_[n] Q_0 and the triangular solve with R; needs
+ *                R_n R_{n+1} <= prod_{j!=n} min(I_j, R_j R_{j+1}) <= 2^22.
+ * QRNE and QR_COMPRESSED run in the FP64 mode through trals_decompose only. */
+typedef enum {
+  TRALS_SOLVE_CHOL = 0,
+  TRALS_SOLVE_QR = 1,
+  TRALS_SOLVE_QRNE = 2,
+  TRALS_SOLVE_QR_COMPRESSED = 3
+} trals_solver;
 
 /* How S_n is formed: structured Gamma chain (Prop. subchain_gram) or the explicit
  * subchain matrix's Gram (G^{!=n}_[2])^T G^{!=n}_[2] (regular TR-ALS, Alg. 1). */

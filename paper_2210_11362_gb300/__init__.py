@@ -30,7 +30,7 @@ X_F64, X_F32, X_BF16 = 0, 1, 2
 MODE_FP64, MODE_FP32, MODE_BF16, MODE_BF16X3 = 0, 1, 2, 3
 MODE_NAMES = {"fp64": MODE_FP64, "fp32": MODE_FP32, "bf16": MODE_BF16, "bf16x3": MODE_BF16X3}
 # trals_solver / trals_gram
-SOLVE_CHOL, SOLVE_QR, SOLVE_QRNE = 0, 1, 2
+SOLVE_CHOL, SOLVE_QR, SOLVE_QRNE, SOLVE_QR_COMPRESSED = 0, 1, 2, 3
 GRAM_STRUCTURED, GRAM_EXPLICIT = 0, 1
 
 EXPORTED = [

@@ -582,7 +582,7 @@ template <bool kInSmem>
 __global__ void __launch_bounds__(256) chol_solve_kernel(const double* __restrict__ Lmat, const double* __restrict__ M,
                                                          int Rn, int64_t In, int Rn1, double* __restrict__ G,
                                                          DevStatus* st, float* __restrict__ G32, int64_t Ist,
-                                                         int fwd_only) {
+                                                         int which) {
   extern __shared__ double sh[];
   constexpr int B = kSolveBlock;
   const int r = Rn * Rn1, nblk = (r + B - 1) / B;
@@ -628,8 +628,8 @@ __global__ void __launch_bounds__(256) chol_solve_kernel(const double* __restric
     return kInSmem ? Ws[q * (B * (B + 1)) + a + (B + 1) * b] : Wg[q * (B * B) + a + B * b];
   };
   auto sum_parts = [&]() { return (part[lane] + part[B + lane]) + (part[2 * B + lane] + part[3 * B + lane]); };
-  // forward: y_q = W_q (y_q - L[q, :p0] y[:p0])
-  for (int q = 0; q < nblk; ++q) {
+  // forward: y_q = W_q (y_q - L[q, :p0] y[:p0])  (skipped for a backward solve alone)
+  for (int q = 0; q < (which == 2 ? 0 : nblk); ++q) {
     const int p0 = q * B;
     if (p0 > 0) {
       if (warp < 4) {
@@ -654,7 +654,7 @@ __global__ void __launch_bounds__(256) chol_solve_kernel(const double* __restric
     __syncthreads();
   }
   // backward: z_q = W_q^T (y_q - L[p1:, q]^T z[p1:])  (skipped for a forward solve alone: z = y)
-  for (int q = fwd_only ? -1 : nblk - 1; q >= 0; --q) {
+  for (int q = which == 1 ? -1 : nblk - 1; q >= 0; --q) {
     const int p0 = q * B, p1 = min(r, p0 + B);
     if (p1 < r) {
       if (warp < 4) {
@@ -961,14 +961,14 @@ size_t chol_solve_smem(int r, bool in_smem) {
 }
 
 void launch_chol_solve(const double* Lmat, const double* M, int Rn, int64_t In, int Rn1, double* G, DevStatus* st,
-                       cudaStream_t s, float* G32, int64_t Ist, bool fwd_only) {
+                       cudaStream_t s, float* G32, int64_t Ist, int part) {
   const int r = Rn * Rn1;
   const size_t smem = chol_solve_smem(r, true);
   if (smem <= 227 * 1024)
-    chol_solve_kernel<true><<<(unsigned)In, 256, smem, s>>>(Lmat, M, Rn, In, Rn1, G, st, G32, Ist, fwd_only ? 1 : 0);
+    chol_solve_kernel<true><<<(unsigned)In, 256, smem, s>>>(Lmat, M, Rn, In, Rn1, G, st, G32, Ist, part);
   else
     chol_solve_kernel<false><<<(unsigned)In, 256, chol_solve_smem(r, false), s>>>(Lmat, M, Rn, In, Rn1, G, st, G32,
-                                                                                 Ist, fwd_only ? 1 : 0);
+                                                                                 Ist, part);
 }
 
 void launch_core_to_f32(const double* G, int Rn, int64_t In, int64_t Ist, int Rn1, float* G32, cudaStream_t s) {

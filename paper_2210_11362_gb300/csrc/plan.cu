@@ -1119,13 +1119,14 @@ trals_status trals_decompose(trals_ctx* ctx, int N, const int64_t* I, const int3
     }
     Xuse = Xd;
   }
-  if (opts && opts->solver == TRALS_SOLVE_QRNE) {
-    // TR-ALS-QRNE (Alg. 4): its own driver, FP64 only
+  if (opts && (opts->solver == TRALS_SOLVE_QRNE || opts->solver == TRALS_SOLVE_QR_COMPRESSED)) {
+    // TR-ALS-QRNE (Alg. 4) and the literal TR-ALS-QR (Alg. 3): their own driver, FP64 only
     if (opts->mode != TRALS_MODE_FP64 || xt != TRALS_X_F64 || opts->gram != TRALS_GRAM_STRUCTURED) {
-      ctx->last_error = "the QRNE solver runs in the FP64 mode with an FP64 X and the structured Gram";
+      ctx->last_error = "the QRNE and compressed-QR solvers run in the FP64 mode with an FP64 X and the structured Gram";
       st = TRALS_E_ARG;
     } else {
-      st = qrne_decompose(ctx, N, I, R, static_cast<const double*>(Xuse), cores, sweeps, rel_res);
+      st = qrne_decompose(ctx, N, I, R, static_cast<const double*>(Xuse), cores, sweeps, rel_res,
+                          opts->solver == TRALS_SOLVE_QR_COMPRESSED);
     }
     if (Xd) cudaFree(Xd);
     return st;

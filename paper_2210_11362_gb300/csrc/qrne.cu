@@ -1,6 +1,7 @@
-// TR-ALS-QRNE (Alg. 4, Sec. 3.3) on the GPU, FP64: the normal equations of the QR-compressed
-// least-squares problem.
+// TR-ALS-QRNE (Alg. 4, Sec. 3.3) and the literal TR-ALS-QR (Alg. 3, Sec. 3.2) on the GPU, FP64: both
+// work on the least-squares problem compressed by the mode-2 QR of every core.
 //
+// TR-ALS-QRNE solves the compressed problem through its normal equations:
 // Every core is factored G_j = R_j x_2 Q_j (mode-2 QR).  A mode-n update then
 //   * compresses X along every other mode, Y = X x_{j != n} Q_j^T (Multi-TTM, Alg. 4 line 8),
 //   * contracts Y with the subchain of the R factors, M_n = Y_[n] V_n[2] (line 9; the FP64 MTTSP of
@@ -15,6 +16,11 @@
 // u^{-1/2}.  A mode with I_j <= R_j R_{j+1} has nothing to compress (case (2) of the mode-2 QR
 // definition: Q_j square); it keeps Q_j = I and R_j = G_j, which leaves M_n and S_n unchanged, since
 // the method needs only G_j = R_j x_2 Q_j with Q_j orthonormal.
+//
+// The literal TR-ALS-QR (Alg. 3) is meant for the compressible regime, where the subchain V_n of the R
+// factors (Alg. 3 line 5) is small: V_n[2] is formed explicitly, factored by Householder QR with Q_0
+// formed explicitly (line 6), W_n = Y_[n] Q_0 (line 8) and G_{n(2)} R^T = W_n is solved by substitution
+// (line 9).  Its core QRs (lines 2 and 10) are Householder QRs too.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -68,6 +74,174 @@ __global__ void ttm_kernel(const double* __restrict__ in, int64_t A, int64_t D, 
 
 __global__ void finalize_ratio_kernel(const double* red2, double* out) { *out = sqrt(fmax(red2[0], 0.0) / red2[1]); }
 
+// R (r x r upper, column-major) -> the R core (R x r x R1): Rc[a + R (c + r b)] = R[c, a + R b]
+__global__ void rcore_from_upper_kernel(const double* __restrict__ Rm, int R, int R1, double* __restrict__ Rc) {
+  const int r = R * R1;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * r; e += gridDim.x * blockDim.x) {
+    const int a = e % R, cb = e / R, c = cb % r, b = cb / r;
+    Rc[e] = Rm[c + (int64_t)r * (a + R * b)];
+  }
+}
+
+// V_n[2] explicitly (J' x r, column-major, column a + R_n b) from the two partial-chain tables of a mode
+// layout: V[k, a + R_n b] = sum_s Ltab(l)[b, s] Utab(u)[s, a], k = l + nL u (eq. subchain_new)
+__global__ void subchain_explicit_kernel(const double* __restrict__ ltab, const double* __restrict__ utab,
+                                         const ModeLayout L, double* __restrict__ V) {
+  const int64_t J = L.nL * L.nU;
+  const int r = L.Rn * L.Rn1;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < J * r; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = e % J;
+    const int c = (int)(e / J), a = c % L.Rn, b = c / L.Rn;
+    const int64_t l = k % L.nL, u = k / L.nL;
+    const double* Lt = ltab + l * (int64_t)L.Rn1 * L.Rs;
+    const double* Ut = utab + u * (int64_t)L.Rs * L.Rn;
+    double acc = 0.0;
+    for (int t = 0; t < L.Rs; ++t) acc = fma(Lt[b + L.Rn1 * t], Ut[t + L.Rs * a], acc);
+    V[e] = acc;
+  }
+}
+
+// W_n = Y_[n] Q_0 (I_n x r): W[i + I_n c] = sum_k Y[offL[l] + offU[u] + i strideN] Q_0[k + J' c]
+__global__ void wn_kernel(const double* __restrict__ Y, const int64_t* __restrict__ offL,
+                          const int64_t* __restrict__ offU, const ModeLayout L, const double* __restrict__ Q0,
+                          double* __restrict__ W) {
+  const int64_t J = L.nL * L.nU;
+  const int r = L.Rn * L.Rn1;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L.In * r; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % L.In, c = e / L.In;
+    const double* q = Q0 + J * c;
+    double a0 = 0.0, a1 = 0.0;
+    int64_t k = 0;
+    for (int64_t u = 0; u < L.nU; ++u)
+      for (int64_t l = 0; l < L.nL; ++l, ++k) {
+        const double y = Y[offL[l] + offU[u] + i * L.strideN];
+        if (k & 1) a1 = fma(y, q[k], a1);
+        else a0 = fma(y, q[k], a0);
+      }
+    W[e] = a0 + a1;
+  }
+}
+
+// L = R^T as a factor buffer (lower triangle, reciprocal diagonal; the diagonal-block inverses follow)
+__global__ void upper_to_lmat_kernel(const double* __restrict__ Rm, int r, double* __restrict__ Lmat) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * r + r; e += gridDim.x * blockDim.x) {
+    if (e < r * r) {
+      const int i = e % r, j = e / r;
+      Lmat[e] = (i >= j) ? Rm[j + (int64_t)r * i] : 0.0;
+    } else {
+      const int j = e - r * r;
+      Lmat[e] = 1.0 / Rm[j + (int64_t)r * j];
+    }
+  }
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int k = 0; k < nw; ++k) t += red[k];   // every thread, same fixed order
+  return t;
+}
+
+// Householder QR of A (m x r, column-major, m >= r) in one CTA (Golub & Van Loan Sec. 5.2): A's columns
+// are overwritten by the Householder vectors; R (r x r upper, column-major) and Q = H_0 ... H_{r-1} [I; 0]
+// (m x r, column-major) are written, signs chosen so that R has a positive diagonal.  A column whose
+// remaining part is at the rounding level, |R_kk| <= 32 r u max_j |a_j| (numerically rank deficient:
+// a column that repeats earlier ones leaves a remainder of about u |a| rather than exact zeros), sets
+// TRALS_E_NOT_SPD with its index and stops.
+__global__ void __launch_bounds__(256) householder_qr_kernel(double* __restrict__ A, int64_t m, int r,
+                                                             double* __restrict__ Rm, double* __restrict__ Q,
+                                                             double* __restrict__ tau, DevStatus* st, int mode) {
+  __shared__ double red[32];
+  __shared__ double sc[2];
+  __shared__ int fail;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  if (tid == 0) fail = 0;
+  // the largest column norm of A, for the rank test
+  double cmax = 0.0;
+  for (int j = warp; j < r; j += nw) {
+    double w = 0.0;
+    for (int64_t i = lane; i < m; i += 32) w = fma(A[i + m * (int64_t)j], A[i + m * (int64_t)j], w);
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    cmax = fmax(cmax, w);
+  }
+  __syncthreads();
+  if (lane == 0) red[warp] = cmax;
+  __syncthreads();
+  double norm0 = 0.0;
+  for (int k = 0; k < nw; ++k) norm0 = fmax(norm0, red[k]);
+  norm0 = sqrt(norm0);
+  const double tol = 32.0 * r * 1.1102230246251565e-16 * norm0;
+  for (int k = 0; k < r; ++k) {
+    double* x = A + m * (int64_t)k;
+    double ss = 0.0;
+    for (int64_t i = k + tid; i < m; i += blockDim.x) ss = fma(x[i], x[i], ss);
+    ss = block_sum(ss, red);
+    if (tid == 0) {
+      const double x0 = x[k], alpha = sqrt(ss);
+      if (!(alpha > tol) || !isfinite(alpha)) {
+        fail = 1;
+        set_status(st, isfinite(alpha) ? TRALS_E_NOT_SPD : TRALS_E_NONFINITE, -1, mode, k, alpha);
+      } else {
+        const double beta = x0 >= 0.0 ? -alpha : alpha;
+        const double v0 = x0 - beta;
+        const double vtv = ss - x0 * x0 + v0 * v0;
+        x[k] = v0;
+        Rm[k + (int64_t)r * k] = beta;
+        sc[0] = 2.0 / vtv;
+        tau[k] = 2.0 / vtv;
+      }
+    }
+    __syncthreads();
+    if (fail) return;
+    const double c = sc[0];
+    // trailing columns: a_j -= c (v^T a_j) v, one warp per column
+    for (int j = k + 1 + warp; j < r; j += nw) {
+      double* y = A + m * (int64_t)j;
+      double w = 0.0;
+      for (int64_t i = k + lane; i < m; i += 32) w = fma(x[i], y[i], w);
+      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+      const double f = c * w;
+      for (int64_t i = k + lane; i < m; i += 32) y[i] = fma(-f, x[i], y[i]);
+    }
+    __syncthreads();
+  }
+  // R above the diagonal: row k of the reduced A
+  for (int e = tid; e < r * r; e += blockDim.x) {
+    const int i = e % r, j = e / r;
+    if (i < j) Rm[e] = A[i + m * (int64_t)j];
+    else if (i > j) Rm[e] = 0.0;
+  }
+  // Q = H_0 ... H_{r-1} [I; 0], accumulated backwards (H_k touches rows >= k and, then, columns >= k)
+  for (int64_t e = tid; e < m * r; e += blockDim.x) Q[e] = ((e % m) == (e / m)) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int k = r - 1; k >= 0; --k) {
+    const double* v = A + m * (int64_t)k;
+    const double c = tau[k];
+    for (int j = k + warp; j < r; j += nw) {
+      double* q = Q + m * (int64_t)j;
+      double w = 0.0;
+      for (int64_t i = k + lane; i < m; i += 32) w = fma(v[i], q[i], w);
+      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+      const double f = c * w;
+      for (int64_t i = k + lane; i < m; i += 32) q[i] = fma(-f, v[i], q[i]);
+    }
+    __syncthreads();
+  }
+  // positive diagonal: flip row k of R and column k of Q where R_kk < 0
+  for (int k = warp; k < r; k += nw) {
+    const bool neg = Rm[k + (int64_t)r * k] < 0.0;   // read by every lane before any lane flips it
+    __syncwarp();
+    if (neg) {
+      for (int j = k + lane; j < r; j += 32) Rm[k + (int64_t)r * j] = -Rm[k + (int64_t)r * j];
+      for (int64_t i = lane; i < m; i += 32) Q[i + m * (int64_t)k] = -Q[i + m * (int64_t)k];
+    }
+  }
+}
+
 struct Buf {
   std::vector<void*> all;
   cudaError_t e = cudaSuccess;
@@ -86,7 +260,7 @@ struct Buf {
 }  // namespace
 
 trals_status qrne_decompose(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R, const double* X,
-                            double* const* cores_host, int sweeps, double* rel_res) {
+                            double* const* cores_host, int sweeps, double* rel_res, bool literal) {
   cudaStream_t s = ctx->stream;
   Buf buf;
   int rr[kMaxOrder];
@@ -183,6 +357,23 @@ trals_status qrne_decompose(trals_ctx* ctx, int N, const int64_t* I, const int32
   double* sc = buf.get<double>(tab);
   double* partials = buf.get<double>(std::max<size_t>(part, 2 * (size_t)gridR));
   double* M = buf.get<double>((size_t)Imax * rmax);
+  double* tau = buf.get<double>(std::max<int64_t>(rmax, 1));
+  // literal Alg. 3: V_n[2] and Q_0 (J' x r) of the largest mode
+  int64_t vmax = 1;
+  if (literal)
+    for (int n = 0; n < N; ++n) vmax = std::max<int64_t>(vmax, LY[n].nL * LY[n].nU * rr[n]);
+  if (literal) {
+    for (int n = 0; n < N; ++n) {
+      const int64_t Jc = LY[n].nL * LY[n].nU;
+      if (Jc < rr[n] || Jc > ((int64_t)1 << 22)) {
+        ctx->last_error = "literal TR-ALS-QR: the compressed subchain of mode " + std::to_string(n) + " has " +
+                          std::to_string(Jc) + " rows (needs R_n R_{n+1} <= rows <= 2^22; use TRALS_SOLVE_QR)";
+        return TRALS_E_ARG;
+      }
+    }
+  }
+  double* V = literal ? buf.get<double>(vmax) : nullptr;
+  double* Q0 = literal ? buf.get<double>(vmax) : nullptr;
   double* red = buf.get<double>(2);
   double* res_dev = buf.get<double>(std::max(1, sweeps));
   TRALS_CUDA_TRY(ctx, buf.e);
@@ -192,22 +383,27 @@ trals_status qrne_decompose(trals_ctx* ctx, int N, const int64_t* I, const int32
   // mode-2 QR of core j (Alg. 4 lines 2 and 11) and the Gram tensor of its R factor (lines 3 and 12)
   auto factor_core = [&](int j) {
     const int Rj = R[j], Rj1 = R[(j + 1) % N], r = rr[j];
-    if (comp[j]) {
+    if (comp[j] && literal) {
+      // Householder mode-2 QR (Alg. 3 lines 2 and 10)
+      unfold2_kernel<<<grid_of(core_el[j], 256), 256, 0, s>>>(G[j], Rj, I[j], Rj1, G2);
+      householder_qr_kernel<<<1, 256, 0, s>>>(G2, I[j], r, Pm, Qm[j], tau, ctx->d_status, j);
+      rcore_from_upper_kernel<<<grid_of((int64_t)r * r, 256), 256, 0, s>>>(Pm, Rj, Rj1, Rc[j]);
+    } else if (comp[j]) {
       const int64_t Ij = I[j];
       unfold2_kernel<<<grid_of(core_el[j], 256), 256, 0, s>>>(G[j], Rj, Ij, Rj1, G2);
       // pass 1: C = G2^T G2 (the Gram of a 1 x I_j x r "core"), L1 L1^T = C, Q1 = G2 L1^{-T}
       launch_gamma(G2, 1, Ij, r, C, s);
       launch_cholesky(C, L1, r, ctx->d_status, nullptr, j, s);
-      launch_chol_solve(L1, G2, 1, Ij, r, Q1, ctx->d_status, s, nullptr, 0, true);
+      launch_chol_solve(L1, G2, 1, Ij, r, Q1, ctx->d_status, s, nullptr, 0, kSolveForward);
       // pass 2 on Q1
       launch_gamma(Q1, 1, Ij, r, C, s);
       launch_cholesky(C, L2, r, ctx->d_status, nullptr, j, s);
-      launch_chol_solve(L2, Q1, 1, Ij, r, Qm[j], ctx->d_status, s, nullptr, 0, true);
+      launch_chol_solve(L2, Q1, 1, Ij, r, Qm[j], ctx->d_status, s, nullptr, 0, kSolveForward);
       // R = R2 R1 = (L1 L2)^T
       launch_gemm_f64(r, r, r, L1, L2, Pm, s);
       rcore_from_lower_kernel<<<grid_of((int64_t)r * r, 256), 256, 0, s>>>(Pm, Rj, Rj1, Rc[j]);
     }
-    launch_gamma(Rc[j], Rj, Yd[j], Rj1, gam[j], s);
+    if (!literal) launch_gamma(Rc[j], Rj, Yd[j], Rj1, gam[j], s);
   };
   for (int j = 0; j < N; ++j) factor_core(j);
 
@@ -215,7 +411,7 @@ trals_status qrne_decompose(trals_ctx* ctx, int N, const int64_t* I, const int32
     for (int n = 0; n < N; ++n) {
       const int Rn = R[n], Rn1 = R[(n + 1) % N], r = rr[n];
       // S_n from the Gram tensors of the R factors: Pi_n = Gamma_{n+1} ... Gamma_{n-1}, regrouped (line 7)
-      {
+      if (!literal) {
         const int c0 = (n + 1) % N;
         const double* cur = gam[c0];
         const int rows = R[c0] * R[c0];
@@ -242,6 +438,25 @@ trals_status qrne_decompose(trals_ctx* ctx, int N, const int64_t* I, const int32
         cur[j] = rr[j];
         src = dst;
         dst = (dst == Ya) ? Yb : Ya;
+      }
+      if (literal) {
+        // Alg. 3: V_n[2] explicitly from the R cores (line 5), its Householder QR V_n[2] = Q_0 R with Q_0
+        // formed (line 6), W_n = Y_[n] Q_0 (line 8), then G_{n(2)} R^T = W_n by substitution (line 9):
+        // G = W L^{-1} with L = R^T, the backward solve alone
+        int64_t d[kMaxOrder];
+        for (int j = 0; j < N; ++j) d[j] = (j == n) ? I[j] : Yd[j];
+        const double* rc[kMaxOrder];
+        for (int j = 0; j < N; ++j) rc[j] = Rc[j];
+        build_tables(LY[n], rc, d, R, lt, ut, sc, s);
+        const int64_t Jc = LY[n].nL * LY[n].nU;
+        subchain_explicit_kernel<<<grid_of(Jc * r, 256), 256, 0, s>>>(lt, ut, LY[n], V);
+        householder_qr_kernel<<<1, 256, 0, s>>>(V, Jc, r, Pm, Q0, tau, ctx->d_status, n);
+        wn_kernel<<<grid_of(I[n] * r, 128), 128, 0, s>>>(src, offL[n], offU[n], LY[n], Q0, M);
+        upper_to_lmat_kernel<<<grid_of((int64_t)r * r + r, 256), 256, 0, s>>>(Pm, r, Lm);
+        launch_chol_block_inverse(Lm, r, s);
+        launch_chol_solve(Lm, M, Rn, I[n], Rn1, G[n], ctx->d_status, s, nullptr, 0, kSolveBackward);
+        factor_core(n);
+        continue;
       }
       // M_n = Y_[n] V_n[2]: the FP64 MTTSP of Y with the R cores (line 9)
       {
@@ -282,6 +497,17 @@ trals_status qrne_decompose(trals_ctx* ctx, int N, const int64_t* I, const int32
   if (rel_res && sweeps > 0)
     TRALS_CUDA_TRY(ctx, cudaMemcpyAsync(rel_res, res_dev, sweeps * sizeof(double), cudaMemcpyDeviceToHost, s));
   TRALS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  // a failed factorization (rank deficiency, non-finite values) was recorded in the status word
+  DevStatus st{};
+  TRALS_CUDA_TRY(ctx, cudaMemcpy(&st, ctx->d_status, sizeof st, cudaMemcpyDeviceToHost));
+  if (st.code != 0) {
+    ctx->last_error = std::string(st.code == TRALS_E_NOT_SPD ? "rank-deficient or non-positive factor"
+                                                             : "non-finite value in a factorization") +
+                      " at core " + std::to_string(st.mode) + ", index " + std::to_string(st.index);
+    launch_zero_status(ctx->d_status, s);
+    cudaStreamSynchronize(s);
+    return (trals_status)st.code;
+  }
   return TRALS_OK;
 }
 

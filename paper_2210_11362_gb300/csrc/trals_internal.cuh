@@ -150,9 +150,11 @@ void launch_chol_block_inverse(double* Lmat, int r, cudaStream_t s);
 // out[i] = the Cholesky kernel's pivot reciprocal square root of d[i], ref[i] = CUDA's rsqrt(d[i])
 void launch_pivot_rsqrt_check(const double* d, int64_t n, double* out, double* ref, cudaStream_t s);
 // With G32 set, the core is also stored in FP32 there (R_n x Ist x R_{n+1}, Ist >= In slices; the
-// slices past In are left as they are).  With fwd_only set only the forward solve runs: Z = M L^{-T}.
+// slices past In are left as they are).  part selects the solves: 0 both (Z = M L^{-T} L^{-1}),
+// 1 the forward one alone (Z = M L^{-T}), 2 the backward one alone (Z = M L^{-1}).
+constexpr int kSolveBoth = 0, kSolveForward = 1, kSolveBackward = 2;
 void launch_chol_solve(const double* Lmat, const double* M, int Rn, int64_t In, int Rn1, double* G,
-                       DevStatus* st, cudaStream_t s, float* G32 = nullptr, int64_t Ist = 0, bool fwd_only = false);
+                       DevStatus* st, cudaStream_t s, float* G32 = nullptr, int64_t Ist = 0, int part = kSolveBoth);
 // FP32 copy of one core (R_n x In x R_{n+1}) into G32 laid out with Ist >= In slices.
 void launch_core_to_f32(const double* G, int Rn, int64_t In, int64_t Ist, int Rn1, float* G32, cudaStream_t s);
 
@@ -204,10 +206,11 @@ void launch_axpy(int64_t n, const double* x, double* y, cudaStream_t s);
 cudaError_t init_qr_attributes();
 
 // ---------------------------------------------------------------- TR-ALS-QRNE (Alg. 4)
-// The whole decomposition by TR-ALS-QRNE in FP64 (X_dev FP64 on the device, cores on the host as in
+// The whole decomposition by TR-ALS-QRNE (literal = false) or by the literal TR-ALS-QR of Alg. 3 with its
+// Multi-TTM (literal = true), in FP64 (X_dev FP64 on the device, cores on the host as in
 // trals_decompose).  Synchronous.
 trals_status qrne_decompose(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R, const double* X_dev,
-                            double* const* cores_host, int sweeps, double* rel_res);
+                            double* const* cores_host, int sweeps, double* rel_res, bool literal = false);
 
 // ---------------------------------------------------------------- asynchronous plan steps (serving)
 // As trals_plan_create / trals_plan_set_cores but without waiting on the stream (host sources may

@@ -708,3 +708,34 @@ def test_qrne_rejects_reduced_precision(ctx):
         P.trals_decompose(ctx, (20, 20, 20), (3, 3, 3), P.tensor_to_device(X, torch.float32), [G.copy() for G in init],
                           1, P.make_opts("fp32", solver=P.SOLVE_QRNE))
     assert e.value.status == P.E_ARG
+
+
+@pytest.mark.parametrize("I,R", [((300, 30, 400), (3, 4, 2)), ((40, 3, 50, 36), (2, 3, 2, 2)),
+                                 ((20, 20, 20), (3, 3, 3)), ((60, 3, 50, 30), (2, 2, 2, 3))])
+def test_decompose_literal_qr_compressed_matches_oracle(ctx, I, R):
+    """The literal TR-ALS-QR (Alg. 3) in the compressible regime on the GPU: Householder mode-2 QRs of
+    the cores, the Multi-TTM, the explicit subchain V_n of the R factors and its Householder QR with Q_0
+    formed, W_n = Y_[n] Q_0 and the triangular solve.  Two sweeps agree with the oracle's Alg. 3 and
+    with Householder least squares on the explicit subchain matrix (regular TR-ALS) within 1e-9."""
+    X, init = _problem(I, R)
+    cores = [G.copy() for G in init]
+    res = P.trals_decompose(ctx, I, R, X, cores, 2, P.make_opts("fp64", solver=P.SOLVE_QR_COMPRESSED))
+    ref, ref_res = O.tr_als_qr(X, init, 2)
+    ls, ls_res = O.tr_als(X, init, 2, "qr")
+    for a, b, c in zip(cores, ref, ls):
+        assert rel(a, b) < 1e-9, rel(a, b)
+        assert rel(a, c) < 1e-9, rel(a, c)
+    np.testing.assert_allclose(res, ref_res, rtol=1e-9)
+
+
+def test_literal_qr_reports_rank_deficiency(ctx):
+    """A core with two equal rank channels (core 3's last index: the columns a = 0 and a = 1 of every
+    G^{!=1}(k) coincide) makes the least-squares problem rank deficient: a Householder QR meets a zero
+    column and the call returns TRALS_E_NOT_SPD instead of a meaningless solution."""
+    I, R = (30, 20, 25), (2, 2, 3)
+    X, init = _problem(I, R)
+    init[2][:, :, 1] = init[2][:, :, 0]
+    cores = [G.copy() for G in init]
+    with pytest.raises(P.TralsError) as e:
+        P.trals_decompose(ctx, I, R, X, cores, 1, P.make_opts("fp64", solver=P.SOLVE_QR_COMPRESSED))
+    assert e.value.status == P.E_NOT_SPD
