@@ -181,6 +181,12 @@ def ls_solve_qr(A: np.ndarray, Xn: np.ndarray) -> np.ndarray:
     return sla.solve_triangular(Rf, Q.T @ Xn.T, lower=False).T
 
 
+def ls_solve_svd(A: np.ndarray, Xn: np.ndarray, rcond: float = 1e-12) -> np.ndarray:
+    """Minimum-norm argmin_Z |A Z^T - Xn^T|_F through the SVD of A, singular values below
+    rcond * sigma_max dropped (the SVD option of the remark after Alg. 3, for rank-deficient A)."""
+    return np.linalg.lstsq(A, Xn.T, rcond=rcond)[0].T
+
+
 def ls_solve_normal(S: np.ndarray, M: np.ndarray) -> np.ndarray:
     """Solve Z S = M with S = A^T A symmetric positive definite, by Cholesky S = L L^T
     and two triangular solves (Golub & Van Loan Sec. 5.3.2, cited for Alg. 2 line 9)."""
@@ -230,6 +236,8 @@ def als_update(X: np.ndarray, cores: List[np.ndarray], n: int, solver: str = "qr
     elif solver == "chol":
         S, M = normal_equation_terms(X, cores, n)
         Z = ls_solve_normal(S, M)
+    elif solver == "svd":
+        Z = ls_solve_svd(subchain_unfolded(cores, n), unfold_mode(X, n))
     else:
         raise ValueError(solver)
     return core_fold2(Z, Rn, Rn1)

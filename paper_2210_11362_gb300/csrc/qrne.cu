@@ -135,6 +135,100 @@ __global__ void upper_to_lmat_kernel(const double* __restrict__ Rm, int r, doubl
   }
 }
 
+// core G (R x I x R1) from its unfolding G2 (I x R R1, column-major, column a + R b)
+__global__ void fold2_kernel(const double* __restrict__ G2, int R, int64_t I, int R1, double* __restrict__ G) {
+  const int64_t total = (int64_t)R * I * R1;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = e % R, ib = e / R, i = ib % I, b = ib / I;
+    G[e] = G2[i + I * (a + (int64_t)R * b)];
+  }
+}
+
+// column j of T (m x r) times sigma_j^+ (zero where the singular value is at the rounding level)
+__global__ void scale_pinv_kernel(double* __restrict__ T, int64_t m, int r, const double* __restrict__ sig) {
+  double smax = 0.0;
+  for (int j = 0; j < r; ++j) smax = fmax(smax, sig[j]);
+  const double tol = 32.0 * r * 1.1102230246251565e-16 * smax;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m * r; e += (int64_t)gridDim.x * blockDim.x) {
+    const double sg = sig[e / m];
+    T[e] = sg > tol ? T[e] / sg : 0.0;
+  }
+}
+
+constexpr int kSvdMaxR = 96;
+// SVD of R (r x r, r <= kSvdMaxR) by one-sided Jacobi (Hestenes; Golub & Van Loan Sec. 8.6.4) in one CTA:
+// rotations on pairs of columns of B = R accumulate in W until every pair is orthogonal to working
+// accuracy; then R = U diag(sigma) V^T with sigma_j = |b_j|, u_j = b_j / sigma_j (zero for sigma_j = 0),
+// V = W.  Each round treats r/2 disjoint pairs (round-robin order), one warp per pair; at most 30
+// sweeps, fewer once a sweep rotates nothing.
+__global__ void __launch_bounds__(256) jacobi_svd_kernel(const double* __restrict__ Rm, int r, double* __restrict__ U,
+                                                         double* __restrict__ sig, double* __restrict__ Vm) {
+  extern __shared__ double svd_sm[];   // B (r x r), then W (r x r)
+  double* B = svd_sm;
+  double* W = svd_sm + r * r;
+  __shared__ int rotated;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int e = tid; e < r * r; e += blockDim.x) {
+    B[e] = Rm[e];
+    W[e] = (e % r == e / r) ? 1.0 : 0.0;
+  }
+  const int P = (r + 1) & ~1;   // players, one dummy when r is odd
+  const double eps = 1.1102230246251565e-16 * r;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+    for (int t = 0; t < P - 1; ++t) {
+      for (int i = warp; i < P / 2; i += nw) {
+        // circle method: pair 0 is (t, P-1), pair i (t + i, t - i) mod (P - 1)
+        int a = (i == 0) ? t : (t + i) % (P - 1);
+        int b = (i == 0) ? P - 1 : (t - i + (P - 1)) % (P - 1);
+        if (a > b) { const int x = a; a = b; b = x; }
+        if (b >= r) continue;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int k = lane; k < r; k += 32) {
+          const double x = B[k + r * a], y = B[k + r * b];
+          al = fma(x, x, al);
+          be = fma(y, y, be);
+          ga = fma(x, y, ga);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (fabs(ga) > eps * sqrt(al * be) && ga != 0.0) {
+          const double zeta = (be - al) / (2.0 * ga);
+          const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + tt * tt), sn = c * tt;
+          for (int k = lane; k < r; k += 32) {
+            const double x = B[k + r * a], y = B[k + r * b];
+            B[k + r * a] = c * x - sn * y;
+            B[k + r * b] = sn * x + c * y;
+            const double wx = W[k + r * a], wy = W[k + r * b];
+            W[k + r * a] = c * wx - sn * wy;
+            W[k + r * b] = sn * wx + c * wy;
+          }
+          if (lane == 0) rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (!rotated) break;
+    __syncthreads();
+  }
+  for (int j = warp; j < r; j += nw) {
+    double ss = 0.0;
+    for (int k = lane; k < r; k += 32) ss = fma(B[k + r * j], B[k + r * j], ss);
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    const double sj = sqrt(ss);
+    if (lane == 0) sig[j] = sj;
+    for (int k = lane; k < r; k += 32) {
+      U[k + r * j] = sj > 0.0 ? B[k + r * j] / sj : 0.0;
+      Vm[k + r * j] = W[k + r * j];
+    }
+  }
+}
+
 __device__ __forceinline__ double block_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -151,10 +245,12 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // (m x r, column-major) are written, signs chosen so that R has a positive diagonal.  A column whose
 // remaining part is at the rounding level, |R_kk| <= 32 r u max_j |a_j| (numerically rank deficient:
 // a column that repeats earlier ones leaves a remainder of about u |a| rather than exact zeros), sets
-// TRALS_E_NOT_SPD with its index and stops.
+// TRALS_E_NOT_SPD with its index and stops; with rd_flag given it is kept instead (R_kk = 0, no
+// reflector: A = Q R still holds to that tolerance, Q orthonormal) and *rd_flag is set to 1.
 __global__ void __launch_bounds__(256) householder_qr_kernel(double* __restrict__ A, int64_t m, int r,
                                                              double* __restrict__ Rm, double* __restrict__ Q,
-                                                             double* __restrict__ tau, DevStatus* st, int mode) {
+                                                             double* __restrict__ tau, DevStatus* st, int mode,
+                                                             int* __restrict__ rd_flag) {
   __shared__ double red[32];
   __shared__ double sc[2];
   __shared__ int fail;
@@ -182,7 +278,12 @@ __global__ void __launch_bounds__(256) householder_qr_kernel(double* __restrict_
     ss = block_sum(ss, red);
     if (tid == 0) {
       const double x0 = x[k], alpha = sqrt(ss);
-      if (!(alpha > tol) || !isfinite(alpha)) {
+      if (rd_flag != nullptr && isfinite(alpha) && !(alpha > tol)) {
+        *rd_flag = 1;   // numerically dependent column: no reflector
+        Rm[k + (int64_t)r * k] = 0.0;
+        sc[0] = 0.0;
+        tau[k] = 0.0;
+      } else if (!(alpha > tol) || !isfinite(alpha)) {
         fail = 1;
         set_status(st, isfinite(alpha) ? TRALS_E_NOT_SPD : TRALS_E_NONFINITE, -1, mode, k, alpha);
       } else {
@@ -374,6 +475,14 @@ trals_status qrne_decompose(trals_ctx* ctx, int N, const int64_t* I, const int32
   }
   double* V = literal ? buf.get<double>(vmax) : nullptr;
   double* Q0 = literal ? buf.get<double>(vmax) : nullptr;
+  // SVD option: U, sigma, V, V^T and W_n U of a rank-deficient subproblem; rank-deficiency flags
+  double* Us = buf.get<double>((size_t)rmax * rmax);
+  double* Vs = buf.get<double>((size_t)rmax * rmax);
+  double* Vt = buf.get<double>((size_t)rmax * rmax);
+  double* sig = buf.get<double>(rmax);
+  double* T1 = buf.get<double>((size_t)Imax * rmax);
+  int* rd_v = buf.get<int>(2);
+  int* rd_core = rd_v + 1;
   double* red = buf.get<double>(2);
   double* res_dev = buf.get<double>(std::max(1, sweeps));
   TRALS_CUDA_TRY(ctx, buf.e);
@@ -386,7 +495,7 @@ trals_status qrne_decompose(trals_ctx* ctx, int N, const int64_t* I, const int32
     if (comp[j] && literal) {
       // Householder mode-2 QR (Alg. 3 lines 2 and 10)
       unfold2_kernel<<<grid_of(core_el[j], 256), 256, 0, s>>>(G[j], Rj, I[j], Rj1, G2);
-      householder_qr_kernel<<<1, 256, 0, s>>>(G2, I[j], r, Pm, Qm[j], tau, ctx->d_status, j);
+      householder_qr_kernel<<<1, 256, 0, s>>>(G2, I[j], r, Pm, Qm[j], tau, ctx->d_status, j, rd_core);
       rcore_from_upper_kernel<<<grid_of((int64_t)r * r, 256), 256, 0, s>>>(Pm, Rj, Rj1, Rc[j]);
     } else if (comp[j]) {
       const int64_t Ij = I[j];
@@ -450,11 +559,32 @@ trals_status qrne_decompose(trals_ctx* ctx, int N, const int64_t* I, const int32
         build_tables(LY[n], rc, d, R, lt, ut, sc, s);
         const int64_t Jc = LY[n].nL * LY[n].nU;
         subchain_explicit_kernel<<<grid_of(Jc * r, 256), 256, 0, s>>>(lt, ut, LY[n], V);
-        householder_qr_kernel<<<1, 256, 0, s>>>(V, Jc, r, Pm, Q0, tau, ctx->d_status, n);
+        TRALS_CUDA_TRY(ctx, cudaMemsetAsync(rd_v, 0, sizeof(int), s));
+        householder_qr_kernel<<<1, 256, 0, s>>>(V, Jc, r, Pm, Q0, tau, ctx->d_status, n, rd_v);
         wn_kernel<<<grid_of(I[n] * r, 128), 128, 0, s>>>(src, offL[n], offU[n], LY[n], Q0, M);
-        upper_to_lmat_kernel<<<grid_of((int64_t)r * r + r, 256), 256, 0, s>>>(Pm, r, Lm);
-        launch_chol_block_inverse(Lm, r, s);
-        launch_chol_solve(Lm, M, Rn, I[n], Rn1, G[n], ctx->d_status, s, nullptr, 0, kSolveBackward);
+        int rd_host = 0;
+        TRALS_CUDA_TRY(ctx, cudaMemcpyAsync(&rd_host, rd_v, sizeof(int), cudaMemcpyDeviceToHost, s));
+        TRALS_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        if (rd_host && r <= kSvdMaxR) {
+          // rank-deficient V_n: the SVD of R (remark after Alg. 3), G_{n(2)} = W_n U Sigma^+ V^T, the
+          // minimum-norm solution of the compressed problem (and of the whole subproblem)
+          const size_t svd_smem = 2 * (size_t)r * r * sizeof(double);
+          TRALS_CUDA_TRY(ctx, cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)svd_smem));
+          jacobi_svd_kernel<<<1, 256, svd_smem, s>>>(Pm, r, Us, sig, Vs);
+          launch_gemm_f64((int)I[n], r, r, M, Us, T1, s);
+          scale_pinv_kernel<<<grid_of(I[n] * r, 256), 256, 0, s>>>(T1, I[n], r, sig);
+          launch_transpose(Vs, r, Vt, s);
+          launch_gemm_f64((int)I[n], r, r, T1, Vt, G2, s);
+          fold2_kernel<<<grid_of(core_el[n], 256), 256, 0, s>>>(G2, Rn, I[n], Rn1, G[n]);
+        } else if (rd_host) {
+          ctx->last_error = "literal TR-ALS-QR: rank-deficient subproblem with R_n R_{n+1} > 96 (SVD limit)";
+          return TRALS_E_NOT_SPD;
+        } else {
+          upper_to_lmat_kernel<<<grid_of((int64_t)r * r + r, 256), 256, 0, s>>>(Pm, r, Lm);
+          launch_chol_block_inverse(Lm, r, s);
+          launch_chol_solve(Lm, M, Rn, I[n], Rn1, G[n], ctx->d_status, s, nullptr, 0, kSolveBackward);
+        }
         factor_core(n);
         continue;
       }

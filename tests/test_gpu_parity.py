@@ -728,14 +728,22 @@ def test_decompose_literal_qr_compressed_matches_oracle(ctx, I, R):
     np.testing.assert_allclose(res, ref_res, rtol=1e-9)
 
 
-def test_literal_qr_reports_rank_deficiency(ctx):
-    """A core with two equal rank channels (core 3's last index: the columns a = 0 and a = 1 of every
-    G^{!=1}(k) coincide) makes the least-squares problem rank deficient: a Householder QR meets a zero
-    column and the call returns TRALS_E_NOT_SPD instead of a meaningless solution."""
+def test_literal_qr_rank_deficient_subproblem_takes_the_svd_of_r(ctx):
+    """The SVD option of the remark after Alg. 3: core 3 with two equal rank channels (its last index,
+    so the columns a = 0 and a = 1 of every G^{!=1}(k) coincide) makes the first core update rank
+    deficient.  The Householder QRs keep the dependent columns (R_kk = 0), and the solve of
+    G_{n(2)} R^T = W_n goes through the SVD of R (one-sided Jacobi) with the negligible singular values
+    dropped: the minimum-norm least-squares core, as the oracle's SVD least squares on the explicit
+    subchain matrix gives it.  One sweep agrees within 1e-8 relative."""
     I, R = (30, 20, 25), (2, 2, 3)
     X, init = _problem(I, R)
     init[2][:, :, 1] = init[2][:, :, 0]
+    A = O.subchain_unfolded(init, 0)
+    s = np.linalg.svd(A, compute_uv=False)
+    assert s[-1] < 1e-12 * s[0]                   # the first subproblem is rank deficient
     cores = [G.copy() for G in init]
-    with pytest.raises(P.TralsError) as e:
-        P.trals_decompose(ctx, I, R, X, cores, 1, P.make_opts("fp64", solver=P.SOLVE_QR_COMPRESSED))
-    assert e.value.status == P.E_NOT_SPD
+    res = P.trals_decompose(ctx, I, R, X, cores, 1, P.make_opts("fp64", solver=P.SOLVE_QR_COMPRESSED))
+    ref, ref_res = O.tr_als(X, init, 1, "svd")
+    for a, b in zip(cores, ref):
+        assert rel(a, b) < 1e-8, rel(a, b)
+    np.testing.assert_allclose(res, ref_res, rtol=1e-9)

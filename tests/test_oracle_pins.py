@@ -281,6 +281,25 @@ def test_signed_selection_cores_keep_subchain_entries_ternary():
     assert np.array_equal(X, np.round(X)) and np.abs(X).max() <= 8
 
 
+def test_svd_solve_is_the_minimum_norm_least_squares_solution():
+    """ls_solve_svd: equal to the QR solution for full-rank A; for a rank-deficient A (two equal columns)
+    it satisfies the normal equations and has no component in the null space of A (the minimum-norm
+    solution), and it is unique where QR least squares is not defined."""
+    rng = np.random.default_rng(30)
+    A = rng.standard_normal((40, 6))
+    Xn = rng.standard_normal((5, 40))
+    np.testing.assert_allclose(O.ls_solve_svd(A, Xn), O.ls_solve_qr(A, Xn), rtol=1e-10, atol=1e-12)
+    A[:, 4] = A[:, 1]
+    Z = O.ls_solve_svd(A, Xn)
+    np.testing.assert_allclose(A.T @ (A @ Z.T - Xn.T), 0.0, atol=1e-10)
+    null = np.zeros(6); null[1], null[4] = 1.0, -1.0
+    assert np.abs(Z @ null).max() < 1e-12
+    # any other least-squares solution (adding a null-space component) is longer
+    Z2 = Z + 0.3 * np.outer(np.ones(5), null)
+    np.testing.assert_allclose(A.T @ (A @ Z2.T - Xn.T), 0.0, atol=1e-10)
+    assert np.linalg.norm(Z2) > np.linalg.norm(Z)
+
+
 def test_ne_and_qr_agree_after_one_sweep():
     X, init = _small_problem()
     c_qr, _ = O.tr_als(X, init, 1, "qr", residual=False)
