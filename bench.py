@@ -510,6 +510,65 @@ def run_ours(args):
     print(json.dumps(line))
 
 
+STABILITY_SOLVERS = {"ne_cholesky": 0, "qr_stabilised": 1, "qrne": 2, "qr_compressed": 3}
+
+
+def run_stability(args):
+    """The ill-conditioned stability experiments of Sec. 4 (B-II: collinearity-controlled cores; B-III:
+    multivariate-t cores with correlation theta^|i-j|, one degree of freedom): 100 x 100 x 100 tensors
+    generated as TR with 5 x 100 x 5 cores, relative noise eta, fitted with ranks 5 from a Gaussian init
+    for 20 sweeps in FP64 by every solver; the final relative residual (explicit, against the FP64 X) of
+    `--trials` seeded trials per point of the grid, summarised by median and spread.  A solver that stops
+    (a non-positive Cholesky pivot) counts as a failure."""
+    import torch
+    import paper_2210_11362_gb300 as P
+    I, R = (100, 100, 100), (5, 5, 5)
+    etas = [1e-4, 1e-7, 1e-10]
+    grids = {"collinear_gamma": [1 - 1e-4, 1 - 1e-7, 1 - 1e-10], "mvt_theta": [1 - 1e-1, 1 - 1e-4, 1 - 1e-7]}
+    ctx = P.trals_create(0)
+    out = {}
+    t_start = time.perf_counter()
+    for exp, levels in grids.items():
+        for lev in levels:
+            for eta in etas:
+                key = f"{exp}={lev:.10g},eta={eta:g}"
+                per = {k: [] for k in STABILITY_SOLVERS}
+                fails = {k: 0 for k in STABILITY_SOLVERS}
+                for t in range(args.trials):
+                    seed = 1000 + t
+                    if exp == "collinear_gamma":
+                        truth = TI.collinear_cores(seed, I, R, lev)
+                    else:
+                        truth = TI.multivariate_t_cores(seed, I, R, lev, dof=1.0)
+                    cd = [P.core_to_device(G) for G in truth]
+                    Xt = torch.empty(int(np.prod(I)), dtype=torch.float64, device="cuda")
+                    P.trals_reconstruct(ctx, I, R, cd, Xt)
+                    noise = torch.from_numpy(TI.flat_f(TI.gaussian_noise(seed, I))).to("cuda")
+                    X = Xt + eta * (torch.linalg.vector_norm(Xt) / torch.linalg.vector_norm(noise)) * noise
+                    init = TI.init_cores(seed, I, R)
+                    for name, solver in STABILITY_SOLVERS.items():
+                        cores = [G.copy() for G in init]
+                        try:
+                            P.trals_decompose(ctx, I, R, X, cores, 20, P.make_opts("fp64", solver=solver))
+                            r2, x2 = P.trals_residual_explicit(ctx, I, R, X, [P.core_to_device(G) for G in cores])
+                            res = float(np.sqrt(max(r2, 0.0) / x2))
+                            if np.isfinite(res):
+                                per[name].append(res)
+                            else:
+                                fails[name] += 1
+                        except P.TralsError:
+                            fails[name] += 1
+                out[key] = {name: {"median": float(np.median(v)) if v else None,
+                                   "q25": float(np.percentile(v, 25)) if v else None,
+                                   "q75": float(np.percentile(v, 75)) if v else None,
+                                   "worst": float(max(v)) if v else None, "failed": fails[name], "runs": len(v)}
+                            for name, v in per.items()}
+    ctx.close()
+    print(json.dumps({"experiment": "stability (Sec. 4, Exp. B-II and B-III)", "tensor": list(I), "ranks": list(R),
+                      "sweeps": 20, "trials": args.trials, "dtype": "f64", "wall_s": time.perf_counter() - t_start,
+                      "results": out}))
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -560,7 +619,13 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
+    ap.add_argument("--stability", action="store_true",
+                    help="run the ill-conditioned stability experiments (Sec. 4, B-II and B-III) instead")
+    ap.add_argument("--trials", type=int, default=10)
     args = ap.parse_args()
+    if args.stability:
+        run_stability(args)
+        return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":

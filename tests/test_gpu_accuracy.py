@@ -111,3 +111,26 @@ def test_smooth_reduced_bf16_qr_gap(ctx):
                       P.make_opts("bf16", solver=P.SOLVE_QR))
     _, ref_res = O.tr_als(X, init, 6, "qr")
     assert abs(O.rel_residual(X, cores) - ref_res[-1]) <= 1e-4
+
+
+def test_stability_collinear_cores_qr_solvers_reach_the_noise_floor(ctx):
+    """Sec. 4, B-II at the paper's shape: 100^3, rank 5, collinearity gamma = 1 - 1e-7, noise 1e-10.  The
+    QR-stabilised and the literal compressed QR solvers come within 1e-7 of the noise floor in 20 sweeps
+    (the stability profile's median is 8e-9); the Cholesky normal equations stop at a non-positive pivot
+    or end far above."""
+    I, R = (100, 100, 100), (5, 5, 5)
+    for seed in (1000, 1001):
+        truth = TI.collinear_cores(seed, I, R, 1 - 1e-7)
+        X = TI.add_relative_noise(O.tr_full(truth), TI.gaussian_noise(seed, I), 1e-10)
+        init = TI.init_cores(seed, I, R)
+        res = {}
+        for name, solver in (("qr", P.SOLVE_QR), ("qrc", P.SOLVE_QR_COMPRESSED), ("ne", P.SOLVE_CHOL)):
+            cores = [G.copy() for G in init]
+            try:
+                P.trals_decompose(ctx, I, R, X, cores, 20, P.make_opts("fp64", solver=solver))
+                res[name] = O.rel_residual(X, cores)
+            except P.TralsError as e:
+                assert name == "ne" and e.status == P.E_NOT_SPD, (name, e)
+                res[name] = np.inf
+        assert res["qr"] < 1e-7 and res["qrc"] < 1e-7, res
+        assert res["ne"] > 100 * res["qr"], res
