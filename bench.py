@@ -344,6 +344,7 @@ def serve_run(P, torch, seed, count, budget_bytes, slots, mode="bf16"):
             "span_s": last - first, "wall_s": wall, "arrival_window_s": reqs[-1].arrival_s,
             "data_generation_s": gen_s, "mode": mode, "slots": slots, "hbm_budget_gb": budget_bytes / 2**30,
             "peak_active": stats["peak_active"], "peak_used_gb": stats["peak_used_bytes"] / 2**30,
+            "host_start_s_total": stats["host_start_s"],
             "final_residual_median": float(np.median(fin)),
             "workload": "512 requests, Poisson 200/s, order U{3..5}, sizes U{16..64}, ranks U{2..8}, "
                         "FP32 X = TR + 1e-2 noise, 15 sweeps"}

@@ -344,6 +344,8 @@ typedef struct {
   size_t used_bytes;       /* footprint of the active requests */
   size_t peak_used_bytes;
   int peak_active;
+  double host_start_s;     /* host time the worker spent starting requests (plan set-up, graph capture,
+                              launches) */
 } trals_server_info;
 
 /* Start a server on `device` with at most max_slots requests in flight whose footprints sum to at

@@ -71,7 +71,7 @@ class Result(ctypes.Structure):
 class ServerInfo(ctypes.Structure):
     _fields_ = [("queued", ctypes.c_int), ("active", ctypes.c_int), ("completed", ctypes.c_uint64),
                 ("used_bytes", ctypes.c_size_t), ("peak_used_bytes", ctypes.c_size_t),
-                ("peak_active", ctypes.c_int)]
+                ("peak_active", ctypes.c_int), ("host_start_s", ctypes.c_double)]
 
 
 _lib = None

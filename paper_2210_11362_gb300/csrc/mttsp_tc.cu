@@ -883,16 +883,15 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiledFn get_encode() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  // looked up once, thread-safely (plans may be built by several host threads at once)
+  static const EncodeTiledFn fn = []() -> EncodeTiledFn {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
+      return reinterpret_cast<EncodeTiledFn>(p);
+    return nullptr;
+  }();
   return fn;
 }
 
@@ -1035,8 +1034,9 @@ TcChoice tc_choose(int N, const int64_t* I, const int32_t* R, int n) {
     c.s_lo = 0;
     c.s_hi = n - 1;
     c.K_S = prod_range(I, 0, n);
-    // rows i + I_n rep: lanes of a warp must hold distinct i_n, so I_n >= 32
-    if ((c.K_S * 2) % 16 == 0 && In <= kRows && In >= 32) consider(c, (R[0] + 3) / 4 * 4 * Rn);
+    // rows i + I_n rep: each repetition's factor block is staged in shared memory per unit, so at
+    // most 16 repetitions (I_n >= 8)
+    if ((c.K_S * 2) % 16 == 0 && In <= kRows && In >= 8) consider(c, (R[0] + 3) / 4 * 4 * Rn);
   }
   // KM-R: n = N-1, S = modes 0..s with s <= N-3
   if (n == N - 1) {

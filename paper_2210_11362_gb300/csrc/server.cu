@@ -94,6 +94,7 @@ struct trals_server {
   std::condition_variable done_cv; // worker -> waiters
   std::thread worker;
   bool stopping = false;
+  double host_start_s = 0;         // host time spent starting requests (plan set-up, graph capture, launches)
   Clock::time_point t0;
   std::string last_error;
 
@@ -204,7 +205,13 @@ void worker_main(trals_server* S) {
     }
     bool progress = !admitted.empty();
     for (int k : admitted) {
+      const auto t0 = Clock::now();
       const trals_status st = start_request(S->slots[k]);
+      const double dt = std::chrono::duration<double>(Clock::now() - t0).count();
+      {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->host_start_s += dt;
+      }
       if (st != TRALS_OK) finish_request(S, S->slots[k], st);
     }
     for (Slot& sl : S->slots) {
@@ -413,6 +420,7 @@ trals_status trals_server_stats(trals_server* S, trals_server_info* out) {
   out->used_bytes = S->used;
   out->peak_used_bytes = S->peak_used;
   out->peak_active = S->peak_active;
+  out->host_start_s = S->host_start_s;
   return TRALS_OK;
 }
 

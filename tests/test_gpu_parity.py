@@ -201,6 +201,7 @@ TC_SHAPES = [
     ((16, 24, 32, 20), (3, 4, 2, 5)),        # every tensor-core geometry, small ranks
     ((40, 40, 40, 40), (8, 10, 12, 10)),     # 40^4 with the ranks of the 40^5 workload
     ((40, 40, 40, 32, 4), (4, 5, 6, 5, 4)),    # order 5: K-major tiles with a large table and with mid modes
+    ((24, 20, 18, 29, 40), (3, 7, 4, 8, 5)),   # short middle modes: K-major tiles of 6, 7 and 4 repetitions
 ]
 
 # Componentwise error bound of the reduced-precision MTTSP against M_ref = X_q G^{!=n}_[2] in FP64

@@ -21,8 +21,10 @@ def test_mttsp_path_pads_the_leading_mode_and_falls_back_when_too_large():
     # 60^4: plans store the BF16 copy with mode 0 padded to 64, so every mode meets TMA's 16-byte
     # stride rule and runs on tensor cores
     assert all(P.trals_mttsp_path((60,) * 4, (10,) * 4, n, "bf16") > 0 for n in range(4))
-    # a middle mode with I_n < 32 and a long K-major block: no tensor-core geometry applies
-    assert P.trals_mttsp_path((41, 39, 20, 41, 39), (2, 2, 7, 8, 3), 2, "bf16") == 0
+    # a middle mode longer than the 128-row tile and a long MN-major block: no tensor-core geometry
+    assert P.trals_mttsp_path((41, 39, 200, 41, 39), (2, 2, 7, 8, 3), 2, "bf16") == 0
+    # a short middle mode (I_n = 20) takes K-major tiles of six repetitions of its rows
+    assert P.trals_mttsp_path((41, 39, 20, 41, 39), (2, 2, 7, 8, 3), 2, "bf16") == 1
     # rank-16 cores: stage-1 table wider than the 128-column accumulator -> CUDA cores
     assert all(P.trals_mttsp_path((256, 256, 3, 256), (16,) * 4, n, "bf16") == 0 for n in range(4))
     # tiny tensors: contraction too short for a tensor-core tile
