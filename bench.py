@@ -293,7 +293,7 @@ def e2e_run(P, torch, w, X_dev, opts, seed, sweeps):
             "residual": float(res[-1])}
 
 
-def serve_run(P, torch, seed, count, budget_bytes, slots, mode="bf16"):
+def serve_run(P, torch, seed, count, budget_bytes, slots, mode="bf16", group_limit=None):
     """The serving workload: `count` TR-ALS requests with Poisson arrivals at 200/s, order uniform in
     3-5, mode sizes uniform in 16-64, ranks uniform in 2-8, FP32 X = TR(N(0,1) cores) + 1e-2 relative
     noise generated on the device from each request's seed, 15 sweeps each, run by the serving loop
@@ -319,6 +319,8 @@ def serve_run(P, torch, seed, count, budget_bytes, slots, mode="bf16"):
     ctx.close()
     opts = P.make_opts(mode)
     srv = P.Server(0, hbm_budget_bytes=budget_bytes, max_slots=slots)
+    if group_limit is not None:
+        srv.set_group_limit(group_limit)
     try:
         tickets = []
         start = time.perf_counter()
@@ -337,6 +339,11 @@ def serve_run(P, torch, seed, count, budget_bytes, slots, mode="bf16"):
     first = min(o[0]["submit_s"] for o in out)
     last = max(o[0]["done_s"] for o in out)
     fin = np.array([o[2][-1] for o in out if o is not None])
+    by_order = {}
+    for N in sorted({len(q.I) for q in reqs}):
+        lo = np.array([o[0]["done_s"] - o[0]["submit_s"] for q, o in zip(reqs, out) if o is not None and len(q.I) == N])
+        by_order[str(N)] = {"requests": int(lo.size), "p50_latency_ms": float(np.percentile(lo, 50) * 1e3),
+                            "p99_latency_ms": float(np.percentile(lo, 99) * 1e3)}
     sweeps = sum(q.sweeps for q in reqs)
     return {"requests": count, "failed": len(bad), "p50_latency_ms": float(np.percentile(lat, 50) * 1e3),
             "p99_latency_ms": float(np.percentile(lat, 99) * 1e3), "max_latency_ms": float(lat.max() * 1e3),
@@ -344,7 +351,9 @@ def serve_run(P, torch, seed, count, budget_bytes, slots, mode="bf16"):
             "span_s": last - first, "wall_s": wall, "arrival_window_s": reqs[-1].arrival_s,
             "data_generation_s": gen_s, "mode": mode, "slots": slots, "hbm_budget_gb": budget_bytes / 2**30,
             "peak_active": stats["peak_active"], "peak_used_gb": stats["peak_used_bytes"] / 2**30,
-            "host_start_s_total": stats["host_start_s"],
+            "latency_by_order": by_order,
+            "host_start_s_total": stats["host_start_s"], "grouped_requests": stats["grouped_completed"],
+            "grouped_steps": stats["grouped_steps"],
             "final_residual_median": float(np.median(fin)),
             "workload": "512 requests, Poisson 200/s, order U{3..5}, sizes U{16..64}, ranks U{2..8}, "
                         "FP32 X = TR + 1e-2 noise, 15 sweeps"}
@@ -505,7 +514,7 @@ def run_ours(args):
         X = X_f64 = flush = None
         torch.cuda.empty_cache()
         line["serving"] = serve_run(P, torch, args.seed, args.serve_requests, int(args.serve_budget_gb * 2**30),
-                                    args.serve_slots)
+                                    args.serve_slots, group_limit=args.serve_group_limit)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_run(w, args.seed, args.cpu_budget)
     print(json.dumps(line))
@@ -620,12 +629,22 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
+    ap.add_argument("--serve-group-limit", type=int, default=None,
+                    help="largest request (entries) served by the grouped step engine (default: the server's)")
+    ap.add_argument("--serve-only", action="store_true", help="run only the serving workload and print its line")
     ap.add_argument("--stability", action="store_true",
                     help="run the ill-conditioned stability experiments (Sec. 4, B-II and B-III) instead")
     ap.add_argument("--trials", type=int, default=10)
     args = ap.parse_args()
     if args.stability:
         run_stability(args)
+        return
+    if args.serve_only:
+        import torch
+        import paper_2210_11362_gb300 as P
+        print(json.dumps({"serving": serve_run(P, torch, args.seed, args.serve_requests,
+                                                int(args.serve_budget_gb * 2**30), args.serve_slots,
+                                                group_limit=args.serve_group_limit)}))
         return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

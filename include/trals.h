@@ -345,11 +345,24 @@ typedef struct {
   size_t peak_used_bytes;
   int peak_active;
   double host_start_s;     /* host time the worker spent starting requests (plan set-up, graph capture,
-                              launches) */
+                              launches; grouped admissions) */
+  uint64_t grouped_completed; /* requests served by the grouped step engine */
+  uint64_t grouped_steps;  /* steps the grouped engine has launched */
 } trals_server_info;
 
-/* Start a server on `device` with at most max_slots requests in flight whose footprints sum to at
- * most hbm_budget_bytes.  Starts one worker thread. */
+/* Start a server on `device` with at most max_slots plan requests in flight, plus up to 64 small
+ * requests in the grouped step engine, whose footprints sum to at most hbm_budget_bytes.  Starts one
+ * worker thread.
+ *
+ * Small requests -- order 3 to 5, every R_k <= 8, at most 2^18 entries (see
+ * trals_server_set_group_limit), FP32 X, mode TRALS_MODE_FP32 or TRALS_MODE_BF16, the Cholesky solve
+ * of the structured Gram chain, no per-sweep explicit residual, sweeps >= 1 -- join the grouped step
+ * engine: each step advances every such request by one core update of Alg. 2 (its own mode n), the
+ * Gamma-chain products, the MTTSP (X_[n] times the subchain in FP32, from the BF16 copy of X in the
+ * BF16 mode), the FP64 Cholesky solve and the Gamma update, as one graph of grouped kernels over a
+ * device table of the active requests.  Results follow the reduced-precision plans' conventions: FP64
+ * cores, no per-sweep residual (NaN), the explicit relative residual against the FP32 X after the last
+ * sweep.  Other requests run as plans (what trals_decompose runs). */
 trals_status trals_server_create(trals_server** out, int device, size_t hbm_budget_bytes, int max_slots);
 /* Stop the server: requests still queued are dropped, active ones finish; results not yet taken
  * are freed.  Joins the worker thread. */
@@ -367,6 +380,10 @@ trals_status trals_server_poll(trals_server* server, uint64_t ticket, trals_resu
 trals_status trals_server_wait(trals_server* server, uint64_t ticket, double timeout_s, trals_result* result,
                                double* const* cores_out, double* rel_res_out);
 trals_status trals_server_stats(trals_server* server, trals_server_info* out);
+/* Requests submitted from now on with at most max_elems entries (and otherwise small, see
+ * trals_server_create) join the grouped step engine; 0 sends every request to a plan.  TRALS_E_ARG for a
+ * negative limit. */
+trals_status trals_server_set_group_limit(trals_server* server, int64_t max_elems);
 /* Message for the last rejected submit or failed request taken by poll/wait. */
 const char* trals_server_last_error(const trals_server* server);
 

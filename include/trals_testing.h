@@ -24,6 +24,13 @@ trals_status trals_testing_mttsp_withheld_copy(trals_ctx* ctx, int N, const int6
                                                const void* X_dev, int mode, const double* const* cores_dev, int n,
                                                double* M_dev, long long spin_cycles);
 
+/* The next `steps` steps of the server's grouped step engine are launched without their descriptor table
+ * being published: the step's first kernel waits for it, gives up after spin_cycles clock cycles (> 0),
+ * and the step then does no work.  Every request that was in one of those steps completes with
+ * TRALS_E_TIMEOUT (its result names the wait); later requests are served normally.  TRALS_E_ARG for a
+ * null server, steps < 0 or spin_cycles <= 0. */
+trals_status trals_testing_server_withhold_steps(trals_server* server, int steps, long long spin_cycles);
+
 #ifdef __cplusplus
 }
 #endif

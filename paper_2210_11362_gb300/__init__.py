@@ -42,7 +42,8 @@ EXPORTED = [
     "trals_gamma", "trals_coef_matrix", "trals_coef_matrix_explicit", "trals_qr_r_factor", "trals_mttsp", "trals_mttsp_noalloc", "trals_mttsp_path", "trals_last_mttsp_path", "trals_testing_mttsp_withheld_copy", "trals_solve_chol", "trals_check_pivot_rsqrt", "trals_reconstruct",
     "trals_residual_explicit", "trals_quantize_bf16",
     "trals_server_create", "trals_server_destroy", "trals_server_submit", "trals_server_poll",
-    "trals_server_wait", "trals_server_stats", "trals_server_last_error",
+    "trals_server_wait", "trals_server_stats", "trals_server_last_error", "trals_server_set_group_limit",
+    "trals_testing_server_withhold_steps",
 ]
 
 
@@ -71,7 +72,8 @@ class Result(ctypes.Structure):
 class ServerInfo(ctypes.Structure):
     _fields_ = [("queued", ctypes.c_int), ("active", ctypes.c_int), ("completed", ctypes.c_uint64),
                 ("used_bytes", ctypes.c_size_t), ("peak_used_bytes", ctypes.c_size_t),
-                ("peak_active", ctypes.c_int), ("host_start_s", ctypes.c_double)]
+                ("peak_active", ctypes.c_int), ("host_start_s", ctypes.c_double),
+                ("grouped_completed", ctypes.c_uint64), ("grouped_steps", ctypes.c_uint64)]
 
 
 _lib = None
@@ -137,6 +139,8 @@ def lib() -> ctypes.CDLL:
                                              _vp]),
         "trals_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(ServerInfo)]),
         "trals_server_last_error": (ctypes.c_char_p, [_vp]),
+        "trals_server_set_group_limit": (ctypes.c_int, [_vp, ctypes.c_int64]),
+        "trals_testing_server_withhold_steps": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_longlong]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -594,6 +598,20 @@ class Server:
     def wait(self, ticket: int, timeout: float = -1.0):
         return self._take(ticket, lib().trals_server_wait, ctypes.c_double(timeout))
 
+    def set_group_limit(self, max_elems: int) -> None:
+        """Requests submitted from now on with at most max_elems entries (and otherwise small) join the
+        grouped step engine; 0 sends every request to a plan."""
+        st = lib().trals_server_set_group_limit(self.handle, int(max_elems))
+        if st != OK:
+            self._err(st, "trals_server_set_group_limit")
+
+    def testing_withhold_steps(self, steps: int, spin_cycles: int) -> None:
+        """Fault injection (include/trals_testing.h): the next `steps` grouped steps run without their
+        descriptor table, so their bounded wait gives up and their requests report TRALS_E_TIMEOUT."""
+        st = lib().trals_testing_server_withhold_steps(self.handle, int(steps), int(spin_cycles))
+        if st != OK:
+            self._err(st, "trals_testing_server_withhold_steps")
+
     def stats(self) -> dict:
         s = ServerInfo()
         st = lib().trals_server_stats(self.handle, ctypes.byref(s))
@@ -639,3 +657,11 @@ def trals_server_stats(server: Server) -> dict:
 
 def trals_server_last_error(server: Server) -> str:
     return lib().trals_server_last_error(server.handle).decode()
+
+
+def trals_server_set_group_limit(server: Server, max_elems: int) -> None:
+    server.set_group_limit(max_elems)
+
+
+def trals_testing_server_withhold_steps(server: Server, steps: int, spin_cycles: int) -> None:
+    server.testing_withhold_steps(steps, spin_cycles)

@@ -1,18 +1,27 @@
 // Serving loop: continuous batching of TR-ALS decompositions on one GPU.
 //
 // Requests (tensors of different orders, sizes and ranks) are submitted from any host thread and
-// queue in arrival order.  A worker thread admits the head of the queue whenever a slot is free and
-// the request's device footprint (its plan workspace, computed on the host by the plan's counting
-// pass, plus a device copy of X when X is on the host) fits in what is left of the HBM budget.  An
-// admitted request gets a resident plan on its slot's own non-blocking stream; its sweeps are
-// enqueued at once as replays of the plan's captured per-sweep CUDA graph, so the work of all
-// active requests overlaps on the device while new requests keep being admitted as slots and
-// memory free up.  Plans allocate stream-ordered, so admitting and retiring requests never
-// synchronises the device.  Every request computes exactly what trals_decompose computes for it
-// alone (the kernels are deterministic and slots share no device state), so a result does not
-// depend on what else was in flight.
+// queue in arrival order.  A worker thread admits queued requests in order whenever their kind of
+// slot is free and the request's device footprint fits in what is left of the HBM budget (a request
+// whose footprint does not fit holds back the ones behind it).  There are two kinds of slot:
+//  - small requests (order <= 5, ranks <= 8, few entries; see grp_eligible) join the grouped step
+//    engine (group.cu): every step advances all of them by one core update through one graph of
+//    grouped kernels over a device table of the active slots, so their launch cost is shared;
+//  - the others get a resident plan on their slot's own non-blocking stream; their sweeps are
+//    enqueued at once as replays of the plan's captured per-sweep CUDA graph, and the tensor-core
+//    MTTSP of the large tensors keeps the device busy meanwhile.
+// The plans are started and retired by a worker thread and the grouped engine is driven by a thread of
+// its own: a plan's set-up and tear-down take up to tens of milliseconds of host time (graph
+// instantiation and destruction wait on the device), which must not hold up the engine's steps.
+// Footprints are computed on the host (the plan's counting pass, or the engine's carve-up, plus a
+// device copy of X when X is on the host).  Plans and workspaces allocate stream-ordered, so admitting
+// and retiring requests never synchronises the device.  A plan request computes exactly what
+// trals_decompose computes for it alone; a grouped request computes the same method in the same
+// precisions with the engine's own kernels.  Either way the kernels are deterministic and slots share
+// no device state, so a result does not depend on what else was in flight.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -22,7 +31,9 @@
 #include <unordered_map>
 #include <vector>
 
+#include "group.cuh"
 #include "trals_internal.cuh"
+#include "../../include/trals_testing.h"
 
 namespace {
 
@@ -42,6 +53,7 @@ struct Request {
   std::vector<std::vector<double>> cores;   // initial cores at submit, fitted cores when done
   std::vector<double> res;                  // relative residual per sweep
   size_t footprint = 0;
+  bool grouped = false;                     // served by the grouped step engine
   double t_submit = 0, t_admit = -1, t_done = -1;
   trals_status status = TRALS_E_PENDING;
   std::string error;
@@ -92,9 +104,23 @@ struct trals_server {
   std::mutex mu;
   std::condition_variable cv;      // submit / stop -> worker
   std::condition_variable done_cv; // worker -> waiters
-  std::thread worker;
+  std::thread worker;                   // admission and the plan requests
+  std::thread engine;                   // the grouped step engine
   bool stopping = false;
+  trals::GroupEngine* grp = nullptr;    // grouped step engine (small requests), driven by its own thread
+  std::deque<Request*> ginbox;          // admitted grouped requests not yet taken by the engine thread
+  std::condition_variable gcv;          // worker / stop -> engine thread
+  // requests up to 2^18 entries (every order-3 tensor of sizes <= 64): larger ones run their MTTSP faster on
+  // the tensor cores of a plan than in the grouped CUDA-core kernel
+  int64_t grp_max_elems = (int64_t)1 << 18;
+  int grp_active = 0;                   // engine slots holding a request
+  uint64_t grouped_completed = 0;
+  uint64_t grouped_steps = 0;
+  int withhold_steps = 0;               // testing: steps whose descriptor table is withheld
+  long long withhold_spin = 0;
   double host_start_s = 0;         // host time spent starting requests (plan set-up, graph capture, launches)
+  cudaMemPool_t pool = nullptr;    // the device's default pool and its release threshold before the server
+  uint64_t pool_threshold = 0;
   Clock::time_point t0;
   std::string last_error;
 
@@ -174,45 +200,97 @@ void finish_request(trals_server* S, Slot& sl, trals_status st) {
   S->done_cv.notify_all();
 }
 
+// A grouped request's outcome: results from the engine's pinned buffers, then its slot is released.
+void finish_grouped(trals_server* S, Request* r, int gslot, trals_status st, const std::string& err) {
+  if (st == TRALS_OK) {
+    const double* cores = nullptr;
+    double res = 0.0;
+    std::string msg;
+    const int code = trals::grp_result(S->grp, gslot, &cores, &res, &msg);
+    if (code != TRALS_OK) {
+      st = (trals_status)code;
+      r->error = msg;
+    } else {
+      size_t off = 0;
+      for (int n = 0; n < r->N; ++n) {
+        std::memcpy(r->cores[n].data(), cores + off, r->cores[n].size() * sizeof(double));
+        off += r->cores[n].size();
+      }
+      // as the reduced-precision plans: no per-sweep residual, the explicit one after the last sweep
+      for (int k = 0; k + 1 < r->sweeps; ++k) r->res[k] = std::nan("");
+      r->res[r->sweeps - 1] = res;
+    }
+  } else {
+    r->error = err;
+  }
+  if (gslot >= 0) trals::grp_release(S->grp, gslot);
+  std::lock_guard<std::mutex> lk(S->mu);
+  r->status = st;
+  r->t_done = S->now();
+  S->used -= r->footprint;
+  if (gslot >= 0) --S->grp_active;
+  ++S->completed;
+  ++S->grouped_completed;
+  S->done_cv.notify_all();
+}
+
 void worker_main(trals_server* S) {
   cudaSetDevice(S->device);
   for (;;) {
     std::vector<int> admitted;
-    int active = 0;
+    int active = 0, handed = 0;
     {
       std::unique_lock<std::mutex> lk(S->mu);
       for (const Slot& sl : S->slots) active += sl.req != nullptr;
       if (S->stopping && active == 0) break;
-      // FIFO admission: the head waits until a slot and its footprint are both available
-      while (!S->stopping && !S->queue.empty()) {
-        Request* r = S->queue.front();
+      // admission in arrival order: a request waits for a slot of its kind (those behind it may pass),
+      // and one whose footprint does not fit holds back the rest
+      int gfree = S->grp ? trals::kGrpMaxSlots - S->grp_active : 0;
+      for (auto it = S->queue.begin(); !S->stopping && it != S->queue.end();) {
+        Request* r = *it;
+        if (S->used + r->footprint > S->budget) break;
         int free_slot = -1;
-        for (int k = 0; k < (int)S->slots.size(); ++k)
-          if (!S->slots[k].req) {
-            free_slot = k;
-            break;
+        if (r->grouped) {
+          if (gfree == 0) {
+            ++it;
+            continue;
           }
-        if (free_slot < 0 || S->used + r->footprint > S->budget) break;
-        S->queue.pop_front();
+          --gfree;
+          S->ginbox.push_back(r);
+          ++S->grp_active;
+          ++handed;
+        } else {
+          for (int k = 0; k < (int)S->slots.size(); ++k)
+            if (!S->slots[k].req) {
+              free_slot = k;
+              break;
+            }
+          if (free_slot < 0) {
+            ++it;
+            continue;
+          }
+          S->slots[free_slot].req = r;
+          admitted.push_back(free_slot);
+          ++active;
+        }
+        it = S->queue.erase(it);
         S->used += r->footprint;
         S->peak_used = std::max(S->peak_used, S->used);
-        S->slots[free_slot].req = r;
         r->t_admit = S->now();
-        admitted.push_back(free_slot);
-        ++active;
       }
-      S->peak_active = std::max(S->peak_active, active);
+      S->peak_active = std::max(S->peak_active, active + S->grp_active);
     }
-    bool progress = !admitted.empty();
+    if (handed) S->gcv.notify_all();
+    bool progress = !admitted.empty() || handed > 0;
+    const auto t0 = Clock::now();
     for (int k : admitted) {
-      const auto t0 = Clock::now();
       const trals_status st = start_request(S->slots[k]);
-      const double dt = std::chrono::duration<double>(Clock::now() - t0).count();
-      {
-        std::lock_guard<std::mutex> lk(S->mu);
-        S->host_start_s += dt;
-      }
       if (st != TRALS_OK) finish_request(S, S->slots[k], st);
+    }
+    if (!admitted.empty()) {
+      const double dt = std::chrono::duration<double>(Clock::now() - t0).count();
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->host_start_s += dt;
     }
     for (Slot& sl : S->slots) {
       if (!sl.req || !sl.plan) continue;
@@ -228,7 +306,60 @@ void worker_main(trals_server* S) {
     }
     if (!progress) {
       std::unique_lock<std::mutex> lk(S->mu);
-      S->cv.wait_for(lk, std::chrono::microseconds(active ? 20 : 2000));
+      S->cv.wait_for(lk, std::chrono::microseconds(active > 0 ? 20 : 2000));
+    }
+  }
+}
+
+// The grouped engine: takes the requests the worker admitted, launches steps while any is active and
+// hands back the finished ones.
+void engine_main(trals_server* S) {
+  cudaSetDevice(S->device);
+  std::vector<Request*> gslot_req(trals::kGrpMaxSlots, nullptr);
+  for (;;) {
+    std::vector<Request*> take;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      if (S->stopping && S->grp_active == 0 && S->ginbox.empty()) break;
+      while (!S->ginbox.empty()) {
+        take.push_back(S->ginbox.front());
+        S->ginbox.pop_front();
+      }
+      if (S->withhold_steps > 0) {
+        trals::grp_withhold(S->grp, S->withhold_steps, S->withhold_spin);
+        S->withhold_steps = 0;
+      }
+    }
+    bool progress = !take.empty();
+    for (Request* r : take) {
+      std::vector<const double*> init(r->N);
+      for (int n = 0; n < r->N; ++n) init[n] = r->cores[n].data();
+      std::string err;
+      const int g = trals::grp_admit(S->grp, r->N, r->I, r->R, static_cast<const float*>(r->X), r->x_on_host != 0,
+                                     r->opts.mode, r->sweeps, init.data(), &err);
+      if (g < 0) finish_grouped(S, r, -1, TRALS_E_CUDA, err);
+      else gslot_req[g] = r;
+    }
+    std::string err;
+    if (trals::grp_step(S->grp, &err)) {
+      progress = true;
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->grouped_steps = trals::grp_steps(S->grp);
+    } else if (!err.empty()) {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->last_error = err;
+    }
+    std::vector<int> done;
+    trals::grp_poll(S->grp, &done);
+    for (int g : done) {
+      Request* r = gslot_req[g];
+      gslot_req[g] = nullptr;
+      finish_grouped(S, r, g, TRALS_OK, std::string());
+      progress = true;
+    }
+    if (!progress) {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->gcv.wait_for(lk, std::chrono::microseconds(trals::grp_busy(S->grp) ? 10 : 2000));
     }
   }
 }
@@ -245,6 +376,16 @@ trals_status trals_server_create(trals_server** out, int device, size_t hbm_budg
   S->budget = hbm_budget_bytes;
   S->max_slots = max_slots;
   S->t0 = Clock::now();
+  // Plans and workspaces allocate stream-ordered from the device's default pool.  Its release threshold
+  // (0 by default) would hand the memory back at every synchronisation, so that each large request
+  // maps gigabytes afresh on the worker thread; keep up to the budget in the pool while the server runs.
+  if (cudaSetDevice(device) == cudaSuccess && cudaDeviceGetDefaultMemPool(&S->pool, device) == cudaSuccess) {
+    cudaMemPoolGetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &S->pool_threshold);
+    uint64_t keep = std::max<uint64_t>(S->pool_threshold, hbm_budget_bytes);
+    cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  } else {
+    S->pool = nullptr;
+  }
   trals_status st = trals_create(&S->sizing, device, nullptr);
   if (st == TRALS_OK) {
     S->slots.resize(max_slots);
@@ -264,11 +405,20 @@ trals_status trals_server_create(trals_server** out, int device, size_t hbm_budg
       }
     }
   }
+  if (st == TRALS_OK) {
+    std::string err;
+    S->grp = trals::grp_create(device, &err);
+    if (!S->grp) {
+      S->last_error = err;
+      st = TRALS_E_CUDA;
+    }
+  }
   if (st != TRALS_OK) {
     trals_server_destroy(S);
     return st;
   }
   S->worker = std::thread(worker_main, S);
+  S->engine = std::thread(engine_main, S);
   *out = S;
   return TRALS_OK;
 }
@@ -285,7 +435,9 @@ void trals_server_destroy(trals_server* S) {
     S->queue.clear();
   }
   S->cv.notify_all();
+  S->gcv.notify_all();
   if (S->worker.joinable()) S->worker.join();
+  if (S->engine.joinable()) S->engine.join();
   for (auto& kv : S->tickets) delete kv.second;
   for (Slot& sl : S->slots) {
     if (sl.ctx) trals_destroy(sl.ctx);
@@ -295,7 +447,12 @@ void trals_server_destroy(trals_server* S) {
     if (sl.h_cores) cudaFreeHost(sl.h_cores);
     if (sl.h_status) cudaFreeHost(sl.h_status);
   }
+  if (S->grp) trals::grp_destroy(S->grp);
   if (S->sizing) trals_destroy(S->sizing);
+  if (S->pool) {
+    cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &S->pool_threshold);
+    cudaMemPoolTrimTo(S->pool, 0);
+  }
   delete S;
 }
 
@@ -326,12 +483,17 @@ trals_status trals_server_submit(trals_server* S, const trals_request* q, uint64
     const void* xprobe = q->x_on_host ? reinterpret_cast<const void*>(uintptr_t(1) << 40) : q->X;
     st = trals_plan_footprint(S->sizing, r->N, r->I, r->R, xprobe, r->xt, &r->opts, &fp);
     if (st != TRALS_OK) S->last_error = trals_last_error(S->sizing);
+    r->grouped = st == TRALS_OK && S->grp &&
+                 trals::grp_eligible(r->N, r->I, r->R, r->xt, r->opts, r->sweeps, S->grp_max_elems);
   }
   if (st != TRALS_OK) {
     delete r;
     return st;
   }
-  r->footprint = fp + (r->x_on_host ? ((r->x_bytes + 255) & ~(size_t)255) : 0);
+  if (r->grouped)
+    r->footprint = trals::grp_footprint(r->N, r->I, r->R, r->opts.mode, r->x_on_host != 0);
+  else
+    r->footprint = fp + (r->x_on_host ? ((r->x_bytes + 255) & ~(size_t)255) : 0);
   if (r->footprint > S->budget) {
     std::lock_guard<std::mutex> lk(S->mu);
     S->last_error = "request footprint " + std::to_string(r->footprint) + " B exceeds the HBM budget " +
@@ -421,6 +583,23 @@ trals_status trals_server_stats(trals_server* S, trals_server_info* out) {
   out->peak_used_bytes = S->peak_used;
   out->peak_active = S->peak_active;
   out->host_start_s = S->host_start_s;
+  out->grouped_completed = S->grouped_completed;
+  out->grouped_steps = S->grouped_steps;
+  return TRALS_OK;
+}
+
+trals_status trals_server_set_group_limit(trals_server* S, int64_t max_elems) {
+  if (!S || max_elems < 0) return TRALS_E_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->grp_max_elems = max_elems;
+  return TRALS_OK;
+}
+
+trals_status trals_testing_server_withhold_steps(trals_server* S, int steps, long long spin_cycles) {
+  if (!S || steps < 0 || spin_cycles <= 0) return TRALS_E_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->withhold_steps = steps;
+  S->withhold_spin = spin_cycles;
   return TRALS_OK;
 }
 

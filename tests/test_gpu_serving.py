@@ -1,5 +1,7 @@
 """Serving loop (continuous batching) through the C ABI: every result is the same alone and in the
-mix, admission respects the HBM budget, and oversized requests are rejected."""
+mix, for requests served as plans and by the grouped step engine; grouped results agree with the plans'
+and with the oracle; admission respects the HBM budget; oversized requests are rejected; a grouped
+step whose descriptor table never comes gives up within its bound and reports TRALS_E_TIMEOUT."""
 import numpy as np
 import pytest
 
@@ -39,7 +41,8 @@ def problems(ctx):
 
 
 @pytest.mark.parametrize("mode", ["bf16", "fp32"])
-def test_results_same_alone_and_in_the_mix(ctx, problems, mode):
+def test_plan_results_same_alone_and_in_the_mix(ctx, problems, mode):
+    """Requests served as plans (the grouped engine switched off) equal trals_decompose bit for bit."""
     sweeps = 5
     opts = P.make_opts(mode)
     alone = []
@@ -49,12 +52,14 @@ def test_results_same_alone_and_in_the_mix(ctx, problems, mode):
         alone.append((cores, res))
     srv = P.Server(0, hbm_budget_bytes=8 << 30, max_slots=4)
     try:
+        srv.set_group_limit(0)
         tickets = [srv.submit(I, R, X, init, sweeps, opts) for (I, R), (X, init) in zip(SHAPES, problems)]
         out = [srv.wait(t, timeout=120.0) for t in tickets]
         stats = srv.stats()
     finally:
         srv.close()
     assert stats["peak_active"] >= 2, stats        # requests really overlapped
+    assert stats["grouped_completed"] == 0, stats
     for (cores_a, res_a), got in zip(alone, out):
         assert got is not None
         info, cores_m, res_m = got
@@ -65,12 +70,112 @@ def test_results_same_alone_and_in_the_mix(ctx, problems, mode):
         assert info["submit_s"] <= info["admit_s"] <= info["done_s"]
 
 
+GROUP_ALL = 1 << 22   # a group limit above every test shape: all of them join the grouped engine
+
+
+def _serve(problems, sweeps, opts, picks, budget=8 << 30, limit=GROUP_ALL, one_at_a_time=False, slots=4):
+    srv = P.Server(0, hbm_budget_bytes=budget, max_slots=slots)
+    try:
+        if limit is not None:
+            srv.set_group_limit(limit)
+        out = []
+        if one_at_a_time:
+            for k in picks:
+                t = srv.submit(SHAPES[k][0], SHAPES[k][1], problems[k][0], problems[k][1], sweeps, opts)
+                out.append(srv.wait(t, timeout=120.0))
+        else:
+            tickets = [srv.submit(SHAPES[k][0], SHAPES[k][1], problems[k][0], problems[k][1], sweeps, opts)
+                       for k in picks]
+            out = [srv.wait(t, timeout=120.0) for t in tickets]
+        stats = srv.stats()
+    finally:
+        srv.close()
+    return out, stats
+
+
+@pytest.mark.parametrize("mode", ["bf16", "fp32"])
+def test_grouped_results_same_alone_and_in_the_mix(problems, mode):
+    """The grouped step engine: each request served alone and served in the mix (all active together,
+    in different modes n at every step) gives the same cores and residual bit for bit."""
+    opts = P.make_opts(mode)
+    picks = list(range(len(SHAPES)))
+    alone, st_a = _serve(problems, 5, opts, picks, one_at_a_time=True)
+    mixed, st_m = _serve(problems, 5, opts, picks)
+    assert st_a["grouped_completed"] == st_m["grouped_completed"] == len(SHAPES), (st_a, st_m)
+    assert st_m["peak_active"] >= 2, st_m
+    for k, (a, m) in enumerate(zip(alone, mixed)):
+        assert a[0]["status"] == P.OK and m[0]["status"] == P.OK, (k, a[0], m[0])
+        for ga, gm in zip(a[1], m[1]):
+            np.testing.assert_array_equal(ga, gm)
+        np.testing.assert_array_equal(a[2], m[2])
+        assert np.isnan(a[2][:-1]).all() and 0.0 < a[2][-1] < 1.0
+
+
+@pytest.mark.parametrize("mode", ["bf16", "fp32"])
+def test_grouped_results_agree_with_the_plans(ctx, problems, mode):
+    """Grouped and plan results of the same requests, started near the generating cores.  In the FP32
+    mode both compute the same method in the same precisions, summed in different orders: the cores
+    agree to FP32 rounding (amplified by the conditioning of the solves) and the final residuals to
+    1e-6.  In the BF16 mode the tensor-core plans also round the subchain table to BF16 where the
+    grouped MTTSP keeps it in FP32, so the two differ by BF16 rounding: 2e-5 on the residual, 2e-2 on
+    the cores (both far inside the 1e-4 residual gap the reduced precision is held to)."""
+    rng = np.random.default_rng(3)
+    opts = P.make_opts(mode)
+    tol, rtol = (2e-2, 2e-5) if mode == "bf16" else (1e-4, 1e-6)
+    for k, (I, R) in enumerate(SHAPES):
+        init = [G + 1e-2 * rng.standard_normal(G.shape) for G in TI.gaussian_cores(100 + k, I, R)]
+        cores = [G.copy() for G in init]
+        res = P.trals_decompose(ctx, I, R, problems[k][0], cores, 5, opts)
+        srv = P.Server(0, hbm_budget_bytes=8 << 30, max_slots=2)
+        try:
+            srv.set_group_limit(GROUP_ALL)
+            got = srv.wait(srv.submit(I, R, problems[k][0], init, 5, opts), timeout=120.0)
+            assert srv.stats()["grouped_completed"] == 1
+        finally:
+            srv.close()
+        assert got[0]["status"] == P.OK, got[0]
+        assert abs(got[2][-1] - res[-1]) <= rtol, (k, got[2][-1], res[-1])
+        for a, b in zip(cores, got[1]):
+            assert np.linalg.norm(a - b) <= tol * np.linalg.norm(a), (k, np.linalg.norm(a - b) / np.linalg.norm(a))
+
+
+def test_grouped_and_plan_requests_together(problems):
+    """With the group limit between the sizes, the small requests go to the grouped engine and the rest
+    to plans in the same run; all complete."""
+    sizes = [int(np.prod(I)) for I, _ in SHAPES]
+    limit = int(np.median(sizes))
+    out, stats = _serve(problems, 3, P.make_opts("bf16"), list(range(len(SHAPES))), limit=limit)
+    assert all(o is not None and o[0]["status"] == P.OK for o in out)
+    assert stats["grouped_completed"] == sum(n <= limit for n in sizes), (stats, sizes, limit)
+
+
+def test_grouped_step_timeout_reports_status(problems):
+    """A step launched without its descriptor table: the doorbell wait gives up after its bound (2e6
+    cycles, about a millisecond), the step does no work, the requests it carried complete with
+    TRALS_E_TIMEOUT, and the next requests are served normally."""
+    opts = P.make_opts("fp32")
+    srv = P.Server(0, hbm_budget_bytes=8 << 30, max_slots=2)
+    try:
+        srv.set_group_limit(GROUP_ALL)
+        srv.testing_withhold_steps(1, 2_000_000)
+        t = [srv.submit(SHAPES[k][0], SHAPES[k][1], problems[k][0], problems[k][1], 2, opts) for k in (0, 1)]
+        first = [srv.wait(x, timeout=60.0) for x in t]
+        again = srv.wait(srv.submit(SHAPES[0][0], SHAPES[0][1], problems[0][0], problems[0][1], 2, opts),
+                         timeout=60.0)
+    finally:
+        srv.close()
+    assert any(f[0]["status"] == P.E_TIMEOUT for f in first), [f[0] for f in first]
+    assert all(f[0]["status"] in (P.OK, P.E_TIMEOUT) for f in first)
+    assert again[0]["status"] == P.OK, again[0]
+
+
 def test_admission_respects_the_budget(ctx, problems):
     opts = P.make_opts("bf16")
     fps = [P.trals_plan_footprint(ctx, I, R, X, opts) for (I, R), (X, _) in zip(SHAPES, problems)]
     budget = sorted(fps)[-1] + sorted(fps)[-2]     # room for the two largest at most
     srv = P.Server(0, hbm_budget_bytes=budget, max_slots=8)
     try:
+        srv.set_group_limit(0)
         tickets = [srv.submit(I, R, X, init, 3, opts) for (I, R), (X, init) in zip(SHAPES, problems)]
         out = [srv.wait(t, timeout=120.0) for t in tickets]
         stats = srv.stats()
@@ -81,6 +186,18 @@ def test_admission_respects_the_budget(ctx, problems):
     assert stats["completed"] == len(SHAPES)
     for o, fp in zip(out, fps):
         assert o[0]["footprint_bytes"] == fp
+
+
+def test_grouped_admission_respects_the_budget(problems):
+    opts = P.make_opts("bf16")
+    picks = list(range(len(SHAPES)))
+    alone, _ = _serve(problems, 2, opts, picks, one_at_a_time=True)
+    fps = sorted(a[0]["footprint_bytes"] for a in alone)
+    budget = fps[-1] + fps[-2]
+    out, stats = _serve(problems, 2, opts, picks, budget=budget)
+    assert all(o is not None and o[0]["status"] == P.OK for o in out)
+    assert stats["peak_used_bytes"] <= budget, (stats, budget)
+    assert stats["grouped_completed"] == len(SHAPES)
 
 
 def test_footprint_equals_plan_bytes(ctx, problems):
