@@ -1214,7 +1214,7 @@ trals_status trals_qr_r_factor(trals_ctx* ctx, int N, const int64_t* I, const in
   if (e == cudaSuccess) e = cudaMalloc(&R0, z.R_elems * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&R1, z.R_elems * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&W, std::max<int64_t>(z.W_elems, 1) * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&Lm, ((size_t)r * r + r) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&Lm, lmat_elems(r) * sizeof(double));   // the factor layout, block inverses included
   if (e == cudaSuccess) {
     launch_qr_factor(N, I, R, n, cores_dev, B, R0, R1, W, Lm, ctx->d_status, nullptr, ctx->stream);
     launch_transpose(Lm, r, R_dev, ctx->stream);
