@@ -876,9 +876,13 @@ struct GroupEngine {
   unsigned* dseq = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  // kernel nodes whose grids follow the step's work (K1, K2, K3, K4, K5, K6) and their parameters
+  // kernel nodes whose grids follow the step's work (K1, K2, K3, K4, K5, K6), their functions, and the
+  // one argument they all take (the device table), held here so that a node update never points into
+  // storage the graph owns
   cudaGraphNode_t knode[6] = {};
-  cudaKernelNodeParams kparam[6] = {};
+  const void* kfunc[6] = {};
+  const GrpTable* karg = nullptr;
+  void* kargv[1] = {nullptr};
   unsigned kgrid[6] = {};
   cudaEvent_t step_ev[4] = {};
   unsigned seq = 0;                 // last step launched
@@ -991,12 +995,14 @@ GroupEngine* grp_create(int device, std::string* err) {
       for (int k = 0; k < 6; ++k)
         if (kp.func == funcs[k]) {
           e->knode[k] = nd;
-          e->kparam[k] = kp;
+          e->kfunc[k] = funcs[k];
           e->kgrid[k] = kp.gridDim.x;
         }
     }
     for (int k = 0; k < 6; ++k)
       if (!e->knode[k]) return fail("graph nodes", cudaErrorInvalidValue);
+    e->karg = e->dtab;
+    e->kargv[0] = &e->karg;
   }
   if ((c = cudaStreamSynchronize(e->stream)) != cudaSuccess) return fail("init", c);
   return e;
@@ -1240,8 +1246,13 @@ bool grp_step(GroupEngine* e, std::string* err) {
     for (int k = 0; k < 6; ++k) {
       const unsigned g = std::max(1u, std::min(want[k], (unsigned)(k == 3 ? kGrpMaxSlots : 2 * e->nsm)));
       if (g == e->kgrid[k]) continue;
-      cudaKernelNodeParams kp = e->kparam[k];
+      cudaKernelNodeParams kp{};
+      kp.func = const_cast<void*>(e->kfunc[k]);
       kp.gridDim = dim3(g, 1, 1);
+      kp.blockDim = dim3(kThreads, 1, 1);
+      kp.sharedMemBytes = 0;
+      kp.kernelParams = e->kargv;
+      kp.extra = nullptr;
       const cudaError_t c = cudaGraphExecKernelNodeSetParams(e->exec, e->knode[k], &kp);
       if (c != cudaSuccess) {
         if (err) *err = std::string("grouped engine: step grid: ") + cudaGetErrorString(c);
