@@ -459,7 +459,7 @@ def roofline_for(w, mode, kernel_ms, peaks, src, step_ms=None):
         out.update({"achieved_contraction": ach_step, "frac_contraction": ach_step / peak,
                     "contraction_ms_per_mode": step_ms,
                     "frac_contraction_of": "the whole contraction step (last table link + kernel + FP64 "
-                                           "partial reduction); the >= 0.60 target applies to this one"})
+                                           "partial reduction)"})
     return out
 
 
