@@ -58,8 +58,10 @@ typedef enum {
   TRALS_E_PENDING = 8     /* serving: result not ready yet */
 } trals_status;
 
-/* Element type of the caller's X. */
-typedef enum { TRALS_X_F64 = 0, TRALS_X_F32 = 1, TRALS_X_BF16 = 2 } trals_xtype;
+/* Element type of the caller's X.  TRALS_X_BF16PAIR: 2 prod(I) BF16 values, the hi plane of every
+ * element (column-major) followed by the lo plane, value hi + lo (the split trals_quantize_bf16 writes);
+ * accepted by trals_mttsp in the BF16 modes (BF16 and BF16X2 read the hi plane). */
+typedef enum { TRALS_X_F64 = 0, TRALS_X_F32 = 1, TRALS_X_BF16 = 2, TRALS_X_BF16PAIR = 3 } trals_xtype;
 
 /* Storage of X and arithmetic of the RHS contraction M_n (the Gram chain, S_n and the solve are
  * FP64 in every mode).
@@ -72,8 +74,17 @@ typedef enum { TRALS_X_F64 = 0, TRALS_X_F32 = 1, TRALS_X_BF16 = 2 } trals_xtype;
  *  BF16X3: X split once into hi/lo BF16 pairs (hi = bf16(x), lo = bf16(x - hi)), the subchain
  *          table likewise; on the tensor cores every K step is three BF16 products
  *          (X_hi T_hi + X_hi T_lo + X_lo T_hi) into one FP32 accumulator (the CUDA-core path reads
- *          hi + lo in FP32 arithmetic). */
-typedef enum { TRALS_MODE_FP64 = 0, TRALS_MODE_FP32 = 1, TRALS_MODE_BF16 = 2, TRALS_MODE_BF16X3 = 3 } trals_mode;
+ *          hi + lo in FP32 arithmetic).
+ *  BF16X2: X quantised once to BF16 as in BF16, the subchain table split into hi/lo BF16 pairs;
+ *          two products per K step (X T_hi + X T_lo): only the rounding of X remains.  Off the
+ *          tensor-core geometries as BF16. */
+typedef enum {
+  TRALS_MODE_FP64 = 0,
+  TRALS_MODE_FP32 = 1,
+  TRALS_MODE_BF16 = 2,
+  TRALS_MODE_BF16X3 = 3,
+  TRALS_MODE_BF16X2 = 4
+} trals_mode;
 
 /* Solver for the R_n R_{n+1} subproblem:
  *  CHOL          Cholesky on the normal equations (Alg. 2 line 9);
@@ -235,8 +246,10 @@ trals_status trals_coef_matrix_explicit(trals_ctx* ctx, int N, const int64_t* I,
 
 /* MTTSP of mode n (Alg. 2 lines 7-8): M_dev (I_n x r, FP64) = X_[n] G^{!=n}_[2], with the
  * subchain rows generated on the fly from cores_dev (FP64) in the arithmetic of `mode`
- * (X element type must match the mode: F64 for FP64, F32 for FP32, BF16 for BF16;
- * BF16X3 takes X as BF16 hi followed by BF16 lo halves, 2 * prod(I) elements). */
+ * (X element type must match the mode: F64 for FP64, F32 for FP32, BF16 or BF16PAIR for BF16 and
+ * BF16X2 (the hi plane is read), BF16PAIR -- or BF16 laid out the same way -- for BF16X3: the hi
+ * plane followed by the lo plane, 2 * prod(I) elements).  trals_last_mttsp_path tells which kernel
+ * ran. */
 trals_status trals_mttsp(trals_ctx* ctx, int N, const int64_t* I, const int32_t* R,
                          const void* X_dev, int xt, int mode, const double* const* cores_dev, int n,
                          double* M_dev);

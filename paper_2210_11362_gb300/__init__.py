@@ -25,10 +25,10 @@ OK, E_ARG, E_OOM, E_CUDA, E_NOT_SPD, E_NONFINITE, E_TIMEOUT, E_REJECTED, E_PENDI
 STATUS_NAMES = {0: "OK", 1: "E_ARG", 2: "E_OOM", 3: "E_CUDA", 4: "E_NOT_SPD", 5: "E_NONFINITE",
                 6: "E_TIMEOUT", 7: "E_REJECTED", 8: "E_PENDING"}
 # trals_xtype
-X_F64, X_F32, X_BF16 = 0, 1, 2
+X_F64, X_F32, X_BF16, X_BF16PAIR = 0, 1, 2, 3
 # trals_mode
-MODE_FP64, MODE_FP32, MODE_BF16, MODE_BF16X3 = 0, 1, 2, 3
-MODE_NAMES = {"fp64": MODE_FP64, "fp32": MODE_FP32, "bf16": MODE_BF16, "bf16x3": MODE_BF16X3}
+MODE_FP64, MODE_FP32, MODE_BF16, MODE_BF16X3, MODE_BF16X2 = 0, 1, 2, 3, 4
+MODE_NAMES = {"fp64": MODE_FP64, "fp32": MODE_FP32, "bf16": MODE_BF16, "bf16x3": MODE_BF16X3, "bf16x2": MODE_BF16X2}
 # trals_solver / trals_gram
 SOLVE_CHOL, SOLVE_QR, SOLVE_QRNE, SOLVE_QR_COMPRESSED = 0, 1, 2, 3
 GRAM_STRUCTURED, GRAM_EXPLICIT = 0, 1
@@ -381,12 +381,14 @@ def trals_qr_r_factor(ctx: Context, I, R, cores_dev: Sequence, n: int, R_dev) ->
               "trals_qr_r_factor")
 
 
-def trals_mttsp(ctx: Context, I, R, X_dev, mode, cores_dev: Sequence, n: int, M_dev) -> None:
+def trals_mttsp(ctx: Context, I, R, X_dev, mode, cores_dev: Sequence, n: int, M_dev, xt: Optional[int] = None) -> None:
+    """M_n of X_dev; xt overrides the element type taken from the tensor (X_BF16PAIR for a hi/lo pair)."""
     N, Ia, Ra = _shape(I, R)
     if isinstance(mode, str):
         mode = MODE_NAMES[mode]
-    ctx.check(lib().trals_mttsp(ctx.handle, N, ctypes.addressof(Ia), ctypes.addressof(Ra), _ptr(X_dev), _xtype(X_dev),
-                                int(mode), _ptr_array([_ptr(c) for c in cores_dev]), int(n), _ptr(M_dev)),
+    ctx.check(lib().trals_mttsp(ctx.handle, N, ctypes.addressof(Ia), ctypes.addressof(Ra), _ptr(X_dev),
+                                _xtype(X_dev) if xt is None else int(xt), int(mode),
+                                _ptr_array([_ptr(c) for c in cores_dev]), int(n), _ptr(M_dev)),
               "trals_mttsp")
 
 

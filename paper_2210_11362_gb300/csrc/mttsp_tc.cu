@@ -63,7 +63,8 @@ struct TcArgs {
   int withhold;      // fault injection for tests: the producer skips its first copy (see tc_set_fault)
   uint32_t tx_bytes;
   uint32_t idesc;
-  int x3;            // bf16x3: X and the table as hi/lo BF16 pairs, three products per K step
+  int xpl, tpl;      // BF16 planes of X and of the table per stage: 1 (BF16), or 2 (hi/lo pairs): bf16x2
+                     // splits the table (two products per K step), bf16x3 both (three products)
   const float* F;    // [fac][NX][SYP]
   float* partials;   // [grid][In * r]
   DevStatus* status;
@@ -267,8 +268,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int bBytes = ((a.W_pad * 128) + 1023) & ~1023;
-  const int planes = a.x3 ? 2 : 1;                 // stage: X hi [, X lo], table hi [, table lo]
-  const int stageBytes = planes * (kABytes + bBytes);
+  // stage: X hi [, X lo], table hi [, table lo]
+  const int stageBytes = a.xpl * kABytes + a.tpl * bBytes;
   const int NS = a.ns;
   // stage-2 factor blocks: per row (MM), or the blocks of a tile, double buffered
   float* F_s = reinterpret_cast<float*>(base + NS * stageBytes);
@@ -333,10 +334,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           // MMA issuer's wait for it runs out and the kernel reports TRALS_E_TIMEOUT
           if (!(a.withhold && j == 0 && ks == ks0)) {
             uint8_t* A = base + stage * stageBytes;
-            uint8_t* B = A + planes * kABytes;
+            uint8_t* B = A + a.xpl * kABytes;
             mbar_expect_tx(&full[stage], a.tx_bytes);
             const int k0 = ks * kKT;
-            for (int pl = 0; pl < planes; ++pl) {
+            for (int pl = 0; pl < a.tpl; ++pl) tma_load_2d(B + pl * bBytes, pl ? &tmTl : &tmT, &full[stage], k0, 0, pol_tab);
+            for (int pl = 0; pl < a.xpl; ++pl) {
               const CUtensorMap* mx = pl ? &tmXl : &tmX;
               uint8_t* Ap = A + pl * kABytes;
               if (a.variant == KM_L) {
@@ -350,7 +352,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int at = 0; at < 2; ++at)
                   tma_load_3d(Ap + at * kAtomBytes, mx, &full[stage], (int)(pc * 64), k0, (int)(2 * op + at), pol_x);
               }
-              tma_load_2d(B + pl * bBytes, pl ? &tmTl : &tmT, &full[stage], k0, 0, pol_tab);
             }
             ++issued[stage];
           }
@@ -395,19 +396,22 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           const uint32_t A = smem_u32(base + stage * stageBytes);
-          const uint32_t B = A + (uint32_t)(planes * kABytes);
+          const uint32_t B = A + (uint32_t)(a.xpl * kABytes);
 #pragma unroll
           for (int jj = 0; jj < kKT / 16; ++jj) {
             const bool mn = a.variant == MM || a.variant == MM_L;
             const uint64_t ad = mn ? sdesc(A + 2048u * jj, kAtomBytes, 1024) : sdesc(A + 32u * jj, 16, 1024);
             const uint64_t bd = sdesc(B + 32u * jj, 16, 1024);
             umma_bf16(d, ad, bd, a.idesc, (ks > ks0 || jj > 0) ? 1u : 0u);
-            if (a.x3) {
-              // split-BF16 products: X_hi T_lo + X_lo T_hi (X_lo T_lo is below FP32 rounding)
-              const uint32_t Al = A + (uint32_t)kABytes;
-              const uint64_t adl = mn ? sdesc(Al + 2048u * jj, kAtomBytes, 1024) : sdesc(Al + 32u * jj, 16, 1024);
+            // split-BF16 products: X_hi T_lo (bf16x2, bf16x3) and X_lo T_hi (bf16x3); X_lo T_lo is below
+            // FP32 rounding
+            if (a.tpl == 2) {
               const uint64_t bdl = sdesc(B + (uint32_t)bBytes + 32u * jj, 16, 1024);
               umma_bf16(d, ad, bdl, a.idesc, 1u);
+            }
+            if (a.xpl == 2) {
+              const uint32_t Al = A + (uint32_t)kABytes;
+              const uint64_t adl = mn ? sdesc(Al + 2048u * jj, kAtomBytes, 1024) : sdesc(Al + 32u * jj, 16, 1024);
               umma_bf16(d, adl, bd, a.idesc, 1u);
             }
           }
@@ -935,7 +939,7 @@ struct TcImpl {
   int64_t core_off[kMaxOrder + 1] = {};
   int SYP = 4;
   __nv_bfloat16* tab = nullptr;
-  __nv_bfloat16* tab_lo = nullptr;   // bf16x3 only
+  __nv_bfloat16* tab_lo = nullptr;   // split-table modes (bf16x2, bf16x3) only
   float* F = nullptr;
   float* partials = nullptr;
   int64_t E = 0;
@@ -1093,7 +1097,8 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   if (err) *err = cudaSuccess;
   p.valid = false;
   const bool x3 = mode == TRALS_MODE_BF16X3;
-  if (mode != TRALS_MODE_BF16 && !(x3 && Xlo != nullptr)) return 0;
+  const bool tlo = x3 || mode == TRALS_MODE_BF16X2;   // the table as hi/lo planes
+  if (mode != TRALS_MODE_BF16 && mode != TRALS_MODE_BF16X2 && !(x3 && Xlo != nullptr)) return 0;
   if ((reinterpret_cast<uintptr_t>(X) & 15) != 0) return 0;
   if (x3 && (reinterpret_cast<uintptr_t>(Xlo) & 15) != 0) return 0;
   if (!get_encode()) return 0;
@@ -1215,9 +1220,9 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   A.fs_stride = (A.NX * impl->SYP + 7) / 8 * 8 + 4;
   A.ms_stride = A.r | 1;   // odd row stride: lanes with different i_n hit different banks
 
-  A.tx_bytes += (uint32_t)(A.W_pad * 128);
-  A.x3 = x3 ? 1 : 0;
-  if (x3) A.tx_bytes *= 2;   // hi and lo planes of X and of the table
+  A.xpl = x3 ? 2 : 1;
+  A.tpl = tlo ? 2 : 1;
+  A.tx_bytes = (uint32_t)(A.xpl * A.tx_bytes + A.tpl * A.W_pad * 128);   // X box(es), then table box(es)
   // MMA instruction descriptor: D=F32, A=B=BF16, A major per variant, B K-major, N=W_pad, M=128
   A.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((A.variant == MM || A.variant == MM_L ? 1u : 0u) << 15) |
             ((uint32_t)(A.W_pad >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
@@ -1264,7 +1269,7 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   size_t fixed = 1024 + (size_t)((fs_rows * A.fs_stride + 1) & ~1) * 4 + (2 * kNSMax + 4) * 8 + 64;
   if (A.variant == MM_L)   // one x-column of every row, and the I_0 x r sums
     fixed += (size_t)((kRows * (A.NY | 1) + 1) & ~1) * 4 + (size_t)((In * A.ms_stride + 1) & ~1) * 4;
-  const size_t stage = (size_t)(x3 ? 2 : 1) * ((size_t)kABytes + bBytes);
+  const size_t stage = (size_t)A.xpl * kABytes + (size_t)A.tpl * bBytes;
   const int ns = (int)std::min<size_t>(kNSMax, fixed < (size_t)kSmemBudget ? (kSmemBudget - fixed) / stage : 0);
   if (ns < 2) {
     delete impl;
@@ -1308,8 +1313,8 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
                            chainMax * sizeof(float), (size_t)A.W_pad * impl->Kpad * sizeof(__nv_bfloat16),
                            (size_t)nfac * A.NX * impl->SYP * sizeof(float),
                            (size_t)impl->grid * impl->E * sizeof(float),
-                           x3 ? (size_t)A.W_pad * impl->Kpad * sizeof(__nv_bfloat16) : 0};
-  const int nalloc = x3 ? 7 : 6;
+                           tlo ? (size_t)A.W_pad * impl->Kpad * sizeof(__nv_bfloat16) : 0};
+  const int nalloc = tlo ? 7 : 6;
   if (count_bytes) {
     for (int k = 0; k < nalloc; ++k) *count_bytes += (std::max<size_t>(sizes[k], 16) + 255) & ~(size_t)255;
     delete impl;
@@ -1340,13 +1345,13 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   impl->tab = static_cast<__nv_bfloat16*>(q[3]);
   impl->F = static_cast<float*>(q[4]);
   impl->partials = static_cast<float*>(q[5]);
-  impl->tab_lo = x3 ? static_cast<__nv_bfloat16*>(q[6]) : nullptr;
+  impl->tab_lo = tlo ? static_cast<__nv_bfloat16*>(q[6]) : nullptr;
   A.F = impl->F;
   A.partials = impl->partials;
   // padding of the packed table and factor stays zero: the fused last-link kernel writes live entries only
   e = cudaMemsetAsync(impl->tab, 0, sizes[3], s);
   if (e == cudaSuccess) e = cudaMemsetAsync(impl->F, 0, sizes[4], s);
-  if (e == cudaSuccess && x3) e = cudaMemsetAsync(impl->tab_lo, 0, sizes[6], s);
+  if (e == cudaSuccess && tlo) e = cudaMemsetAsync(impl->tab_lo, 0, sizes[6], s);
   if (e != cudaSuccess) {
     if (err) *err = e;
     delete impl;
@@ -1355,7 +1360,7 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
     return 0;
   }
   if (!encode_bf16(&impl->tmT, impl->tab, 2, tdims, tstrides, tbox) ||
-      (x3 && !encode_bf16(&impl->tmTl, impl->tab_lo, 2, tdims, tstrides, tbox))) {
+      (tlo && !encode_bf16(&impl->tmTl, impl->tab_lo, 2, tdims, tstrides, tbox))) {
     delete impl;
     for (void* a : p.allocs) cudaFreeAsync(a, s);
     p.allocs.clear();
@@ -1449,8 +1454,8 @@ int tc_enqueue_main(TcPlan& p, double* const* cores, double* M, cudaStream_t s, 
   }
   if (before_kernel) cudaStreamWaitEvent(s, before_kernel, 0);
   if (ev0) cudaEventRecord(ev0, s);
-  const CUtensorMap& xl = A.x3 ? impl->tmXl : impl->tmX;   // unread unless x3
-  const CUtensorMap& tl = A.x3 ? impl->tmTl : impl->tmT;
+  const CUtensorMap& xl = A.xpl == 2 ? impl->tmXl : impl->tmX;   // unread with one X plane
+  const CUtensorMap& tl = A.tpl == 2 ? impl->tmTl : impl->tmT;     // unread with one table plane
   switch (impl->SYP) {
     case 4: mttsp_tc_kernel<4><<<impl->grid, kThreads, impl->smem, s>>>(impl->tmX, impl->tmT, xl, tl, A); break;
     case 8: mttsp_tc_kernel<8><<<impl->grid, kThreads, impl->smem, s>>>(impl->tmX, impl->tmT, xl, tl, A); break;

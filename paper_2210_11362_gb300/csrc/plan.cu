@@ -603,7 +603,7 @@ trals_status plan_build(trals_ctx* ctx, int N, const int64_t* I, const int32_t* 
     return TRALS_E_ARG;
   }
   trals_opts o = opts ? *opts : trals_opts{TRALS_MODE_FP64, TRALS_SOLVE_CHOL, TRALS_GRAM_STRUCTURED, 0};
-  if (o.mode < TRALS_MODE_FP64 || o.mode > TRALS_MODE_BF16X3 || xt < TRALS_X_F64 || xt > TRALS_X_BF16) {
+  if (o.mode < TRALS_MODE_FP64 || o.mode > TRALS_MODE_BF16X2 || xt < TRALS_X_F64 || xt > TRALS_X_BF16) {
     ctx->last_error = "unknown mode or X type";
     return TRALS_E_ARG;
   }
@@ -651,7 +651,7 @@ trals_status plan_build(trals_ctx* ctx, int N, const int64_t* I, const int32_t* 
   } while (0)
 
   for (int n = 0; n < N; ++n) p->Ist[n] = I[n];
-  if ((o.mode == TRALS_MODE_BF16 || o.mode == TRALS_MODE_BF16X3) && I[0] % 8 != 0) p->Ist[0] = (I[0] + 7) / 8 * 8;
+  if (o.mode != TRALS_MODE_FP64 && o.mode != TRALS_MODE_FP32 && I[0] % 8 != 0) p->Ist[0] = (I[0] + 7) / 8 * 8;
   p->numel_st = p->numel / I[0] * p->Ist[0];
   const bool padded = p->Ist[0] != I[0];
   int maxR2 = 0, maxr = 0;
@@ -755,7 +755,7 @@ trals_status plan_build(trals_ctx* ctx, int N, const int64_t* I, const int32_t* 
   // X as the MTTSP reads it (quantised once, K7), and |X|^2 from the full-precision source.
   p->Xk = X_dev;
   p->xk_t = xt;
-  if (o.mode == TRALS_MODE_BF16 && (xt != TRALS_X_BF16 || padded)) {
+  if ((o.mode == TRALS_MODE_BF16 || o.mode == TRALS_MODE_BF16X2) && (xt != TRALS_X_BF16 || padded)) {
     __nv_bfloat16* q = nullptr;
     PLAN_TRY(p->alloc(&q, (size_t)p->numel_st));
     if (!counting) {
@@ -1236,12 +1236,14 @@ trals_status trals_mttsp(trals_ctx* ctx, int N, const int64_t* I, const int32_t*
   ctx->last_mttsp_path = -1;
   trals_status st = check_shape(ctx, N, I, R);
   if (st != TRALS_OK) return st;
+  const bool bf_mode = mode == TRALS_MODE_BF16 || mode == TRALS_MODE_BF16X2 || mode == TRALS_MODE_BF16X3;
   const bool ok_type = (mode == TRALS_MODE_FP64 && xt == TRALS_X_F64) || (mode == TRALS_MODE_FP32 && xt == TRALS_X_F32) ||
-                       ((mode == TRALS_MODE_BF16 || mode == TRALS_MODE_BF16X3) && xt == TRALS_X_BF16);
+                       (bf_mode && (xt == TRALS_X_BF16 || xt == TRALS_X_BF16PAIR));
   if (!ok_type) {
     ctx->last_error = "X element type does not match the mode";
     return TRALS_E_ARG;
   }
+  if (xt == TRALS_X_BF16PAIR) xt = TRALS_X_BF16;   // the hi plane leads; bf16x3 reads the lo plane after it
   cudaStream_t s = ctx->stream;
   int64_t numel = 1;
   for (int k = 0; k < N; ++k) numel *= I[k];
@@ -1352,7 +1354,7 @@ trals_status trals_testing_mttsp_withheld_copy(trals_ctx* ctx, int N, const int6
 
 int trals_mttsp_path(int N, const int64_t* I, const int32_t* R, int n, int mode) {
   if (N < 3 || N > TRALS_MAX_ORDER || !I || !R || n < 0 || n >= N) return -1;
-  if (mode != TRALS_MODE_BF16 && mode != TRALS_MODE_BF16X3) return 0;
+  if (mode != TRALS_MODE_BF16 && mode != TRALS_MODE_BF16X2 && mode != TRALS_MODE_BF16X3) return 0;
   // plans store the BF16 copy with mode 0 padded to a multiple of 8
   int64_t Ist[TRALS_MAX_ORDER];
   for (int j = 0; j < N; ++j) Ist[j] = I[j];

@@ -237,7 +237,7 @@ def _mode_input(ctx, X, mode):
     with the FP64 values they hold."""
     I = X.shape
     numel = int(np.prod(I))
-    if mode == "bf16":
+    if mode in ("bf16", "bf16x2"):
         Xb = P.tensor_to_device(X, torch.bfloat16)
         return Xb, TI.unflat_f(Xb.double().cpu().numpy(), I)
     Xd = P.tensor_to_device(X)
@@ -253,7 +253,7 @@ def _run_mttsp(ctx, I, R, Xdev, mode, cores, n):
     return M.cpu().numpy().reshape(I[n], r, order="F"), P.trals_last_mttsp_path(ctx)
 
 
-@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("mode", ["bf16", "bf16x2", "bf16x3"])
 @pytest.mark.parametrize("I,R", TC_SHAPES)
 def test_mttsp_tensor_cores_exact_on_integer_data(ctx, I, R, mode):
     """On data where every intermediate is exact (small-integer X, subchain entries in {-1, 0, 1})
@@ -269,7 +269,33 @@ def test_mttsp_tensor_cores_exact_on_integer_data(ctx, I, R, mode):
         assert np.array_equal(got, ref), (n, P.MTTSP_PATHS[path], np.abs(got - ref).max())
 
 
-@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+def test_mttsp_bf16_pair_input(ctx):
+    """X given as a BF16 hi/lo pair (X_BF16PAIR): bf16x3 reads both planes, bit for bit what the same
+    buffer gives when typed as plain BF16 (the layout bf16x3 has always taken); BF16 and bf16x2 read the
+    hi plane only, bit for bit what the hi plane alone gives."""
+    I, R = TC_SHAPES[1]
+    X, _ = _problem(I, R)
+    cores = TI.gaussian_cores(9, I, R)
+    pair, _ = _mode_input(ctx, X, "bf16x3")
+    numel = int(np.prod(I))
+    hi = pair[:numel].clone()
+    cd = [P.core_to_device(G) for G in cores]
+    r = R[1] * R[2]
+    outs = {}
+    for tag, buf, mode, xt in [("x3pair", pair, "bf16x3", P.X_BF16PAIR), ("x3bf16", pair, "bf16x3", None),
+                               ("bfpair", pair, "bf16", P.X_BF16PAIR), ("bfhi", hi, "bf16", None),
+                               ("x2pair", pair, "bf16x2", P.X_BF16PAIR), ("x2hi", hi, "bf16x2", None)]:
+        M = torch.full((I[1] * r,), float("nan"), dtype=torch.float64, device="cuda")
+        P.trals_mttsp(ctx, I, R, buf, mode, cd, 1, M, xt=xt)
+        assert P.trals_last_mttsp_path(ctx) > 0, tag
+        outs[tag] = M.cpu().numpy()
+    assert np.array_equal(outs["x3pair"], outs["x3bf16"])
+    assert np.array_equal(outs["bfpair"], outs["bfhi"])
+    assert np.array_equal(outs["x2pair"], outs["x2hi"])
+    assert not np.array_equal(outs["x3pair"], outs["bfhi"])
+
+
+@pytest.mark.parametrize("mode", ["bf16", "bf16x2", "bf16x3"])
 @pytest.mark.parametrize("I,R", TC_SHAPES)
 def test_mttsp_tensor_cores_componentwise_bound(ctx, I, R, mode):
     """Gaussian data: every element of M_n within the componentwise bound above (and normwise
@@ -277,6 +303,8 @@ def test_mttsp_tensor_cores_componentwise_bound(ctx, I, R, mode):
     X, _ = _problem(I, R)
     cores = TI.gaussian_cores(9, I, R)
     Xdev, Xq = _mode_input(ctx, X, mode)
+    # bf16x2 rounds X (the reference is taken on the rounded X) but splits the table: only the table's
+    # hi/lo residue and the FP32 accumulation remain, as in bf16x3
     u, normwise = (U_BF16, 4e-3) if mode == "bf16" else (U_BF16X3, 5e-5)
     for n in range(len(I)):
         got, path = _run_mttsp(ctx, I, R, Xdev, mode, cores, n)
@@ -596,7 +624,7 @@ def _near_truth_problem(I, R, eta, seed):
 
 
 @pytest.mark.parametrize("solver", ["chol", "qr"])
-@pytest.mark.parametrize("mode", ["fp32", "bf16", "bf16x3"])
+@pytest.mark.parametrize("mode", ["fp32", "bf16", "bf16x2", "bf16x3"])
 @pytest.mark.parametrize("I,R,eta", [((30, 30, 30, 30), (6, 6, 6, 6), 1e-3), ((40, 24, 32), (4, 5, 3), 1e-2)])
 def test_reduced_precision_residual_gap(ctx, mode, I, R, eta, solver):
     """Reduced-precision modes reach the FP64 oracle's residual within 1e-4 (absolute), compared at
@@ -632,7 +660,7 @@ def test_tr60x4_rank10_full_size_one_sweep(ctx):
         assert rel(a, b) < 1e-9
 
 
-@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("mode", ["bf16", "bf16x2", "bf16x3"])
 def test_explicit_per_sweep_residual_in_reduced_modes(ctx, mode):
     """explicit_residual=1 in a reduced-precision mode: every sweep's residual comes from the FP32
     regeneration pass and matches the oracle's residual of the cores after that sweep."""
