@@ -204,9 +204,13 @@ trals_status trals_plan_explicit_residual(trals_plan* plan, double* rel_res_host
 trals_status trals_plan_time_mttsp(trals_plan* plan, int n, float* kernel_ms, float* total_ms);
 /* Device pointer of core n (FP64, layout above), valid until the plan is destroyed. */
 const double* trals_plan_core_dev(const trals_plan* plan, int n);
-/* Which kernel the plan uses for the MTTSP of mode n (codes of trals_mttsp_path).  This can differ
- * from trals_mttsp_path when the TMA descriptor encoder rejects a tensor-core geometry or X is not
- * 16-byte aligned: the plan then falls back to the CUDA cores. */
+/* Which kernel the plan uses for the MTTSP of mode n (codes of trals_mttsp_path, plus 5: the two-stage
+ * GEMM MTTSP, taken in the FP32, BF16 and BF16X2 modes by modes without a tensor-core geometry whose
+ * stage-1 table is 64 to 256 columns wide, for tensors of at least 2^21 entries: X is first contracted
+ * with the subchain table of the modes that lead it in memory, a plain GEMM through cuBLAS (FP32, or
+ * BF16 operands with FP32 accumulation), then with the other table in this library's kernels).  This
+ * can also differ from trals_mttsp_path when the TMA descriptor encoder rejects a tensor-core geometry
+ * or X is not 16-byte aligned: the plan then falls back to the CUDA cores. */
 int trals_plan_mttsp_path(const trals_plan* plan, int n);
 /* Number of kernel launches one sweep issues (for launch accounting). */
 int trals_plan_launches_per_sweep(const trals_plan* plan);

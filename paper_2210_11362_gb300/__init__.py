@@ -400,7 +400,8 @@ def trals_mttsp_noalloc(ctx: Context, I, R, X_dev, cores_dev: Sequence, n: int, 
               "trals_mttsp_noalloc")
 
 
-MTTSP_PATHS = {0: "cuda-cores", 1: "tc-kmajor-left", 2: "tc-kmajor-right", 3: "tc-mnmajor", 4: "tc-mnmajor-left"}
+MTTSP_PATHS = {0: "cuda-cores", 1: "tc-kmajor-left", 2: "tc-kmajor-right", 3: "tc-mnmajor", 4: "tc-mnmajor-left",
+               5: "two-stage-gemm"}
 
 
 def trals_last_mttsp_path(ctx: Context) -> int:

@@ -10,6 +10,7 @@
 
 #include "trals_internal.cuh"
 #include "mttsp_tc.cuh"
+#include "mttsp_gemm.cuh"
 #include "../../include/trals_testing.h"
 
 using namespace trals;
@@ -198,6 +199,10 @@ struct trals_plan {
   int launches = 0;
   TcPlan tc[TRALS_MAX_ORDER];
   bool use_tc[TRALS_MAX_ORDER] = {};
+  // two-stage GEMM MTTSP for modes without a tensor-core geometry (reduced modes): of Xk, and of the
+  // FP32 residual tensor E of the QR solve's refinement
+  GemmMttsp gemm[TRALS_MAX_ORDER];
+  GemmMttsp gemmE[TRALS_MAX_ORDER];
   // FP32 copies of the cores for the tensor-core subchain tables (core 0 with Ist[0] slices, the padded
   // ones zero): refreshed at the start of every run and by each core update inside the sweep
   float* c32buf = nullptr;
@@ -289,6 +294,11 @@ int enqueue_mttsp(trals_plan* p, int n, cudaStream_t s, cudaEvent_t ev0 = nullpt
     else
       launches += tc_enqueue(p->tc[n], p->Xk, p->cores, p->M, s, ev0, ev1);
     return launches;
+  }
+  if (p->gemm[n].valid) {
+    const int l = gemm_mttsp_enqueue(p->gemm[n], p->ctx, p->Xk, p->cores, p->I, p->R, p->M, s, ev0, ev1);
+    if (l >= 0) return launches + l;
+    p->gemm[n].valid = false;   // cuBLAS failed (reported in last_error): the CUDA-core kernel below
   }
   build_tables(L, p->cores, p->I, p->R, p->ltab, p->utab, p->tscratch, s);
   launches += L.N - 1;
@@ -384,7 +394,11 @@ int enqueue_qr_refinement(trals_plan* p, int n, cudaStream_t s) {
     launch_residual_f32(L, p->ltab, p->utab, fl, nl, nu, p->offL[n], p->offU[n], p->cores[n], p->X, p->xt,
                         p->partials, residual_f32_grid(L), s, static_cast<float*>(p->E));
     a.xt = TRALS_X_F32;
-    if (mttsp_simt_f32_fits(L)) {
+    int gl = -1;
+    if (p->gemmE[n].valid) gl = gemm_mttsp_enqueue(p->gemmE[n], p->ctx, p->E, p->cores, p->I, p->R, p->dM, s);
+    if (gl >= 0) {
+      launches += gl - 1;
+    } else if (mttsp_simt_f32_fits(L)) {
       a.gridX = mttsp_simt_f32_grid(L);
       launch_mttsp_simt_f32(a, fl, fl + nl, s);   // the tables' FP32 copies are still in the scratch
     } else {
@@ -548,6 +562,7 @@ void trals_destroy(trals_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->d_zero_ctr) cudaFree(ctx->d_zero_ctr);
+  gemm_release(ctx);
   if (ctx->owns_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -799,6 +814,37 @@ trals_status plan_build(trals_ctx* ctx, int N, const int64_t* I, const int32_t* 
       if (ok && !counting) {
         tc_set_status(p->tc[n], ctx->d_status);
         p->bytes += p->tc[n].bytes;
+      }
+    }
+  }
+  // the two-stage GEMM MTTSP where no tensor-core geometry applies (FP32, BF16 and BF16X2 modes; the QR
+  // solve's refinement reads the FP32 residual tensor), all its modes on one shared workspace
+  if (o.mode == TRALS_MODE_FP32 || o.mode == TRALS_MODE_BF16 || o.mode == TRALS_MODE_BF16X2) {
+    const int xm = o.mode == TRALS_MODE_FP32 ? kGemmF32 : o.mode == TRALS_MODE_BF16 ? kGemmBF16 : kGemmBF16Split;
+    bool any = false;
+    for (int n = 0; n < N; ++n) {
+      if (!p->use_tc[n]) any |= gemm_mttsp_plan(p->gemm[n], N, I, p->Ist, R, n, xm) != 0;
+      if (o.solver == TRALS_SOLVE_QR) any |= gemm_mttsp_plan(p->gemmE[n], N, I, I, R, n, kGemmF32) != 0;
+    }
+    if (any && !counting && !gemm_prepare(ctx)) {
+      for (int n = 0; n < N; ++n) p->gemm[n].valid = p->gemmE[n].valid = false;
+      any = false;
+    }
+    if (any) {
+      size_t need[kGemmBufs] = {};
+      for (int n = 0; n < N; ++n)
+        for (const GemmMttsp* g : {&p->gemm[n], &p->gemmE[n]})
+          if (g->valid)
+            for (int k = 0; k < kGemmBufs; ++k) need[k] = std::max(need[k], g->need[k]);
+      void* bufs[kGemmBufs] = {};
+      for (int k = 0; k < kGemmBufs; ++k) {
+        unsigned char* b = nullptr;
+        if (need[k]) PLAN_TRY(p->alloc(&b, need[k]));
+        bufs[k] = b;
+      }
+      for (int n = 0; n < N; ++n) {
+        if (p->gemm[n].valid) gemm_mttsp_bind(p->gemm[n], bufs);
+        if (p->gemmE[n].valid) gemm_mttsp_bind(p->gemmE[n], bufs);
       }
     }
   }
@@ -1086,7 +1132,7 @@ const double* trals_plan_core_dev(const trals_plan* p, int n) {
 
 int trals_plan_mttsp_path(const trals_plan* p, int n) {
   if (!p || n < 0 || n >= p->N) return -1;
-  return p->use_tc[n] ? tc_variant(p->tc[n]) + 1 : 0;
+  return p->use_tc[n] ? tc_variant(p->tc[n]) + 1 : p->gemm[n].valid ? 5 : 0;
 }
 
 int trals_plan_launches_per_sweep(const trals_plan* p) {

@@ -243,6 +243,7 @@ struct trals_ctx {
   trals::DevStatus* d_status = nullptr;   // per-context device status word
   int* d_zero_ctr = nullptr;              // a device int holding 0 (sweep counter for one-off calls)
   int last_mttsp_path = -1;               // kernel the last trals_mttsp call ran (trals_mttsp_path codes)
+  void* cublas = nullptr;                 // cuBLAS handle of the two-stage GEMM MTTSP (created on demand)
 };
 
 #define TRALS_CUDA_TRY(ctx, call)                                                        \

@@ -393,6 +393,59 @@ def test_plan_mttsp_full_size_40x5(ctx):
             plan.close()
 
 
+# Wide subchain tables (R = 16: 256 columns) have no tensor-core geometry; with at least 2^21 entries the
+# reduced modes take the two-stage GEMM MTTSP (path 5).  I_0 = 60 makes the BF16 modes pad mode 0 to 64,
+# which the GEMM's table (modes 1-3) and T's rows (mode 0) must follow.
+GEMM_SHAPE = ((60, 64, 3, 200), (16, 16, 16, 16))
+_GEMM_REF = {}
+
+
+def _gemm_plan_M(ctx, I, R, X, cores, mode, n):
+    plan = P.Plan(ctx, I, R, P.tensor_to_device(X, torch.float32), P.make_opts(mode))
+    try:
+        plan.set_cores(cores)
+        assert [plan.mttsp_path(k) for k in range(len(I))] == [5] * len(I)
+        r = R[n] * R[(n + 1) % len(I)]
+        M = torch.full((I[n] * r,), float("nan"), dtype=torch.float64, device="cuda")
+        plan.mttsp(n, M)
+        torch.cuda.synchronize()
+        return M.cpu().numpy().reshape(I[n], r, order="F")
+    finally:
+        plan.close()
+
+
+@pytest.mark.parametrize("mode", ["fp32", "bf16", "bf16x2"])
+def test_plan_two_stage_gemm_mttsp_exact_on_integer_data(ctx, mode):
+    """Integer X and signed-selection cores: every product and sum of both stages is an exact integer
+    in FP32 and BF16, so M_n must equal the FP64 oracle bit for bit in every mode n (forms 1 and 2, the
+    padded leading mode included)."""
+    I, R = GEMM_SHAPE
+    X, cores = _integer_problem(I, R, seed=8)
+    for n in range(len(I)):
+        if ("int", n) not in _GEMM_REF:
+            _GEMM_REF[("int", n)] = O.mttsp(X, cores, n)
+        got = _gemm_plan_M(ctx, I, R, X, cores, mode, n)
+        ref = _GEMM_REF[("int", n)]
+        assert np.array_equal(got, ref), (mode, n, np.abs(got - ref).max())
+
+
+@pytest.mark.parametrize("mode,n", [("fp32", 2), ("fp32", 3), ("bf16", 0), ("bf16x2", 1)])
+def test_plan_two_stage_gemm_mttsp_componentwise_bound(ctx, mode, n):
+    """Gaussian data: every element of M_n within the componentwise bound of the X the mode reads
+    (FP32, or BF16 with the table in BF16 or split)."""
+    I, R = GEMM_SHAPE
+    X = TI.gaussian_noise(8, I)
+    cores = TI.gaussian_cores(8, I, R)
+    Xt = torch.from_numpy(TI.flat_f(X)).to(torch.float32)
+    xq_t = Xt if mode == "fp32" else Xt.to(torch.bfloat16)
+    Xq = TI.unflat_f(xq_t.double().numpy(), I)
+    u = {"fp32": 2.0 ** -24, "bf16": U_BF16, "bf16x2": U_BF16X3}[mode]
+    got = _gemm_plan_M(ctx, I, R, X, cores, mode, n)
+    ref = O.mttsp(Xq, cores, n)
+    ratio = float((np.abs(got - ref) / componentwise_tol(Xq, cores, n, u)).max())
+    assert ratio <= 1.0, (mode, n, ratio)
+
+
 def test_solve_chol_matches_oracle(ctx):
     I, R = (9, 8, 7), (3, 4, 2)
     X, init = _problem(I, R)
