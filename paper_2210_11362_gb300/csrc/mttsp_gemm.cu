@@ -126,6 +126,35 @@ __global__ void __launch_bounds__(256) gemm_stage2_kernel(const float* __restric
   if (col < r) part[(int64_t)c * In * r + i + In * col] = acc;
 }
 
+// P of gemm_residual_enqueue, stored row-contiguous: P[w + W1 row].
+template <int FORM>
+__global__ void residual_p_kernel(const double* __restrict__ G, const float* __restrict__ tabO, int64_t rowsT, int W1,
+                                  int WO, int64_t nO, int64_t In, int Rn, int Rn1, int Rs, float* __restrict__ P) {
+  const int64_t total = rowsT * W1;
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = x / W1;
+    const int w = (int)(x - row * W1);
+    float acc = 0.0f;
+    if (FORM == 1) {   // row = i + In l, w = s + Rs a
+      const int64_t i = row % In, l = row / In;
+      const int s = w % Rs, a = w / Rs;
+      const float* Lr = tabO + l * WO + Rn1 * s;   // L(l)[b, s] at b + Rn1 s
+      for (int b = 0; b < Rn1; ++b) acc = fmaf((float)G[a + (int64_t)Rn * (i + In * b)], Lr[b], acc);
+    } else {           // row = u + nO i, w = b + Rn1 s
+      const int64_t u = row % nO, i = row / nO;
+      const int b = w % Rn1, s = w / Rn1;
+      const float* Ur = tabO + u * WO + s;         // U(u)[s, a] at s + Rs a
+      for (int a = 0; a < Rn; ++a) acc = fmaf(Ur[(int64_t)Rs * a], (float)G[a + (int64_t)Rn * (i + In * b)], acc);
+    }
+    P[x] = acc;
+  }
+}
+
+__global__ void f64_to_f32_kernel(const double* __restrict__ src, int64_t n, float* __restrict__ dst) {
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
+    dst[x] = (float)src[x];
+}
+
 // M[e] = sum over chunks of part[c E + e] in FP64, chunks in order.
 __global__ void gemm_reduce_kernel(const float* __restrict__ part, int nchunk, int64_t E, double* __restrict__ M) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
@@ -241,22 +270,85 @@ void gemm_mttsp_bind(GemmMttsp& g, void* const* q) {
 
 bool gemm_prepare(trals_ctx* ctx) { return handle_of(ctx) != nullptr; }
 
-int gemm_mttsp_enqueue(GemmMttsp& g, trals_ctx* ctx, const void* X, double* const* cores, const int64_t* I,
-                       const int32_t* R, double* M, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
+namespace {
+// The subchain tables of the current cores: FP64, then the GEMM's table and the stage-2 table converted.
+int prepare_tables(GemmMttsp& g, double* const* cores, const int64_t* I, const int32_t* R, cudaStream_t s) {
   const ModeLayout& L = g.L;
   const int N = L.N, n = g.n;
   const int Rn = R[n], Rn1 = R[(n + 1) % N], Rs = L.Rs;
   const int WO = g.form == 1 ? Rn1 * Rs : Rs * Rn;
-  int launches = 0;
   build_tables(L, cores, I, R, g.ltab64, g.utab64, g.scr64, s);
-  launches += N - 1;
   // the GEMM's table: U for n < N-1, L for n = N-1; the other one for stage 2
   const double* tk = (n == N - 1) ? g.ltab64 : g.utab64;
   const double* to = (n == N - 1) ? g.utab64 : g.ltab64;
   table_convert_kernel<<<grid_for(g.K * g.W1), 256, 0, s>>>(tk, g.K, g.W1, g.padK ? 1 : 0, g.I0, g.I0st, g.xmode, g.tabK,
                                                            g.tabK_lo);
   table_convert_kernel<<<grid_for(g.nOther * WO), 256, 0, s>>>(to, g.nOther, WO, 0, 0, 1, kGemmF32, g.tabO, nullptr);
-  launches += 2;
+  return N - 1 + 2;
+}
+}  // namespace
+
+int gemm_residual_enqueue(GemmMttsp& g, trals_ctx* ctx, const void* X, int xt, double* const* cores, const int64_t* I,
+                          const int32_t* R, float* E, cudaStream_t s) {
+  if (g.xmode != kGemmF32 || g.padK || g.I0st != g.I0 || (xt != TRALS_X_F32 && xt != TRALS_X_F64)) {
+    ctx->last_error = "two-stage residual: FP32 operands of an unpadded X only";
+    return -1;
+  }
+  const ModeLayout& L = g.L;
+  const int N = L.N, n = g.n;
+  const int Rn = R[n], Rn1 = R[(n + 1) % N], Rs = L.Rs;
+  const int WO = g.form == 1 ? Rn1 * Rs : Rs * Rn;
+  int launches = prepare_tables(g, cores, I, R, s);
+  const int64_t numel = g.K * g.rowsT;
+  if (xt == TRALS_X_F32) {
+    if (cudaMemcpyAsync(E, X, (size_t)numel * sizeof(float), cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+      ctx->last_error = "two-stage residual: copy of X";
+      return -1;
+    }
+  } else {
+    f64_to_f32_kernel<<<grid_for(numel), 256, 0, s>>>(static_cast<const double*>(X), numel, E);
+    ++launches;
+  }
+  if (g.form == 1)
+    residual_p_kernel<1><<<grid_for(g.rowsT * g.W1), 256, 0, s>>>(cores[n], g.tabO, g.rowsT, g.W1, WO, g.nOther, g.In,
+                                                                  Rn, Rn1, Rs, g.T);
+  else
+    residual_p_kernel<2><<<grid_for(g.rowsT * g.W1), 256, 0, s>>>(cores[n], g.tabO, g.rowsT, g.W1, WO, g.nOther, g.In,
+                                                                  Rn, Rn1, Rs, g.T);
+  ++launches;
+  cublasHandle_t h = handle_of(ctx);
+  if (!h) {
+    ctx->last_error = "cuBLAS handle unavailable";
+    return -1;
+  }
+  const CublasApi& c = api();
+  const float minus_one = -1.0f, one = 1.0f;
+  cublasStatus_t st = c.set_stream(h, s);
+  if (st == CUBLAS_STATUS_SUCCESS) st = c.set_workspace(h, g.ws, g.ws_bytes);
+  if (st == CUBLAS_STATUS_SUCCESS) {
+    if (n == 0)   // E (rowsT x K) -= P^T (rowsT x W1) tab (W1 x K)
+      st = c.gemm(h, CUBLAS_OP_T, CUBLAS_OP_N, (int)g.rowsT, (int)g.K, g.W1, &minus_one, g.T, CUDA_R_32F, g.W1,
+                  g.tabK, CUDA_R_32F, g.W1, &one, E, CUDA_R_32F, (int)g.rowsT, CUBLAS_COMPUTE_32F,
+                  CUBLAS_GEMM_DEFAULT);
+    else          // E (K x rowsT) -= tab^T (K x W1) P (W1 x rowsT)
+      st = c.gemm(h, CUBLAS_OP_T, CUBLAS_OP_N, (int)g.K, (int)g.rowsT, g.W1, &minus_one, g.tabK, CUDA_R_32F, g.W1,
+                  g.T, CUDA_R_32F, g.W1, &one, E, CUDA_R_32F, (int)g.K, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+  }
+  if (st != CUBLAS_STATUS_SUCCESS) {
+    ctx->last_error = "cuBLAS GEMM of the two-stage residual failed (status " + std::to_string((int)st) + ")";
+    return -1;
+  }
+  return launches;
+}
+
+int gemm_mttsp_enqueue(GemmMttsp& g, trals_ctx* ctx, const void* X, double* const* cores, const int64_t* I,
+                       const int32_t* R, double* M, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
+                       bool tables_ready) {
+  const ModeLayout& L = g.L;
+  const int N = L.N, n = g.n;
+  const int Rn = R[n], Rn1 = R[(n + 1) % N], Rs = L.Rs;
+  const int WO = g.form == 1 ? Rn1 * Rs : Rs * Rn;
+  int launches = tables_ready ? 0 : prepare_tables(g, cores, I, R, s);
   // stage 1: T^T (W1 x rowsT, so that each row of T is contiguous) = table (W1 x K) times X
   cublasHandle_t h = handle_of(ctx);
   if (!h) {

@@ -59,10 +59,18 @@ int gemm_mttsp_plan(GemmMttsp& g, int N, const int64_t* I, const int64_t* Ist, c
 void gemm_mttsp_bind(GemmMttsp& g, void* const* bufs);
 // Enqueue M_n (I_n x r, FP64) on s from X (as stored) and the FP64 cores.  Returns the launches of this
 // library's kernels, or -1 with ctx->last_error set when cuBLAS fails.
-// ev0 / ev1 (optional) are recorded on s directly before the GEMM and after the FP64 reduction.
+// ev0 / ev1 (optional) are recorded on s directly before the GEMM and after the FP64 reduction.  With
+// tables_ready the subchain tables of the current cores are taken as left by gemm_residual_enqueue.
 int gemm_mttsp_enqueue(GemmMttsp& g, trals_ctx* ctx, const void* X, double* const* cores, const int64_t* I,
                        const int32_t* R, double* M, cudaStream_t s, cudaEvent_t ev0 = nullptr,
-                       cudaEvent_t ev1 = nullptr);
+                       cudaEvent_t ev1 = nullptr, bool tables_ready = false);
+// The residual tensor E = X - X_hat (FP32, X's layout, unpadded) of the cores, by the same split: with
+// P the product of core n and the stage-2 table (P[(i + I l), s + R_s a] = sum_b G_n(i)[a, b] L(l)[b, s]
+// in form 1; P[(u + nU i), b + R_{n+1} s] = sum_a U(u)[s, a] G_n(i)[a, b] in form 2), X_hat is the GEMM
+// of the GEMM-side table with P, taken with coefficient -1 onto E = X.  FP32 modes only (g.xmode F32,
+// no padding); X is FP32 or FP64 (xt).  Returns launches, or -1 with ctx->last_error set.
+int gemm_residual_enqueue(GemmMttsp& g, trals_ctx* ctx, const void* X, int xt, double* const* cores, const int64_t* I,
+                          const int32_t* R, float* E, cudaStream_t s);
 // Create the context's cuBLAS handle ahead of any stream capture; false when cuBLAS is unavailable.
 bool gemm_prepare(trals_ctx* ctx);
 // Release the context's cuBLAS handle (trals_destroy).

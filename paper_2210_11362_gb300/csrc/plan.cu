@@ -370,42 +370,56 @@ int enqueue_explicit_residual(trals_plan* p, cudaStream_t s) {
 int enqueue_qr_refinement(trals_plan* p, int n, cudaStream_t s) {
   const ModeLayout& L = p->lay[n];
   const int N = p->N;
-  int launches = N - 1;
-  build_tables(L, p->cores, p->I, p->R, p->ltab, p->utab, p->tscratch, s);
-  MttspSimtArgs a;
-  a.X = p->E;
-  a.ltab = p->ltab;
-  a.utab = p->utab;
-  a.offL = p->offL[n];
-  a.offU = p->offU[n];
-  a.L = L;
-  a.partials = p->partials;
-  a.M = p->dM;
-  if (p->opts.mode == TRALS_MODE_FP64) {
-    launch_reconstruct(L, p->ltab, p->utab, p->offL[n], p->offU[n], p->cores[n], p->E, TRALS_X_F64, p->X, p->xt,
-                       nullptr, p->gridX[n], s, true);
-    a.xt = TRALS_X_F64;
-    a.gridX = p->gridX[n];
-    launch_mttsp_simt(a, s);
-    launches += 3;
-  } else {
-    const int64_t nl = L.nL * L.Rn1 * L.Rs, nu = L.nU * L.Rs * L.Rn;
-    float* fl = reinterpret_cast<float*>(p->tscratch);
-    launch_residual_f32(L, p->ltab, p->utab, fl, nl, nu, p->offL[n], p->offU[n], p->cores[n], p->X, p->xt,
-                        p->partials, residual_f32_grid(L), s, static_cast<float*>(p->E));
-    a.xt = TRALS_X_F32;
-    int gl = -1;
-    if (p->gemmE[n].valid) gl = gemm_mttsp_enqueue(p->gemmE[n], p->ctx, p->E, p->cores, p->I, p->R, p->dM, s);
-    if (gl >= 0) {
-      launches += gl - 1;
-    } else if (mttsp_simt_f32_fits(L)) {
-      a.gridX = mttsp_simt_f32_grid(L);
-      launch_mttsp_simt_f32(a, fl, fl + nl, s);   // the tables' FP32 copies are still in the scratch
+  int launches = 0;
+  bool done = false;
+  if (p->opts.mode != TRALS_MODE_FP64 && p->gemmE[n].valid) {
+    // the residual tensor and its MTTSP by the two-stage GEMM route (the subchain tables built once)
+    const int r1 = gemm_residual_enqueue(p->gemmE[n], p->ctx, p->X, p->xt, p->cores, p->I, p->R,
+                                         static_cast<float*>(p->E), s);
+    const int r2 = r1 >= 0 ? gemm_mttsp_enqueue(p->gemmE[n], p->ctx, p->E, p->cores, p->I, p->R, p->dM, s, nullptr,
+                                                nullptr, true)
+                           : -1;
+    if (r1 >= 0 && r2 >= 0) {
+      launches += r1 + r2;
+      done = true;
     } else {
+      p->gemmE[n].valid = false;   // cuBLAS failed (reported in last_error): the CUDA-core kernels below
+    }
+  }
+  if (!done) {
+    launches += N - 1;
+    build_tables(L, p->cores, p->I, p->R, p->ltab, p->utab, p->tscratch, s);
+    MttspSimtArgs a;
+    a.X = p->E;
+    a.ltab = p->ltab;
+    a.utab = p->utab;
+    a.offL = p->offL[n];
+    a.offU = p->offU[n];
+    a.L = L;
+    a.partials = p->partials;
+    a.M = p->dM;
+    if (p->opts.mode == TRALS_MODE_FP64) {
+      launch_reconstruct(L, p->ltab, p->utab, p->offL[n], p->offU[n], p->cores[n], p->E, TRALS_X_F64, p->X, p->xt,
+                         nullptr, p->gridX[n], s, true);
+      a.xt = TRALS_X_F64;
       a.gridX = p->gridX[n];
       launch_mttsp_simt(a, s);
+      launches += 3;
+    } else {
+      const int64_t nl = L.nL * L.Rn1 * L.Rs, nu = L.nU * L.Rs * L.Rn;
+      float* fl = reinterpret_cast<float*>(p->tscratch);
+      launch_residual_f32(L, p->ltab, p->utab, fl, nl, nu, p->offL[n], p->offU[n], p->cores[n], p->X, p->xt,
+                          p->partials, residual_f32_grid(L), s, static_cast<float*>(p->E));
+      a.xt = TRALS_X_F32;
+      if (mttsp_simt_f32_fits(L)) {
+        a.gridX = mttsp_simt_f32_grid(L);
+        launch_mttsp_simt_f32(a, fl, fl + nl, s);   // the tables' FP32 copies are still in the scratch
+      } else {
+        a.gridX = p->gridX[n];
+        launch_mttsp_simt(a, s);
+      }
+      launches += 4;
     }
-    launches += 4;
   }
   launch_chol_solve(p->Lmat, p->dM, L.Rn, L.In, L.Rn1, p->dG, p->ctx->d_status, s);
   launch_axpy((int64_t)L.Rn * L.In * L.Rn1, p->dG, p->cores[n], s);

@@ -446,6 +446,38 @@ def test_plan_two_stage_gemm_mttsp_componentwise_bound(ctx, mode, n):
     assert ratio <= 1.0, (mode, n, ratio)
 
 
+def test_qr_solver_two_stage_refinement_matches_fp64(ctx):
+    """QR-stabilised solve in the FP32 mode on a shape whose MTTSPs take the two-stage GEMM route: its
+    refinement steps form the residual tensor E = X - X_hat and the MTTSP of E by GEMMs as well.  Started
+    near the generating cores, two sweeps must land on the FP64 QR run's residual to 1e-7 (the
+    refinement lifts the FP32 right-hand side to the accuracy of the source X)."""
+    I, R = (60, 64, 3, 200), (8, 8, 8, 8)
+    truth = TI.gaussian_cores(11, I, R)
+    cd = [P.core_to_device(G) for G in truth]
+    Xt = torch.empty(int(np.prod(I)), dtype=torch.float64, device="cuda")
+    P.trals_reconstruct(ctx, I, R, cd, Xt)
+    noise = torch.from_numpy(TI.flat_f(TI.gaussian_noise(11, I))).cuda()
+    X64 = (Xt + 1e-2 * (torch.linalg.vector_norm(Xt) / torch.linalg.vector_norm(noise)) * noise).contiguous()
+    X32 = X64.to(torch.float32)
+    rng = np.random.default_rng(11)
+    init = [G + 1e-2 * rng.standard_normal(G.shape) for G in truth]
+    res = {}
+    for mode, X in (("fp64", X64), ("fp32", X32)):
+        plan = P.Plan(ctx, I, R, X, P.make_opts(mode, solver=P.SOLVE_QR))
+        try:
+            if mode == "fp32":
+                assert [plan.mttsp_path(n) for n in range(4)] == [5] * 4
+            plan.set_cores(init)
+            plan.run(2)
+            torch.cuda.synchronize()
+            r2, x2 = P.trals_residual_explicit(ctx, I, R, X64, [plan.core_dev(n) for n in range(4)])
+            res[mode] = float(np.sqrt(max(r2, 0.0) / x2))
+        finally:
+            plan.close()
+    assert 1e-3 < res["fp64"] < 1e-1
+    assert abs(res["fp32"] - res["fp64"]) <= 1e-7, res
+
+
 def test_solve_chol_matches_oracle(ctx):
     I, R = (9, 8, 7), (3, 4, 2)
     X, init = _problem(I, R)
