@@ -63,8 +63,8 @@ struct TcArgs {
   int withhold;      // fault injection for tests: the producer skips its first copy (see tc_set_fault)
   uint32_t tx_bytes;
   uint32_t idesc;
-  int xpl, tpl;      // BF16 planes of X and of the table per stage: 1 (BF16), or 2 (hi/lo pairs): bf16x2
-                     // splits the table (two products per K step), bf16x3 both (three products)
+  int x3;            // split-BF16 planes: 0 none; 1 bf16x2, the table as hi/lo (two products per K step);
+                     // 2 bf16x3, X and the table as hi/lo (three products)
   const float* F;    // [fac][NX][SYP]
   float* partials;   // [grid][In * r]
   DevStatus* status;
@@ -260,16 +260,18 @@ __device__ __forceinline__ bool get_unit(const TcArgs& a, int64_t j, int64_t& ti
 }
 
 // SYP: the stage-2 dot length (inner subchain rank padded to a multiple of 4); the stage-1 result of a
-// row is T[y * SYP + z] (y < NY, z < SYP) and is held in registers.
-template <int SYP>
+// row is T[y * SYP + z] (y < NY, z < SYP) and is held in registers.  SPLIT: the split-BF16 modes
+// (a.x3 != 0), compiled apart so that the plain BF16 kernel carries none of their code.
+template <int SYP, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
     mttsp_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmT,
                     const __grid_constant__ CUtensorMap tmXl, const __grid_constant__ CUtensorMap tmTl, const TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int bBytes = ((a.W_pad * 128) + 1023) & ~1023;
-  // stage: X hi [, X lo], table hi [, table lo]
-  const int stageBytes = a.xpl * kABytes + a.tpl * bBytes;
+  const int planes = SPLIT ? 2 : 1;                // stage: X hi [, X lo], table hi [, table lo]
+  // (bf16x2 leaves the X lo slot of its stages unused)
+  const int stageBytes = planes * (kABytes + bBytes);
   const int NS = a.ns;
   // stage-2 factor blocks: per row (MM), or the blocks of a tile, double buffered
   float* F_s = reinterpret_cast<float*>(base + NS * stageBytes);
@@ -334,12 +336,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           // MMA issuer's wait for it runs out and the kernel reports TRALS_E_TIMEOUT
           if (!(a.withhold && j == 0 && ks == ks0)) {
             uint8_t* A = base + stage * stageBytes;
-            uint8_t* B = A + a.xpl * kABytes;
+            uint8_t* B = A + planes * kABytes;
             mbar_expect_tx(&full[stage], a.tx_bytes);
             const int k0 = ks * kKT;
-            for (int pl = 0; pl < a.tpl; ++pl) tma_load_2d(B + pl * bBytes, pl ? &tmTl : &tmT, &full[stage], k0, 0, pol_tab);
-            for (int pl = 0; pl < a.xpl; ++pl) {
+            for (int pl = 0; pl < planes; ++pl) {
               const CUtensorMap* mx = pl ? &tmXl : &tmX;
+              if (SPLIT && pl == 1 && a.x3 == 1) {   // bf16x2: the table's lo plane only
+                tma_load_2d(B + bBytes, &tmTl, &full[stage], k0, 0, pol_tab);
+                continue;
+              }
               uint8_t* Ap = A + pl * kABytes;
               if (a.variant == KM_L) {
                 tma_load_3d(Ap, mx, &full[stage], k0, 0, (int)(tile * a.nrep), pol_x);
@@ -352,6 +357,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int at = 0; at < 2; ++at)
                   tma_load_3d(Ap + at * kAtomBytes, mx, &full[stage], (int)(pc * 64), k0, (int)(2 * op + at), pol_x);
               }
+              tma_load_2d(B + pl * bBytes, pl ? &tmTl : &tmT, &full[stage], k0, 0, pol_tab);
             }
             ++issued[stage];
           }
@@ -396,23 +402,23 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           const uint32_t A = smem_u32(base + stage * stageBytes);
-          const uint32_t B = A + (uint32_t)(a.xpl * kABytes);
+          const uint32_t B = A + (uint32_t)(planes * kABytes);
 #pragma unroll
           for (int jj = 0; jj < kKT / 16; ++jj) {
             const bool mn = a.variant == MM || a.variant == MM_L;
             const uint64_t ad = mn ? sdesc(A + 2048u * jj, kAtomBytes, 1024) : sdesc(A + 32u * jj, 16, 1024);
             const uint64_t bd = sdesc(B + 32u * jj, 16, 1024);
             umma_bf16(d, ad, bd, a.idesc, (ks > ks0 || jj > 0) ? 1u : 0u);
-            // split-BF16 products: X_hi T_lo (bf16x2, bf16x3) and X_lo T_hi (bf16x3); X_lo T_lo is below
-            // FP32 rounding
-            if (a.tpl == 2) {
+            if (SPLIT) {
+              // split-BF16 products: X_hi T_lo (bf16x2, bf16x3) + X_lo T_hi (bf16x3); X_lo T_lo is below
+              // FP32 rounding
               const uint64_t bdl = sdesc(B + (uint32_t)bBytes + 32u * jj, 16, 1024);
               umma_bf16(d, ad, bdl, a.idesc, 1u);
-            }
-            if (a.xpl == 2) {
-              const uint32_t Al = A + (uint32_t)kABytes;
-              const uint64_t adl = mn ? sdesc(Al + 2048u * jj, kAtomBytes, 1024) : sdesc(Al + 32u * jj, 16, 1024);
-              umma_bf16(d, adl, bd, a.idesc, 1u);
+              if (a.x3 == 2) {
+                const uint32_t Al = A + (uint32_t)kABytes;
+                const uint64_t adl = mn ? sdesc(Al + 2048u * jj, kAtomBytes, 1024) : sdesc(Al + 32u * jj, 16, 1024);
+                umma_bf16(d, adl, bd, a.idesc, 1u);
+              }
             }
           }
           umma_commit(&empty[stage]);
@@ -671,6 +677,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+}
+
+using TcKernel = void (*)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, TcArgs);
+
+// The instantiation for a stage-2 dot length (4, 8, 12, 16) and split mode.
+static TcKernel tc_kernel_for(int syp, bool split) {
+  switch (syp) {
+    case 4: return split ? mttsp_tc_kernel<4, true> : mttsp_tc_kernel<4, false>;
+    case 8: return split ? mttsp_tc_kernel<8, true> : mttsp_tc_kernel<8, false>;
+    case 12: return split ? mttsp_tc_kernel<12, true> : mttsp_tc_kernel<12, false>;
+    default: return split ? mttsp_tc_kernel<16, true> : mttsp_tc_kernel<16, false>;
+  }
 }
 
 // M[e] = sum_g partials[g * E + e] in FP64: a block takes 32 consecutive e; warp w sums g = w, w+8, ...
@@ -1220,9 +1238,9 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   A.fs_stride = (A.NX * impl->SYP + 7) / 8 * 8 + 4;
   A.ms_stride = A.r | 1;   // odd row stride: lanes with different i_n hit different banks
 
-  A.xpl = x3 ? 2 : 1;
-  A.tpl = tlo ? 2 : 1;
-  A.tx_bytes = (uint32_t)(A.xpl * A.tx_bytes + A.tpl * A.W_pad * 128);   // X box(es), then table box(es)
+  A.x3 = x3 ? 2 : tlo ? 1 : 0;
+  // X box(es) (hi, and lo in bf16x3), then table box(es) (hi, and lo in both split modes)
+  A.tx_bytes = (uint32_t)((x3 ? 2 : 1) * A.tx_bytes + (tlo ? 2 : 1) * A.W_pad * 128);
   // MMA instruction descriptor: D=F32, A=B=BF16, A major per variant, B K-major, N=W_pad, M=128
   A.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((A.variant == MM || A.variant == MM_L ? 1u : 0u) << 15) |
             ((uint32_t)(A.W_pad >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
@@ -1269,7 +1287,7 @@ int tc_plan(TcPlan& p, int N, const int64_t* I, const int32_t* R, int n, int mod
   size_t fixed = 1024 + (size_t)((fs_rows * A.fs_stride + 1) & ~1) * 4 + (2 * kNSMax + 4) * 8 + 64;
   if (A.variant == MM_L)   // one x-column of every row, and the I_0 x r sums
     fixed += (size_t)((kRows * (A.NY | 1) + 1) & ~1) * 4 + (size_t)((In * A.ms_stride + 1) & ~1) * 4;
-  const size_t stage = (size_t)A.xpl * kABytes + (size_t)A.tpl * bBytes;
+  const size_t stage = (size_t)(tlo ? 2 : 1) * ((size_t)kABytes + bBytes);
   const int ns = (int)std::min<size_t>(kNSMax, fixed < (size_t)kSmemBudget ? (kSmemBudget - fixed) / stage : 0);
   if (ns < 2) {
     delete impl;
@@ -1454,14 +1472,9 @@ int tc_enqueue_main(TcPlan& p, double* const* cores, double* M, cudaStream_t s, 
   }
   if (before_kernel) cudaStreamWaitEvent(s, before_kernel, 0);
   if (ev0) cudaEventRecord(ev0, s);
-  const CUtensorMap& xl = A.xpl == 2 ? impl->tmXl : impl->tmX;   // unread with one X plane
-  const CUtensorMap& tl = A.tpl == 2 ? impl->tmTl : impl->tmT;     // unread with one table plane
-  switch (impl->SYP) {
-    case 4: mttsp_tc_kernel<4><<<impl->grid, kThreads, impl->smem, s>>>(impl->tmX, impl->tmT, xl, tl, A); break;
-    case 8: mttsp_tc_kernel<8><<<impl->grid, kThreads, impl->smem, s>>>(impl->tmX, impl->tmT, xl, tl, A); break;
-    case 12: mttsp_tc_kernel<12><<<impl->grid, kThreads, impl->smem, s>>>(impl->tmX, impl->tmT, xl, tl, A); break;
-    default: mttsp_tc_kernel<16><<<impl->grid, kThreads, impl->smem, s>>>(impl->tmX, impl->tmT, xl, tl, A); break;
-  }
+  const CUtensorMap& xl = A.x3 == 2 ? impl->tmXl : impl->tmX;   // unread unless bf16x3
+  const CUtensorMap& tl = A.x3 ? impl->tmTl : impl->tmT;         // unread without a split table
+  tc_kernel_for(impl->SYP, A.x3 != 0)<<<impl->grid, kThreads, impl->smem, s>>>(impl->tmX, impl->tmT, xl, tl, A);
   ++launches;
   if (ev1) cudaEventRecord(ev1, s);
   {
@@ -1517,10 +1530,10 @@ void tc_destroy(TcPlan& p) {
 }
 
 cudaError_t init_tc_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(mttsp_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(mttsp_tc_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(mttsp_tc_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(mttsp_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
+  cudaError_t e = cudaSuccess;
+  for (int syp = 4; syp <= 16 && e == cudaSuccess; syp += 4)
+    for (int sp = 0; sp < 2 && e == cudaSuccess; ++sp)
+      e = cudaFuncSetAttribute(tc_kernel_for(syp, sp != 0), cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
   return e;
 }
 
