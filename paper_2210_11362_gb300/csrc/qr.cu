@@ -21,24 +21,44 @@ namespace trals {
 
 namespace {
 
-constexpr int QT = 256;   // threads per QR CTA
+// Threads per QR CTA.  A Householder step's columns are spread over 32 warps (a leaf: one column per
+// warp and pass; a merge: eight columns per warp, four lanes each), so most steps are one pass and
+// enough independent FP64 chains are in flight to keep the SM's FP64 unit issuing.
+constexpr int QT = 1024;
 
-__device__ __forceinline__ double block_sum(double v, double* red) {
+// CTA-wide sum of each thread's part of a column's sum of squares; then one thread forms the
+// Householder reflector of that column from it and from x0 (the entry on the diagonal, read by that
+// thread after the first barrier): red[32] = the sum, red[33] = alpha (the new diagonal entry),
+// red[34] = v0 (the reflector's entry on the diagonal), red[35] = tau = 2 / |v|^2.  kWithX0: the sum
+// already includes x0^2 (else the sum runs over the entries below the diagonal only).  With v0_dst set
+// that thread also stores v0 there.  The FP64 unit of an SM issues one warp instruction at a time
+// whatever the number of active lanes, so the square root and the division are done once, not by
+// every thread.
+template <bool kWithX0>
+__device__ __forceinline__ void householder_scalars(double part, const double* x0p, double* v0_dst, double* red) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) red[w] = v;
+  if (lane == 0) red[w] = part;
   __syncthreads();
   if (w == 0) {
-    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    double s = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) red[32] = v;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      const double x0 = *x0p;
+      const double below = kWithX0 ? s - x0 * x0 : s;
+      const double nrm = sqrt(kWithX0 ? s : fma(x0, x0, s));
+      const double alpha = x0 >= 0.0 ? -nrm : nrm;
+      const double v0 = x0 - alpha;
+      red[32] = s;
+      red[33] = alpha;
+      red[34] = v0;
+      red[35] = 2.0 / (below + v0 * v0);
+      if (v0_dst && s != 0.0) *v0_dst = v0;
+    }
   }
   __syncthreads();
-  v = red[32];
-  __syncthreads();
-  return v;
 }
 
 // Householder QR (GvL Alg. 5.2.1) of the m x C matrix W (column-major, leading dimension ld) in place,
@@ -53,19 +73,22 @@ __device__ void cta_householder_qr(double* W, int m, int C, int64_t ld, double* 
       v[i] = x;
       s = fma(x, x, s);
     }
-    s = block_sum(s, red);
-    if (s == 0.0) continue;   // uniform: the column is already zero
-    const double x0 = v[j];
-    const double nrm = sqrt(s);
-    const double alpha = x0 >= 0.0 ? -nrm : nrm;
-    const double v0 = x0 - alpha;
-    const double tau = 2.0 / (s - x0 * x0 + v0 * v0);
-    __syncthreads();
-    if (threadIdx.x == 0) v[j] = v0;
-    __syncthreads();
+    householder_scalars<true>(s, &v[j], &v[j], red);   // v[j] <- v0
+    if (red[32] == 0.0) {   // uniform: the column is already zero
+      __syncthreads();
+      continue;
+    }
+    const double alpha = red[33], tau = red[35];
     for (int c = j + 1 + warp; c < C; c += nw) {
-      double w = 0.0;
-      for (int i = j + lane; i < m; i += 32) w = fma(v[i], W[i + (int64_t)ld * c], w);
+      // two partial sums (rows i and i + 32 of each 64) halve the dependent chain
+      double w0 = 0.0, w1 = 0.0;
+      int i = j + lane;
+      for (; i + 32 < m; i += 64) {
+        w0 = fma(v[i], W[i + (int64_t)ld * c], w0);
+        w1 = fma(v[i + 32], W[i + 32 + (int64_t)ld * c], w1);
+      }
+      if (i < m) w0 = fma(v[i], W[i + (int64_t)ld * c], w0);
+      double w = w0 + w1;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
       const double f = tau * w;
@@ -85,7 +108,8 @@ __device__ void cta_householder_qr(double* W, int m, int C, int64_t ld, double* 
 // hold R, the bottom block is zero.
 __device__ void cta_householder_stacked(double* W, int C, int64_t ld, double* v, double* red) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double* Wb = W + C;   // bottom block: Wb[i + ld c]
+  const int q = lane & 3;   // four lanes per column: a column's dot product and update
+  double* Wb = W + C;       // bottom block: Wb[i + ld c]
   for (int j = 0; j < C; ++j) {
     double s = 0.0;
     for (int i = threadIdx.x; i <= j; i += blockDim.x) {
@@ -93,22 +117,33 @@ __device__ void cta_householder_stacked(double* W, int C, int64_t ld, double* v,
       v[i] = x;
       s = fma(x, x, s);
     }
-    s = block_sum(s, red);
-    if (s == 0.0) continue;   // uniform: the bottom part of the column is already zero
-    const double x0 = W[j + ld * j];
-    const double s_all = fma(x0, x0, s);
-    const double nrm = sqrt(s_all);
-    const double alpha = x0 >= 0.0 ? -nrm : nrm;
-    const double v0 = x0 - alpha;
-    const double tau = 2.0 / (s + v0 * v0);
-    for (int c = j + 1 + warp; c < C; c += nw) {
-      double w = lane == 0 ? v0 * W[j + ld * c] : 0.0;
-      for (int i = lane; i <= j; i += 32) w = fma(v[i], Wb[i + ld * c], w);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-      const double f = tau * w;
-      if (lane == 0) W[j + ld * c] = fma(-f, v0, W[j + ld * c]);
-      for (int i = lane; i <= j; i += 32) Wb[i + ld * c] = fma(-f, v[i], Wb[i + ld * c]);
+    householder_scalars<false>(s, &W[j + ld * j], nullptr, red);
+    if (red[32] == 0.0) {   // uniform: the bottom part of the column is already zero
+      __syncthreads();
+      continue;
+    }
+    const double alpha = red[33], v0 = red[34], tau = red[35];
+    // eight columns per warp and pass (the loop bound is uniform per warp, so the shuffles see all lanes)
+    for (int c0 = j + 1 + 8 * warp; c0 < C; c0 += 8 * nw) {
+      const int c = c0 + (lane >> 2);
+      const bool ok = c < C;
+      double w0 = (ok && q == 0) ? v0 * W[j + ld * c] : 0.0, w1 = 0.0;
+      if (ok) {
+        int i = q;
+        for (; i + 4 <= j; i += 8) {
+          w0 = fma(v[i], Wb[i + ld * c], w0);
+          w1 = fma(v[i + 4], Wb[i + 4 + ld * c], w1);
+        }
+        if (i <= j) w0 = fma(v[i], Wb[i + ld * c], w0);
+      }
+      double w = w0 + w1;
+      w += __shfl_xor_sync(0xffffffffu, w, 1);
+      w += __shfl_xor_sync(0xffffffffu, w, 2);
+      if (ok) {
+        const double f = tau * w;
+        if (q == 0) W[j + ld * c] = fma(-f, v0, W[j + ld * c]);
+        for (int i = q; i <= j; i += 4) Wb[i + ld * c] = fma(-f, v[i], Wb[i + ld * c]);
+      }
     }
     if (threadIdx.x == 0) W[j + ld * j] = alpha;
     for (int i = threadIdx.x; i <= j; i += blockDim.x) Wb[i + ld * j] = 0.0;
