@@ -22,10 +22,11 @@ mode n-1); every other index convention is the paper's:
 What it computes is regular TR-ALS (Alg. 1): the subchain matrix is formed
 explicitly and each subproblem (eq. tr_als) is solved by Householder QR
 least squares, or by Cholesky on the explicit normal equations (the
-Golub & Van Loan Sec. 5.3.2 method the paper cites for Alg. 2), plus the
-literal TR-ALS-QR (Alg. 3) for small shapes.  The paper proves TR-ALS-NE and
-TR-ALS-QR equal TR-ALS in exact arithmetic (remarks after Alg. 2 and Alg. 3),
-so this oracle is the reference for every GPU solver.
+Golub & Van Loan Sec. 5.3.2 method the paper cites for Alg. 2), plus
+TR-ALS-QR (Alg. 3, derived from the least-squares problem of Sec. 3.2) for
+small shapes.  The paper proves TR-ALS-NE and TR-ALS-QR equal TR-ALS in exact
+arithmetic (remarks after Alg. 2 and Alg. 3), so this oracle is the reference
+for every GPU solver.
 
 Parity pins: every function here is pinned by tests/test_oracle_pins.py to
 brute force, closed forms or library special cases; nothing is "parity
