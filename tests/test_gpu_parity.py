@@ -123,6 +123,31 @@ def test_qr_r_factor_matches_householder_qr(ctx, I, R):
         assert rel(got, Rref) < 1e-11, (n, rel(got, Rref))
 
 
+def test_qr_r_factor_structurally_rank_deficient_subchain(ctx):
+    """Core n+1 zero for one value of its left rank index makes the columns of G^{!=n}_[2] with that
+    index vanish.  The TSQR leaves and merges take their skip paths for those columns (no reflector:
+    the column is already zero), the call reports the rank deficiency as TRALS_E_NOT_SPD (a zero
+    diagonal of R), and the factor it leaves still satisfies R^T R = A^T A: R is not unique for a
+    rank-deficient A, its Gram matrix is."""
+    I, R = (40, 24, 33, 20), (4, 6, 3, 5)
+    cores = TI.gaussian_cores(6, I, R)
+    n = 0
+    cores[1][2, :, :] = 0.0   # G_1(i) row r_1 = 2 is zero for every i
+    A = O.subchain_unfolded(cores, n)
+    zero_cols = np.where(~A.any(axis=0))[0]
+    assert list(zero_cols) == [8, 9, 10, 11]   # columns a + R_0 r_1 with r_1 = 2
+    r = R[0] * R[1]
+    Rd = torch.zeros(r * r, dtype=torch.float64, device="cuda")
+    with pytest.raises(P.TralsError) as err:
+        P.trals_qr_r_factor(ctx, I, R, [P.core_to_device(G) for G in cores], n, Rd)
+    assert err.value.status == P.E_NOT_SPD
+    got = Rd.cpu().numpy().reshape(r, r, order="F")
+    assert np.allclose(np.tril(got, -1), 0.0)
+    assert np.all(np.diag(got)[zero_cols] == 0.0)
+    assert np.all(got[:, zero_cols] == 0.0)
+    assert rel(got.T @ got, A.T @ A) < 1e-12
+
+
 @pytest.mark.parametrize("I,R", SHAPES[:3] + [((40, 24, 33, 20), (4, 6, 3, 5))])
 def test_decompose_qr_one_sweep_matches_oracle(ctx, I, R):
     """solver = QR in FP64: cores after one sweep within 1e-9 of the oracle's Householder QR least
