@@ -216,7 +216,7 @@ def time_mode(P, torch, w, X, mode, steps, warmup, seed, flush_buf, X_full, opts
 
 def smooth_qr_run(P, torch, seed, peaks, flush):
     """Sub-line: the 256x256x3x256 sinusoid workload (R = 16) in the BF16 mode with the QR-stabilised
-    solve, the path its ill-conditioned subproblems need (Cholesky stops with TRALS_E_NOT_SPD there).
+    solve (Sec. 3.2), the solver for subproblems whose normal equations are not numerically SPD.
     One warm-up sweep and two timed sweeps (L2 evicted between them), the explicit residual against the
     FP64 X, and the MTTSP of each mode timed alone (the path the plan runs: the two-stage GEMM MTTSP,
     timed from its GEMM through its FP64 reduction)."""
