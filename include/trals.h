@@ -67,10 +67,12 @@ typedef enum { TRALS_X_F64 = 0, TRALS_X_F32 = 1, TRALS_X_BF16 = 2, TRALS_X_BF16P
  * FP64 in every mode).
  *  FP64  : X read as FP64, MTTSP in FP64 on the CUDA cores.
  *  FP32  : X read as FP32 (converted once from FP64 if needed); MTTSP on the CUDA cores in FP32
- *          arithmetic, per-block sums reduced in FP64.
+ *          arithmetic, per-block sums reduced in FP64 (a plan takes the two-stage GEMM MTTSP instead
+ *          where trals_plan_mttsp_path reports code 5).
  *  BF16  : X quantised once to BF16 (round to nearest even); MTTSP on BF16 tensor cores
  *          (tcgen05) with FP32 accumulation where trals_mttsp_path reports a tensor-core
- *          geometry, else on the CUDA cores in FP32 arithmetic.
+ *          geometry, else on the CUDA cores in FP32 arithmetic (or, in a plan, the two-stage GEMM
+ *          MTTSP, code 5 of trals_plan_mttsp_path).
  *  BF16X3: X split once into hi/lo BF16 pairs (hi = bf16(x), lo = bf16(x - hi)), the subchain
  *          table likewise; on the tensor cores every K step is three BF16 products
  *          (X_hi T_hi + X_hi T_lo + X_lo T_hi) into one FP32 accumulator (the CUDA-core path reads
