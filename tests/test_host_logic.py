@@ -25,10 +25,21 @@ def test_mttsp_path_pads_the_leading_mode_and_falls_back_when_too_large():
     assert P.trals_mttsp_path((41, 39, 200, 41, 39), (2, 2, 7, 8, 3), 2, "bf16") == 0
     # a short middle mode (I_n = 20) takes K-major tiles of six repetitions of its rows
     assert P.trals_mttsp_path((41, 39, 20, 41, 39), (2, 2, 7, 8, 3), 2, "bf16") == 1
-    # rank-16 cores: stage-1 table wider than the 128-column accumulator -> CUDA cores
+    # rank-16 cores: stage-1 table wider than the 128-column accumulator -> no tensor-core geometry
+    # (trals_mttsp runs the CUDA cores; a plan takes the two-stage GEMM MTTSP there)
     assert all(P.trals_mttsp_path((256, 256, 3, 256), (16,) * 4, n, "bf16") == 0 for n in range(4))
     # tiny tensors: contraction too short for a tensor-core tile
     assert all(P.trals_mttsp_path((20, 20, 20), (3, 3, 3), n, "bf16") == 0 for n in range(3))
+
+
+def test_split_bf16_modes_take_the_bf16_geometries():
+    """bf16x2 and bf16x3 run the same tensor-core geometries as BF16 on the bench workloads: their
+    stages (two BF16 planes of the table, and of X for bf16x3) still fit the shared-memory plan."""
+    for I, R in (((40,) * 5, (8, 10, 12, 10, 8)), ((60,) * 4, (10,) * 4)):
+        ref = [P.trals_mttsp_path(I, R, n, "bf16") for n in range(len(I))]
+        assert all(p > 0 for p in ref)
+        for mode in ("bf16x2", "bf16x3"):
+            assert [P.trals_mttsp_path(I, R, n, mode) for n in range(len(I))] == ref, mode
 
 
 def test_mttsp_path_rejects_bad_arguments():
