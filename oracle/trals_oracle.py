@@ -228,6 +228,27 @@ def mttsp(X: np.ndarray, cores: Sequence[np.ndarray], n: int, block: int = 1 << 
     return M
 
 
+def mttsp_column(X: np.ndarray, cores: Sequence[np.ndarray], n: int, a: int, b: int) -> np.ndarray:
+    """Column a + R_n b of M_n = X_[n] G^{!=n}_[2] (Alg. 2 lines 7-8) without the subchain matrix:
+    the column's subchain entries g(k) = G^{!=n}(k)[b, a] = e_b^T G_{n+1}(i_{n+1}) ... G_{n-1}(i_{n-1}) e_a
+    (eq. subchain_new) are formed for all k by carrying the row vector e_b^T G_{n+1}(i_{n+1}) ... through
+    the chain, one mode at a time (k = overline{i_{n+1} .. i_{n-1}}, first index fastest), then
+    M_n[:, a + R_n b] = X_[n] g.  Memory is J_n / I_{n-1} x R plus J_n, so sampled columns of a large
+    tensor's M_n stay cheap."""
+    N = len(cores)
+    modes = chain_modes(N, n)
+    V = cores[modes[0]][b, :, :]                      # (I_{c1}, R): row vectors over k so far
+    for m in modes[1:-1]:
+        G = cores[m]                                  # (R_c, I_c, R_{c+1})
+        Rc, Ic, Rd = G.shape
+        # V'[k + K i, :] = V[k, :] @ G(i)
+        W = (V @ G.reshape(Rc, Ic * Rd)).reshape(V.shape[0], Ic, Rd)   # W[k, i, d]
+        V = W.transpose(1, 0, 2).reshape(Ic * V.shape[0], Rd)           # row i K + k
+    last = cores[modes[-1]]                           # (R_c, I_c, R_n): the column a of each slice
+    g = (V @ last[:, :, a]).reshape(-1, order="F")    # g[k + K i] = V[k] . G_last(i)[:, a]
+    return unfold_mode(X, n) @ g
+
+
 def als_update(X: np.ndarray, cores: List[np.ndarray], n: int, solver: str = "qr") -> np.ndarray:
     """One TR-ALS core update (Alg. 1 lines 4-5): G_n = argmin |G^{!=n}_[2] Z^T - X_[n]^T|_F."""
     Rn, Rn1 = cores[n].shape[0], cores[n].shape[2]

@@ -264,6 +264,34 @@ def test_mttsp_blockwise_matches_model_identity():
         np.testing.assert_allclose(O.mttsp(Xt, init, n, block=5), want, rtol=1e-10, atol=1e-9 * np.abs(want).max())
 
 
+def test_mttsp_column_matches_brute_force():
+    """O.mttsp_column (one column of M_n from the subchain entries carried through the chain, for
+    sampled checks of large tensors) against a brute-force sum over every multi-index of the other
+    modes: M_n[i, a + R_n b] = sum X(.., i_n = i, ..) (G_{n+1}(i_{n+1}) ... G_{n-1}(i_{n-1}))[b, a]
+    (the mode-n unfolding and eq. subchain_new), with the other modes indexed through the tensor's
+    axes, not through a linear index."""
+    I, R = (3, 4, 2, 3), (2, 3, 2, 2)
+    N = len(I)
+    cores = TI.gaussian_cores(11, I, R)
+    X = np.random.default_rng(11).standard_normal(I)
+    for n in range(N):
+        others = [(n + t) % N for t in range(1, N)]
+        for a in range(R[n]):
+            for b in range(R[(n + 1) % N]):
+                want = np.zeros(I[n])
+                for i in range(I[n]):
+                    for idx in itertools.product(*[range(I[m]) for m in others]):
+                        P = np.eye(R[(n + 1) % N])
+                        full = [0] * N
+                        full[n] = i
+                        for m, im in zip(others, idx):
+                            P = P @ cores[m][:, im, :]
+                            full[m] = im
+                        want[i] += X[tuple(full)] * P[b, a]
+                got = O.mttsp_column(X, cores, n, a, b)
+                np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
+
+
 def test_signed_selection_cores_keep_subchain_entries_ternary():
     """The exact-arithmetic GPU tests rely on every subchain entry of these cores being -1, 0 or +1
     with at most one nonzero per row of each G^{!=n}(k) (brute force through the oracle)."""
