@@ -91,3 +91,23 @@ def test_multivariate_t_cores_correlation_and_layout():
     Z = O.core_unfold2(H[0])
     cos = abs(Z[:, 0] @ Z[:, 1]) / (np.linalg.norm(Z[:, 0]) * np.linalg.norm(Z[:, 1]))
     assert cos > 1 - 1e-5
+
+
+def test_sinusoid_tensor_matches_its_definition():
+    """The smooth workload's generator against its elementwise definition (a sum of separable sinusoid
+    products, 0-based indices), and the column-major flattening the library reads."""
+    import itertools
+    import math
+
+    import numpy as np
+
+    import trals_inputs as TI
+    I = (4, 5, 3)
+    f, phi = TI.sinusoid_params(3, 5, len(I))
+    X = TI.sinusoid_tensor(I, f, phi)
+    for idx in itertools.product(*[range(d) for d in I]):
+        want = sum(math.prod(math.sin(2.0 * math.pi * f[t, m] * idx[m] / I[m] + phi[t, m]) for m in range(len(I)))
+                   for t in range(f.shape[0]))
+        assert abs(X[idx] - want) < 1e-12
+    flat = TI.flat_f(X)
+    assert flat[1] == X[1, 0, 0] and flat[I[0]] == X[0, 1, 0] and flat[I[0] * I[1]] == X[0, 0, 1]
